@@ -1,0 +1,320 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests re-types the oracle's arithmetic: each checks it against
+an independent characterisation (brute force on tiny grids, closed forms,
+invariants, textbook special cases).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_12399_gb300 import synthetic as S
+from tests import _refgeom as R
+
+
+def _all_pairs(d):
+    """All pairs (diagram + zero-persistence) as dicts keyed by birth cell."""
+    out = []
+    for key in ("pairs", "zero"):
+        P = d[key]
+        for i in range(len(P["vb"])):
+            out.append((int(P["dim"][i]), int(P["essential"][i]), int(P["vb"][i]), int(P["vd"][i]),
+                        int(P["cb"][i]), int(P["cd"][i])))
+    return out
+
+
+def _closed_form_counts(lx, ly, lz):
+    def c(mask):
+        n = 1
+        for bit, L in ((1, lx), (2, ly), (4, lz)):
+            n *= (L - 1) if (mask & bit) else L
+        return n
+    V = lx * ly * lz
+    E = sum(c(m) for m in range(1, 8))
+    F = 0
+    for a in range(1, 8):
+        for b in range(1, 8):
+            if a & b == 0:
+                F += c(a | b)
+    T = 6 * c(7)
+    return V, E, F, T
+
+
+TINY = [((2, 2, 2), "uniform", 0), ((2, 2, 2), "ties", 1), ((2, 2, 2), "signed_zero", 2),
+        ((2, 2, 3), "uniform", 3), ((2, 3, 2), "ties", 4), ((3, 2, 2), "normal", 5)]
+
+
+@pytest.mark.parametrize("shape,kind,seed", TINY + [((3, 3, 3), "uniform", 7), ((3, 3, 3), "ties", 8)])
+def test_filtration_is_the_lexicographic_order(shape, kind, seed):
+    """Section 2.2: simplices sorted by their decreasing vertex-rank lists."""
+    f = S.random_field(shape, seed=seed, kind=kind)
+    d = oracle.diagram(f, with_filtration=True)
+    Sref, rank, _ = R.filtration(shape, f)
+    assert np.array_equal(d["rank"], rank.astype(np.uint32))
+    ref_cells = [R.cell_id(shape, s) for s in Sref]
+    assert [int(c) for c in d["filtration"]] == ref_cells
+
+
+@pytest.mark.parametrize("shape,kind,seed", TINY)
+def test_pairs_reproduce_every_persistent_betti_number(shape, kind, seed):
+    """beta_p^{i,j} from Z/2 ranks equals #pairs alive over [i, j] (all i <= j)."""
+    f = S.random_field(shape, seed=seed, kind=kind)
+    d = oracle.diagram(f, with_zero=True, with_filtration=True)
+    Sref, _, _ = R.filtration(shape, f)
+    cols = R.boundary_masks(Sref)
+    pos = {R.cell_id(shape, s): k for k, s in enumerate(Sref)}
+    N = len(Sref)
+    pairs = _all_pairs(d)
+    assert sum(1 for p in pairs if p[1]) == 1
+    births, deaths = [], []
+    for dim, ess, vb, vd, cb, cd in pairs:
+        births.append((dim, pos[cb], None if ess else pos[cd]))
+    # every simplex is in exactly one pair or is the essential one
+    used = [pos[p[4]] for p in pairs] + [pos[p[5]] for p in pairs if not p[1]]
+    assert sorted(used) == list(range(N))
+    rng = np.random.default_rng(seed)
+    ij = [(i, j) for i in range(N) for j in range(i, N)]
+    if len(ij) > 1500:
+        ij = [ij[k] for k in rng.choice(len(ij), 1500, replace=False)] + [(i, i) for i in range(N)]
+    for i, j in ij:
+        for p in range(3):
+            pred = sum(1 for (dim, b, dd) in births if dim == p and b <= i and (dd is None or dd > j))
+            assert pred == R.persistent_betti(Sref, cols, p, i, j), (i, j, p)
+
+
+@pytest.mark.parametrize("shape,seed,kind", [((4, 5, 6), 0, "uniform"), ((6, 4, 5), 1, "ties"),
+                                             ((5, 5, 5), 2, "signed_zero"), ((7, 6, 5), 3, "normal")])
+def test_d0_pairs_are_bottleneck_paths(shape, seed, kind):
+    """Elder rule in dimension 0: each vertex dies at the minimax edge to an older vertex."""
+    f = S.random_field(shape, seed=seed, kind=kind)
+    d = oracle.diagram(f, with_zero=True)
+    ref, rank, order = R.d0_by_bottleneck(shape, f)
+    got = {}
+    for dim, ess, vb, vd, cb, cd in _all_pairs(d):
+        if dim == 0:
+            if ess:
+                assert rank[vb] == 0
+            else:
+                got[vb] = cd
+    assert set(got) == set(ref)
+    for v, key in ref.items():
+        chain = sorted((order[key[0]], order[key[1]]), key=lambda u: sum(R.coords(shape)(u)))
+        assert got[v] == R.cell_id(shape, tuple(chain))
+
+
+@pytest.mark.parametrize("shape,seed,kind", [((4, 4, 4), 0, "uniform"), ((5, 4, 3), 1, "ties"),
+                                             ((3, 4, 5), 2, "normal")])
+def test_d2_pairs_are_dual_bottleneck_paths(shape, seed, kind):
+    """Dimension 2 by duality: each tetrahedron dies at the widest dual path's
+    narrowest triangle towards an older tetrahedron or the outside."""
+    f = S.random_field(shape, seed=seed, kind=kind)
+    d = oracle.diagram(f, with_zero=True)
+    ref = R.d2_by_bottleneck(shape, f)
+    got = {}
+    for dim, ess, vb, vd, cb, cd in _all_pairs(d):
+        if dim == 2:
+            got[cd] = cb
+    assert len(got) == len(ref)
+    for T, t in ref.items():
+        assert got[R.cell_id(shape, T)] == R.cell_id(shape, t)
+
+
+@pytest.mark.parametrize("shape,seed,kind", [((9, 7, 8), 0, "uniform"), ((6, 6, 6), 1, "ties"),
+                                             ((10, 9, 8), 2, "normal"), ((5, 5, 5), 3, "signed_zero")])
+def test_counts_euler_and_single_essential(shape, seed, kind):
+    lz, ly, lx = shape
+    f = S.random_field(shape, seed=seed, kind=kind)
+    d = oracle.diagram(f, with_zero=True, with_filtration=True)
+    V, E, F, T = _closed_form_counts(lx, ly, lz)
+    assert len(d["filtration"]) == V + E + F + T
+    P = d["pairs"]
+    crit = [0, 0, 0, 0]
+    for i in range(len(P["vb"])):
+        crit[int(P["cb"][i]) >> 60] += 1
+        if not P["essential"][i]:
+            crit[int(P["cd"][i]) >> 60] += 1
+            assert P["vb"][i] != P["vd"][i]
+            assert d["rank"][P["vd"][i]] > d["rank"][P["vb"][i]]
+            assert (int(P["cd"][i]) >> 60) == (int(P["cb"][i]) >> 60) + 1 == P["dim"][i] + 1
+    assert crit[0] - crit[1] + crit[2] - crit[3] == 1  # Euler characteristic of the cube
+    ess = np.flatnonzero(P["essential"])
+    assert len(ess) == 1
+    e = ess[0]
+    assert P["dim"][e] == 0 and d["rank"][P["vb"][e]] == 0 and d["rank"][P["vd"][e]] == V - 1
+    Z = d["zero"]
+    assert np.all(Z["vb"] == Z["vd"])
+
+
+def test_generic_linear_field_has_empty_finite_diagram():
+    f = S.linear_field((8, 7, 6), (1.0, 2.1, 4.3))
+    d = oracle.diagram(f)
+    assert len(d["pairs"]["vb"]) == 1 and d["pairs"]["essential"][0] == 1
+
+
+def test_interior_peak_gives_one_dominant_void():
+    shape = (11, 12, 13)
+    f = S.gaussian_bumps(shape, [(0.52, 0.47, 0.5)], [0.18], [1.0])
+    d = oracle.diagram(f)
+    P = d["pairs"]
+    flat = f.ravel()
+    lz, ly, lx = shape
+    x, y, z = np.meshgrid(np.arange(lx), np.arange(ly), np.arange(lz), indexing="xy")
+    bnd = np.zeros(shape, bool)
+    bnd[0], bnd[-1], bnd[:, 0], bnd[:, -1], bnd[:, :, 0], bnd[:, :, -1] = (True,) * 6
+    bidx = np.flatnonzero(bnd.ravel())
+    vb_ref = bidx[np.lexsort((bidx, flat[bidx]))[-1]]
+    vd_ref = int(np.lexsort((np.arange(flat.size), flat))[-1])
+    i2 = np.flatnonzero(P["dim"] == 2)
+    pers = flat[P["vd"][i2]] - flat[P["vb"][i2]]
+    k = i2[np.argmax(pers)]
+    assert P["vd"][k] == vd_ref and P["vb"][k] == vb_ref
+    assert pers.max() >= 0.9 * (flat.max() - flat[vb_ref])
+
+
+def test_ring_distance_gives_one_dominant_loop():
+    """Distance to a circle of radius rho: the 1-cycle around the ring is born
+    near 0 and dies at the 2-saddle at the circle's centre, value rho."""
+    shape = (21, 21, 21)
+    rho = 0.3
+    f = S.ring_distance(shape, (0.5, 0.5, 0.5), rho)
+    d = oracle.diagram(f)
+    P = d["pairs"]
+    flat = f.ravel()
+    i1 = np.flatnonzero(P["dim"] == 1)
+    pers = flat[P["vd"][i1]] - flat[P["vb"][i1]]
+    k = i1[np.argmax(pers)]
+    centre = 10 + 21 * (10 + 21 * 10)
+    assert P["vd"][k] == centre
+    assert flat[P["vd"][k]] == np.float32(rho)
+    h = 1.0 / (shape[0] - 1)  # the discretised ring closes within one grid spacing
+    assert flat[P["vb"][k]] < h
+    others = np.delete(pers, np.argmax(pers))
+    assert others.size == 0 or others.max() < h
+
+
+def _brute_assign(pb, pd, tb, td):
+    def c(i, j):
+        return (float(pb[i]) - float(tb[j])) ** 2 + (float(pd[i]) - float(td[j])) ** 2
+
+    def dg(b, dd):
+        return 0.5 * (float(dd) - float(b)) ** 2
+    best = np.inf
+    n, k = len(pb), len(tb)
+    for choice in itertools.product(range(-1, n), repeat=k):
+        used = [x for x in choice if x >= 0]
+        if len(used) != len(set(used)):
+            continue
+        cost = 0.0
+        for j, i in enumerate(choice):
+            cost += c(i, j) if i >= 0 else dg(tb[j], td[j])
+        for i in range(n):
+            if i not in used:
+                cost += dg(pb[i], pd[i])
+        best = min(best, cost)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_assignment_is_optimal_by_brute_force(seed):
+    """Eq. 1 with q = 2: the exact reduced assignment reaches the brute-force minimum."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 8))
+    k = int(rng.integers(1, 5))
+    b = rng.uniform(0, 1, n)
+    pb = b.astype(np.float32)
+    pd = (b + rng.uniform(0, 0.5, n) * (rng.uniform(size=n) < 0.6)).astype(np.float32)
+    tb_ = rng.uniform(0, 1, k)
+    tb = tb_.astype(np.float32)
+    td = (tb_ + rng.uniform(0.1, 0.6, k)).astype(np.float32)
+    if seed % 3 == 0:  # targets sitting on some points
+        m = min(n, k)
+        tb[:m], td[:m] = pb[:m], pd[:m]
+    tgt, cost = oracle.assign(pb, pd, tb, td)
+    ref = _brute_assign(pb, pd, tb, td)
+    assert abs(cost - ref) <= 1e-12 * max(1.0, ref)
+    used = tgt[tgt >= 0]
+    assert len(used) == len(set(used.tolist()))
+
+
+def _isolated_pair_field():
+    """A linear ramp with one raised interior vertex: one small saddle-max pair."""
+    shape = (6, 7, 8)
+    f = S.linear_field(shape, (1.0, 2.1, 4.3)).copy()
+    v = 3 + 8 * (3 + 7 * 3)
+    flat = f.ravel()
+    flat[v] += 2.0  # above all 14 neighbours: a lone interior maximum
+    return f, v
+
+
+def test_isolated_pair_moves_to_its_midpoint_in_one_step():
+    """Section 4.1 with alpha = 0.5: birth and death vertices meet at (b + d) / 2."""
+    f, v = _isolated_pair_field()
+    d = oracle.diagram(f)
+    P = d["pairs"]
+    fin = np.flatnonzero(P["essential"] == 0)
+    assert len(fin) == 1
+    vb, vd = int(P["vb"][fin[0]]), int(P["vd"][fin[0]])
+    assert vd == v
+    s = oracle.Solver(f, tau=0.99)
+    st0 = s.stats()
+    b, dd = f.ravel()[vb], f.ravel()[vd]
+    assert st0["loss0"] == pytest.approx(0.5 * (float(dd) - float(b)) ** 2, rel=0, abs=1e-15)
+    s.iterate(0.5, 0.5)
+    g = s.field().ravel()
+    m = np.float32(np.float32(b + dd) * np.float32(0.5))
+    assert g[vb] == m and g[vd] == m
+    changed = np.flatnonzero(g != f.ravel())
+    assert set(changed.tolist()) <= {vb, vd}
+    # the pair is now cancelled: the solver stops, even with the loss test off
+    assert s.done(stop_s=0.0)
+
+
+def test_cut_mode_moves_only_the_birth_vertex():
+    """Section 5.3: alpha_d = 0 leaves the death vertex in place."""
+    f, v = _isolated_pair_field()
+    d = oracle.diagram(f)
+    P = d["pairs"]
+    k = np.flatnonzero(P["essential"] == 0)[0]
+    vb, vd = int(P["vb"][k]), int(P["vd"][k])
+    s = oracle.Solver(f, tau=0.99)
+    s.iterate(0.5, 0.0)
+    g = s.field().ravel()
+    assert g[vd] == f.ravel()[vd]
+    b, dd = f.ravel()[vb], f.ravel()[vd]
+    assert g[vb] == np.float32(np.float32(b + dd) * np.float32(0.5))
+
+
+def test_linear_field_needs_no_iteration():
+    s = oracle.Solver(S.linear_field((5, 6, 7)), tau=0.01)
+    assert s.done(stop_s=0.0)
+    assert s.stats()["loss0"] == 0.0
+
+
+def test_signal_pairs_are_assigned_to_themselves_at_start():
+    f = S.random_field((6, 6, 6), seed=3)
+    s = oracle.Solver(f, tau=0.2)
+    P, T = s.points(), s.targets()
+    sig = P["tgt"] >= 0
+    for i in np.flatnonzero(sig):
+        t = P["tgt"][i]
+        assert (P["vb"][i], P["vd"][i], P["dim"][i]) == (T["vb"][t], T["vd"][t], T["dim"][t])
+        assert P["birth"][i] == T["birth"][t] and P["death"][i] == T["death"][t]
+    pers = P["death"] - P["birth"]
+    theta = np.float32(np.float32(0.2) * np.float32(f.max() - f.min()))
+    assert np.all(sig == ((pers >= theta) | (P["essential"] == 1)))
+    assert s.stats()["loss"] == pytest.approx(float(np.sum(0.5 * (P["death"][~sig].astype(np.float64)
+                                                                   - P["birth"][~sig]) ** 2)), rel=1e-12)
+
+
+def test_small_solve_reaches_the_loss_stop_rule():
+    """Algorithm 1: stop once L(f_j) <= s L(f_0), s = 0.01."""
+    f = S.gaussian_mixture((12, 12, 12), n_bumps=4, seed=5)
+    s = oracle.Solver(f, tau=0.1)
+    s.run(stop_s=0.01, max_iters=200)
+    st = s.stats()
+    assert st["iter"] < 50 and st["loss"] <= 0.01 * st["loss0"]
+    P = s.points()
+    # every signal target is still matched
+    assert len(set(P["tgt"][P["tgt"] >= 0].tolist())) == len(s.targets()["vb"])
