@@ -1,0 +1,175 @@
+/*
+ * tsf.h -- C ABI of the GB300 topological simplification solver.
+ *
+ * The library implements the solver of "A Practical Solver for Scalar Data
+ * Topological Simplification" (Algorithm 1 with the accelerations of
+ * Sections 4.1-4.3) for a 3D fp32 scalar field on the Freudenthal
+ * triangulation of a regular grid, every stage as a CUDA kernel on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid and values.  A field has lx * ly * lz vertices (each >= 2); vertex
+ * (x, y, z) has id x + lx * (y + ly * z) and its value is values[id] (C order
+ * of a (lz, ly, lx) array).  Values must be finite; -0.0 equals +0.0; equal
+ * values are ordered by vertex id (Section 2.1).
+ *
+ * Cells.  A simplex is identified by (dim << 60) | (base << 6) | type, where
+ * the simplex is the chain base, base+A, base+A+B, base+(1,1,1) of cube
+ * corners (axis masks x = 1, y = 2, z = 4): an edge has type A, a triangle or
+ * tetrahedron type 8*A + B, a vertex type 0.  The essential class has
+ * cell_death = UINT64_MAX.
+ *
+ * Memory.  The library owns every device buffer of a field.  Pointers passed
+ * in are owned by the caller; a flag next to each pointer says whether it is
+ * a device pointer (1) or a host pointer (0).  All work is enqueued on the
+ * CUDA stream given at creation (NULL = the legacy default stream), and every
+ * call has finished on that stream when it returns.
+ *
+ * Errors.  Every function returns TSF_OK (0) or a negative code; no C++
+ * exception crosses the boundary.  tsf_status_string() names a code.  A
+ * device-side bound that was hit (a loop or wait limit) surfaces as
+ * TSF_ETIMEOUT; the field stays usable.
+ */
+#ifndef TSF_H
+#define TSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSF_OK 0
+#define TSF_EINVAL (-1)      /* bad argument: null pointer, grid < 2 per axis, bad parameter */
+#define TSF_ENAN (-2)        /* a value is NaN or infinite */
+#define TSF_ENOMEM (-3)      /* device allocation failed */
+#define TSF_ECUDA (-4)       /* a CUDA call failed */
+#define TSF_ETIMEOUT (-5)    /* a device loop hit its bound; results of the call are invalid */
+#define TSF_ENOTARGET (-6)   /* a solver call before a target diagram was set */
+#define TSF_ECAPACITY (-7)   /* an output buffer is too small; *n_out holds the size needed */
+#define TSF_EINTERNAL (-8)   /* an internal consistency check failed */
+
+typedef struct tsf_field tsf_field;
+
+/* One point of a persistence diagram (Section 2.2): the pair (sigma_b,
+ * sigma_d) of the lexicographic filtration, its birth/death vertices (the
+ * highest vertex of each simplex) and their values.  dim is the homology
+ * dimension (0: minimum-1-saddle, 1: 1-saddle-2-saddle, 2: 2-saddle-maximum);
+ * essential = 1 marks the class that never dies, reported at
+ * (f(v_min), f(v_max)) (Section 2.2). */
+typedef struct {
+  int32_t dim;
+  int32_t essential;
+  uint32_t v_birth, v_death;
+  uint64_t cell_birth, cell_death;
+  float birth, death;
+} tsf_pair; /* 40 bytes */
+
+/* Solver parameters.
+ * alpha_b, alpha_d: step sizes of the birth and death gradients (Section 4.1;
+ *   0.5 is the paper's default, Section 5; alpha_d = 0 cuts handles and
+ *   alpha_b = 0 fills them, Section 5.3).
+ * stop_s: Algorithm 1 stops once loss_j <= stop_s * loss_0 (<= 0: off; the
+ *   paper uses 0.01).
+ * cancel_eps: the solver also stops once no diagonal-matched point has
+ *   persistence > cancel_eps (every non-signal pair cancelled).
+ * max_iters: j_max of Algorithm 1 (the paper uses 1000).
+ * fast_gradient_update: 1 recomputes the gradient only around vertices the
+ *   last step changed (Section 4.2); 0 recomputes it everywhere.  Results are
+ *   identical either way. */
+typedef struct {
+  float alpha_b, alpha_d;
+  float stop_s;
+  float cancel_eps;
+  int32_t max_iters;
+  int32_t fast_gradient_update;
+} tsf_params;
+
+/* Per-iteration statistics. */
+typedef struct {
+  int32_t iters;              /* j */
+  int32_t done;               /* 1 when the stop rule holds */
+  double loss0, loss;         /* W2^2 between D(f_0) / D(f_j) and the target (Eq. 2) */
+  int64_t n_points;           /* points of D(f_j), essential class included */
+  int64_t n_pairs[3];         /* finite points per dimension */
+  int64_t n_critical[4];      /* critical vertices, edges, triangles, tetrahedra */
+  int64_t n_uncancelled;      /* diagonal-matched points with persistence > cancel_eps */
+  int64_t n_still;            /* points still since the previous iteration (Section 4.3) */
+  int64_t n_nonstill_matched; /* non-still points matched to a target */
+  int64_t n_updated_vertices; /* vertices whose value the last step changed */
+  int64_t n_gradient_vertices;/* lower stars recomputed by the last diagram */
+  double ms_diagram, ms_assign, ms_step; /* host wall time of the three stages */
+} tsf_stats;
+
+/* Creates a field from lx*ly*lz values (host or device memory, copied).
+ * cuda_stream: a cudaStream_t, or NULL.  Errors: TSF_EINVAL, TSF_ENAN,
+ * TSF_ENOMEM, TSF_ECUDA.  On success *out owns all device memory. */
+int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_device, void* cuda_stream,
+                     tsf_field** out);
+
+/* Frees the field and its device memory.  NULL is accepted. */
+int tsf_destroy_field(tsf_field* field);
+
+/* Persistence diagram D(f) of the field's current values (Section 2.2; the
+ * pairs of the lexicographic filtration whose birth and death vertices
+ * differ, plus the essential class), in diagram order: increasing birth, then
+ * death (Section 2.4), then birth vertex, death vertex and birth cell.
+ * out: cap entries (host or device per out_on_device), may be NULL when cap
+ * is 0.  *n_out receives the number of points; TSF_ECAPACITY if cap is too
+ * small (nothing written). */
+int tsf_compute_diagram(tsf_field* field, tsf_pair* out, int64_t cap, int64_t* n_out, int out_on_device);
+
+/* Target diagram (Section 3) = D(f_0) without the non-signal pairs, where a
+ * pair is signal when its persistence fl(death - birth) >= fl(fraction *
+ * fl(max f_0 - min f_0)); the essential class is always kept.  f_0 is the
+ * field's current values.  Resets the solver to iteration 0 and assigns
+ * every signal point to itself (Section 4.3).  Errors: TSF_EINVAL if
+ * fraction < 0. */
+int tsf_set_signal_threshold(tsf_field* field, float fraction_of_range);
+
+/* Explicit target diagram: n host-memory points (dim, essential, v_birth,
+ * v_death, birth, death are used; cells are ignored).  The essential class of
+ * D(f_0) is added when no entry is essential.  Iteration 0 assigns each point
+ * of D(f_0) to the target with the same (dim, essential, v_birth, v_death),
+ * and the rest by the exact reduced assignment. */
+int tsf_set_signal_pairs(tsf_field* field, const tsf_pair* pairs, int64_t n);
+
+/* One solver iteration j -> j+1 (Algorithm 1): gradient step with phi*_j
+ * (Section 4.1), diagram of f_{j+1} (Sections 2.2, 4.2), assignment
+ * phi*_{j+1} (Section 4.3, exact).  stats may be NULL.  Errors:
+ * TSF_ENOTARGET before a target was set, TSF_EINVAL for bad parameters. */
+int tsf_solver_step(tsf_field* field, const tsf_params* params, tsf_stats* stats);
+
+/* Iterates tsf_solver_step until the stop rule holds, then copies the field
+ * to out_values (lx*ly*lz floats, host or device; may be NULL). */
+int tsf_simplify(tsf_field* field, const tsf_params* params, float* out_values, int out_on_device, tsf_stats* stats);
+
+/* Copies the current values to out (lx*ly*lz floats, host or device). */
+int tsf_get_field(tsf_field* field, float* out, int out_on_device);
+
+/* Overwrites the current values (restart from a saved field; the still-pair
+ * history is reset, so the next assignment starts cold). */
+int tsf_set_field(tsf_field* field, const float* values, int values_on_device);
+
+/* The current assignment, in the order of the last diagram: target[i] is the
+ * index of point i's target in the target list (tsf_get_targets), or -1 for
+ * the diagonal; still[i] is 1 for still points.  Host memory, cap entries
+ * each (either may be NULL). */
+int tsf_get_assignment(tsf_field* field, int32_t* target, int32_t* still, int64_t cap, int64_t* n_out);
+
+/* The target diagram, in target order (diagram order of the targets), host memory. */
+int tsf_get_targets(tsf_field* field, tsf_pair* out, int64_t cap, int64_t* n_out);
+
+/* Every zero-persistence pair (Section 2.2: v_b == v_d) of the current
+ * values, as cell ids: out[2k] = birth cell, out[2k+1] = death cell (host
+ * memory, unordered).  These are the pairs of the lower-star discrete
+ * gradient (Section 4.2); intended for verification on small grids. */
+int tsf_zero_pairs(tsf_field* field, uint64_t* out, int64_t cap_pairs, int64_t* n_out);
+
+/* Human-readable name of a status code. */
+const char* tsf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSF_H */

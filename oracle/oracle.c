@@ -462,6 +462,7 @@ typedef struct {
   int32_t dim, ess;
   uint32_t vb, vd;
   float b, d;
+  uint64_t src; /* birth cell of the D(f0) pair it came from, or input index */
 } otarget_t;
 
 struct or_solver {
@@ -506,6 +507,7 @@ static int cmp_target(const void* a, const void* b) {
   if (x->vd != y->vd) return x->vd < y->vd ? -1 : 1;
   if (x->dim != y->dim) return x->dim < y->dim ? -1 : 1;
   if (x->ess != y->ess) return x->ess < y->ess ? -1 : 1;
+  if (x->src != y->src) return x->src < y->src ? -1 : 1;
   return 0;
 }
 
@@ -955,7 +957,7 @@ static void solver_start(or_solver* s) {
     R[t].ess = s->T[t].ess;
     R[t].vb = s->T[t].vb;
     R[t].vd = s->T[t].vd;
-    R[t].cb = 0;
+    R[t].cb = s->T[t].src; /* duplicates of one key pair up in source order */
     R[t].cd = 0;
     R[t].b = s->T[t].b;
     R[t].d = s->T[t].d;
@@ -995,6 +997,7 @@ or_solver* or_solver_create(int lx, int ly, int lz, const float* f0, float tau, 
       t->vd = p->vd;
       t->b = p->b;
       t->d = p->d;
+      t->src = p->cb;
     }
   }
   solver_start(s);
@@ -1017,6 +1020,7 @@ or_solver* or_solver_create_targets(int lx, int ly, int lz, const float* f0, int
     t->vd = vd[i];
     t->b = birth[i];
     t->d = death[i];
+    t->src = (uint64_t)i;
     if (essential[i]) has_ess = 1;
   }
   if (!has_ess)
@@ -1029,6 +1033,7 @@ or_solver* or_solver_create_targets(int lx, int ly, int lz, const float* f0, int
         t->vd = s->P[i].vd;
         t->b = s->P[i].b;
         t->d = s->P[i].d;
+        t->src = (uint64_t)n;
       }
   solver_start(s);
   return s;

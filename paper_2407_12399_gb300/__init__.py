@@ -1,0 +1,280 @@
+"""Python binding of libtsf.so, the GB300 topological simplification solver.
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  The functions keep the C ABI's names and arguments
+(include/tsf.h); ``Field`` wraps them for numpy arrays and torch tensors.
+Importing this package needs no GPU; the first call that touches the
+library loads it and fails loudly if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtsf.so")
+
+TSF_OK = 0
+TSF_EINVAL = -1
+TSF_ENAN = -2
+TSF_ENOMEM = -3
+TSF_ECUDA = -4
+TSF_ETIMEOUT = -5
+TSF_ENOTARGET = -6
+TSF_ECAPACITY = -7
+TSF_EINTERNAL = -8
+
+
+class tsf_pair(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("essential", ctypes.c_int32), ("v_birth", ctypes.c_uint32),
+                ("v_death", ctypes.c_uint32), ("cell_birth", ctypes.c_uint64), ("cell_death", ctypes.c_uint64),
+                ("birth", ctypes.c_float), ("death", ctypes.c_float)]
+
+
+PAIR_DTYPE = np.dtype([("dim", np.int32), ("essential", np.int32), ("v_birth", np.uint32), ("v_death", np.uint32),
+                       ("cell_birth", np.uint64), ("cell_death", np.uint64), ("birth", np.float32),
+                       ("death", np.float32)])
+assert PAIR_DTYPE.itemsize == ctypes.sizeof(tsf_pair) == 40
+
+
+class tsf_params(ctypes.Structure):
+    _fields_ = [("alpha_b", ctypes.c_float), ("alpha_d", ctypes.c_float), ("stop_s", ctypes.c_float),
+                ("cancel_eps", ctypes.c_float), ("max_iters", ctypes.c_int32),
+                ("fast_gradient_update", ctypes.c_int32)]
+
+
+class tsf_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("done", ctypes.c_int32), ("loss0", ctypes.c_double),
+                ("loss", ctypes.c_double), ("n_points", ctypes.c_int64), ("n_pairs", ctypes.c_int64 * 3),
+                ("n_critical", ctypes.c_int64 * 4), ("n_uncancelled", ctypes.c_int64), ("n_still", ctypes.c_int64),
+                ("n_nonstill_matched", ctypes.c_int64), ("n_updated_vertices", ctypes.c_int64),
+                ("n_gradient_vertices", ctypes.c_int64), ("ms_diagram", ctypes.c_double),
+                ("ms_assign", ctypes.c_double), ("ms_step", ctypes.c_double)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_set_signal_threshold",
+           "tsf_set_signal_pairs", "tsf_solver_step", "tsf_simplify", "tsf_get_field", "tsf_set_field",
+           "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string")
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if the CUDA extension was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2407_12399_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        I64 = ctypes.c_int64
+        sig = {
+            "tsf_create_field": [I, I, I, P, I, P, ctypes.POINTER(P)],
+            "tsf_destroy_field": [P],
+            "tsf_compute_diagram": [P, P, I64, ctypes.POINTER(I64), I],
+            "tsf_set_signal_threshold": [P, ctypes.c_float],
+            "tsf_set_signal_pairs": [P, P, I64],
+            "tsf_solver_step": [P, ctypes.POINTER(tsf_params), ctypes.POINTER(tsf_stats)],
+            "tsf_simplify": [P, ctypes.POINTER(tsf_params), P, I, ctypes.POINTER(tsf_stats)],
+            "tsf_get_field": [P, P, I],
+            "tsf_set_field": [P, P, I],
+            "tsf_get_assignment": [P, P, P, I64, ctypes.POINTER(I64)],
+            "tsf_get_targets": [P, P, I64, ctypes.POINTER(I64)],
+            "tsf_zero_pairs": [P, P, I64, ctypes.POINTER(I64)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.tsf_status_string.argtypes = [ctypes.c_int]
+        L.tsf_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+class TsfError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {tsf_status_string(code)} ({code})")
+
+
+def tsf_status_string(code: int) -> str:
+    return lib().tsf_status_string(code).decode()
+
+
+def _check(code, where):
+    if code != TSF_OK:
+        raise TsfError(code, where)
+
+
+# --- thin wrappers with the C names (pointers as ints, sizes as ints) -------
+def tsf_create_field(lx, ly, lz, values_ptr, values_on_device, cuda_stream=0):
+    h = ctypes.c_void_p()
+    _check(lib().tsf_create_field(lx, ly, lz, values_ptr, values_on_device, cuda_stream or None, ctypes.byref(h)),
+           "tsf_create_field")
+    return h
+
+
+def tsf_destroy_field(h):
+    return lib().tsf_destroy_field(h)
+
+
+def tsf_compute_diagram(h, out_ptr, cap, out_on_device=0):
+    n = ctypes.c_int64(0)
+    r = lib().tsf_compute_diagram(h, out_ptr, cap, ctypes.byref(n), out_on_device)
+    return r, n.value
+
+
+def tsf_set_signal_threshold(h, fraction):
+    _check(lib().tsf_set_signal_threshold(h, fraction), "tsf_set_signal_threshold")
+
+
+def tsf_set_signal_pairs(h, pairs_ptr, n):
+    _check(lib().tsf_set_signal_pairs(h, pairs_ptr, n), "tsf_set_signal_pairs")
+
+
+def tsf_solver_step(h, params, stats=None):
+    st = stats if stats is not None else tsf_stats()
+    _check(lib().tsf_solver_step(h, ctypes.byref(params), ctypes.byref(st)), "tsf_solver_step")
+    return st
+
+
+def tsf_simplify(h, params, out_ptr=None, out_on_device=0, stats=None):
+    st = stats if stats is not None else tsf_stats()
+    _check(lib().tsf_simplify(h, ctypes.byref(params), out_ptr, out_on_device, ctypes.byref(st)), "tsf_simplify")
+    return st
+
+
+def tsf_get_field(h, out_ptr, out_on_device=0):
+    _check(lib().tsf_get_field(h, out_ptr, out_on_device), "tsf_get_field")
+
+
+def tsf_set_field(h, values_ptr, values_on_device=0):
+    _check(lib().tsf_set_field(h, values_ptr, values_on_device), "tsf_set_field")
+
+
+def tsf_get_assignment(h, target_ptr, still_ptr, cap):
+    n = ctypes.c_int64(0)
+    r = lib().tsf_get_assignment(h, target_ptr, still_ptr, cap, ctypes.byref(n))
+    return r, n.value
+
+
+def tsf_get_targets(h, out_ptr, cap):
+    n = ctypes.c_int64(0)
+    r = lib().tsf_get_targets(h, out_ptr, cap, ctypes.byref(n))
+    return r, n.value
+
+
+def tsf_zero_pairs(h, out_ptr, cap):
+    n = ctypes.c_int64(0)
+    r = lib().tsf_zero_pairs(h, out_ptr, cap, ctypes.byref(n))
+    return r, n.value
+
+
+def params(alpha_b=0.5, alpha_d=0.5, stop_s=0.01, cancel_eps=0.0, max_iters=1000, fast_gradient_update=1):
+    return tsf_params(alpha_b, alpha_d, stop_s, cancel_eps, max_iters, fast_gradient_update)
+
+
+def _ptr_of(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return a.data_ptr(), 1 if a.is_cuda else 0
+    except ImportError:  # pragma: no cover
+        pass
+    raise TypeError(type(a))
+
+
+class Field:
+    """A field on the GPU.  values: (Lz, Ly, Lx) float32 numpy array or tensor."""
+
+    def __init__(self, values, stream=None):
+        shape = tuple(values.shape)
+        if len(shape) != 3:
+            raise ValueError("values must be (Lz, Ly, Lx)")
+        if isinstance(values, np.ndarray):
+            values = np.ascontiguousarray(values, dtype=np.float32)
+        else:
+            values = values.contiguous()
+        self.shape = shape
+        lz, ly, lx = shape
+        p, dev = _ptr_of(values)
+        s = 0
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._h = tsf_create_field(lx, ly, lz, p, dev, s)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            tsf_destroy_field(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def diagram(self):
+        r, n = tsf_compute_diagram(self._h, None, 0)
+        if r not in (TSF_OK, TSF_ECAPACITY):
+            _check(r, "tsf_compute_diagram")
+        out = np.zeros(n, PAIR_DTYPE)
+        r, n = tsf_compute_diagram(self._h, out.ctypes.data, n)
+        _check(r, "tsf_compute_diagram")
+        return out
+
+    def set_threshold(self, fraction):
+        tsf_set_signal_threshold(self._h, fraction)
+
+    def set_targets(self, pairs):
+        pairs = np.ascontiguousarray(pairs, PAIR_DTYPE)
+        tsf_set_signal_pairs(self._h, pairs.ctypes.data, len(pairs))
+
+    def step(self, **kw):
+        return tsf_solver_step(self._h, params(**kw)).as_dict()
+
+    def simplify(self, **kw):
+        out = np.zeros(self.shape, np.float32)
+        st = tsf_simplify(self._h, params(**kw), out.ctypes.data, 0)
+        return out, st.as_dict()
+
+    def values(self):
+        out = np.zeros(self.shape, np.float32)
+        tsf_get_field(self._h, out.ctypes.data, 0)
+        return out
+
+    def assignment(self):
+        r, n = tsf_get_assignment(self._h, None, None, 0)
+        tgt = np.zeros(n, np.int32)
+        still = np.zeros(n, np.int32)
+        r, n = tsf_get_assignment(self._h, tgt.ctypes.data, still.ctypes.data, n)
+        _check(r, "tsf_get_assignment")
+        return tgt, still
+
+    def targets(self):
+        r, n = tsf_get_targets(self._h, None, 0)
+        out = np.zeros(n, PAIR_DTYPE)
+        r, n = tsf_get_targets(self._h, out.ctypes.data, n)
+        _check(r, "tsf_get_targets")
+        return out
+
+    def zero_pairs(self):
+        r, n = tsf_zero_pairs(self._h, None, 0)
+        out = np.zeros(2 * max(n, 1), np.uint64)
+        r, n = tsf_zero_pairs(self._h, out.ctypes.data, n)
+        _check(r, "tsf_zero_pairs")
+        return out[: 2 * n].reshape(-1, 2)

@@ -1,0 +1,581 @@
+// k_pairs.cu -- persistence pairs of the critical cells.
+//
+// The critical cells left by the lower-star gradient are paired exactly as
+// the plain reduction of the lexicographic filtration would pair them:
+//   D0 (minimum, 1-saddle): integral lines from both ends of each critical
+//     edge down to minima, then the elder rule over critical edges in
+//     increasing order (union-find);
+//   D2 (2-saddle, maximum): by duality, integral lines from the two
+//     tetrahedra (or the outside) of each critical triangle up to maxima, then
+//     the elder rule over critical triangles in decreasing order, the outside
+//     of the domain being the oldest node;
+//   D1 (1-saddle, 2-saddle): the column reduction of the critical triangles
+//     left over, restricted to positive edges, where a gradient-paired edge is
+//     eliminated with its triangle's reduced column.
+// The union-find runs in rounds of deterministic reservations: an item
+// commits when no earlier item touches the component that would die, which
+// gives exactly the sequential elder-rule result whatever the schedule.
+#include "tsf_kernels.cuh"
+#include "tsf_star.cuh"
+
+namespace tsf {
+
+constexpr int kTraceLimit = 1 << 26;
+constexpr int kUFT = 1024;
+
+// ---------------------------------------------------------------------------
+// integral lines
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t trace_down(uint32_t w, const uint8_t* __restrict__ vnext8,
+                                              const uint32_t* __restrict__ cidx, const NbrDelta& nd) {
+  for (int s = 0; s < kTraceLimit; ++s) {
+    int k = vnext8[w];
+    if (k == kVnextMin) return (int32_t)cidx[w];
+    w = (uint32_t)((int32_t)w + nd.d[k]);
+  }
+  return -1;
+}
+
+__global__ void k_d0_trace(int n1, CritLists L, const uint8_t* __restrict__ vnext8, const uint32_t* __restrict__ cidx,
+                           NbrDelta nd, int32_t* __restrict__ ends, uint32_t* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n1) return;
+  uint32_t vn = L.c1_vn[i];
+  uint32_t v = vn >> 4;
+  int k = (int)(vn & 15u);
+  uint32_t u = (uint32_t)((int32_t)v + nd.d[k]);
+  int32_t a = trace_down(v, vnext8, cidx, nd), b = trace_down(u, vnext8, cidx, nd);
+  if (a < 0 || b < 0) atomicOr(status, kErrTrace);
+  ends[2 * i] = a < 0 ? 0 : a;
+  ends[2 * i + 1] = b < 0 ? 0 : b;
+}
+
+__device__ __forceinline__ Rec ld_rec(const Rec* rec, uint32_t v) {
+  const uint4* p = reinterpret_cast<const uint4*>(rec + v);
+  uint4 a = __ldg(p), b = __ldg(p + 1);
+  Rec r;
+  r.w[0] = a.x; r.w[1] = a.y; r.w[2] = a.z; r.w[3] = a.w;
+  r.w[4] = b.x; r.w[5] = b.y; r.w[6] = b.z; r.w[7] = b.w;
+  return r;
+}
+
+// Ascending integral line in the dual: from tetrahedron (w, tau) follow the
+// record codes to a maximum (its index) or to the outside (returns n3).
+__device__ int32_t trace_up(uint32_t w, int tau, const Rec* __restrict__ rec, const uint32_t* __restrict__ cidx,
+                            const NbrDelta& nd, int n3) {
+  Rec r = ld_rec(rec, w);
+  for (int s = 0; s < kTraceLimit; ++s) {
+    int code = rec_tet_code(r, tau);
+    if (code == kCodeMax) return (int32_t)cidx[w];
+    if (code == kCodeOut) return n3;
+    if (code < 24) {
+      tau = code;
+      continue;
+    }
+    if (code >= 96) return -1;
+    int t2 = (code - 24) / 3, j = (code - 24) % 3;
+    int c = c_geo.tri[t2][j];
+    int p = c_geo.tri[t2][(j + 1) % 3], q = c_geo.tri[t2][(j + 2) % 3];
+    int i0 = nbr_index(-c_geo.off[c][0], -c_geo.off[c][1], -c_geo.off[c][2]);
+    int i1 = nbr_index(c_geo.off[p][0] - c_geo.off[c][0], c_geo.off[p][1] - c_geo.off[c][1],
+                       c_geo.off[p][2] - c_geo.off[c][2]);
+    int i2 = nbr_index(c_geo.off[q][0] - c_geo.off[c][0], c_geo.off[q][1] - c_geo.off[c][1],
+                       c_geo.off[q][2] - c_geo.off[c][2]);
+    if (i0 < 0 || i1 < 0 || i2 < 0) return -1;
+    tau = c_geo.tri_of3[i0][i1][i2];
+    if (tau < 0) return -1;
+    w = (uint32_t)((int32_t)w + nd.d[c]);
+    r = ld_rec(rec, w);
+  }
+  return -1;
+}
+
+__global__ void k_d2_trace(Dims d, int n2, int n3, CritLists L, const uint32_t* __restrict__ rank,
+                           const Rec* __restrict__ rec, const uint32_t* __restrict__ cidx, NbrDelta nd,
+                           int32_t* __restrict__ ends, uint32_t* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  uint32_t ve = L.c2_ve[i];
+  uint32_t v = ve >> 6;
+  int e = (int)(ve & 63u);
+  int a = c_geo.edge[e][0], b = c_geo.edge[e][1];
+  int x, y, z;
+  vxyz(d, v, x, y, z);
+  uint32_t rv = rank[v];
+  for (int k = 0; k < 2; ++k) {
+    int t = c_geo.edge_tri[e][k];
+    int j = 0;
+    while (c_geo.tri[t][j] == a || c_geo.tri[t][j] == b) ++j;
+    int c = c_geo.tri[t][j];
+    int nx, ny, nz;
+    int32_t res;
+    if (!nbr_xyz(d, x, y, z, c, nx, ny, nz)) {
+      res = n3;
+    } else {
+      uint32_t wc = vid(d, nx, ny, nz);
+      if (rank[wc] < rv) {
+        res = trace_up(v, t, rec, cidx, nd, n3);
+      } else {
+        int i0 = nbr_index(-c_geo.off[c][0], -c_geo.off[c][1], -c_geo.off[c][2]);
+        int i1 = nbr_index(c_geo.off[a][0] - c_geo.off[c][0], c_geo.off[a][1] - c_geo.off[c][1],
+                           c_geo.off[a][2] - c_geo.off[c][2]);
+        int i2 = nbr_index(c_geo.off[b][0] - c_geo.off[c][0], c_geo.off[b][1] - c_geo.off[c][1],
+                           c_geo.off[b][2] - c_geo.off[c][2]);
+        int tau = (i0 >= 0 && i1 >= 0 && i2 >= 0) ? c_geo.tri_of3[i0][i1][i2] : -1;
+        res = tau < 0 ? -1 : trace_up(wc, tau, rec, cidx, nd, n3);
+      }
+    }
+    if (res < 0) {
+      atomicOr(status, kErrTrace);
+      res = n3;
+    }
+    ends[2 * i + k] = res;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// elder-rule union-find by rounds of deterministic reservations (one block)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int uf_root(int32_t* parent, int x) {
+  for (int s = 0; s < kTraceLimit; ++s) {
+    int p = parent[x];
+    if (p == x) return x;
+    int gp = parent[p];
+    if (gp != p) parent[x] = gp;
+    x = gp;
+  }
+  return x;
+}
+
+__device__ __forceinline__ int block_exscan_int(int v, int& total) {
+  __shared__ int sw[kUFT / 32 + 1];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sw[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int s = sw[lane];
+    int si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xFFFFFFFFu, si, o);
+      if (lane >= o) si += t;
+    }
+    sw[lane] = si - s;
+    if (lane == 31) sw[32] = si;
+  }
+  __syncthreads();
+  int res = sw[wid] + inc - v;
+  total = sw[32];
+  __syncthreads();
+  return res;
+}
+
+// n items (priority i, or n-1-i when `reverse`), nn nodes.  Younger node =
+// larger index (reverse = false) or smaller index (reverse = true).
+// kill[i] = node killed by item i, or -1 (item closes a cycle).
+__global__ void __launch_bounds__(kUFT) k_uf_rounds(int n, int nn, bool reverse, const int32_t* __restrict__ ends,
+                                                    int32_t* parent, int32_t* reserve, int32_t* listA,
+                                                    int32_t* listB, int32_t* roots, int32_t* kill,
+                                                    uint32_t* status) {
+  __shared__ int s_n;
+  for (int x = threadIdx.x; x < nn; x += kUFT) {
+    parent[x] = x;
+    reserve[x] = 0x7FFFFFFF;
+  }
+  for (int i = threadIdx.x; i < n; i += kUFT) {
+    kill[i] = -1;
+    listA[i] = i;
+  }
+  if (threadIdx.x == 0) s_n = n;
+  __syncthreads();
+  int32_t* cur = listA;
+  int32_t* nxt = listB;
+  for (int round = 0;; ++round) {
+    int m = s_n;
+    if (m == 0) break;
+    if (round > n + 2) {
+      if (threadIdx.x == 0) atomicOr(status, kErrRounds);
+      break;
+    }
+    for (int k = threadIdx.x; k < m; k += kUFT) {
+      int i = cur[k];
+      int a = uf_root(parent, ends[2 * i]), b = uf_root(parent, ends[2 * i + 1]);
+      roots[2 * i] = a;
+      roots[2 * i + 1] = b;
+      if (a != b) {
+        int pr = reverse ? n - 1 - i : i;
+        atomicMin(&reserve[a], pr);
+        atomicMin(&reserve[b], pr);
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += kUFT) {
+      int i = cur[k];
+      int a = roots[2 * i], b = roots[2 * i + 1];
+      if (a == b) continue;
+      int young = reverse ? min(a, b) : max(a, b);
+      int old = a + b - young;
+      int pr = reverse ? n - 1 - i : i;
+      if (reserve[young] == pr) {
+        parent[young] = old;
+        kill[i] = young;
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += kUFT) {
+      int i = cur[k];
+      int a = roots[2 * i], b = roots[2 * i + 1];
+      if (a != b) {
+        reserve[a] = 0x7FFFFFFF;
+        reserve[b] = 0x7FFFFFFF;
+      }
+    }
+    int cnt = 0;
+    for (int base = 0; base < m; base += kUFT) {
+      int k = base + threadIdx.x;
+      int keep = 0, i = 0;
+      if (k < m) {
+        i = cur[k];
+        keep = (roots[2 * i] != roots[2 * i + 1]) && kill[i] < 0;
+      }
+      int tot;
+      int ex = block_exscan_int(keep, tot);
+      if (keep) nxt[cnt + ex] = i;
+      cnt += tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_n = cnt;
+    __syncthreads();
+    int32_t* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+}
+
+__global__ void k_mark_d0(int n1, const int32_t* __restrict__ kill, uint8_t* __restrict__ killed) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n1) killed[i] = kill[i] >= 0 ? 1 : 0;
+}
+
+void launch_d0(const Dims& d, const NbrDelta& nd, const CritLists& L, int n0, int n1, const uint8_t* vnext8,
+               const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status, cudaStream_t st) {
+  if (n1 > 0) {
+    k_d0_trace<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, vnext8, cidx, nd, S.ends, status);
+    k_uf_rounds<<<1, kUFT, 0, st>>>(n1, n0, false, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
+                                    P.d0_min, status);
+    k_mark_d0<<<(n1 + 255) / 256, 256, 0, st>>>(n1, P.d0_min, P.d0_killed);
+  }
+}
+
+void launch_d2(const Dims& d, const NbrDelta& nd, const CritLists& L, int n2, int n3, const uint32_t* rank,
+               const Rec* rec, const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status,
+               cudaStream_t st) {
+  if (n2 > 0) {
+    k_d2_trace<<<(n2 + 255) / 256, 256, 0, st>>>(d, n2, n3, L, rank, rec, cidx, nd, S.ends, status);
+    k_uf_rounds<<<1, kUFT, 0, st>>>(n2, n3 + 1, true, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
+                                    P.d2_max, status);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// D1: column reduction of the critical triangles not paired in D2
+// ---------------------------------------------------------------------------
+struct D1Ctx {
+  Dims d;
+  NbrDelta nd;
+  const uint32_t* rank;
+  const uint32_t* order;
+  const Rec* rec;
+  const uint32_t* c1base;
+  CritLists L;
+  const uint8_t* d0_killed;
+};
+
+__device__ __forceinline__ int nbr_of_pair(const Dims& d, uint32_t hi, uint32_t lo) {
+  int hx, hy, hz, lx, ly, lz;
+  vxyz(d, hi, hx, hy, hz);
+  vxyz(d, lo, lx, ly, lz);
+  return nbr_index(lx - hx, ly - hy, lz - hz);
+}
+
+__device__ int crit_edge_index(const D1Ctx& c, uint32_t hi, const Rec& r, int k) {
+  int cnt = __popc(rec_crit_edges(r));
+  uint32_t base = c.c1base[hi];
+  for (int j = 0; j < cnt; ++j)
+    if ((int)(c.L.c1_vn[base + j] & 15u) == k) return (int)(base + j);
+  return -1;
+}
+
+// 0: negative edge (not a row of the D1 matrix), 1: positive and critical,
+// 2: positive and paired with a triangle in its lower star.
+__device__ int edge_status(const D1Ctx& c, uint32_t p, uint32_t q, unsigned long long& key, int& ci) {
+  uint32_t rp = c.rank[p], rq = c.rank[q];
+  uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
+  key = ((unsigned long long)max(rp, rq) << 32) | min(rp, rq);
+  int k = nbr_of_pair(c.d, hi, lo);
+  Rec r = ld_rec(c.rec, hi);
+  if (rec_vnext(r) == k) return 0;
+  if ((rec_crit_edges(r) >> k) & 1u) {
+    ci = crit_edge_index(c, hi, r, k);
+    if (ci < 0) return 0;
+    return c.d0_killed[ci] ? 0 : 1;
+  }
+  return 2;
+}
+
+struct Heap {
+  unsigned long long* h;
+  uint32_t off, cap, size;
+};
+
+__device__ bool heap_push(D1Work& W, Heap& H, unsigned long long key, uint32_t* status) {
+  if (H.size == H.cap) {
+    uint32_t ncap = H.cap * 2;
+    uint32_t noff = atomicAdd(W.pool_head, ncap);
+    if ((unsigned long long)noff + ncap > W.pool_cap) {
+      atomicOr(status, kErrPool);
+      return false;
+    }
+    unsigned long long* nh = W.pool + noff;
+    for (uint32_t i = 0; i < H.size; ++i) nh[i] = H.h[i];
+    H.h = nh;
+    H.off = noff;
+    H.cap = ncap;
+  }
+  uint32_t i = H.size++;
+  H.h[i] = key;
+  while (i > 0) {
+    uint32_t p = (i - 1) >> 1;
+    if (H.h[p] >= H.h[i]) break;
+    unsigned long long t = H.h[p];
+    H.h[p] = H.h[i];
+    H.h[i] = t;
+    i = p;
+  }
+  return true;
+}
+
+__device__ unsigned long long heap_pop(Heap& H) {
+  unsigned long long top = H.h[0];
+  unsigned long long last = H.h[--H.size];
+  uint32_t i = 0;
+  while (true) {
+    uint32_t l = 2 * i + 1;
+    if (l >= H.size) break;
+    uint32_t r = l + 1;
+    uint32_t m = (r < H.size && H.h[r] > H.h[l]) ? r : l;
+    if (H.h[m] <= last) break;
+    H.h[i] = H.h[m];
+    i = m;
+  }
+  if (H.size > 0) H.h[i] = last;
+  return top;
+}
+
+// largest entry present an odd number of times (Z/2), 0 if the column is empty
+__device__ unsigned long long heap_low(Heap& H) {
+  while (H.size > 0) {
+    unsigned long long top = heap_pop(H);
+    int c = 1;
+    while (H.size > 0 && H.h[0] == top) {
+      heap_pop(H);
+      ++c;
+    }
+    if (c & 1) return top;
+  }
+  return 0ull;
+}
+
+__device__ __forceinline__ Heap heap_of(D1Work& W, int j) {
+  Heap H;
+  H.off = W.hoff[j];
+  H.cap = W.hcap[j];
+  H.size = W.hsize[j];
+  H.h = W.pool + H.off;
+  return H;
+}
+__device__ __forceinline__ void heap_store(D1Work& W, int j, const Heap& H) {
+  W.hoff[j] = H.off;
+  W.hcap[j] = H.cap;
+  W.hsize[j] = H.size;
+}
+
+__device__ void push_if_positive(const D1Ctx& c, D1Work& W, Heap& H, uint32_t p, uint32_t q, uint32_t* status) {
+  unsigned long long key;
+  int ci;
+  if (edge_status(c, p, q, key, ci) != 0) heap_push(W, H, key, status);
+}
+
+__global__ void k_d1_select(int n2, const int32_t* __restrict__ d2_max, uint32_t* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n2) flag[i] = d2_max[i] < 0 ? 1u : 0u;
+}
+__global__ void k_d1_gather(int n2, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                            int32_t* __restrict__ cols, int32_t* __restrict__ d1_edge) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n2) {
+    d1_edge[i] = -1;
+    if (flag[i]) cols[pos[i]] = i;
+  }
+}
+
+__global__ void k_d1_init(D1Ctx c, D1Work W, int ncols, int32_t* owner, int n1, uint32_t* status) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int k = j; k < n1; k += gridDim.x * blockDim.x) owner[k] = 0x7FFFFFFF;
+  if (j >= ncols) return;
+  uint32_t cap = 16;
+  uint32_t off = atomicAdd(W.pool_head, cap);
+  if ((unsigned long long)off + cap > W.pool_cap) {
+    atomicOr(status, kErrPool);
+    W.hoff[j] = 0;
+    W.hcap[j] = 0;
+    W.hsize[j] = 0;
+    W.low[j] = 0;
+    W.lowc[j] = -1;
+    return;
+  }
+  Heap H;
+  H.off = off;
+  H.cap = cap;
+  H.size = 0;
+  H.h = W.pool + off;
+  uint32_t ve = c.L.c2_ve[W.cols[j]];
+  uint32_t v = ve >> 6;
+  int e = (int)(ve & 63u);
+  uint32_t a = (uint32_t)((int32_t)v + c.nd.d[c_geo.edge[e][0]]);
+  uint32_t b = (uint32_t)((int32_t)v + c.nd.d[c_geo.edge[e][1]]);
+  push_if_positive(c, W, H, v, a, status);
+  push_if_positive(c, W, H, v, b, status);
+  push_if_positive(c, W, H, a, b, status);
+  heap_store(W, j, H);
+  W.low[j] = 0;
+  W.lowc[j] = -1;
+}
+
+constexpr int kD1StepLimit = 1 << 22;
+
+// Phase A: reduce each column by the gradient-paired rows until its low is a
+// critical edge; claim that edge (smallest column wins).
+__global__ void k_d1_expand(D1Ctx c, D1Work W, int ncols, int32_t* owner, uint32_t* status) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  if (W.lowc[j] >= 0) {
+    atomicMin(&owner[W.lowc[j]], j);
+    return;
+  }
+  Heap H = heap_of(W, j);
+  unsigned long long low = W.low[j];
+  for (int step = 0; step < kD1StepLimit; ++step) {
+    if (low == 0) low = heap_low(H);
+    if (low == 0) {
+      atomicOr(status, kErrEmptyColumn);
+      break;
+    }
+    uint32_t hi = c.order[(uint32_t)(low >> 32)];
+    uint32_t lo = c.order[(uint32_t)(low & 0xFFFFFFFFull)];
+    int k = nbr_of_pair(c.d, hi, lo);
+    Rec r = ld_rec(c.rec, hi);
+    if ((rec_crit_edges(r) >> k) & 1u) {
+      int ci = crit_edge_index(c, hi, r, k);
+      W.lowc[j] = ci;
+      atomicMin(&owner[ci], j);
+      break;
+    }
+    // gradient edge hi*lo paired with a triangle of hi's lower star: add that
+    // triangle's reduced column (hi*lo cancels the low)
+    Star s;
+    star_load(s, c.d, hi, c.rank);
+    int8_t pa[14], pb[14];
+    int y = -1;
+    int n = star_chain(s, k, pa, pb, y);
+    if (n < 0) {
+      atomicOr(status, kErrInconsistent);
+      break;
+    }
+    push_if_positive(c, W, H, hi, (uint32_t)((int32_t)hi + c.nd.d[y]), status);
+    for (int t = 0; t < n; ++t)
+      push_if_positive(c, W, H, (uint32_t)((int32_t)hi + c.nd.d[pa[t]]), (uint32_t)((int32_t)hi + c.nd.d[pb[t]]),
+                       status);
+    low = 0;
+    if (step == kD1StepLimit - 1) atomicOr(status, kErrRounds);
+  }
+  W.low[j] = low;
+  heap_store(W, j, H);
+}
+
+// Phase B: a column whose low is owned by an earlier column adds that column.
+__global__ void k_d1_add(D1Work W, int ncols, const int32_t* __restrict__ owner, uint32_t* status) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  int ci = W.lowc[j];
+  if (ci < 0) return;
+  int o = owner[ci];
+  if (o == j) return;
+  Heap H = heap_of(W, j);
+  uint32_t osz = W.hsize[o];
+  const unsigned long long* oh = W.pool + W.hoff[o];
+  for (uint32_t t = 0; t < osz; ++t)
+    if (!heap_push(W, H, oh[t], status)) break;
+  heap_store(W, j, H);
+  W.low[j] = 0;
+  W.lowc[j] = -1;
+  W.flags[0] = 1;
+}
+
+__global__ void k_d1_finish(D1Work W, int ncols, int32_t* __restrict__ d1_edge) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < ncols) d1_edge[W.cols[j]] = W.lowc[j];
+}
+
+void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
+               const uint32_t* order, const Rec* rec, const uint32_t* c1base, D1Work& W, PairOut& P,
+               uint32_t* status, int32_t* h_flags, cudaStream_t st) {
+  if (n2 == 0) return;
+  // candidate columns, in increasing triangle order
+  uint32_t* flag = reinterpret_cast<uint32_t*>(W.lowc);  // scratch (n2 entries available)
+  uint32_t* pos = reinterpret_cast<uint32_t*>(W.hsize);
+  uint32_t* sums = reinterpret_cast<uint32_t*>(W.hcap);
+  k_d1_select<<<(n2 + 255) / 256, 256, 0, st>>>(n2, P.d2_max, flag);
+  exclusive_scan_u32(flag, pos, n2, sums, st);
+  k_d1_gather<<<(n2 + 255) / 256, 256, 0, st>>>(n2, flag, pos, W.cols, P.d1_edge);
+  // number of columns = pos[n2-1] + flag[n2-1]
+  uint32_t tail[2];
+  cudaMemcpyAsync(&tail[0], pos + n2 - 1, 4, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&tail[1], flag + n2 - 1, 4, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  int ncols = (int)(tail[0] + tail[1]);
+  h_flags[1] = ncols;
+  if (ncols == 0) return;
+  D1Ctx c;
+  c.d = d;
+  c.nd = nd;
+  c.rank = rank;
+  c.order = order;
+  c.rec = rec;
+  c.c1base = c1base;
+  c.L = L;
+  c.d0_killed = P.d0_killed;
+  cudaMemsetAsync(W.pool_head, 0, 4, st);
+  int nb = (max(ncols, n1) + 255) / 256;
+  k_d1_init<<<nb, 256, 0, st>>>(c, W, ncols, W.owner, n1, status);
+  for (int round = 0; round < 1 << 20; ++round) {
+    cudaMemsetAsync(W.flags, 0, 4, st);
+    k_d1_expand<<<(ncols + 127) / 128, 128, 0, st>>>(c, W, ncols, W.owner, status);
+    k_d1_add<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, W.owner, status);
+    cudaMemcpyAsync(h_flags, W.flags, 4, cudaMemcpyDeviceToHost, st);
+    uint32_t hs = 0;
+    cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (hs & (kErrPool | kErrEmptyColumn | kErrInconsistent | kErrRounds)) break;
+    if (h_flags[0] == 0) break;
+  }
+  k_d1_finish<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, P.d1_edge);
+}
+
+}  // namespace tsf

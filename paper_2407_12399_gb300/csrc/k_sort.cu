@@ -1,0 +1,225 @@
+// k_sort.cu -- global vertex order (Section 2.1 / Section 2.2): a stable LSD
+// radix sort of (value key, vertex id), 4 passes of 8 bits, then the rank
+// scatter.  Stability of every pass keeps equal values in id order, which is
+// the id tie-break of the vertex order.
+#include "tsf_kernels.cuh"
+
+namespace tsf {
+
+constexpr int kRT = 256;            // threads
+constexpr int kRW = kRT / 32;       // warps
+constexpr int kRI = 16;             // items per thread
+constexpr int kRTile = kRT * kRI;   // 4096 items per tile
+constexpr int kRWarpItems = kRTile / kRW;  // 512 items per warp, contiguous
+
+__device__ __forceinline__ uint32_t rs_key(bool first, const float* __restrict__ f, const uint32_t* __restrict__ keys,
+                                           int64_t i) {
+  return first ? value_key(__ldg(f + i)) : __ldg(keys + i);
+}
+
+__global__ void k_rs_hist(int64_t n, int shift, bool first, const float* __restrict__ f,
+                          const uint32_t* __restrict__ keys, uint32_t* __restrict__ counts, int ntiles,
+                          uint32_t* status) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kRTile;
+  bool bad = false;
+#pragma unroll 4
+  for (int k = 0; k < kRI; ++k) {
+    int64_t i = base + (int64_t)k * kRT + threadIdx.x;
+    if (i < n) {
+      if (first) bad |= !isfinite(__ldg(f + i));
+      uint32_t key = rs_key(first, f, keys, i);
+      atomicAdd(&h[(key >> shift) & 255u], 1u);
+    }
+  }
+  if (bad) atomicOr(status, kErrNaN);
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(int64_t n, int shift, bool first, bool last, const float* __restrict__ f,
+                             const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                             const uint32_t* __restrict__ offsets, int ntiles) {
+  __shared__ uint32_t whist[kRW][256];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRW * 256; i += kRT) (&whist[0][0])[i] = 0;
+  __syncthreads();
+  int64_t wbase_item = (int64_t)blockIdx.x * kRTile + (int64_t)w * kRWarpItems;
+  // 1) per-warp digit histogram of the warp's contiguous 512 items
+  for (int c = 0; c < kRWarpItems / 32; ++c) {
+    int64_t i = wbase_item + c * 32 + lane;
+    uint32_t dg = 256;
+    if (i < n) dg = (rs_key(first, f, keys_in, i) >> shift) & 255u;
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+    int leader = __ffs(peers) - 1;
+    if (lane == leader && dg < 256) whist[w][dg] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // 2) warp bases: global tile offset + counts of earlier warps
+  {
+    uint32_t d = threadIdx.x;
+    uint32_t run = offsets[(int64_t)d * ntiles + blockIdx.x];
+    for (int ww = 0; ww < kRW; ++ww) {
+      uint32_t c = whist[ww][d];
+      whist[ww][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  // 3) stable scatter, warp by warp, 32 items at a time
+  unsigned lt = (1u << lane) - 1u;
+  for (int c = 0; c < kRWarpItems / 32; ++c) {
+    int64_t i = wbase_item + c * 32 + lane;
+    uint32_t key = 0, dg = 256, val = 0;
+    if (i < n) {
+      key = rs_key(first, f, keys_in, i);
+      dg = (key >> shift) & 255u;
+      val = first ? (uint32_t)i : __ldg(vals_in + i);
+    }
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+    uint32_t pos = 0;
+    if (dg < 256) pos = whist[w][dg] + __popc(peers & lt);
+    __syncwarp();
+    if (dg < 256) {
+      if (!last) keys_out[pos] = key;
+      vals_out[pos] = val;
+      if (lane == __ffs(peers) - 1) whist[w][dg] += __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_rank_scatter(int64_t n, const uint32_t* __restrict__ order, uint32_t* __restrict__ rank) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rank[__ldg(order + i)] = (uint32_t)i;
+}
+
+// ---- exclusive scan of uint32 (block sums, one-block scan, apply) ---------
+constexpr int kST = 1024, kSI = 4, kSTile = kST * kSI;
+
+__device__ __forceinline__ uint32_t block_exscan_u32(uint32_t v, uint32_t& total) {
+  static_assert(kST == 1024, "one warp scans the 32 warp sums");
+  __shared__ uint32_t sw[kST / 32 + 1];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sw[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = sw[lane];
+    uint32_t si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xFFFFFFFFu, si, o);
+      if (lane >= o) si += t;
+    }
+    sw[lane] = si - s;
+    if (lane == 31) sw[32] = si;
+  }
+  __syncthreads();
+  uint32_t res = sw[wid] + inc - v;
+  total = sw[32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+  uint32_t acc = 0;
+  int64_t base = (int64_t)blockIdx.x * kSTile;
+  for (int k = 0; k < kSI; ++k) {
+    int64_t i = base + (int64_t)threadIdx.x * kSI + k;
+    if (i < n) acc += in[i];
+  }
+  uint32_t tot = 0;
+  block_exscan_u32(acc, tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(uint32_t* __restrict__ sums, int nb) {
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b = 0; b < nb; b += kST) {
+    int i = b + threadIdx.x;
+    uint32_t v = i < nb ? sums[i] : 0;
+    uint32_t tot = 0;
+    uint32_t ex = block_exscan_u32(v, tot);
+    uint32_t c = carry;
+    if (i < nb) sums[i] = c + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c + tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, int64_t n, const uint32_t* __restrict__ sums,
+                             uint32_t* __restrict__ out) {
+  int64_t base = (int64_t)blockIdx.x * kSTile;
+  uint32_t loc[kSI];
+  uint32_t acc = 0;
+  for (int k = 0; k < kSI; ++k) {
+    int64_t i = base + (int64_t)threadIdx.x * kSI + k;
+    loc[k] = i < n ? in[i] : 0;
+    acc += loc[k];
+  }
+  uint32_t tot = 0;
+  uint32_t ex = block_exscan_u32(acc, tot) + sums[blockIdx.x];
+  for (int k = 0; k < kSI; ++k) {
+    int64_t i = base + (int64_t)threadIdx.x * kSI + k;
+    if (i < n) out[i] = ex;
+    ex += loc[k];
+  }
+}
+
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t st) {
+  int nb = (int)((n + kSTile - 1) / kSTile);
+  if (nb == 0) return;
+  k_scan_sums<<<nb, kST, 0, st>>>(in, n, sums);
+  k_scan_top<<<1, kST, 0, st>>>(sums, nb);
+  k_scan_apply<<<nb, kST, 0, st>>>(in, n, sums, out);
+}
+
+int64_t sort_scratch_words(int64_t n) {
+  int64_t ntiles = (n + kRTile - 1) / kRTile;
+  int64_t counts = 256 * ntiles;
+  int64_t sums = (counts + kSTile - 1) / kSTile + 1;
+  return 4 * n + 2 * counts + sums + 64;
+}
+
+// Vertex order: order[r] = id of the r-th vertex, rank[id] = r.
+void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, uint32_t* scratch, uint32_t* status,
+                  cudaStream_t st) {
+  int ntiles = (int)((n + kRTile - 1) / kRTile);
+  int64_t ncounts = 256 * (int64_t)ntiles;
+  uint32_t* kA = scratch;
+  uint32_t* vA = kA + n;
+  uint32_t* kB = vA + n;
+  uint32_t* vB = kB + n;
+  uint32_t* counts = vB + n;
+  uint32_t* offs = counts + ncounts;
+  uint32_t* sums = offs + ncounts;
+  const uint32_t* kin = nullptr;
+  const uint32_t* vin = nullptr;
+  for (int pass = 0; pass < 4; ++pass) {
+    bool first = pass == 0, last = pass == 3;
+    int shift = 8 * pass;
+    uint32_t* kout = (pass & 1) ? kB : kA;
+    uint32_t* vout = last ? order : ((pass & 1) ? vB : vA);
+    k_rs_hist<<<ntiles, kRT, 0, st>>>(n, shift, first, f, kin, counts, ntiles, status);
+    exclusive_scan_u32(counts, offs, ncounts, sums, st);
+    k_rs_scatter<<<ntiles, kRT, 0, st>>>(n, shift, first, last, f, kin, vin, kout, vout, offs, ntiles);
+    kin = kout;
+    vin = vout;
+  }
+  k_rank_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, order, rank);
+}
+
+}  // namespace tsf

@@ -1,0 +1,107 @@
+// tsf_geo.cuh -- the Freudenthal triangulation of a regular grid, seen from
+// one vertex (paper Section 2.1: the implicit triangulation of the grid).
+//
+// Every vertex v has 14 neighbours v + o, where o (or -o) is a non-zero 0/1
+// vector.  Three points form a triangle, four a tetrahedron, exactly when they
+// are pairwise neighbours (the triangulation is a flag complex: pairwise
+// comparable corners of one cube form a chain).  The *link* of v is a
+// triangulated sphere with 14 vertices, 36 edges and 24 triangles; the
+// simplices containing v are v itself, 14 edges v*a, 36 triangles v*(a,b) and
+// 24 tetrahedra v*(a,b,c) for link vertices a, link edges (a,b) and link
+// triangles (a,b,c).  All tables below are computed at compile time from that
+// definition.
+#pragma once
+#include <cstdint>
+
+namespace tsf {
+
+struct Geo {
+  int8_t off[14][3];        // neighbour offsets; 0..6 = +mask(1..7), 7..13 = -mask(1..7)
+  int8_t edge[36][2];       // link edge -> neighbour indices (a < b)
+  int8_t edge_idx[14][14];  // neighbour pair -> link edge, -1 if not adjacent
+  int8_t tri[24][3];        // link triangle -> neighbour indices (a < b < c)
+  int8_t tri_edge[24][3];   // link triangle -> its three link edges
+  int8_t edge_tri[36][2];   // link edge -> the two link triangles containing it
+  uint16_t adj[14];         // link adjacency bitmask per neighbour
+  int8_t nbr_of[27];        // (dx+1) + 3 (dy+1) + 9 (dz+1) -> neighbour index, -1
+  int8_t tri_of3[14][14][14];  // neighbour triple -> link triangle, -1
+};
+
+constexpr bool geo_is_nbr(int dx, int dy, int dz) {
+  if (dx == 0 && dy == 0 && dz == 0) return false;
+  if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return false;
+  return (dx >= 0 && dy >= 0 && dz >= 0) || (dx <= 0 && dy <= 0 && dz <= 0);
+}
+
+constexpr Geo make_geo() {
+  Geo g{};
+  for (int m = 1; m < 8; ++m) {
+    g.off[m - 1][0] = (int8_t)(m & 1);
+    g.off[m - 1][1] = (int8_t)((m >> 1) & 1);
+    g.off[m - 1][2] = (int8_t)((m >> 2) & 1);
+    g.off[m + 6][0] = (int8_t)(-(m & 1));
+    g.off[m + 6][1] = (int8_t)(-((m >> 1) & 1));
+    g.off[m + 6][2] = (int8_t)(-((m >> 2) & 1));
+  }
+  for (int i = 0; i < 27; ++i) g.nbr_of[i] = -1;
+  for (int i = 0; i < 14; ++i) g.nbr_of[(g.off[i][0] + 1) + 3 * (g.off[i][1] + 1) + 9 * (g.off[i][2] + 1)] = (int8_t)i;
+  for (int i = 0; i < 14; ++i) {
+    g.adj[i] = 0;
+    for (int j = 0; j < 14; ++j) g.edge_idx[i][j] = -1;
+  }
+  int ne = 0;
+  for (int i = 0; i < 14; ++i)
+    for (int j = i + 1; j < 14; ++j)
+      if (geo_is_nbr(g.off[j][0] - g.off[i][0], g.off[j][1] - g.off[i][1], g.off[j][2] - g.off[i][2])) {
+        g.edge[ne][0] = (int8_t)i;
+        g.edge[ne][1] = (int8_t)j;
+        g.edge_idx[i][j] = g.edge_idx[j][i] = (int8_t)ne;
+        g.adj[i] = (uint16_t)(g.adj[i] | (1u << j));
+        g.adj[j] = (uint16_t)(g.adj[j] | (1u << i));
+        ++ne;
+      }
+  for (int e = 0; e < 36; ++e) g.edge_tri[e][0] = g.edge_tri[e][1] = -1;
+  for (int i = 0; i < 14; ++i)
+    for (int j = 0; j < 14; ++j)
+      for (int k = 0; k < 14; ++k) g.tri_of3[i][j][k] = -1;
+  int nt = 0;
+  for (int i = 0; i < 14; ++i)
+    for (int j = i + 1; j < 14; ++j)
+      for (int k = j + 1; k < 14; ++k)
+        if (g.edge_idx[i][j] >= 0 && g.edge_idx[i][k] >= 0 && g.edge_idx[j][k] >= 0) {
+          g.tri[nt][0] = (int8_t)i;
+          g.tri[nt][1] = (int8_t)j;
+          g.tri[nt][2] = (int8_t)k;
+          int es[3] = {g.edge_idx[i][j], g.edge_idx[i][k], g.edge_idx[j][k]};
+          for (int s = 0; s < 3; ++s) {
+            g.tri_edge[nt][s] = (int8_t)es[s];
+            if (g.edge_tri[es[s]][0] < 0) g.edge_tri[es[s]][0] = (int8_t)nt;
+            else g.edge_tri[es[s]][1] = (int8_t)nt;
+          }
+          int p[3] = {i, j, k};
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              for (int c = 0; c < 3; ++c)
+                if (a != b && a != c && b != c) g.tri_of3[p[a]][p[b]][p[c]] = (int8_t)nt;
+          ++nt;
+        }
+  return g;
+}
+
+constexpr Geo kGeo = make_geo();
+
+constexpr int geo_count_edges() {
+  int n = 0;
+  for (int i = 0; i < 14; ++i)
+    for (int j = i + 1; j < 14; ++j) n += kGeo.edge_idx[i][j] >= 0;
+  return n;
+}
+constexpr bool geo_edges_have_two_triangles() {
+  for (int e = 0; e < 36; ++e)
+    if (kGeo.edge_tri[e][0] < 0 || kGeo.edge_tri[e][1] < 0) return false;
+  return true;
+}
+static_assert(geo_count_edges() == 36, "the link of a Freudenthal vertex has 36 edges");
+static_assert(geo_edges_have_two_triangles(), "the link is a closed surface: 24 triangles, 2 per edge");
+
+}  // namespace tsf

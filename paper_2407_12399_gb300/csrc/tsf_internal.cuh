@@ -1,0 +1,128 @@
+// tsf_internal.cuh -- device-side building blocks shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tsf_geo.cuh"
+
+namespace tsf {
+
+// Device status word bits (a kernel that hits a bound sets one and returns).
+enum : uint32_t {
+  kErrTrace = 1u << 0,     // an integral-line trace exceeded its step bound
+  kErrRounds = 1u << 1,    // a union-find / reduction round loop exceeded its bound
+  kErrPool = 1u << 2,      // the D1 column pool is exhausted (host retries larger)
+  kErrInconsistent = 1u << 3,  // local pairing contradiction (must never happen)
+  kErrEmptyColumn = 1u << 4,   // a saddle-saddle column reduced to zero
+  kErrSpin = 1u << 5,      // a bounded spin-wait gave up
+  kErrCapacity = 1u << 6,  // an output list is larger than its buffer
+};
+
+static __constant__ Geo c_geo = make_geo();
+
+// ---------------------------------------------------------------------------
+// Per-vertex gradient record (32 bytes), bit layout:
+//   [0,4)     vnext: neighbour index of the vertex's paired edge, 15 = minimum
+//   [4,18)    critical lower-star edges v*a, by neighbour index a
+//   [18,54)   critical lower-star triangles v*(a,b), by link edge index
+//   [54]      the lower star holds a critical tetrahedron (a maximum)
+//   [56,224)  24 x 7-bit codes, one per link triangle tau (tetrahedron v*tau):
+//               0..23    tau is non-critical; the integral line continues in
+//                        the same lower star, at link triangle `code`
+//               24..95   it continues at link triangle (code-24)/3 of v's link,
+//                        whose vertex number (code-24)%3 is higher than v: the
+//                        next tetrahedron belongs to that vertex's lower star
+//               124      it continues to the outside of the domain
+//               125      tau is critical (a maximum)
+//               127      tau is not in the lower star of v
+// ---------------------------------------------------------------------------
+struct __align__(16) Rec {
+  uint32_t w[8];
+};
+
+enum : int { kCodeOut = 124, kCodeMax = 125, kCodeNone = 127, kVnextMin = 15 };
+
+__host__ __device__ inline uint32_t rec_bits(const Rec& r, int off, int n) {
+  int wi = off >> 5, bi = off & 31;
+  uint64_t lo = r.w[wi];
+  uint64_t hi = (wi + 1 < 8) ? r.w[wi + 1] : 0;
+  uint64_t both = lo | (hi << 32);
+  return (uint32_t)((both >> bi) & ((1ull << n) - 1));
+}
+__host__ __device__ inline void rec_set(Rec& r, int off, int n, uint32_t val) {
+  for (int i = 0; i < n; ++i) {
+    int b = off + i;
+    uint32_t bit = (val >> i) & 1u;
+    r.w[b >> 5] = (r.w[b >> 5] & ~(1u << (b & 31))) | (bit << (b & 31));
+  }
+}
+__host__ __device__ inline int rec_vnext(const Rec& r) { return (int)(r.w[0] & 15u); }
+__host__ __device__ inline uint32_t rec_crit_edges(const Rec& r) { return (r.w[0] >> 4) & 0x3FFFu; }
+__host__ __device__ inline uint64_t rec_crit_tris(const Rec& r) {
+  uint64_t lo = r.w[0] >> 18;                 // 14 bits
+  uint64_t hi = (uint64_t)(r.w[1] & 0x3FFFFFu);  // 22 bits
+  return lo | (hi << 14);
+}
+__host__ __device__ inline bool rec_has_max(const Rec& r) { return (r.w[1] >> 22) & 1u; }
+__host__ __device__ inline int rec_tet_code(const Rec& r, int tau) { return (int)rec_bits(r, 56 + 7 * tau, 7); }
+
+// Grid helpers -------------------------------------------------------------
+struct Dims {
+  int lx, ly, lz;
+  int64_t nv;
+};
+
+__device__ __forceinline__ void vxyz(const Dims& d, uint32_t v, int& x, int& y, int& z) {
+  x = (int)(v % (uint32_t)d.lx);
+  uint32_t t = v / (uint32_t)d.lx;
+  y = (int)(t % (uint32_t)d.ly);
+  z = (int)(t / (uint32_t)d.ly);
+}
+__device__ __forceinline__ bool nbr_xyz(const Dims& d, int x, int y, int z, int i, int& nx, int& ny, int& nz) {
+  nx = x + c_geo.off[i][0];
+  ny = y + c_geo.off[i][1];
+  nz = z + c_geo.off[i][2];
+  return nx >= 0 && ny >= 0 && nz >= 0 && nx < d.lx && ny < d.ly && nz < d.lz;
+}
+__device__ __forceinline__ uint32_t vid(const Dims& d, int x, int y, int z) {
+  return (uint32_t)x + (uint32_t)d.lx * ((uint32_t)y + (uint32_t)d.ly * (uint32_t)z);
+}
+__device__ __forceinline__ int nbr_index(int dx, int dy, int dz) {
+  return c_geo.nbr_of[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+}
+
+// Monotone float -> uint32 key for the vertex order (Section 2.1: ties are
+// broken by vertex id; -0.0 and +0.0 are the same value).
+__device__ __forceinline__ uint32_t value_key(float f) {
+  uint32_t u = __float_as_uint(f);
+  if (u == 0x80000000u) u = 0u;
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Canonical cell id: (dim << 60) | (base << 6) | type, base = the lowest
+// corner of the chain, type = axis mask (edges) or 8*A + B (triangles,
+// tetrahedra).  `xs` are vertex coordinates, any order.
+__device__ inline uint64_t cell_id_of(const Dims& d, int n, int (*xs)[3]) {
+  // chain order = increasing coordinate sum (the simplex is a chain)
+  int idx[4] = {0, 1, 2, 3};
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0; --j) {
+      int a = idx[j], b = idx[j - 1];
+      if (xs[a][0] + xs[a][1] + xs[a][2] < xs[b][0] + xs[b][1] + xs[b][2]) {
+        idx[j] = b;
+        idx[j - 1] = a;
+      }
+    }
+  auto mask = [&](int p, int q) {
+    return (xs[q][0] - xs[p][0]) | ((xs[q][1] - xs[p][1]) << 1) | ((xs[q][2] - xs[p][2]) << 2);
+  };
+  int base_i = idx[0];
+  uint64_t base = vid(d, xs[base_i][0], xs[base_i][1], xs[base_i][2]);
+  int type = 0;
+  if (n == 2) type = mask(idx[0], idx[1]);
+  if (n >= 3) type = mask(idx[0], idx[1]) * 8 + mask(idx[1], idx[2]);
+  return ((uint64_t)(n - 1) << 60) | (base << 6) | (uint64_t)type;
+}
+
+}  // namespace tsf

@@ -1,0 +1,89 @@
+// tsf_kernels.cuh -- buffers shared between kernel translation units, and the
+// host-side launch functions each unit exports to the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tsf_internal.cuh"
+
+namespace tsf {
+
+enum : uint32_t { kErrNaN = 1u << 7 };
+
+// Critical cells, each list in lexicographic order (Section 2.2).
+struct CritLists {
+  uint32_t* c0;       // minima: vertex id
+  uint64_t* c1_key;   // critical edges: (rank_hi << 32) | rank_lo
+  uint32_t* c1_vn;    // critical edges: (v << 4) | neighbour index of the lower end
+  uint32_t* c2_ve;    // critical triangles: (v << 6) | link edge index
+  uint32_t* c3;       // maxima: (v << 5) | link triangle index
+  int cap0, cap1, cap2, cap3;
+};
+
+// Neighbour offsets as vertex-id deltas for one grid.
+struct NbrDelta {
+  int32_t d[14];
+};
+
+// Persistence pairs of the critical cells.
+struct PairOut {
+  int32_t* d0_min;     // per critical edge: index of the minimum it kills, -1
+  int32_t* d2_max;     // per critical triangle: index of the maximum it kills, -1
+  int32_t* d1_edge;    // per critical triangle: critical edge paired (D1), -1
+  uint8_t* d0_killed;  // per critical edge: 1 if it is a D0 death (negative)
+};
+
+// ---- k_sort.cu -----------------------------------------------------------
+int64_t sort_scratch_words(int64_t n);
+void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, uint32_t* scratch, uint32_t* status,
+                  cudaStream_t st);
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t st);
+
+// ---- k_gradient.cu -------------------------------------------------------
+void launch_gradient(const Dims& d, const uint32_t* rank, const uint8_t* dirty, Rec* rec, uint8_t* vnext8,
+                     uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st);
+int crit_tiles(int64_t nv);
+void launch_crit_count(const Dims& d, const uint32_t* order, const Rec* rec, int4* tile_counts, int4* totals,
+                       cudaStream_t st);
+void launch_crit_write(const Dims& d, const uint32_t* order, const uint32_t* rank, const Rec* rec,
+                       const int4* tile_off, const CritLists& L, uint32_t* cidx, uint32_t* c1base, uint32_t* c2base,
+                       uint32_t* status, cudaStream_t st);
+void launch_zero_pairs(const Dims& d, const uint32_t* rank, unsigned long long* out, int64_t cap,
+                       unsigned long long* count, uint32_t* status, cudaStream_t st);
+
+// ---- k_pairs.cu ----------------------------------------------------------
+struct PairScratch {
+  int32_t* ends;      // 2 per item: component endpoints
+  int32_t* parent;    // union-find parents over nodes
+  int32_t* reserve;   // per node reservation
+  int32_t* listA;     // active item lists
+  int32_t* listB;
+  int32_t* roots;     // 2 per item
+  int32_t* counter;   // device counters (>= 4 ints)
+};
+void launch_d0(const Dims& d, const NbrDelta& nd, const CritLists& L, int n0, int n1, const uint8_t* vnext8,
+               const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status, cudaStream_t st);
+void launch_d2(const Dims& d, const NbrDelta& nd, const CritLists& L, int n2, int n3, const uint32_t* rank,
+               const Rec* rec, const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status,
+               cudaStream_t st);
+
+struct D1Work {
+  int32_t* cols;          // candidate triangle index per column
+  unsigned long long* low;  // current low per column (0 = to be recomputed)
+  uint32_t* hoff;         // heap offset in the pool
+  uint32_t* hcap;         // heap capacity
+  uint32_t* hsize;        // heap size
+  int32_t* lowc;          // critical edge index of the low
+  int32_t* owner;         // per critical edge: smallest column holding it as low
+  unsigned long long* pool;
+  uint32_t pool_cap;
+  uint32_t* pool_head;
+  int32_t* flags;         // [0] changed, [1] number of candidate columns
+};
+// returns 0 on success, otherwise a status bit (kErrPool: retry with a larger pool)
+void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
+               const uint32_t* order, const Rec* rec, const uint32_t* c1base, D1Work& W, PairOut& P,
+               uint32_t* status, int32_t* h_flags, cudaStream_t st);
+
+}  // namespace tsf

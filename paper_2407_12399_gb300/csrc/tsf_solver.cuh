@@ -1,0 +1,87 @@
+// tsf_solver.cuh -- diagram points, targets and the solver's scratch buffers.
+#pragma once
+#include "tsf_kernels.cuh"
+
+namespace tsf {
+
+// A point of the persistence diagram (Section 2.2), with its assignment.
+struct Pt {
+  float b, d;        // f(v_b), f(v_d)
+  uint32_t vb, vd;   // birth / death vertices
+  uint64_t cb, cd;   // birth / death cells (cd = ~0 for the essential class)
+  int32_t dim, ess;
+  int32_t tgt;       // index into the target list, -1 = diagonal
+  int32_t still;     // 1 if (dim, v_b, v_d) was in the previous diagram
+};
+
+// A point of the target diagram (Section 3).
+struct Tg {
+  float b, d;
+  uint32_t vb, vd;
+  uint64_t src;      // birth cell of the D(f0) pair it came from, or input index
+  int32_t dim, ess;
+};
+
+struct Cand {
+  double w;  // c(p,t) - diag(p)
+  int32_t p; // index in the group's point list
+  int32_t t; // index in the group's target list
+};
+
+struct Contrib {
+  uint32_t v;
+  uint32_t key;  // monotone key of c (summation order)
+  float c;
+  uint32_t pad;
+};
+
+struct HungWork {
+  double* u;
+  double* v;
+  double* minv;
+  double* row;
+  int32_t* pm;
+  int32_t* way;
+  uint8_t* used;
+};
+
+struct SolverBufs {
+  Pt* tmp_pts;
+  int32_t *idxA, *idxB, *idxC, *idxD;
+  int* count;
+  uint32_t *u32a, *u32b, *u32c;
+  uint8_t* taken;
+  int32_t *plist, *tlist;
+  Cand* cands;
+  Cand* kept;
+  uint32_t* nkept;
+  uint32_t* is_col;
+  uint32_t* colpos;
+  int32_t* col_point;
+  int32_t* col_to_row;
+  double* diag_t;
+  HungWork H;
+  double* terms;
+  double* dsum;
+  unsigned long long* counters;
+  Contrib* contrib;
+  int cap_k, cap_cand, cap_cols;
+  int64_t cap_kept;
+};
+
+struct AssignStats {
+  int k[4];
+};
+
+int build_diagram(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, int n3, const PairOut& P,
+                  const uint32_t* order, const float* f, SolverBufs& B, Pt* out, int cap, cudaStream_t st);
+int make_targets(int np, const Pt* pts, float theta, SolverBufs& B, Tg* T, cudaStream_t st);
+void targets_as_points(int nt, const Tg* T, Pt* R, cudaStream_t st);
+int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBufs& B, uint32_t* status,
+           AssignStats* as, cudaStream_t st);
+void loss_and_counts(int np, const Pt* pts, int nt, const Tg* T, float cancel_eps, SolverBufs& B, double* h_loss,
+                     unsigned long long* h_counts, cudaStream_t st);
+int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float alpha_d, float* f, uint8_t* dirty,
+                      SolverBufs& B, cudaStream_t st);
+
+}  // namespace tsf

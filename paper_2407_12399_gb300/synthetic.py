@@ -100,17 +100,39 @@ def gradient_noise(shape, rng, octaves=4, base_freq=4):
     return out
 
 
-def _segment_min_dist(points, a, b, chunk=8192):
-    """min over segments [a_k, b_k] of the Euclidean distance, per point."""
+def _seg_dist(p, a, b):
     ab = b - a
     ab2 = np.maximum((ab * ab).sum(-1), 1e-30)
+    ap = p[:, None, :] - a[None]
+    t = np.clip((ap * ab[None]).sum(-1) / ab2[None], 0.0, 1.0)
+    d = ap - t[..., None] * ab[None]
+    return np.sqrt((d * d).sum(-1))
+
+
+def _segment_min_dist(points, a, b, shape, block=8):
+    """min over segments [a_k, b_k] of the Euclidean distance, per grid point.
+
+    Exact: for each block of voxels, a segment is skipped only when a lower
+    bound of its distance to the block exceeds an upper bound of another
+    segment's distance to every voxel of the block."""
+    lz, ly, lx = shape
     out = np.empty(points.shape[0], dtype=np.float64)
-    for s in range(0, points.shape[0], chunk):
-        p = points[s:s + chunk, None, :]
-        ap = p - a[None]
-        t = np.clip((ap * ab[None]).sum(-1) / ab2[None], 0.0, 1.0)
-        d = ap - t[..., None] * ab[None]
-        out[s:s + chunk] = np.sqrt((d * d).sum(-1).min(-1))
+    lo_s = np.minimum(a, b)
+    hi_s = np.maximum(a, b)
+    idx = np.arange(points.shape[0]).reshape(shape)
+    for z0 in range(0, lz, block):
+        for y0 in range(0, ly, block):
+            for x0 in range(0, lx, block):
+                ids = idx[z0:z0 + block, y0:y0 + block, x0:x0 + block].ravel()
+                p = points[ids]
+                bmin, bmax = p.min(0), p.max(0)
+                centre = 0.5 * (bmin + bmax)
+                half = 0.5 * float(np.linalg.norm(bmax - bmin))
+                gap = np.maximum(0.0, np.maximum(lo_s - bmax[None], bmin[None] - hi_s))
+                lb = np.sqrt((gap * gap).sum(-1))
+                ub = _seg_dist(centre[None], a, b)[0] + half
+                keep = lb <= ub.min()
+                out[ids] = _seg_dist(p, a[keep], b[keep]).min(-1)
     return out
 
 
@@ -162,7 +184,7 @@ def filament_field(shape=(128, 128, 128), seed=1, n_loops=64, n_seg=8,
     b = np.concatenate(b_list)
     z, y, x = _coords(shape)
     pts = np.stack(np.broadcast_arrays(x, y, z), axis=-1).reshape(-1, 3)
-    dist = _segment_min_dist(pts, a, b).reshape(shape)
+    dist = _segment_min_dist(pts, a, b, shape).reshape(shape)
     f = -(dist - tube_radius)
     k = np.arange(-3, 4)
     wk = np.exp(-0.5 * (k / blur_sigma) ** 2)

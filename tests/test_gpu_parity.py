@@ -1,0 +1,186 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_12399_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2407_12399_gb300 import build as B
+    B.build()
+    oracle.build()
+
+
+def gpu_field(f):
+    import torch
+
+    import paper_2407_12399_gb300 as tsf
+    return tsf.Field(torch.from_numpy(np.ascontiguousarray(f, np.float32)).cuda())
+
+
+def bits(x):
+    return np.asarray(x, np.float32).view(np.uint32)
+
+
+def gpu_rows(d):
+    return [(int(r["dim"]), int(r["essential"]), int(r["v_birth"]), int(r["v_death"]), int(r["cell_birth"]),
+             int(r["cell_death"]), int(bits(r["birth"])), int(bits(r["death"]))) for r in d]
+
+
+def oracle_rows(f, P):
+    flat = np.asarray(f, np.float32).ravel()
+    rows = []
+    for i in range(len(P["vb"])):
+        vb, vd = int(P["vb"][i]), int(P["vd"][i])
+        rows.append((int(P["dim"][i]), int(P["essential"][i]), vb, vd, int(P["cb"][i]), int(P["cd"][i]),
+                     int(bits(flat[vb])), int(bits(flat[vd]))))
+
+    def key(r):  # diagram order: birth, death, v_b, v_d, birth cell
+        return (float(np.uint32(r[6]).view(np.float32)), float(np.uint32(r[7]).view(np.float32)), r[2], r[3], r[4])
+    return sorted(rows, key=key)
+
+
+SMALL = [((2, 2, 2), "uniform", 0), ((3, 3, 3), "ties", 1), ((4, 5, 6), "uniform", 2), ((5, 4, 3), "signed_zero", 3),
+         ((6, 7, 5), "normal", 4), ((9, 8, 7), "ties", 5), ((16, 16, 16), "uniform", 6), ((3, 17, 9), "uniform", 7),
+         ((12, 11, 10), "normal", 8)]
+
+
+def _field(case):
+    shape, kind, seed = case
+    return S.random_field(shape, seed=seed, kind=kind)
+
+
+NAMED = {
+    "plain_32": lambda: S.plain_32(),
+    "ring_21": lambda: S.ring_distance((21, 21, 21), (0.5, 0.5, 0.5), 0.3),
+    "peak_13": lambda: S.gaussian_bumps((11, 12, 13), [(0.52, 0.47, 0.5)], [0.18], [1.0]),
+    "filament_40": lambda: S.filament_field((40, 40, 40), seed=1, n_loops=12),
+    "linear": lambda: S.linear_field((8, 7, 6)),
+    "constant": lambda: np.zeros((6, 5, 4), np.float32),
+}
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"{c[0]}-{c[1]}")
+def test_zero_persistence_pairs_match(case):
+    """The lower-star gradient equals the oracle's zero-persistence pairs."""
+    f = _field(case)
+    got = gpu_field(f).zero_pairs()
+    Z = oracle.diagram(f, with_zero=True)["zero"]
+    assert set(map(tuple, got.tolist())) == set(zip(Z["cb"].tolist(), Z["cd"].tolist()))
+    assert len(got) == len(Z["cb"])
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"{c[0]}-{c[1]}")
+def test_diagram_matches_exactly(case):
+    f = _field(case)
+    got = gpu_rows(gpu_field(f).diagram())
+    assert got == oracle_rows(f, oracle.diagram(f)["pairs"])
+
+
+@pytest.mark.parametrize("name", sorted(NAMED))
+def test_named_field_diagrams_match_exactly(name):
+    f = NAMED[name]()
+    fld = gpu_field(f)
+    got = gpu_rows(fld.diagram())
+    assert got == oracle_rows(f, oracle.diagram(f)["pairs"])
+
+
+def _points_rows(P, keyset=("dim", "essential", "vb", "vd", "cb", "cd")):
+    return list(zip(*(P[k].tolist() for k in keyset)))
+
+
+@pytest.mark.parametrize("fast", [1, 0])
+@pytest.mark.parametrize("name,tau,iters", [("plain_32", 0.1, 6), ("filament_40", 0.05, 4)])
+def test_solver_trajectory_is_bit_exact(name, tau, iters, fast):
+    f0 = NAMED[name]()
+    fld = gpu_field(f0)
+    fld.set_threshold(tau)
+    ref = oracle.Solver(f0, tau=tau)
+    T = fld.targets()
+    RT = ref.targets()
+    assert list(zip(T["v_birth"].tolist(), T["v_death"].tolist(), T["dim"].tolist())) == \
+        list(zip(RT["vb"].tolist(), RT["vd"].tolist(), RT["dim"].tolist()))
+    for j in range(iters):
+        tgt, still = fld.assignment()
+        P = ref.points()
+        assert tgt.tolist() == P["tgt"].tolist(), f"assignment differs at j={j}"
+        assert still.tolist() == P["still"].tolist()
+        st = fld.step(fast_gradient_update=fast, stop_s=0.0)
+        ref.iterate(stop_s=0.0)
+        g, r = fld.values(), ref.field()
+        assert np.array_equal(bits(g), bits(r)), f"field differs after step {j + 1}"
+        d = fld.diagram()
+        P = ref.points()
+        assert [(x[0], x[1], x[2], x[3], x[4], x[5]) for x in gpu_rows(d)] == _points_rows(P)
+        rs = ref.stats()
+        assert st["loss"] == pytest.approx(rs["loss"], rel=1e-12, abs=1e-300)
+        assert st["n_updated_vertices"] == rs["updated"]
+        assert st["n_still"] == rs["still"]
+
+
+def test_fast_gradient_update_equals_full_recompute():
+    f0 = S.plain_32()
+    a, b = gpu_field(f0), gpu_field(f0)
+    a.set_threshold(0.1)
+    b.set_threshold(0.1)
+    for _ in range(4):
+        sa = a.step(fast_gradient_update=1, stop_s=0.0)
+        sb = b.step(fast_gradient_update=0, stop_s=0.0)
+        assert np.array_equal(bits(a.values()), bits(b.values()))
+        assert gpu_rows(a.diagram()) == gpu_rows(b.diagram())
+        assert sa["n_gradient_vertices"] < sb["n_gradient_vertices"]
+
+
+def test_explicit_targets_match_oracle():
+    f0 = S.gaussian_mixture((14, 13, 12), n_bumps=5, seed=9)
+    d = oracle.diagram(f0)["pairs"]
+    flat = f0.ravel()
+    pers = flat[d["vd"]] - flat[d["vb"]]
+    keep = np.argsort(-pers)[:4]
+    import paper_2407_12399_gb300 as tsf
+    tg = np.zeros(len(keep), tsf.PAIR_DTYPE)
+    tg["dim"], tg["essential"] = d["dim"][keep], d["essential"][keep]
+    tg["v_birth"], tg["v_death"] = d["vb"][keep], d["vd"][keep]
+    tg["birth"], tg["death"] = flat[d["vb"][keep]], flat[d["vd"][keep]] - np.float32(0.01)
+    fld = gpu_field(f0)
+    fld.set_targets(tg)
+    ref = oracle.Solver(f0, targets={"dim": tg["dim"], "essential": tg["essential"], "vb": tg["v_birth"],
+                                     "vd": tg["v_death"], "birth": tg["birth"], "death": tg["death"]})
+    for j in range(3):
+        assert fld.assignment()[0].tolist() == ref.points()["tgt"].tolist()
+        fld.step(stop_s=0.0)
+        ref.iterate(stop_s=0.0)
+        assert np.array_equal(bits(fld.values()), bits(ref.field()))
+
+
+def test_nan_and_bad_arguments_are_rejected():
+    import paper_2407_12399_gb300 as tsf
+    f = S.random_field((5, 5, 5), seed=0)
+    f[2, 2, 2] = np.nan
+    fld = gpu_field(f)
+    with pytest.raises(tsf.TsfError) as e:
+        fld.diagram()
+    assert e.value.code == tsf.TSF_ENAN
+    fld2 = gpu_field(S.random_field((5, 5, 5), seed=0))
+    with pytest.raises(tsf.TsfError) as e:
+        fld2.step()
+    assert e.value.code == tsf.TSF_ENOTARGET
+    with pytest.raises(tsf.TsfError) as e:
+        gpu_field(np.zeros((1, 4, 4), np.float32))
+    assert e.value.code == tsf.TSF_EINVAL
+
+
+def test_simplify_reaches_the_loss_rule():
+    f0 = S.plain_32()
+    fld = gpu_field(f0)
+    fld.set_threshold(0.1)
+    g, st = fld.simplify(stop_s=0.01)
+    assert st["done"] == 1 and st["loss"] <= 0.01 * st["loss0"]
+    ref = oracle.Solver(f0, tau=0.1)
+    ref.run(stop_s=0.01)
+    assert st["iters"] == ref.stats()["iter"]
+    assert np.array_equal(bits(g), bits(ref.field()))
