@@ -1,0 +1,289 @@
+"""Benchmark: solver iterations per second on the 128^3 filament field.
+
+One step = one solver iteration (Algorithm 1): gradient step, persistence
+diagram of the new field (vertex order, lower-star gradient, critical cells,
+D0/D2/D1 pairs), still pairs and exact reduced assignment, loss.  Inputs are
+resident in HBM; L2 is flushed (a 256 MiB write) before every timed step and
+the step is timed with CUDA events on the solver's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun): the
+path has no exchange step, so there is no collective on the data path.
+--impl reference times the CPU oracle (plain boundary-matrix reduction and the
+same solver loop) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "filament_128"
+SHAPE = (128, 128, 128)
+TAU = 0.05
+METRIC = "solver iterations/s (128^3 filament field, fp32)"
+UNIT = "iters/s"
+CPU_SAMPLE = (64, 64, 64)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_field():
+    from paper_2407_12399_gb300 import synthetic
+    return synthetic.filament_field(SHAPE, seed=1)
+
+
+def cpu_baseline(f0, steps=2):
+    """The oracle as it stands, single-threaded, on the 64^3 corner crop."""
+    import oracle
+    crop = np.ascontiguousarray(f0[:CPU_SAMPLE[0], :CPU_SAMPLE[1], :CPU_SAMPLE[2]])
+    s = oracle.Solver(crop, tau=TAU)
+    t = time.perf_counter()
+    for _ in range(steps):
+        s.iterate(stop_s=0.0)
+    dt = time.perf_counter() - t
+    scale = float(np.prod(CPU_SAMPLE)) / float(np.prod(SHAPE))
+    return {"value": steps / dt * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle iterations on the {CPU_SAMPLE[0]}^3 corner crop of the {SHAPE[0]}^3 field "
+                      f"({dt:.1f} s), scaled by the vertex ratio {scale:.4f}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    f0 = make_field()
+    crop = np.ascontiguousarray(f0[:CPU_SAMPLE[0], :CPU_SAMPLE[1], :CPU_SAMPLE[2]])
+    scale = float(np.prod(CPU_SAMPLE)) / float(np.prod(SHAPE))
+    s = oracle.Solver(crop, tau=TAU)
+    for _ in range(args.warmup):
+        s.iterate(stop_s=0.0)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        s.iterate(stop_s=0.0)
+    dt = time.perf_counter() - t
+    value = args.steps / dt * scale
+    sample = (f"each step: one oracle iteration on the {CPU_SAMPLE[0]}^3 corner crop of the {SHAPE[0]}^3 field, "
+              f"scaled by the vertex ratio {scale:.4f}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(SHAPE), "signal_threshold": TAU},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2407_12399_gb300 as tsf
+    from paper_2407_12399_gb300 import build as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    tsf.lib()
+
+    f0 = make_field()
+    nv = f0.size
+    stream = torch.cuda.Stream()
+    dev_f0 = torch.from_numpy(f0).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    p = tsf.params(stop_s=0.0)
+
+    # warm-up on a separate field from the same input
+    warm = tsf.Field(dev_f0, stream=stream)
+    warm.set_threshold(TAU)
+    for _ in range(args.warmup):
+        tsf.tsf_solver_step(warm._h, p)
+    warm.close()
+
+    fld = tsf.Field(dev_f0, stream=stream)
+    fld.set_threshold(TAU)
+    tsf.tsf_profile_enable(fld._h, 1)
+    launches0 = tsf.tsf_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+                ev[k][0].record(stream)
+            st = tsf.tsf_solver_step(fld._h, p)
+            ev[k][1].record(stream)
+            stats.append(st.as_dict())
+        torch.cuda.synchronize()
+    launches = tsf.tsf_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    prof = tsf.tsf_profile_read(fld._h)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    fld.close()
+
+    # end to end through the public API, host buffers: create from host
+    # values, set the signal, simplify to the paper's stop rule, read back
+    e2e = None
+    tts = None
+    if rank == 0:
+        host = np.ascontiguousarray(f0)
+        t = time.perf_counter()
+        h = tsf.tsf_create_field(SHAPE[2], SHAPE[1], SHAPE[0], host.ctypes.data, 0, stream.cuda_stream)
+        tsf.tsf_set_signal_threshold(h, TAU)
+        out = np.empty_like(host)
+        st = tsf.tsf_simplify(h, tsf.params(stop_s=0.01), out.ctypes.data, 0)
+        tts = time.perf_counter() - t
+        tsf.tsf_destroy_field(h)
+        iters = max(st.iters, 1)
+        e2e = {"value": iters / tts, "unit": UNIT, "h2d_bytes_per_step": int(4 * nv / iters),
+               "d2h_bytes_per_step": int(4 * nv / iters), "iterations": int(st.iters),
+               "time_to_simplified_field_s": tts, "stop_rule": "loss <= 0.01 loss_0 (Algorithm 1)"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    hbm, peak_kind = peaks()
+    # dominant single kernel: the lower-star gradient (one launch per step)
+    g_ms, g_calls = prof["gradient"]
+    n_grad = float(np.mean([s["n_gradient_vertices"] for s in stats]))
+    grad_bytes = nv * 1.0 + n_grad * (4.0 + 32.0 + 1.0)
+    grad_avg_ms = g_ms / max(g_calls, 1)
+    so_ms, so_calls = prof["vertex_order"]
+    sort_bytes = nv * 80.0  # 4 radix passes (hist read + scatter read/write) + rank scatter
+    shares = {k: round(v[0] / max(total_ms, 1e-9), 4) for k, v in prof.items()}
+    top = max(prof, key=lambda k: prof[k][0])
+    value = world * args.steps / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(SHAPE), "signal_threshold": TAU, "alpha": 0.5,
+                   "fast_gradient_update": 1, "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"kernel": "k_gradient (lower-star gradient, Section 4.2 incremental)", "bound": "hbm",
+                     "achieved": grad_bytes / (grad_avg_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": grad_bytes / (grad_avg_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                     "peak_kind": peak_kind, "avg_launch_ms": grad_avg_ms,
+                     "algorithmic_bytes_per_launch": grad_bytes},
+        "vertex_order_roofline": {"achieved": sort_bytes / (so_ms / max(so_calls, 1) * 1e-3) / 1e9, "unit": "GB/s",
+                                  "avg_ms": so_ms / max(so_calls, 1), "algorithmic_bytes": sort_bytes},
+        "stage_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+        "stage_share": shares, "top_stage": top,
+        "solver": {"points_per_step": float(np.mean([s["n_points"] for s in stats])),
+                   "critical_per_step": np.mean([s["n_critical"] for s in stats], axis=0).tolist(),
+                   "still_fraction": float(np.mean([s["n_still"] / max(s["n_points"], 1) for s in stats])),
+                   "gradient_vertices_per_step": n_grad, "updated_vertices_per_step":
+                       float(np.mean([s["n_updated_vertices"] for s in stats])),
+                   "step_ms": [round(x, 3) for x in step_ms]},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(f0)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

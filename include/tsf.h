@@ -166,6 +166,22 @@ int tsf_get_targets(tsf_field* field, tsf_pair* out, int64_t cap, int64_t* n_out
  * gradient (Section 4.2); intended for verification on small grids. */
 int tsf_zero_pairs(tsf_field* field, uint64_t* out, int64_t cap_pairs, int64_t* n_out);
 
+/* Diagnostics.  With profiling on, every stage of the solver is bracketed by
+ * CUDA events on the field's stream and its device time accumulated (this
+ * adds a stream synchronisation per stage).  Stages, in pipeline order:
+ * 0 vertex order (sort + ranks), 1 lower-star gradient, 2 critical cells,
+ * 3 D0 pairs, 4 D2 pairs, 5 D1 pairs, 6 diagram points, 7 assignment,
+ * 8 loss, 9 gradient step.  tsf_profile_read fills ms[] and calls[] (cap >=
+ * TSF_NSTAGES entries each) with the totals since profiling was enabled;
+ * enabling again resets them. */
+#define TSF_NSTAGES 10
+int tsf_profile_enable(tsf_field* field, int enable);
+int tsf_profile_read(tsf_field* field, double* ms, int64_t* calls, int cap);
+const char* tsf_stage_name(int stage);
+
+/* Number of kernels this library has launched in this process. */
+int64_t tsf_kernel_launches(void);
+
 /* Human-readable name of a status code. */
 const char* tsf_status_string(int status);
 

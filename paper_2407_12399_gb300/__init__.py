@@ -63,7 +63,9 @@ class tsf_stats(ctypes.Structure):
 
 EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_set_signal_threshold",
            "tsf_set_signal_pairs", "tsf_solver_step", "tsf_simplify", "tsf_get_field", "tsf_set_field",
-           "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string")
+           "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
+           "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches")
+TSF_NSTAGES = 10
 
 _lib = None
 
@@ -98,6 +100,14 @@ def lib():
             fn.restype = ctypes.c_int
         L.tsf_status_string.argtypes = [ctypes.c_int]
         L.tsf_status_string.restype = ctypes.c_char_p
+        L.tsf_profile_enable.argtypes = [P, I]
+        L.tsf_profile_enable.restype = I
+        L.tsf_profile_read.argtypes = [P, P, P, I]
+        L.tsf_profile_read.restype = I
+        L.tsf_stage_name.argtypes = [I]
+        L.tsf_stage_name.restype = ctypes.c_char_p
+        L.tsf_kernel_launches.argtypes = []
+        L.tsf_kernel_launches.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -179,6 +189,25 @@ def tsf_zero_pairs(h, out_ptr, cap):
     n = ctypes.c_int64(0)
     r = lib().tsf_zero_pairs(h, out_ptr, cap, ctypes.byref(n))
     return r, n.value
+
+
+def tsf_profile_enable(h, enable=1):
+    _check(lib().tsf_profile_enable(h, enable), "tsf_profile_enable")
+
+
+def tsf_profile_read(h):
+    ms = np.zeros(TSF_NSTAGES, np.float64)
+    calls = np.zeros(TSF_NSTAGES, np.int64)
+    _check(lib().tsf_profile_read(h, ms.ctypes.data, calls.ctypes.data, TSF_NSTAGES), "tsf_profile_read")
+    return {tsf_stage_name(i): (float(ms[i]), int(calls[i])) for i in range(TSF_NSTAGES)}
+
+
+def tsf_stage_name(i):
+    return lib().tsf_stage_name(i).decode()
+
+
+def tsf_kernel_launches():
+    return int(lib().tsf_kernel_launches())
 
 
 def params(alpha_b=0.5, alpha_d=0.5, stop_s=0.01, cancel_eps=0.0, max_iters=1000, fast_gradient_update=1):

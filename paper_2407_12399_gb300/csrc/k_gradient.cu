@@ -290,7 +290,7 @@ namespace tsf {
 void launch_gradient(const Dims& d, const uint32_t* rank, const uint8_t* dirty, Rec* rec, uint8_t* vnext8,
                      uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st) {
   unsigned nb = (unsigned)((d.nv + 127) / 128);
-  k_gradient<<<nb, 128, 0, st>>>(d, rank, dirty, rec, vnext8, status, n_recomputed);
+  k_gradient<<<nb, 128, 0, st>>>(d, rank, dirty, rec, vnext8, status, n_recomputed); note_launch();
 }
 
 int crit_tiles(int64_t nv) { return (int)((nv + kCTile - 1) / kCTile); }
@@ -298,19 +298,19 @@ int crit_tiles(int64_t nv) { return (int)((nv + kCTile - 1) / kCTile); }
 void launch_crit_count(const Dims& d, const uint32_t* order, const Rec* rec, int4* tile_counts, int4* totals,
                        cudaStream_t st) {
   int nt = crit_tiles(d.nv);
-  k_crit_count<<<nt, kCT, 0, st>>>(d.nv, order, rec, tile_counts);
-  k_crit_scan<<<1, kCT, 0, st>>>(nt, tile_counts, totals);
+  k_crit_count<<<nt, kCT, 0, st>>>(d.nv, order, rec, tile_counts); note_launch();
+  k_crit_scan<<<1, kCT, 0, st>>>(nt, tile_counts, totals); note_launch();
 }
 
 void launch_crit_write(const Dims& d, const uint32_t* order, const uint32_t* rank, const Rec* rec,
                        const int4* tile_off, const CritLists& L, uint32_t* cidx, uint32_t* c1base, uint32_t* c2base,
                        uint32_t* status, cudaStream_t st) {
-  k_crit_write<<<crit_tiles(d.nv), kCT, 0, st>>>(d, order, rank, rec, tile_off, L, cidx, c1base, c2base, status);
+  k_crit_write<<<crit_tiles(d.nv), kCT, 0, st>>>(d, order, rank, rec, tile_off, L, cidx, c1base, c2base, status); note_launch();
 }
 
 void launch_zero_pairs(const Dims& d, const uint32_t* rank, unsigned long long* out, int64_t cap,
                        unsigned long long* count, uint32_t* status, cudaStream_t st) {
-  k_zero_pairs<<<(unsigned)((d.nv + 127) / 128), 128, 0, st>>>(d, rank, out, cap, count, status);
+  k_zero_pairs<<<(unsigned)((d.nv + 127) / 128), 128, 0, st>>>(d, rank, out, cap, count, status); note_launch();
 }
 
 }  // namespace tsf

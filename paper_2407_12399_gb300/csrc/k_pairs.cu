@@ -266,10 +266,10 @@ __global__ void k_mark_d0(int n1, const int32_t* __restrict__ kill, uint8_t* __r
 void launch_d0(const Dims& d, const NbrDelta& nd, const CritLists& L, int n0, int n1, const uint8_t* vnext8,
                const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status, cudaStream_t st) {
   if (n1 > 0) {
-    k_d0_trace<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, vnext8, cidx, nd, S.ends, status);
+    k_d0_trace<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, vnext8, cidx, nd, S.ends, status); note_launch();
     k_uf_rounds<<<1, kUFT, 0, st>>>(n1, n0, false, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
-                                    P.d0_min, status);
-    k_mark_d0<<<(n1 + 255) / 256, 256, 0, st>>>(n1, P.d0_min, P.d0_killed);
+                                    P.d0_min, status); note_launch();
+    k_mark_d0<<<(n1 + 255) / 256, 256, 0, st>>>(n1, P.d0_min, P.d0_killed); note_launch();
   }
 }
 
@@ -277,9 +277,9 @@ void launch_d2(const Dims& d, const NbrDelta& nd, const CritLists& L, int n2, in
                const Rec* rec, const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status,
                cudaStream_t st) {
   if (n2 > 0) {
-    k_d2_trace<<<(n2 + 255) / 256, 256, 0, st>>>(d, n2, n3, L, rank, rec, cidx, nd, S.ends, status);
+    k_d2_trace<<<(n2 + 255) / 256, 256, 0, st>>>(d, n2, n3, L, rank, rec, cidx, nd, S.ends, status); note_launch();
     k_uf_rounds<<<1, kUFT, 0, st>>>(n2, n3 + 1, true, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
-                                    P.d2_max, status);
+                                    P.d2_max, status); note_launch();
   }
 }
 
@@ -541,9 +541,9 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   uint32_t* flag = reinterpret_cast<uint32_t*>(W.lowc);  // scratch (n2 entries available)
   uint32_t* pos = reinterpret_cast<uint32_t*>(W.hsize);
   uint32_t* sums = reinterpret_cast<uint32_t*>(W.hcap);
-  k_d1_select<<<(n2 + 255) / 256, 256, 0, st>>>(n2, P.d2_max, flag);
+  k_d1_select<<<(n2 + 255) / 256, 256, 0, st>>>(n2, P.d2_max, flag); note_launch();
   exclusive_scan_u32(flag, pos, n2, sums, st);
-  k_d1_gather<<<(n2 + 255) / 256, 256, 0, st>>>(n2, flag, pos, W.cols, P.d1_edge);
+  k_d1_gather<<<(n2 + 255) / 256, 256, 0, st>>>(n2, flag, pos, W.cols, P.d1_edge); note_launch();
   // number of columns = pos[n2-1] + flag[n2-1]
   uint32_t tail[2];
   cudaMemcpyAsync(&tail[0], pos + n2 - 1, 4, cudaMemcpyDeviceToHost, st);
@@ -563,11 +563,11 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.d0_killed = P.d0_killed;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   int nb = (max(ncols, n1) + 255) / 256;
-  k_d1_init<<<nb, 256, 0, st>>>(c, W, ncols, W.owner, n1, status);
+  k_d1_init<<<nb, 256, 0, st>>>(c, W, ncols, W.owner, n1, status); note_launch();
   for (int round = 0; round < 1 << 20; ++round) {
     cudaMemsetAsync(W.flags, 0, 4, st);
-    k_d1_expand<<<(ncols + 127) / 128, 128, 0, st>>>(c, W, ncols, W.owner, status);
-    k_d1_add<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, W.owner, status);
+    k_d1_expand<<<(ncols + 127) / 128, 128, 0, st>>>(c, W, ncols, W.owner, status); note_launch();
+    k_d1_add<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, W.owner, status); note_launch();
     cudaMemcpyAsync(h_flags, W.flags, 4, cudaMemcpyDeviceToHost, st);
     uint32_t hs = 0;
     cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st);
@@ -575,7 +575,7 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
     if (hs & (kErrPool | kErrEmptyColumn | kErrInconsistent | kErrRounds)) break;
     if (h_flags[0] == 0) break;
   }
-  k_d1_finish<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, P.d1_edge);
+  k_d1_finish<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, P.d1_edge); note_launch();
 }
 
 }  // namespace tsf

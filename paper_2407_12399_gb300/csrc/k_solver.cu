@@ -43,9 +43,9 @@ __global__ void k_iota(int n, int32_t* a) {
 template <class Less>
 static int32_t* merge_sort(int n, int32_t* a, int32_t* b, Less less, cudaStream_t st) {
   if (n <= 0) return a;
-  k_iota<<<(n + 255) / 256, 256, 0, st>>>(n, a);
+  k_iota<<<(n + 255) / 256, 256, 0, st>>>(n, a); note_launch();
   for (int w = 1; w < n; w *= 2) {
-    k_merge_pass<<<(n + 255) / 256, 256, 0, st>>>(n, w, a, b, less);
+    k_merge_pass<<<(n + 255) / 256, 256, 0, st>>>(n, w, a, b, less); note_launch();
     int32_t* t = a;
     a = b;
     b = t;
@@ -194,13 +194,13 @@ int build_diagram(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1,
   cudaMemsetAsync(B.count, 0, sizeof(int), st);
   int n = max(max(n1, n2), 1);
   k_build_points<<<(n + 255) / 256, 256, 0, st>>>(d, nd, L, n1, n2, n3, P.d0_min, P.d1_edge, P.d2_max, order, f,
-                                                  B.tmp_pts, B.count, cap);
+                                                  B.tmp_pts, B.count, cap); note_launch();
   int np = 0;
   cudaMemcpyAsync(&np, B.count, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   if (np > cap) return -np;
   int32_t* idx = merge_sort(np, B.idxA, B.idxB, DiagLess{B.tmp_pts}, st);
-  k_gather_pts<<<(np + 255) / 256, 256, 0, st>>>(np, idx, B.tmp_pts, out);
+  k_gather_pts<<<(np + 255) / 256, 256, 0, st>>>(np, idx, B.tmp_pts, out); note_launch();
   return np;
 }
 
@@ -233,9 +233,9 @@ __global__ void k_write_targets(int np, const Pt* __restrict__ pts, const uint32
 int make_targets(int np, const Pt* pts, float theta, SolverBufs& B, Tg* T, cudaStream_t st) {
   uint32_t* flag = B.u32a;
   uint32_t* pos = B.u32b;
-  k_select_targets<<<(np + 255) / 256, 256, 0, st>>>(np, pts, theta, flag);
+  k_select_targets<<<(np + 255) / 256, 256, 0, st>>>(np, pts, theta, flag); note_launch();
   exclusive_scan_u32(flag, pos, np, B.u32c, st);
-  k_write_targets<<<(np + 255) / 256, 256, 0, st>>>(np, pts, flag, pos, T);
+  k_write_targets<<<(np + 255) / 256, 256, 0, st>>>(np, pts, flag, pos, T); note_launch();
   uint32_t tail[2];
   cudaMemcpyAsync(&tail[0], pos + np - 1, 4, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&tail[1], flag + np - 1, 4, cudaMemcpyDeviceToHost, st);
@@ -587,46 +587,46 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBu
   cudaMemsetAsync(B.taken, 0, (size_t)max(nt, 1), st);
   int32_t* ck = merge_sort(np, B.idxA, B.idxB, KeyLess{pts}, st);
   int32_t* rk = nr > 0 ? merge_sort(nr, B.idxC, B.idxD, KeyLess{ref}, st) : B.idxC;
-  k_still<<<(np + 255) / 256, 256, 0, st>>>(np, pts, ck, nr, ref, rk, B.tmp_pts, B.taken);
+  k_still<<<(np + 255) / 256, 256, 0, st>>>(np, pts, ck, nr, ref, rk, B.tmp_pts, B.taken); note_launch();
   cudaMemcpyAsync(pts, B.tmp_pts, sizeof(Pt) * (size_t)np, cudaMemcpyDeviceToDevice, st);
   // 2) reduced problems, group by group
   as->k[0] = as->k[1] = as->k[2] = as->k[3] = 0;
   for (int g = 0; g < 4; ++g) {
-    k_group_flags<<<(np + 255) / 256, 256, 0, st>>>(np, pts, g, B.u32a);
+    k_group_flags<<<(np + 255) / 256, 256, 0, st>>>(np, pts, g, B.u32a); note_launch();
     exclusive_scan_u32(B.u32a, B.u32b, np, B.u32c, st);
     int npg = (int)read_tail(B.u32a, B.u32b, np, st);
-    k_compact<<<(np + 255) / 256, 256, 0, st>>>(np, B.u32a, B.u32b, B.plist);
+    k_compact<<<(np + 255) / 256, 256, 0, st>>>(np, B.u32a, B.u32b, B.plist); note_launch();
     int k = 0;
     if (nt > 0) {
-      k_tgroup_flags<<<(nt + 255) / 256, 256, 0, st>>>(nt, T, B.taken, g, B.u32a);
+      k_tgroup_flags<<<(nt + 255) / 256, 256, 0, st>>>(nt, T, B.taken, g, B.u32a); note_launch();
       exclusive_scan_u32(B.u32a, B.u32b, nt, B.u32c, st);
       k = (int)read_tail(B.u32a, B.u32b, nt, st);
-      k_compact<<<(nt + 255) / 256, 256, 0, st>>>(nt, B.u32a, B.u32b, B.tlist);
+      k_compact<<<(nt + 255) / 256, 256, 0, st>>>(nt, B.u32a, B.u32b, B.tlist); note_launch();
     }
     as->k[g] = k;
     if (k == 0 || npg == 0) continue;
     if (g == 3) {
-      k_essential<<<(npg + 255) / 256, 256, 0, st>>>(npg, B.plist, k, B.tlist, pts);
+      k_essential<<<(npg + 255) / 256, 256, 0, st>>>(npg, B.plist, k, B.tlist, pts); note_launch();
       continue;
     }
     if (k > B.cap_k) return -1;
-    k_cand_count<<<k, 256, 0, st>>>(npg, B.plist, pts, k, B.tlist, T, B.u32a);
+    k_cand_count<<<k, 256, 0, st>>>(npg, B.plist, pts, k, B.tlist, T, B.u32a); note_launch();
     exclusive_scan_u32(B.u32a, B.u32b, k, B.u32c, st);
     int nc = (int)read_tail(B.u32a, B.u32b, k, st);
     if (nc > B.cap_cand) return -2;
     if (nc == 0) continue;
-    k_cand_fill<<<k, 256, 0, st>>>(npg, B.plist, pts, k, B.tlist, T, B.u32b, B.cands);
+    k_cand_fill<<<k, 256, 0, st>>>(npg, B.plist, pts, k, B.tlist, T, B.u32b, B.cands); note_launch();
     int32_t* ci = merge_sort(nc, B.idxC, B.idxD, CandLess{B.cands}, st);
     cudaMemsetAsync(B.is_col, 0, sizeof(uint32_t) * (size_t)npg, st);
     cudaMemsetAsync(B.nkept, 0, sizeof(uint32_t) * (size_t)k, st);
-    k_cand_keep<<<(nc + 255) / 256, 256, 0, st>>>(nc, ci, B.cands, B.u32b, k, B.is_col, B.kept, B.nkept);
+    k_cand_keep<<<(nc + 255) / 256, 256, 0, st>>>(nc, ci, B.cands, B.u32b, k, B.is_col, B.kept, B.nkept); note_launch();
     exclusive_scan_u32(B.is_col, B.colpos, npg, B.u32c, st);
     int mc = (int)read_tail(B.is_col, B.colpos, npg, st);
     if (mc + k + 1 > B.cap_cols) return -3;
-    k_colpos<<<(npg + 255) / 256, 256, 0, st>>>(npg, B.is_col, B.colpos, B.colpos, B.col_point);
-    k_diag_t<<<(k + 255) / 256, 256, 0, st>>>(k, B.tlist, T, B.diag_t);
-    k_hungarian<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, B.H, B.col_to_row, status);
-    k_apply_assignment<<<(mc + 255) / 256, 256, 0, st>>>(mc, B.col_to_row, B.col_point, B.plist, B.tlist, pts);
+    k_colpos<<<(npg + 255) / 256, 256, 0, st>>>(npg, B.is_col, B.colpos, B.colpos, B.col_point); note_launch();
+    k_diag_t<<<(k + 255) / 256, 256, 0, st>>>(k, B.tlist, T, B.diag_t); note_launch();
+    k_hungarian<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, B.H, B.col_to_row, status); note_launch();
+    k_apply_assignment<<<(mc + 255) / 256, 256, 0, st>>>(mc, B.col_to_row, B.col_point, B.plist, B.tlist, pts); note_launch();
   }
   return 0;
 }
@@ -677,9 +677,9 @@ void loss_and_counts(int np, const Pt* pts, int nt, const Tg* T, float cancel_ep
   cudaMemsetAsync(B.counters, 0, sizeof(unsigned long long) * 4, st);
   cudaMemsetAsync(B.taken, 0, (size_t)max(nt, 1), st);
   if (np > 0)
-    k_loss_terms<<<(np + 255) / 256, 256, 0, st>>>(np, pts, nt, T, cancel_eps, B.terms, B.taken, B.counters);
-  if (nt > 0) k_loss_tterms<<<(nt + 255) / 256, 256, 0, st>>>(np, nt, T, B.taken, B.terms);
-  k_sum<<<1, 1024, 0, st>>>(np + nt, B.terms, B.dsum);
+    k_loss_terms<<<(np + 255) / 256, 256, 0, st>>>(np, pts, nt, T, cancel_eps, B.terms, B.taken, B.counters); note_launch();
+  if (nt > 0) k_loss_tterms<<<(nt + 255) / 256, 256, 0, st>>>(np, nt, T, B.taken, B.terms); note_launch();
+  k_sum<<<1, 1024, 0, st>>>(np + nt, B.terms, B.dsum); note_launch();
   cudaMemcpyAsync(h_loss, B.dsum, sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(h_counts, B.counters, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -750,12 +750,12 @@ int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float a
   cudaMemsetAsync(B.count, 0, sizeof(int), st);
   cudaMemsetAsync(B.counters, 0, sizeof(unsigned long long), st);
   if (np == 0) return 0;
-  k_contrib<<<(np + 255) / 256, 256, 0, st>>>(np, pts, T, alpha_b, alpha_d, B.contrib, B.count);
+  k_contrib<<<(np + 255) / 256, 256, 0, st>>>(np, pts, T, alpha_b, alpha_d, B.contrib, B.count); note_launch();
   int nc = 0;
   cudaMemcpyAsync(&nc, B.count, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   int32_t* idx = merge_sort(nc, B.idxA, B.idxB, ContribLess{B.contrib}, st);
-  k_apply_step<<<(nc + 255) / 256, 256, 0, st>>>(nc, idx, B.contrib, f, dirty, B.counters);
+  k_apply_step<<<(nc + 255) / 256, 256, 0, st>>>(nc, idx, B.contrib, f, dirty, B.counters); note_launch();
   unsigned long long nupd = 0;
   cudaMemcpyAsync(&nupd, B.counters, sizeof(nupd), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -763,7 +763,7 @@ int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float a
 }
 
 void targets_as_points(int nt, const Tg* T, Pt* R, cudaStream_t st) {
-  if (nt > 0) k_targets_as_points<<<(nt + 255) / 256, 256, 0, st>>>(nt, T, R);
+  if (nt > 0) k_targets_as_points<<<(nt + 255) / 256, 256, 0, st>>>(nt, T, R); note_launch();
 }
 
 }  // namespace tsf

@@ -182,9 +182,9 @@ __global__ void k_scan_apply(const uint32_t* __restrict__ in, int64_t n, const u
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t st) {
   int nb = (int)((n + kSTile - 1) / kSTile);
   if (nb == 0) return;
-  k_scan_sums<<<nb, kST, 0, st>>>(in, n, sums);
-  k_scan_top<<<1, kST, 0, st>>>(sums, nb);
-  k_scan_apply<<<nb, kST, 0, st>>>(in, n, sums, out);
+  k_scan_sums<<<nb, kST, 0, st>>>(in, n, sums); note_launch();
+  k_scan_top<<<1, kST, 0, st>>>(sums, nb); note_launch();
+  k_scan_apply<<<nb, kST, 0, st>>>(in, n, sums, out); note_launch();
 }
 
 int64_t sort_scratch_words(int64_t n) {
@@ -213,13 +213,13 @@ void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, ui
     int shift = 8 * pass;
     uint32_t* kout = (pass & 1) ? kB : kA;
     uint32_t* vout = last ? order : ((pass & 1) ? vB : vA);
-    k_rs_hist<<<ntiles, kRT, 0, st>>>(n, shift, first, f, kin, counts, ntiles, status);
+    k_rs_hist<<<ntiles, kRT, 0, st>>>(n, shift, first, f, kin, counts, ntiles, status); note_launch();
     exclusive_scan_u32(counts, offs, ncounts, sums, st);
-    k_rs_scatter<<<ntiles, kRT, 0, st>>>(n, shift, first, last, f, kin, vin, kout, vout, offs, ntiles);
+    k_rs_scatter<<<ntiles, kRT, 0, st>>>(n, shift, first, last, f, kin, vin, kout, vout, offs, ntiles); note_launch();
     kin = kout;
     vin = vout;
   }
-  k_rank_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, order, rank);
+  k_rank_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, order, rank); note_launch();
 }
 
 }  // namespace tsf

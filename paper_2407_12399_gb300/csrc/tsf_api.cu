@@ -9,11 +9,19 @@
 #include <cstring>
 #include <vector>
 
+#include <atomic>
+
 #include "../../include/tsf.h"
 #include "tsf_kernels.cuh"
 #include "tsf_solver.cuh"
 
 using namespace tsf;
+
+namespace tsf {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace tsf
 
 namespace {
 
@@ -81,9 +89,48 @@ struct tsf_field {
   int64_t n_updated = 0, n_gradient = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
+  // profiling: event pairs recorded around stages, resolved after each call
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, size_t>> ev_pending;  // (stage, index of the pair in ev_pool)
+  int ev_open[TSF_NSTAGES] = {};
+  double prof_ms[TSF_NSTAGES] = {};
+  int64_t prof_calls[TSF_NSTAGES] = {};
 };
 
 namespace {
+
+enum Stage { kSort, kGrad, kCrit, kD0, kD2, kD1, kPoints, kAssign, kLoss, kStep };
+
+void stage_begin(tsf_field* F, int s) {
+  if (!F->prof) return;
+  size_t k = F->ev_pending.size();
+  while (F->ev_pool.size() < 2 * (k + 1)) {
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e));
+    F->ev_pool.push_back(e);
+  }
+  F->ev_pending.push_back({s, k});
+  F->ev_open[s] = (int)k;
+  ck(cudaEventRecord(F->ev_pool[2 * k], F->st));
+}
+void stage_end(tsf_field* F, int s) {
+  if (!F->prof) return;
+  ck(cudaEventRecord(F->ev_pool[2 * (size_t)F->ev_open[s] + 1], F->st));
+}
+// called once the stream is idle (end of a public call)
+void profile_resolve(tsf_field* F) {
+  if (F->ev_pending.empty()) return;
+  cudaStreamSynchronize(F->st);
+  for (auto& pe : F->ev_pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, F->ev_pool[2 * pe.second], F->ev_pool[2 * pe.second + 1]) == cudaSuccess) {
+      F->prof_ms[pe.first] += ms;
+      F->prof_calls[pe.first] += 1;
+    }
+  }
+  F->ev_pending.clear();
+}
 
 void grow_crit(tsf_field* F, int n0, int n1, int n2, int n3) {
   auto need = [](int have, int want) { return want > have ? std::max(want + want / 2, 1024) : have; };
@@ -289,15 +336,20 @@ int compute_diagram(tsf_field* F, bool incremental) {
   cudaStream_t st = F->st;
   double t0 = now_ms();
   ck(cudaMemsetAsync(F->status, 0, 4, st));
+  stage_begin(F, kSort);
   vertex_order(F->f, F->d.nv, F->order, F->rank, F->sort_scratch, F->status, st);
+  stage_end(F, kSort);
   uint32_t s = read_status(F);
   if (s & kErrNaN) return TSF_ENAN;
   bool inc = incremental && F->records_valid && F->dirty_valid;
   ck(cudaMemsetAsync(F->counter, 0, 8, st));
+  stage_begin(F, kGrad);
   launch_gradient(F->d, F->rank, inc ? F->dirty : nullptr, F->rec, F->vnext8, F->status, F->counter, st);
+  stage_end(F, kGrad);
   unsigned long long ngrad = 0;
   ck(cudaMemcpyAsync(&ngrad, F->counter, 8, cudaMemcpyDeviceToHost, st));
   F->records_valid = true;
+  stage_begin(F, kCrit);
   launch_crit_count(F->d, F->order, F->rec, F->tile_counts, F->totals, st);
   int4 tot;
   ck(cudaMemcpyAsync(&tot, F->totals, sizeof(int4), cudaMemcpyDeviceToHost, st));
@@ -310,8 +362,13 @@ int compute_diagram(tsf_field* F, bool incremental) {
   grow_crit(F, F->n0, F->n1, F->n2, F->n3);
   launch_crit_write(F->d, F->order, F->rank, F->rec, F->tile_counts, F->L, F->cidx, F->c1base, F->c2base, F->status,
                     st);
+  stage_end(F, kCrit);
+  stage_begin(F, kD0);
   launch_d0(F->d, F->nd, F->L, F->n0, F->n1, F->vnext8, F->cidx, F->PS, F->PO, F->status, st);
+  stage_end(F, kD0);
+  stage_begin(F, kD2);
   launch_d2(F->d, F->nd, F->L, F->n2, F->n3, F->rank, F->rec, F->cidx, F->PS, F->PO, F->status, st);
+  stage_end(F, kD2);
   s = read_status(F);
   if (status_code(s) != TSF_OK) return status_code(s);
   // D1, growing the column pool until it suffices
@@ -327,8 +384,10 @@ int compute_diagram(tsf_field* F, bool incremental) {
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
     ck(cudaMemsetAsync(F->status, 0, 4, st));
+    stage_begin(F, kD1);
     launch_d1(F->d, F->nd, F->L, F->n1, F->n2, F->rank, F->order, F->rec, F->c1base, F->W, F->PO, F->status,
               F->h_flags, st);
+    stage_end(F, kD1);
     s = read_status(F);
     if ((s & kErrPool) && attempt < 6) continue;
     break;
@@ -337,7 +396,9 @@ int compute_diagram(tsf_field* F, bool incremental) {
   // points
   int want_pts = F->n0 + F->n2 + 1;
   grow_solver(F, want_pts, F->nt);
+  stage_begin(F, kPoints);
   int np = build_diagram(F->d, F->nd, F->L, F->n1, F->n2, F->n3, F->PO, F->order, F->f, F->B, F->pts, F->cap_pts, st);
+  stage_end(F, kPoints);
   if (np < 0) return TSF_EINTERNAL;
   F->np = np;
   F->diagram_current = true;
@@ -351,7 +412,9 @@ int run_assign(tsf_field* F, const Pt* ref, int nr) {
   AssignStats as;
   for (int attempt = 0; attempt < 8; ++attempt) {
     ck(cudaMemsetAsync(F->status, 0, 4, F->st));
+    stage_begin(F, kAssign);
     int r = assign(F->np, F->pts, nr, ref, F->nt, F->T, F->B, F->status, &as, F->st);
+    stage_end(F, kAssign);
     if (r == 0) break;
     if (r == -2) grow_assign(F, std::max(2 * F->B.cap_cand, 4096), 0);
     else if (r == -3) grow_assign(F, 0, std::max(2 * F->B.cap_cols, 4096));
@@ -391,7 +454,9 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
 }
 
 int eval(tsf_field* F, float cancel_eps) {
+  stage_begin(F, kLoss);
   loss_and_counts(F->np, F->pts, F->nt, F->T, cancel_eps, F->B, &F->loss, F->counts, F->st);
+  stage_end(F, kLoss);
   return TSF_OK;
 }
 
@@ -426,8 +491,10 @@ int step(tsf_field* F, const tsf_params* p, tsf_stats* stats) {
   cudaStream_t st = F->st;
   double t0 = now_ms();
   bool fast = p->fast_gradient_update != 0;
+  stage_begin(F, kStep);
   if (fast) ck(cudaMemsetAsync(F->dirty, 0, (size_t)F->d.nv, st));
   F->n_updated = gradient_step(F->np, F->pts, F->T, p->alpha_b, p->alpha_d, F->f, fast ? F->dirty : nullptr, F->B, st);
+  stage_end(F, kStep);
   F->dirty_valid = fast;
   F->ms_step = now_ms() - t0;
   // previous diagram (with its assignment) becomes the still-pair reference
@@ -453,6 +520,13 @@ int guarded(Fn&& fn) {
   } catch (...) {
     return TSF_EINTERNAL;
   }
+}
+
+template <class Fn>
+int guarded_f(tsf_field* F, Fn&& fn) {
+  int r = guarded(fn);
+  profile_resolve(F);
+  return r;
 }
 
 }  // namespace
@@ -552,6 +626,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(B.counters);
   dev_free(B.contrib);
   if (F->h_flags) cudaFreeHost(F->h_flags);
+  for (auto e : F->ev_pool) cudaEventDestroy(e);
   delete F;
   return TSF_OK;
 }
@@ -602,7 +677,7 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
 
 int tsf_compute_diagram(tsf_field* F, tsf_pair* out, int64_t cap, int64_t* n_out, int out_on_device) {
   if (!F || !n_out || cap < 0 || (cap > 0 && !out)) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_f(F, [&]() {
     if (!F->diagram_current) {
       int r = compute_diagram(F, false);
       if (r) return r;
@@ -633,7 +708,7 @@ int tsf_compute_diagram(tsf_field* F, tsf_pair* out, int64_t cap, int64_t* n_out
 
 int tsf_set_signal_threshold(tsf_field* F, float fraction) {
   if (!F || !(fraction >= 0.0f)) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_f(F, [&]() {
     int r = compute_diagram(F, false);
     if (r) return r;
     float lo = 0, hi = 0;
@@ -654,7 +729,7 @@ int tsf_set_signal_threshold(tsf_field* F, float fraction) {
 
 int tsf_set_signal_pairs(tsf_field* F, const tsf_pair* pairs, int64_t n) {
   if (!F || n < 0 || (n > 0 && !pairs)) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_f(F, [&]() {
     int r = compute_diagram(F, false);
     if (r) return r;
     std::vector<Tg> t((size_t)n);
@@ -714,14 +789,14 @@ int tsf_solver_step(tsf_field* F, const tsf_params* p, tsf_stats* stats) {
   if (!F) return TSF_EINVAL;
   if (check_params(p)) return TSF_EINVAL;
   if (!F->have_targets) return TSF_ENOTARGET;
-  return guarded([&]() { return step(F, p, stats); });
+  return guarded_f(F, [&]() { return step(F, p, stats); });
 }
 
 int tsf_simplify(tsf_field* F, const tsf_params* p, float* out_values, int out_on_device, tsf_stats* stats) {
   if (!F) return TSF_EINVAL;
   if (check_params(p)) return TSF_EINVAL;
   if (!F->have_targets) return TSF_ENOTARGET;
-  return guarded([&]() {
+  return guarded_f(F, [&]() {
     eval(F, p->cancel_eps);
     int done = is_done(F, p);
     fill_stats(F, p, stats, done);
@@ -827,5 +902,35 @@ int tsf_zero_pairs(tsf_field* F, uint64_t* out, int64_t cap_pairs, int64_t* n_ou
     return rc;
   });
 }
+
+int tsf_profile_enable(tsf_field* F, int enable) {
+  if (!F) return TSF_EINVAL;
+  return guarded([&]() {
+    profile_resolve(F);
+    F->prof = enable != 0;
+    for (int i = 0; i < TSF_NSTAGES; ++i) {
+      F->prof_ms[i] = 0;
+      F->prof_calls[i] = 0;
+    }
+    return TSF_OK;
+  });
+}
+
+int tsf_profile_read(tsf_field* F, double* ms, int64_t* calls, int cap) {
+  if (!F || cap < TSF_NSTAGES) return TSF_EINVAL;
+  for (int i = 0; i < TSF_NSTAGES; ++i) {
+    if (ms) ms[i] = F->prof_ms[i];
+    if (calls) calls[i] = F->prof_calls[i];
+  }
+  return TSF_OK;
+}
+
+const char* tsf_stage_name(int s) {
+  static const char* names[TSF_NSTAGES] = {"vertex_order", "gradient", "critical_cells", "pairs_d0", "pairs_d2",
+                                           "pairs_d1", "diagram_points", "assignment", "loss", "gradient_step"};
+  return (s >= 0 && s < TSF_NSTAGES) ? names[s] : "unknown";
+}
+
+int64_t tsf_kernel_launches(void) { return (int64_t)tsf::launches(); }
 
 }  // extern "C"

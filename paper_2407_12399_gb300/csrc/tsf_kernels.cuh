@@ -11,6 +11,10 @@ namespace tsf {
 
 enum : uint32_t { kErrNaN = 1u << 7 };
 
+// Number of kernels this library has launched (process-wide).
+void note_launch();
+long long launches();
+
 // Critical cells, each list in lexicographic order (Section 2.2).
 struct CritLists {
   uint32_t* c0;       // minima: vertex id
