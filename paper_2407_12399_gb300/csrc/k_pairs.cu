@@ -425,112 +425,171 @@ __global__ void k_d1_gather(int n2, const uint32_t* __restrict__ flag, const uin
   }
 }
 
-__global__ void k_d1_init(D1Ctx c, D1Work W, int ncols, int32_t* owner, int n1, uint32_t* status) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int k = j; k < n1; k += gridDim.x * blockDim.x) owner[k] = 0x7FFFFFFF;
-  if (j >= ncols) return;
-  uint32_t cap = 16;
+// Growable array in the pool (a column's heap or its Morse boundary).
+struct Vec {
+  unsigned long long* h;
+  uint32_t off, cap, size;
+};
+
+__device__ bool vec_alloc(D1Work& W, Vec& v, uint32_t cap, uint32_t* status) {
   uint32_t off = atomicAdd(W.pool_head, cap);
   if ((unsigned long long)off + cap > W.pool_cap) {
     atomicOr(status, kErrPool);
-    W.hoff[j] = 0;
-    W.hcap[j] = 0;
-    W.hsize[j] = 0;
-    W.low[j] = 0;
-    W.lowc[j] = -1;
-    return;
+    return false;
   }
+  v.off = off;
+  v.cap = cap;
+  v.size = 0;
+  v.h = W.pool + off;
+  return true;
+}
+
+__device__ bool vec_push(D1Work& W, Vec& v, unsigned long long x, uint32_t* status) {
+  if (v.size == v.cap) {
+    Vec n;
+    if (!vec_alloc(W, n, v.cap * 2, status)) return false;
+    for (uint32_t i = 0; i < v.size; ++i) n.h[i] = v.h[i];
+    n.size = v.size;
+    v = n;
+  }
+  v.h[v.size++] = x;
+  return true;
+}
+
+__device__ __forceinline__ Heap as_heap(const Vec& v) {
   Heap H;
-  H.off = off;
-  H.cap = cap;
-  H.size = 0;
-  H.h = W.pool + off;
+  H.h = v.h;
+  H.off = v.off;
+  H.cap = v.cap;
+  H.size = v.size;
+  return H;
+}
+
+constexpr int kD1StepLimit = 1 << 24;
+
+// Phase 1: Morse boundary of each candidate triangle t: its boundary (positive
+// edges) with every gradient-paired edge eliminated by its triangle's reduced
+// column, largest first, one lower star at a time.  Output: the critical
+// edges left (C1 indices), in decreasing lexicographic order.
+__global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols) return;
+  W.hsize[j] = 0;
+  W.hoff[j] = 0;
+  Vec hv, out;
+  if (!vec_alloc(W, hv, 32, status) || !vec_alloc(W, out, 8, status)) return;
+  Heap H = as_heap(hv);
   uint32_t ve = c.L.c2_ve[W.cols[j]];
-  uint32_t v = ve >> 6;
-  int e = (int)(ve & 63u);
-  uint32_t a = (uint32_t)((int32_t)v + c.nd.d[c_geo.edge[e][0]]);
-  uint32_t b = (uint32_t)((int32_t)v + c.nd.d[c_geo.edge[e][1]]);
-  push_if_positive(c, W, H, v, a, status);
-  push_if_positive(c, W, H, v, b, status);
-  push_if_positive(c, W, H, a, b, status);
-  heap_store(W, j, H);
-  W.low[j] = 0;
-  W.lowc[j] = -1;
-}
-
-constexpr int kD1StepLimit = 1 << 22;
-
-// Phase A: reduce each column by the gradient-paired rows until its low is a
-// critical edge; claim that edge (smallest column wins).
-__global__ void k_d1_expand(D1Ctx c, D1Work W, int ncols, int32_t* owner, uint32_t* status) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ncols) return;
-  if (W.lowc[j] >= 0) {
-    atomicMin(&owner[W.lowc[j]], j);
-    return;
-  }
-  Heap H = heap_of(W, j);
-  unsigned long long low = W.low[j];
-  for (int step = 0; step < kD1StepLimit; ++step) {
-    if (low == 0) low = heap_low(H);
-    if (low == 0) {
-      atomicOr(status, kErrEmptyColumn);
-      break;
+  uint32_t v0 = ve >> 6;
+  int e0 = (int)(ve & 63u);
+  uint32_t a0 = (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][0]]);
+  uint32_t b0 = (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][1]]);
+  push_if_positive(c, W, H, v0, a0, status);
+  push_if_positive(c, W, H, v0, b0, status);
+  push_if_positive(c, W, H, a0, b0, status);
+  for (int step = 0;; ++step) {
+    if (step >= kD1StepLimit) {
+      atomicOr(status, kErrRounds);
+      return;
     }
-    uint32_t hi = c.order[(uint32_t)(low >> 32)];
-    uint32_t lo = c.order[(uint32_t)(low & 0xFFFFFFFFull)];
-    int k = nbr_of_pair(c.d, hi, lo);
-    Rec r = ld_rec(c.rec, hi);
-    if ((rec_crit_edges(r) >> k) & 1u) {
-      int ci = crit_edge_index(c, hi, r, k);
-      W.lowc[j] = ci;
-      atomicMin(&owner[ci], j);
-      break;
+    unsigned long long top = heap_low(H);
+    if (top == 0) break;
+    uint32_t rv = (uint32_t)(top >> 32);
+    uint32_t v = c.order[rv];
+    // every entry of v's lower star, with its parity, by neighbour index
+    uint32_t m = 1u << nbr_of_pair(c.d, v, c.order[(uint32_t)(top & 0xFFFFFFFFull)]);
+    while (H.size > 0 && (uint32_t)(H.h[0] >> 32) == rv) {
+      unsigned long long e = heap_pop(H);
+      m ^= 1u << nbr_of_pair(c.d, v, c.order[(uint32_t)(e & 0xFFFFFFFFull)]);
     }
-    // gradient edge hi*lo paired with a triangle of hi's lower star: add that
-    // triangle's reduced column (hi*lo cancels the low)
+    if (!m) continue;
+    Rec r = ld_rec(c.rec, v);
+    uint32_t crit = rec_crit_edges(r);
     Star s;
-    star_load(s, c.d, hi, c.rank);
-    int8_t pa[14], pb[14];
-    int y = -1;
-    int n = star_chain(s, k, pa, pb, y);
-    if (n < 0) {
-      atomicOr(status, kErrInconsistent);
+    star_load(s, c.d, v, c.rank);
+    int8_t y_of[14];
+    uint64_t path_of[14];
+    star_chains(s, y_of, path_of);
+    for (int p = s.nl - 1; p >= 1; --p) {
+      int x = s.by_pos[p];
+      if (!((m >> x) & 1u)) continue;
+      m &= ~(1u << x);
+      if ((crit >> x) & 1u) {
+        int ci = crit_edge_index(c, v, r, x);
+        if (ci >= 0 && !c.d0_killed[ci]) vec_push(W, out, (unsigned long long)ci, status);
+        continue;
+      }
+      int y = y_of[x];
+      if (y < 0) {
+        atomicOr(status, kErrInconsistent);
+        return;
+      }
+      if (y != s.by_pos[0]) m ^= 1u << y;  // w*y stays in this lower star (w*y negative if y is the lowest)
+      for (uint64_t pm = path_of[x]; pm; pm &= pm - 1) {
+        int le = __ffsll((long long)pm) - 1;
+        uint32_t pa = (uint32_t)((int32_t)v + c.nd.d[c_geo.edge[le][0]]);
+        uint32_t pb = (uint32_t)((int32_t)v + c.nd.d[c_geo.edge[le][1]]);
+        push_if_positive(c, W, H, pa, pb, status);
+      }
+    }
+  }
+  W.hoff[j] = out.off;
+  W.hsize[j] = out.size;
+}
+
+// Phase 2 (one block): reduce the Morse boundaries, smallest column owning
+// each low; every addition is of an earlier column.
+__global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int ncols, int n1, int32_t* d1_edge, uint32_t* status) {
+  __shared__ int changed;
+  for (int k = threadIdx.x; k < n1; k += kUFT) W.owner[k] = 0x7FFFFFFF;
+  __syncthreads();
+  for (int round = 0;; ++round) {
+    if (round > ncols + 2) {
+      if (threadIdx.x == 0) atomicOr(status, kErrRounds);
       break;
     }
-    push_if_positive(c, W, H, hi, (uint32_t)((int32_t)hi + c.nd.d[y]), status);
-    for (int t = 0; t < n; ++t)
-      push_if_positive(c, W, H, (uint32_t)((int32_t)hi + c.nd.d[pa[t]]), (uint32_t)((int32_t)hi + c.nd.d[pb[t]]),
-                       status);
-    low = 0;
-    if (step == kD1StepLimit - 1) atomicOr(status, kErrRounds);
+    if (threadIdx.x == 0) changed = 0;
+    for (int j = threadIdx.x; j < ncols; j += kUFT)
+      if (W.hsize[j] > 0) atomicMin(&W.owner[(int)W.pool[W.hoff[j]]], j);
+    __syncthreads();
+    for (int j = threadIdx.x; j < ncols; j += kUFT) {
+      uint32_t n = W.hsize[j];
+      if (n == 0) continue;
+      const unsigned long long* a = W.pool + W.hoff[j];
+      int o = W.owner[(int)a[0]];
+      if (o == j) continue;
+      uint32_t no = W.hsize[o];
+      const unsigned long long* b = W.pool + W.hoff[o];
+      uint32_t cap = n + no;
+      uint32_t off = atomicAdd(W.pool_head, cap);
+      if ((unsigned long long)off + cap > W.pool_cap) {
+        atomicOr(status, kErrPool);
+        continue;
+      }
+      unsigned long long* d = W.pool + off;
+      uint32_t i = 0, k = 0, m = 0;
+      while (i < n && k < no) {  // both decreasing: symmetric difference
+        if (a[i] > b[k]) d[m++] = a[i++];
+        else if (b[k] > a[i]) d[m++] = b[k++];
+        else {
+          ++i;
+          ++k;
+        }
+      }
+      while (i < n) d[m++] = a[i++];
+      while (k < no) d[m++] = b[k++];
+      if (m == 0) atomicOr(status, kErrEmptyColumn);
+      W.hoff[j] = off;
+      W.hsize[j] = m;
+      changed = 1;
+    }
+    __syncthreads();
+    int ch = changed;
+    __syncthreads();
+    if (!ch) break;
   }
-  W.low[j] = low;
-  heap_store(W, j, H);
-}
-
-// Phase B: a column whose low is owned by an earlier column adds that column.
-__global__ void k_d1_add(D1Work W, int ncols, const int32_t* __restrict__ owner, uint32_t* status) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ncols) return;
-  int ci = W.lowc[j];
-  if (ci < 0) return;
-  int o = owner[ci];
-  if (o == j) return;
-  Heap H = heap_of(W, j);
-  uint32_t osz = W.hsize[o];
-  const unsigned long long* oh = W.pool + W.hoff[o];
-  for (uint32_t t = 0; t < osz; ++t)
-    if (!heap_push(W, H, oh[t], status)) break;
-  heap_store(W, j, H);
-  W.low[j] = 0;
-  W.lowc[j] = -1;
-  W.flags[0] = 1;
-}
-
-__global__ void k_d1_finish(D1Work W, int ncols, int32_t* __restrict__ d1_edge) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < ncols) d1_edge[W.cols[j]] = W.lowc[j];
+  for (int j = threadIdx.x; j < ncols; j += kUFT)
+    d1_edge[W.cols[j]] = W.hsize[j] > 0 ? (int)W.pool[W.hoff[j]] : -1;
 }
 
 void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
@@ -544,7 +603,6 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   k_d1_select<<<(n2 + 255) / 256, 256, 0, st>>>(n2, P.d2_max, flag); note_launch();
   exclusive_scan_u32(flag, pos, n2, sums, st);
   k_d1_gather<<<(n2 + 255) / 256, 256, 0, st>>>(n2, flag, pos, W.cols, P.d1_edge); note_launch();
-  // number of columns = pos[n2-1] + flag[n2-1]
   uint32_t tail[2];
   cudaMemcpyAsync(&tail[0], pos + n2 - 1, 4, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&tail[1], flag + n2 - 1, 4, cudaMemcpyDeviceToHost, st);
@@ -562,20 +620,8 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.L = L;
   c.d0_killed = P.d0_killed;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
-  int nb = (max(ncols, n1) + 255) / 256;
-  k_d1_init<<<nb, 256, 0, st>>>(c, W, ncols, W.owner, n1, status); note_launch();
-  for (int round = 0; round < 1 << 20; ++round) {
-    cudaMemsetAsync(W.flags, 0, 4, st);
-    k_d1_expand<<<(ncols + 127) / 128, 128, 0, st>>>(c, W, ncols, W.owner, status); note_launch();
-    k_d1_add<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, W.owner, status); note_launch();
-    cudaMemcpyAsync(h_flags, W.flags, 4, cudaMemcpyDeviceToHost, st);
-    uint32_t hs = 0;
-    cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    if (hs & (kErrPool | kErrEmptyColumn | kErrInconsistent | kErrRounds)) break;
-    if (h_flags[0] == 0) break;
-  }
-  k_d1_finish<<<(ncols + 255) / 256, 256, 0, st>>>(W, ncols, P.d1_edge); note_launch();
+  k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
+  k_d1_reduce<<<1, kUFT, 0, st>>>(W, ncols, n1, P.d1_edge, status); note_launch();
 }
 
 }  // namespace tsf

@@ -285,3 +285,64 @@ __device__ inline int star_chain(const Star& s, int x, int8_t* pa, int8_t* pb, i
 }
 
 }  // namespace tsf
+
+namespace tsf {
+
+// For every lower neighbour x killed in the forward sweep: y_of[x] = the
+// older representative its component merged with, path_of[x] = the link
+// edges (bitmask) of the forest path x ... y through the killing edge.  The
+// reduced column of the triangle paired with w*x is w*x + w*y + path.
+__device__ inline void star_chains(const Star& s, int8_t* y_of, uint64_t* path_of) {
+  int8_t par[14];
+  uint32_t tadj[14];
+  for (int i = 0; i < 14; ++i) {
+    par[i] = (int8_t)i;
+    tadj[i] = 0;
+    y_of[i] = -1;
+    path_of[i] = 0;
+  }
+  auto tree_path = [&](int src, int dst) -> uint64_t {
+    if (src == dst) return 0ull;
+    int8_t prev[14];
+    for (int i = 0; i < 14; ++i) prev[i] = -1;
+    uint32_t seen = 1u << src, frontier = 1u << src;
+    while (frontier && !((seen >> dst) & 1u)) {
+      uint32_t nf = 0;
+      for (uint32_t fm = frontier; fm; fm &= fm - 1) {
+        int u = __ffs(fm) - 1;
+        for (uint32_t m = tadj[u] & ~seen; m; m &= m - 1) {
+          int w2 = __ffs(m) - 1;
+          prev[w2] = (int8_t)u;
+          seen |= 1u << w2;
+          nf |= 1u << w2;
+        }
+      }
+      frontier = nf;
+    }
+    uint64_t bits = 0;
+    for (int c = dst; c != src && prev[c] >= 0; c = prev[c]) bits ^= 1ull << c_geo.edge_idx[c][prev[c]];
+    return bits;
+  };
+  for (int p = 1; p < s.nl; ++p) {
+    int a = s.by_pos[p];
+    uint32_t nb = c_geo.adj[a] & s.lower;
+    for (int q = 0; q < p; ++q) {
+      int b = s.by_pos[q];
+      if (!((nb >> b) & 1u)) continue;
+      int ra = uf_find(par, p), rb = uf_find(par, q);
+      if (ra == rb) continue;
+      int young = ra > rb ? ra : rb, old = ra > rb ? rb : ra;
+      int x = s.by_pos[young];
+      int in_x = (ra == young) ? a : b;
+      int other = (ra == young) ? b : a;
+      int y = s.by_pos[old];
+      y_of[x] = (int8_t)y;
+      path_of[x] = tree_path(x, in_x) ^ (1ull << c_geo.edge_idx[a][b]) ^ tree_path(other, y);
+      par[young] = (int8_t)old;
+      tadj[a] |= 1u << b;
+      tadj[b] |= 1u << a;
+    }
+  }
+}
+
+}  // namespace tsf
