@@ -257,7 +257,11 @@ def run_gpu(args):
         "solver": {"points_per_step": float(np.mean([s["n_points"] for s in stats])),
                    "critical_per_step": np.mean([s["n_critical"] for s in stats], axis=0).tolist(),
                    "still_fraction": float(np.mean([s["n_still"] / max(s["n_points"], 1) for s in stats])),
-                   "gradient_vertices_per_step": n_grad, "updated_vertices_per_step":
+                   "gradient_vertices_per_step": n_grad,
+                   "d1_columns": float(np.mean([s["d1_columns"] for s in stats])),
+                   "d1_lower_stars_visited": float(np.mean([s["d1_blocks_total"] for s in stats])),
+                   "d1_lower_stars_max_column": float(np.mean([s["d1_blocks_max"] for s in stats])),
+                   "updated_vertices_per_step":
                        float(np.mean([s["n_updated_vertices"] for s in stats])),
                    "step_ms": [round(x, 3) for x in step_ms]},
         "gpu_launches": int(launches),

@@ -98,6 +98,9 @@ typedef struct {
   int64_t n_nonstill_matched; /* non-still points matched to a target */
   int64_t n_updated_vertices; /* vertices whose value the last step changed */
   int64_t n_gradient_vertices;/* lower stars recomputed by the last diagram */
+  int64_t d1_columns;         /* saddle-saddle columns (negative critical triangles) */
+  int64_t d1_blocks_total;    /* lower stars visited to build their Morse boundaries */
+  int64_t d1_blocks_max;      /* ... by the largest column */
   double ms_diagram, ms_assign, ms_step; /* host wall time of the three stages */
 } tsf_stats;
 

@@ -487,6 +487,7 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
   push_if_positive(c, W, H, v0, a0, status);
   push_if_positive(c, W, H, v0, b0, status);
   push_if_positive(c, W, H, a0, b0, status);
+  int nblocks = 0;
   for (int step = 0;; ++step) {
     if (step >= kD1StepLimit) {
       atomicOr(status, kErrRounds);
@@ -503,6 +504,7 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
       m ^= 1u << nbr_of_pair(c.d, v, c.order[(uint32_t)(e & 0xFFFFFFFFull)]);
     }
     if (!m) continue;
+    ++nblocks;
     Rec r = ld_rec(c.rec, v);
     uint32_t crit = rec_crit_edges(r);
     Star s;
@@ -535,6 +537,8 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
   }
   W.hoff[j] = out.off;
   W.hsize[j] = out.size;
+  atomicAdd(&W.stats[0], (unsigned long long)nblocks);
+  atomicMax(&W.stats[1], (unsigned long long)nblocks);
 }
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
@@ -620,6 +624,7 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.L = L;
   c.d0_killed = P.d0_killed;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
+  cudaMemsetAsync(W.stats, 0, 16, st);
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
   k_d1_reduce<<<1, kUFT, 0, st>>>(W, ncols, n1, P.d1_edge, status); note_launch();
 }

@@ -87,6 +87,8 @@ struct tsf_field {
   double loss = 0, loss0 = 0;
   unsigned long long counts[4] = {0, 0, 0, 0};
   int64_t n_updated = 0, n_gradient = 0;
+  unsigned long long d1_stats[2] = {0, 0};
+  int d1_cols = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
   // profiling: event pairs recorded around stages, resolved after each call
@@ -383,12 +385,20 @@ int compute_diagram(tsf_field* F, bool incremental) {
     F->W.pool_cap = F->pool_cap;
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
+    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 2));
     ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
     launch_d1(F->d, F->nd, F->L, F->n1, F->n2, F->rank, F->order, F->rec, F->c1base, F->W, F->PO, F->status,
               F->h_flags, st);
     stage_end(F, kD1);
     s = read_status(F);
+    F->d1_cols = F->n2 > 0 ? F->h_flags[1] : 0;
+    if (F->d1_cols > 0) {
+      ck(cudaMemcpyAsync(F->d1_stats, F->W.stats, 16, cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+    } else {
+      F->d1_stats[0] = F->d1_stats[1] = 0;
+    }
     if ((s & kErrPool) && attempt < 6) continue;
     break;
   }
@@ -447,6 +457,9 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
   out->n_nonstill_matched = (int64_t)F->counts[2];
   out->n_updated_vertices = F->n_updated;
   out->n_gradient_vertices = F->n_gradient;
+  out->d1_columns = F->d1_cols;
+  out->d1_blocks_total = (int64_t)F->d1_stats[0];
+  out->d1_blocks_max = (int64_t)F->d1_stats[1];
   out->ms_diagram = F->ms_diag;
   out->ms_assign = F->ms_assign;
   out->ms_step = F->ms_step;
@@ -590,6 +603,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->W.pool);
   dev_free(F->W.pool_head);
   dev_free(F->W.flags);
+  dev_free(F->W.stats);
   SolverBufs& B = F->B;
   dev_free(F->pts);
   dev_free(F->prev);

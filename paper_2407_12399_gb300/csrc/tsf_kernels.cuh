@@ -84,6 +84,7 @@ struct D1Work {
   uint32_t pool_cap;
   uint32_t* pool_head;
   int32_t* flags;         // [0] changed, [1] number of candidate columns
+  unsigned long long* stats;  // [0] lower stars visited, [1] max per column
 };
 // returns 0 on success, otherwise a status bit (kErrPool: retry with a larger pool)
 void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
