@@ -474,6 +474,7 @@ constexpr int kD1StepLimit = 1 << 24;
 __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ncols) return;
+  if (W.redo && !W.redo[j]) return;
   W.hsize[j] = 0;
   W.hoff[j] = 0;
   Vec hv, out;
@@ -539,6 +540,277 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
   W.hsize[j] = out.size;
   atomicAdd(&W.stats[0], (unsigned long long)nblocks);
   atomicMax(&W.stats[1], (unsigned long long)nblocks);
+}
+
+// ---------------------------------------------------------------------------
+// Phase 1, warp per column.  Pending entries are kept as (column, vertex) ->
+// parity mask over the 14 edge directions of the vertex's lower star, in a
+// hash table; the frontier is the descending list of ranks with a pending
+// mask, in shared memory.  Each round the warp takes the 32 highest pending
+// lower stars, one per lane.  The projection is linear, so a lower star that
+// receives entries after it was processed simply comes back.
+// ---------------------------------------------------------------------------
+constexpr int kFront = 4096;
+
+__device__ __forceinline__ uint32_t hslot(const D1Work& W, unsigned long long key, uint32_t* status) {
+  uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
+  for (uint32_t probe = 0; probe < W.hash_cap; ++probe) {
+    unsigned long long k = W.hkeys[h];
+    if (k == key) return h;
+    if (k == ~0ull) {
+      unsigned long long old = atomicCAS(&W.hkeys[h], ~0ull, key);
+      if (old == ~0ull || old == key) return h;
+    }
+    h = (h + 1) & (W.hash_cap - 1);
+  }
+  atomicOr(status, kErrPool);
+  return 0xFFFFFFFFu;
+}
+
+__global__ void k_hash_clear(D1Work W) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < W.hash_cap) {
+    W.hkeys[i] = ~0ull;
+    W.hmask[i] = 0;
+  }
+}
+
+__device__ __forceinline__ int warp_exscan(int v, int& total) {
+  int lane = threadIdx.x & 31;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  return inc - v;
+}
+
+constexpr int kNewPerLane = 48;
+
+__global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
+  __shared__ uint32_t fa[kFront], fb[kFront];
+  __shared__ uint32_t stage[2048];  // >= next power of two of 32 * kNewPerLane
+  __shared__ unsigned long long outv[256];
+  const int lane = threadIdx.x;
+  const int j = blockIdx.x;
+  if (j >= ncols) return;
+  unsigned long long colkey = (unsigned long long)j << 32;
+  uint32_t* front = fa;
+  uint32_t* other = fb;
+  int nf = 0;
+  int nout = 0;
+  bool failed = false;
+  // seed: the boundary of the critical triangle, as parity masks
+  if (lane == 0) {
+    uint32_t ve = c.L.c2_ve[W.cols[j]];
+    uint32_t v0 = ve >> 6;
+    int e0 = (int)(ve & 63u);
+    uint32_t ends[3][2] = {{v0, (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][0]])},
+                           {v0, (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][1]])},
+                           {(uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][0]]),
+                            (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][1]])}};
+    for (int k = 0; k < 3; ++k) {
+      uint32_t p = ends[k][0], q = ends[k][1];
+      uint32_t rp = c.rank[p], rq = c.rank[q];
+      uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
+      uint32_t h = hslot(W, colkey | hi, status);
+      if (h == 0xFFFFFFFFu) continue;
+      uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo));
+      if (old == 0) {
+        // insert rank(hi) into the (tiny) front, kept descending and unique
+        uint32_t r = max(rp, rq);
+        int pos = 0;
+        while (pos < nf && front[pos] > r) ++pos;
+        if (pos == nf || front[pos] != r) {
+          for (int t = nf; t > pos; --t) front[t] = front[t - 1];
+          front[pos] = r;
+          ++nf;
+        }
+      }
+    }
+  }
+  nf = __shfl_sync(0xFFFFFFFFu, nf, 0);
+  __syncwarp();
+  int visits = 0;
+  for (int round = 0; nf > 0; ++round) {
+    if (round > kD1StepLimit) {
+      if (lane == 0) atomicOr(status, kErrRounds);
+      failed = true;
+      break;
+    }
+    int nb = min(32, nf);
+    int nnew = 0;
+    uint32_t mynew[kNewPerLane];
+    int myout = 0;
+    unsigned long long myouts[14];
+    bool overflow = false;
+    if (lane < nb) {
+      uint32_t r = front[lane];
+      uint32_t v = c.order[r];
+      uint32_t h = hslot(W, colkey | v, status);
+      uint32_t m = h == 0xFFFFFFFFu ? 0u : atomicExch(&W.hmask[h], 0u);
+      if (m) {
+        ++visits;
+        Rec rc = ld_rec(c.rec, v);
+        uint32_t crit = rec_crit_edges(rc);
+        Star s;
+        star_load(s, c.d, v, c.rank);
+        int8_t y_of[14];
+        uint64_t path_of[14];
+        star_chains(s, y_of, path_of);
+        for (int p = s.nl - 1; p >= 1; --p) {
+          int x = s.by_pos[p];
+          if (!((m >> x) & 1u)) continue;
+          m &= ~(1u << x);
+          if ((crit >> x) & 1u) {
+            int ci = crit_edge_index(c, v, rc, x);
+            if (ci >= 0 && !c.d0_killed[ci]) myouts[myout++] = (unsigned long long)ci;
+            continue;
+          }
+          int y = y_of[x];
+          if (y < 0) {
+            atomicOr(status, kErrInconsistent);
+            continue;
+          }
+          if (y != s.by_pos[0]) m ^= 1u << y;
+          for (uint64_t pm = path_of[x]; pm; pm &= pm - 1) {
+            int le = __ffsll((long long)pm) - 1;
+            int na = c_geo.edge[le][0], nbv = c_geo.edge[le][1];
+            uint32_t ra = s.nr[na], rb = s.nr[nbv];
+            int hn = ra > rb ? na : nbv, ln = ra > rb ? nbv : na;
+            uint32_t hv = (uint32_t)((int32_t)v + c.nd.d[hn]);
+            // direction of the lower end seen from the higher end
+            int dir = nbr_index(c_geo.off[ln][0] - c_geo.off[hn][0], c_geo.off[ln][1] - c_geo.off[hn][1],
+                                c_geo.off[ln][2] - c_geo.off[hn][2]);
+            uint32_t hh = hslot(W, colkey | hv, status);
+            if (hh == 0xFFFFFFFFu) continue;
+            uint32_t bit = 1u << dir;
+            uint32_t old = atomicXor(&W.hmask[hh], bit);
+            if (old == 0) {
+              if (nnew < kNewPerLane) mynew[nnew++] = max(ra, rb);
+              else overflow = true;
+            }
+          }
+        }
+      }
+    }
+    if (__any_sync(0xFFFFFFFFu, overflow)) {
+      failed = true;
+      break;
+    }
+    // outputs of this round
+    int otot;
+    int ooff = warp_exscan(myout, otot);
+    if (otot > 0) {
+      if (nout + otot > 256) {
+        failed = true;
+        break;
+      }
+      for (int k = 0; k < myout; ++k) outv[nout + ooff + k] = myouts[k];
+      nout += otot;
+    }
+    // new ranks: stage, sort descending (bitonic), merge with front[nb:]
+    int ntot;
+    int noff = warp_exscan(nnew, ntot);
+    for (int k = 0; k < nnew; ++k) stage[noff + k] = mynew[k];
+    int n2 = 1;
+    while (n2 < ntot) n2 <<= 1;
+    for (int k = ntot + lane; k < n2; k += 32) stage[k] = 0;
+    __syncwarp();
+    for (int size = 2; size <= n2; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = lane; i < n2; i += 32) {
+          int jx = i ^ stride;
+          if (jx > i) {
+            bool desc = (i & size) == 0;
+            uint32_t a = stage[i], b = stage[jx];
+            if ((a < b) == desc) {
+              stage[i] = b;
+              stage[jx] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    // merge front[nb..nf) (descending, unique) with stage[0..ntot) (descending)
+    int rest = nf - nb;
+    if (rest + ntot > kFront) {
+      failed = true;
+      break;
+    }
+    // output position k takes i elements from A = front[nb..nf) and k-i from
+    // B = stage[0..ntot), both descending (merge path, A first on ties)
+    int total = rest + ntot;
+    for (int k = lane; k < total; k += 32) {
+      int lo = max(0, k - ntot), hi = min(k, rest);
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (front[nb + mid] >= stage[k - mid - 1]) lo = mid + 1;
+        else hi = mid;
+      }
+      int i = lo, jb = k - lo;
+      other[k] = (i < rest && (jb >= ntot || front[nb + i] >= stage[jb])) ? front[nb + i] : stage[jb];
+    }
+    __syncwarp();
+    // unique (keep the first of equal neighbours)
+    int keep_total = 0;
+    for (int base = 0; base < total; base += 32) {
+      int k = base + lane;
+      int keep = (k < total) && (k == 0 || other[k] != other[k - 1]);
+      uint32_t val = k < total ? other[k] : 0;
+      int t;
+      int off = warp_exscan(keep, t);
+      __syncwarp();
+      if (keep) front[keep_total + off] = val;
+      keep_total += t;
+      __syncwarp();
+    }
+    nf = keep_total;
+    __syncwarp();
+  }
+  // fallback for this column, or the sorted, mod-2 reduced output
+  int vsum = visits;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) vsum += __shfl_down_sync(0xFFFFFFFFu, vsum, o);
+  if (failed) {
+    if (lane == 0) {
+      W.redo[j] = 1;
+      W.hsize[j] = 0;
+    }
+    return;
+  }
+  if (lane == 0) {
+    // insertion sort descending, then cancel equal pairs
+    for (int i = 1; i < nout; ++i) {
+      unsigned long long t = outv[i];
+      int k = i - 1;
+      while (k >= 0 && outv[k] < t) {
+        outv[k + 1] = outv[k];
+        --k;
+      }
+      outv[k + 1] = t;
+    }
+    int m = 0;
+    for (int i = 0; i < nout;) {
+      int k = i;
+      while (k < nout && outv[k] == outv[i]) ++k;
+      if ((k - i) & 1) outv[m++] = outv[i];
+      i = k;
+    }
+    Vec o2;
+    if (vec_alloc(W, o2, max(m, 1), status)) {
+      for (int i = 0; i < m; ++i) o2.h[i] = outv[i];
+      W.hoff[j] = o2.off;
+      W.hsize[j] = m;
+    } else {
+      W.hsize[j] = 0;
+    }
+    W.redo[j] = 0;
+    atomicAdd(&W.stats[0], (unsigned long long)vsum);
+    atomicMax(&W.stats[1], (unsigned long long)vsum);
+  }
 }
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
@@ -625,6 +897,8 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.d0_killed = P.d0_killed;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, 16, st);
+  k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();
+  k_d1_morse_warp<<<ncols, 32, 0, st>>>(c, W, ncols, status); note_launch();
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
   k_d1_reduce<<<1, kUFT, 0, st>>>(W, ncols, n1, P.d1_edge, status); note_launch();
 }

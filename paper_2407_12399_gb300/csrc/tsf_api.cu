@@ -165,6 +165,7 @@ void grow_crit(tsf_field* F, int n0, int n1, int n2, int n3) {
     dev_free(F->W.hcap);
     dev_free(F->W.hsize);
     dev_free(F->W.lowc);
+    dev_free(F->W.redo);
     ck(dev_alloc(&F->L.c2_ve, c2));
     ck(dev_alloc(&F->PO.d2_max, c2));
     ck(dev_alloc(&F->PO.d1_edge, c2));
@@ -174,6 +175,7 @@ void grow_crit(tsf_field* F, int n0, int n1, int n2, int n3) {
     ck(dev_alloc(&F->W.hcap, c2));
     ck(dev_alloc(&F->W.hsize, c2));
     ck(dev_alloc(&F->W.lowc, c2));
+    ck(dev_alloc(&F->W.redo, c2));
     F->cap_c2 = c2;
   }
   if (c3 != F->cap_c3) {
@@ -386,6 +388,16 @@ int compute_diagram(tsf_field* F, bool incremental) {
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
     if (!F->W.stats) ck(dev_alloc(&F->W.stats, 2));
+    uint32_t hwant = 1u << 20;
+    while (hwant < (uint32_t)std::min<int64_t>((int64_t)256 * std::max(F->n2, 1), (int64_t)1 << 28)) hwant <<= 1;
+    hwant = (uint32_t)std::min<int64_t>((int64_t)hwant << attempt, (int64_t)1 << 29);
+    if (hwant > F->W.hash_cap) {
+      dev_free(F->W.hkeys);
+      dev_free(F->W.hmask);
+      ck(dev_alloc(&F->W.hkeys, hwant));
+      ck(dev_alloc(&F->W.hmask, hwant));
+      F->W.hash_cap = hwant;
+    }
     ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
     launch_d1(F->d, F->nd, F->L, F->n1, F->n2, F->rank, F->order, F->rec, F->c1base, F->W, F->PO, F->status,
@@ -604,6 +616,9 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->W.pool_head);
   dev_free(F->W.flags);
   dev_free(F->W.stats);
+  dev_free(F->W.hkeys);
+  dev_free(F->W.hmask);
+  dev_free(F->W.redo);
   SolverBufs& B = F->B;
   dev_free(F->pts);
   dev_free(F->prev);

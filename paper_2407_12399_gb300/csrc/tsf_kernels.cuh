@@ -85,6 +85,11 @@ struct D1Work {
   uint32_t* pool_head;
   int32_t* flags;         // [0] changed, [1] number of candidate columns
   unsigned long long* stats;  // [0] lower stars visited, [1] max per column
+  // (column, vertex) -> parity mask of pending entries, open addressing
+  unsigned long long* hkeys;
+  uint32_t* hmask;
+  uint32_t hash_cap;      // power of two
+  int32_t* redo;          // columns whose warp frontier overflowed
 };
 // returns 0 on success, otherwise a status bit (kErrPool: retry with a larger pool)
 void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
