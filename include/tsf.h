@@ -185,6 +185,30 @@ const char* tsf_stage_name(int stage);
 /* Number of kernels this library has launched in this process. */
 int64_t tsf_kernel_launches(void);
 
+/* Zero-persistence pairs without device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc,
+ * e.g. code running inside a framework that owns all device memory through
+ * its own pool, or a latency-critical loop where cudaMalloc's implicit
+ * device-wide synchronisation is not acceptable.  Same result as
+ * tsf_zero_pairs for the same values (as a set; the order is unspecified).
+ *
+ * values: device pointer to lx*ly*lz floats (layout as tsf_create_field);
+ * out: device pointer to cap_pairs pairs (out[2k] = birth cell, out[2k+1] =
+ * death cell), may be NULL when cap_pairs is 0; *n_out (host) receives the
+ * number of pairs, TSF_ECAPACITY when it exceeds cap_pairs.  lx*ly*lz above
+ * TSF_STATIC_MAX_VERTICES is rejected with TSF_EINVAL.
+ *
+ * All intermediate data lives in one fixed device array of about 6.4 MB
+ * (sized for TSF_STATIC_MAX_VERTICES vertices) that every GPU loading this
+ * library holds until the process exits.  Every call shares that array and
+ * finds the previous call's contents in it; calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture. */
+#define TSF_STATIC_MAX_VERTICES 262144
+int tsf_zero_pairs_static(int lx, int ly, int lz, const float* values, uint64_t* out, int64_t cap_pairs,
+                          int64_t* n_out, void* cuda_stream);
+
 /* Human-readable name of a status code. */
 const char* tsf_status_string(int status);
 

@@ -65,7 +65,7 @@ class tsf_stats(ctypes.Structure):
 EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_set_signal_threshold",
            "tsf_set_signal_pairs", "tsf_solver_step", "tsf_simplify", "tsf_get_field", "tsf_set_field",
            "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
-           "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches")
+           "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static")
 TSF_NSTAGES = 10
 
 _lib = None
@@ -94,6 +94,7 @@ def lib():
             "tsf_get_assignment": [P, P, P, I64, ctypes.POINTER(I64)],
             "tsf_get_targets": [P, P, I64, ctypes.POINTER(I64)],
             "tsf_zero_pairs": [P, P, I64, ctypes.POINTER(I64)],
+            "tsf_zero_pairs_static": [I, I, I, P, P, I64, ctypes.POINTER(I64), P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -189,6 +190,13 @@ def tsf_get_targets(h, out_ptr, cap):
 def tsf_zero_pairs(h, out_ptr, cap):
     n = ctypes.c_int64(0)
     r = lib().tsf_zero_pairs(h, out_ptr, cap, ctypes.byref(n))
+    return r, n.value
+
+
+def tsf_zero_pairs_static(lx, ly, lz, values_ptr, out_ptr, cap, cuda_stream=0):
+    """No-allocation variant of tsf_zero_pairs (device pointers in and out)."""
+    n = ctypes.c_int64(0)
+    r = lib().tsf_zero_pairs_static(lx, ly, lz, values_ptr, out_ptr, cap, ctypes.byref(n), cuda_stream or None)
     return r, n.value
 
 
