@@ -208,7 +208,7 @@ def run_gpu(args):
     # values, set the signal, simplify to the paper's stop rule, read back
     e2e = None
     tts = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         host = np.ascontiguousarray(f0)
         t = time.perf_counter()
         h = tsf.tsf_create_field(SHAPE[2], SHAPE[1], SHAPE[0], host.ctypes.data, 0, stream.cuda_stream)
@@ -283,6 +283,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end solve (short profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

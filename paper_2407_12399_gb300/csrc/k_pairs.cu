@@ -660,6 +660,9 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
         int8_t y_of[14];
         uint64_t path_of[14];
         star_chains(s, y_of, path_of);
+        // the link edges pushed to lower stars, accumulated per target star
+        // (every target is a lower neighbour of v) before touching the table
+        uint64_t path = 0;
         for (int p = s.nl - 1; p >= 1; --p) {
           int x = s.by_pos[p];
           if (!((m >> x) & 1u)) continue;
@@ -675,26 +678,32 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
             continue;
           }
           if (y != s.by_pos[0]) m ^= 1u << y;
-          for (uint64_t pm = path_of[x]; pm; pm &= pm - 1) {
-            int le = __ffsll((long long)pm) - 1;
-            int na = c_geo.edge[le][0], nbv = c_geo.edge[le][1];
-            uint32_t ra = s.nr[na], rb = s.nr[nbv];
-            int hn = ra > rb ? na : nbv, ln = ra > rb ? nbv : na;
-            uint32_t hv = (uint32_t)((int32_t)v + c.nd.d[hn]);
-            // direction of the lower end seen from the higher end
-            int dir = nbr_index(c_geo.off[ln][0] - c_geo.off[hn][0], c_geo.off[ln][1] - c_geo.off[hn][1],
-                                c_geo.off[ln][2] - c_geo.off[hn][2]);
-            uint32_t hh = hslot(W, colkey | hv, status);
-            if (hh == 0xFFFFFFFFu) continue;
-            uint32_t bit = 1u << dir;
-            uint32_t old = atomicXor(&W.hmask[hh], bit);
-            if (old == 0) {
-              if (nnew < kNewPerLane) mynew[nnew++] = max(ra, rb);
-              else overflow = true;
-            }
-          }
+          path ^= path_of[x];
         }
-      }
+        uint32_t tmask[14];
+#pragma unroll
+        for (int k = 0; k < 14; ++k) tmask[k] = 0;
+        for (uint64_t pm = path; pm; pm &= pm - 1) {
+          int le = __ffsll((long long)pm) - 1;
+          int na = c_geo.edge[le][0], nbv = c_geo.edge[le][1];
+          bool a_hi = s.nr[na] > s.nr[nbv];
+          int hn = a_hi ? na : nbv, ln = a_hi ? nbv : na;
+          int dir = nbr_index(c_geo.off[ln][0] - c_geo.off[hn][0], c_geo.off[ln][1] - c_geo.off[hn][1],
+                              c_geo.off[ln][2] - c_geo.off[hn][2]);
+          tmask[hn] ^= 1u << dir;
+        }
+#pragma unroll
+        for (int hn = 0; hn < 14; ++hn) {
+          if (!tmask[hn]) continue;
+          uint32_t hv = (uint32_t)((int32_t)v + c.nd.d[hn]);
+          uint32_t hh = hslot(W, colkey | hv, status);
+          if (hh == 0xFFFFFFFFu) continue;
+          uint32_t old = atomicXor(&W.hmask[hh], tmask[hn]);
+          if (old == 0) {
+            if (nnew < kNewPerLane) mynew[nnew++] = s.nr[hn];
+            else overflow = true;
+          }
+        }      }
     }
     if (__any_sync(0xFFFFFFFFu, overflow)) {
       failed = true;

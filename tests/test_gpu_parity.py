@@ -59,6 +59,7 @@ NAMED = {
     "ring_21": lambda: S.ring_distance((21, 21, 21), (0.5, 0.5, 0.5), 0.3),
     "peak_13": lambda: S.gaussian_bumps((11, 12, 13), [(0.52, 0.47, 0.5)], [0.18], [1.0]),
     "filament_40": lambda: S.filament_field((40, 40, 40), seed=1, n_loops=12),
+    "filament_64": lambda: S.filament_field((64, 64, 64), seed=1, n_loops=24),
     "linear": lambda: S.linear_field((8, 7, 6)),
     "constant": lambda: np.zeros((6, 5, 4), np.float32),
 }
