@@ -261,6 +261,8 @@ def run_gpu(args):
                    "d1_columns": float(np.mean([s["d1_columns"] for s in stats])),
                    "d1_lower_stars_visited": float(np.mean([s["d1_blocks_total"] for s in stats])),
                    "d1_lower_stars_max_column": float(np.mean([s["d1_blocks_max"] for s in stats])),
+                   "d1_rounds_total": float(np.mean([s["d1_rounds_total"] for s in stats])),
+                   "d1_rounds_max_column": float(np.mean([s["d1_rounds_max"] for s in stats])),
                    "updated_vertices_per_step":
                        float(np.mean([s["n_updated_vertices"] for s in stats])),
                    "step_ms": [round(x, 3) for x in step_ms]},

@@ -101,6 +101,8 @@ typedef struct {
   int64_t d1_columns;         /* saddle-saddle columns (negative critical triangles) */
   int64_t d1_blocks_total;    /* lower stars visited to build their Morse boundaries */
   int64_t d1_blocks_max;      /* ... by the largest column */
+  int64_t d1_rounds_total;    /* rounds (32 lower stars at most each) over all columns */
+  int64_t d1_rounds_max;      /* ... of the longest column */
   double ms_diagram, ms_assign, ms_step; /* host wall time of the three stages */
 } tsf_stats;
 

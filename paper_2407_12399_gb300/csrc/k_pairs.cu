@@ -634,7 +634,9 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
   nf = __shfl_sync(0xFFFFFFFFu, nf, 0);
   __syncwarp();
   int visits = 0;
+  int rounds = 0;
   for (int round = 0; nf > 0; ++round) {
+    ++rounds;
     if (round > kD1StepLimit) {
       if (lane == 0) atomicOr(status, kErrRounds);
       failed = true;
@@ -819,6 +821,8 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
     W.redo[j] = 0;
     atomicAdd(&W.stats[0], (unsigned long long)vsum);
     atomicMax(&W.stats[1], (unsigned long long)vsum);
+    atomicAdd(&W.stats[2], (unsigned long long)rounds);
+    atomicMax(&W.stats[3], (unsigned long long)rounds);
   }
 }
 
@@ -905,7 +909,7 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.L = L;
   c.d0_killed = P.d0_killed;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
-  cudaMemsetAsync(W.stats, 0, 16, st);
+  cudaMemsetAsync(W.stats, 0, 32, st);
   k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();
   k_d1_morse_warp<<<ncols, 32, 0, st>>>(c, W, ncols, status); note_launch();
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();

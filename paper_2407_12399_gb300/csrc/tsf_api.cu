@@ -87,7 +87,7 @@ struct tsf_field {
   double loss = 0, loss0 = 0;
   unsigned long long counts[4] = {0, 0, 0, 0};
   int64_t n_updated = 0, n_gradient = 0;
-  unsigned long long d1_stats[2] = {0, 0};
+  unsigned long long d1_stats[4] = {0, 0, 0, 0};
   int d1_cols = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
@@ -387,7 +387,7 @@ int compute_diagram(tsf_field* F, bool incremental) {
     F->W.pool_cap = F->pool_cap;
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
-    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 2));
+    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 4));
     uint32_t hwant = 1u << 20;
     while (hwant < (uint32_t)std::min<int64_t>((int64_t)256 * std::max(F->n2, 1), (int64_t)1 << 28)) hwant <<= 1;
     hwant = (uint32_t)std::min<int64_t>((int64_t)hwant << attempt, (int64_t)1 << 29);
@@ -406,10 +406,10 @@ int compute_diagram(tsf_field* F, bool incremental) {
     s = read_status(F);
     F->d1_cols = F->n2 > 0 ? F->h_flags[1] : 0;
     if (F->d1_cols > 0) {
-      ck(cudaMemcpyAsync(F->d1_stats, F->W.stats, 16, cudaMemcpyDeviceToHost, st));
+      ck(cudaMemcpyAsync(F->d1_stats, F->W.stats, 32, cudaMemcpyDeviceToHost, st));
       ck(cudaStreamSynchronize(st));
     } else {
-      F->d1_stats[0] = F->d1_stats[1] = 0;
+      F->d1_stats[0] = F->d1_stats[1] = F->d1_stats[2] = F->d1_stats[3] = 0;
     }
     if ((s & kErrPool) && attempt < 6) continue;
     break;
@@ -472,6 +472,8 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
   out->d1_columns = F->d1_cols;
   out->d1_blocks_total = (int64_t)F->d1_stats[0];
   out->d1_blocks_max = (int64_t)F->d1_stats[1];
+  out->d1_rounds_total = (int64_t)F->d1_stats[2];
+  out->d1_rounds_max = (int64_t)F->d1_stats[3];
   out->ms_diagram = F->ms_diag;
   out->ms_assign = F->ms_assign;
   out->ms_step = F->ms_step;

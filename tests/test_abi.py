@@ -61,4 +61,4 @@ def test_status_strings_and_argument_checks_need_no_gpu(libpath):
 def test_struct_layouts():
     assert ctypes.sizeof(tsf.tsf_pair) == 40
     assert ctypes.sizeof(tsf.tsf_params) == 24
-    assert ctypes.sizeof(tsf.tsf_stats) == 176
+    assert ctypes.sizeof(tsf.tsf_stats) == 192
