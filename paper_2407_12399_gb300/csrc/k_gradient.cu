@@ -10,8 +10,8 @@ namespace tsf {
 // (Section 4.2, fast persistence update); the others keep last iteration's
 // record, which stays exact because their lower stars did not change.
 __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint8_t* __restrict__ dirty,
-                           Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, uint32_t* status,
-                           unsigned long long* n_recomputed) {
+                           Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
+                           uint32_t* status, unsigned long long* n_recomputed) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool work = v < d.nv;
   if (work && dirty) {
@@ -42,6 +42,28 @@ __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint
   dst[0] = make_uint4(r.w[0], r.w[1], r.w[2], r.w[3]);
   dst[1] = make_uint4(r.w[4], r.w[5], r.w[6], r.w[7]);
   vnext8[v] = (uint8_t)(r.w[0] & 15u);
+  if (tab) {
+    int8_t y_of[14];
+    uint64_t path_of[14];
+    star_chains(s, y_of, path_of);
+    D1Tab t;
+    unsigned long long bp = 0, yy = 0;
+    for (int p = 0; p < 14; ++p) bp |= (unsigned long long)((p < s.nl ? s.by_pos[p] : 15) & 15) << (4 * p);
+    bp |= (unsigned long long)s.nl << 56;
+    for (int x = 0; x < 14; ++x) yy |= (unsigned long long)((y_of[x] < 0 ? 15 : y_of[x]) & 15) << (4 * x);
+    t.q[0] = bp;
+    t.q[1] = yy;
+    for (int k = 2; k < 10; ++k) t.q[k] = 0;
+    for (int x = 0; x < 14; ++x) {
+      int off = 36 * x, wi = off >> 6, bi = off & 63;
+      t.q[2 + wi] |= path_of[x] << bi;
+      if (bi > 28) t.q[2 + wi + 1] |= path_of[x] >> (64 - bi);
+    }
+    uint4* dst4 = reinterpret_cast<uint4*>(tab + v);
+    const uint4* src4 = reinterpret_cast<const uint4*>(&t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) dst4[k] = src4[k];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -288,9 +310,9 @@ __global__ void k_zero_pairs(Dims d, const uint32_t* __restrict__ rank, unsigned
 namespace tsf {
 
 void launch_gradient(const Dims& d, const uint32_t* rank, const uint8_t* dirty, Rec* rec, uint8_t* vnext8,
-                     uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st) {
+                     D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st) {
   unsigned nb = (unsigned)((d.nv + 127) / 128);
-  k_gradient<<<nb, 128, 0, st>>>(d, rank, dirty, rec, vnext8, status, n_recomputed); note_launch();
+  k_gradient<<<nb, 128, 0, st>>>(d, rank, dirty, rec, vnext8, tab, status, n_recomputed); note_launch();
 }
 
 int crit_tiles(int64_t nv) { return (int)((nv + kCTile - 1) / kCTile); }

@@ -292,6 +292,7 @@ struct D1Ctx {
   const uint32_t* rank;
   const uint32_t* order;
   const Rec* rec;
+  const D1Tab* tab;
   const uint32_t* c1base;
   CritLists L;
   const uint8_t* d0_killed;
@@ -656,17 +657,25 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
       if (m) {
         ++visits;
         Rec rc = ld_rec(c.rec, v);
+        D1Tab t;
+        {
+          const uint4* s4 = reinterpret_cast<const uint4*>(c.tab + v);
+          uint4* d4 = reinterpret_cast<uint4*>(&t);
+#pragma unroll
+          for (int k = 0; k < 5; ++k) d4[k] = __ldg(s4 + k);
+        }
         uint32_t crit = rec_crit_edges(rc);
-        Star s;
-        star_load(s, c.d, v, c.rank);
-        int8_t y_of[14];
-        uint64_t path_of[14];
-        star_chains(s, y_of, path_of);
+        int nl = (int)((t.q[0] >> 56) & 15ull);
+        int8_t pos[14];
+#pragma unroll
+        for (int k = 0; k < 14; ++k) pos[k] = -1;
+        for (int p = 0; p < nl; ++p) pos[(t.q[0] >> (4 * p)) & 15ull] = (int8_t)p;
+        int lowest = (int)(t.q[0] & 15ull);
         // the link edges pushed to lower stars, accumulated per target star
         // (every target is a lower neighbour of v) before touching the table
         uint64_t path = 0;
-        for (int p = s.nl - 1; p >= 1; --p) {
-          int x = s.by_pos[p];
+        for (int p = nl - 1; p >= 1; --p) {
+          int x = (int)((t.q[0] >> (4 * p)) & 15ull);
           if (!((m >> x) & 1u)) continue;
           m &= ~(1u << x);
           if ((crit >> x) & 1u) {
@@ -674,13 +683,13 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
             if (ci >= 0 && !c.d0_killed[ci]) myouts[myout++] = (unsigned long long)ci;
             continue;
           }
-          int y = y_of[x];
-          if (y < 0) {
+          int y = (int)((t.q[1] >> (4 * x)) & 15ull);
+          if (y == 15) {
             atomicOr(status, kErrInconsistent);
             continue;
           }
-          if (y != s.by_pos[0]) m ^= 1u << y;
-          path ^= path_of[x];
+          if (y != lowest) m ^= 1u << y;
+          path ^= tab_path(t, x);
         }
         uint32_t tmask[14];
 #pragma unroll
@@ -688,13 +697,12 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
         for (uint64_t pm = path; pm; pm &= pm - 1) {
           int le = __ffsll((long long)pm) - 1;
           int na = c_geo.edge[le][0], nbv = c_geo.edge[le][1];
-          bool a_hi = s.nr[na] > s.nr[nbv];
+          bool a_hi = pos[na] > pos[nbv];
           int hn = a_hi ? na : nbv, ln = a_hi ? nbv : na;
           int dir = nbr_index(c_geo.off[ln][0] - c_geo.off[hn][0], c_geo.off[ln][1] - c_geo.off[hn][1],
                               c_geo.off[ln][2] - c_geo.off[hn][2]);
           tmask[hn] ^= 1u << dir;
         }
-#pragma unroll
         for (int hn = 0; hn < 14; ++hn) {
           if (!tmask[hn]) continue;
           uint32_t hv = (uint32_t)((int32_t)v + c.nd.d[hn]);
@@ -702,10 +710,11 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
           if (hh == 0xFFFFFFFFu) continue;
           uint32_t old = atomicXor(&W.hmask[hh], tmask[hn]);
           if (old == 0) {
-            if (nnew < kNewPerLane) mynew[nnew++] = s.nr[hn];
+            if (nnew < kNewPerLane) mynew[nnew++] = __ldg(c.rank + hv);
             else overflow = true;
           }
-        }      }
+        }
+      }
     }
     if (__any_sync(0xFFFFFFFFu, overflow)) {
       failed = true;
@@ -882,8 +891,8 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int ncols, int n1,
 }
 
 void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
-               const uint32_t* order, const Rec* rec, const uint32_t* c1base, D1Work& W, PairOut& P,
-               uint32_t* status, int32_t* h_flags, cudaStream_t st) {
+               const uint32_t* order, const Rec* rec, const D1Tab* tab, const uint32_t* c1base, D1Work& W,
+               PairOut& P, uint32_t* status, int32_t* h_flags, cudaStream_t st) {
   if (n2 == 0) return;
   // candidate columns, in increasing triangle order
   uint32_t* flag = reinterpret_cast<uint32_t*>(W.lowc);  // scratch (n2 entries available)
@@ -905,6 +914,7 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.rank = rank;
   c.order = order;
   c.rec = rec;
+  c.tab = tab;
   c.c1base = c1base;
   c.L = L;
   c.d0_killed = P.d0_killed;

@@ -59,6 +59,7 @@ struct tsf_field {
   float* f = nullptr;
   uint32_t *order = nullptr, *rank = nullptr, *sort_scratch = nullptr;
   Rec* rec = nullptr;
+  D1Tab* tab = nullptr;
   uint8_t *vnext8 = nullptr, *dirty = nullptr;
   uint32_t *cidx = nullptr, *c1base = nullptr, *c2base = nullptr;
   int4 *tile_counts = nullptr, *totals = nullptr;
@@ -348,7 +349,7 @@ int compute_diagram(tsf_field* F, bool incremental) {
   bool inc = incremental && F->records_valid && F->dirty_valid;
   ck(cudaMemsetAsync(F->counter, 0, 8, st));
   stage_begin(F, kGrad);
-  launch_gradient(F->d, F->rank, inc ? F->dirty : nullptr, F->rec, F->vnext8, F->status, F->counter, st);
+  launch_gradient(F->d, F->rank, inc ? F->dirty : nullptr, F->rec, F->vnext8, F->tab, F->status, F->counter, st);
   stage_end(F, kGrad);
   unsigned long long ngrad = 0;
   ck(cudaMemcpyAsync(&ngrad, F->counter, 8, cudaMemcpyDeviceToHost, st));
@@ -400,8 +401,8 @@ int compute_diagram(tsf_field* F, bool incremental) {
     }
     ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
-    launch_d1(F->d, F->nd, F->L, F->n1, F->n2, F->rank, F->order, F->rec, F->c1base, F->W, F->PO, F->status,
-              F->h_flags, st);
+    launch_d1(F->d, F->nd, F->L, F->n1, F->n2, F->rank, F->order, F->rec, F->tab, F->c1base, F->W, F->PO,
+              F->status, F->h_flags, st);
     stage_end(F, kD1);
     s = read_status(F);
     F->d1_cols = F->n2 > 0 ? F->h_flags[1] : 0;
@@ -583,6 +584,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->rank);
   dev_free(F->sort_scratch);
   dev_free(F->rec);
+  dev_free(F->tab);
   dev_free(F->vnext8);
   dev_free(F->dirty);
   dev_free(F->cidx);
@@ -683,6 +685,7 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
     ck(dev_alloc(&F->rank, nv));
     ck(dev_alloc(&F->sort_scratch, sort_scratch_words(nv)));
     ck(dev_alloc(&F->rec, nv));
+    ck(dev_alloc(&F->tab, nv));
     ck(dev_alloc(&F->vnext8, nv));
     ck(dev_alloc(&F->dirty, nv));
     ck(dev_alloc(&F->cidx, nv));

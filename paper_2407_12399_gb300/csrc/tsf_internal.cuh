@@ -67,6 +67,26 @@ __host__ __device__ inline uint64_t rec_crit_tris(const Rec& r) {
 __host__ __device__ inline bool rec_has_max(const Rec& r) { return (r.w[1] >> 22) & 1u; }
 __host__ __device__ inline int rec_tet_code(const Rec& r, int tau) { return (int)rec_bits(r, 56 + 7 * tau, 7); }
 
+// Per-vertex expansion table for the saddle-saddle reduction (80 bytes):
+//   q[0] bits 0..55  lower neighbours by increasing rank (4-bit neighbour
+//                    indices, position p at bits 4p), bits 56..59 their count
+//   q[1]             y of each killed neighbour x (4 bits at 4x, 15 = none):
+//                    the older representative x's link component merged into
+//   q[2..9]          link path x..y of each killed x (36 bits at 36x): the
+//                    reduced column of the triangle paired with edge v*x is
+//                    v*x + v*y + these link edges
+struct __align__(16) D1Tab {
+  unsigned long long q[10];
+};
+
+__host__ __device__ inline uint64_t tab_path(const D1Tab& t, int x) {
+  int off = 36 * x;
+  int wi = off >> 6, bi = off & 63;
+  unsigned long long lo = t.q[2 + wi] >> bi;
+  unsigned long long hi = (bi > 28 && wi + 1 < 8) ? (t.q[2 + wi + 1] << (64 - bi)) : 0ull;
+  return (lo | hi) & ((1ull << 36) - 1);
+}
+
 // Grid helpers -------------------------------------------------------------
 struct Dims {
   int lx, ly, lz;

@@ -46,7 +46,7 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
 
 // ---- k_gradient.cu -------------------------------------------------------
 void launch_gradient(const Dims& d, const uint32_t* rank, const uint8_t* dirty, Rec* rec, uint8_t* vnext8,
-                     uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st);
+                     D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st);
 int crit_tiles(int64_t nv);
 void launch_crit_count(const Dims& d, const uint32_t* order, const Rec* rec, int4* tile_counts, int4* totals,
                        cudaStream_t st);
@@ -93,7 +93,7 @@ struct D1Work {
 };
 // returns 0 on success, otherwise a status bit (kErrPool: retry with a larger pool)
 void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
-               const uint32_t* order, const Rec* rec, const uint32_t* c1base, D1Work& W, PairOut& P,
-               uint32_t* status, int32_t* h_flags, cudaStream_t st);
+               const uint32_t* order, const Rec* rec, const D1Tab* tab, const uint32_t* c1base, D1Work& W,
+               PairOut& P, uint32_t* status, int32_t* h_flags, cudaStream_t st);
 
 }  // namespace tsf
