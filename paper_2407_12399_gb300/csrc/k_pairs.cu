@@ -636,8 +636,11 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
   __syncwarp();
   int visits = 0;
   int rounds = 0;
+  unsigned long long tv = 0, ts = 0, tm = 0, tu = 0, fsum = 0;
   for (int round = 0; nf > 0; ++round) {
     ++rounds;
+    fsum += (unsigned long long)nf;
+    long long c0 = clock64();
     if (round > kD1StepLimit) {
       if (lane == 0) atomicOr(status, kErrRounds);
       failed = true;
@@ -703,23 +706,43 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
                               c_geo.off[ln][2] - c_geo.off[hn][2]);
           tmask[hn] ^= 1u << dir;
         }
+        // the (at most 13) target stars are independent: issue each phase's
+        // memory operations for all of them back to back
+        uint32_t slot[14];
+        unsigned long long seen[14];
+#pragma unroll
         for (int hn = 0; hn < 14; ++hn) {
-          if (!tmask[hn]) continue;
-          uint32_t hv = (uint32_t)((int32_t)v + c.nd.d[hn]);
-          uint32_t hh = hslot(W, colkey | hv, status);
-          if (hh == 0xFFFFFFFFu) continue;
-          uint32_t old = atomicXor(&W.hmask[hh], tmask[hn]);
-          if (old == 0) {
-            if (nnew < kNewPerLane) mynew[nnew++] = __ldg(c.rank + hv);
-            else overflow = true;
+          slot[hn] = 0xFFFFFFFFu;
+          if (tmask[hn]) {
+            unsigned long long key = colkey | (uint32_t)((int32_t)v + c.nd.d[hn]);
+            slot[hn] = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
+            seen[hn] = W.hkeys[slot[hn]];
           }
         }
+#pragma unroll
+        for (int hn = 0; hn < 14; ++hn)
+          if (tmask[hn]) {
+            unsigned long long key = colkey | (uint32_t)((int32_t)v + c.nd.d[hn]);
+            if (seen[hn] != key) slot[hn] = hslot(W, key, status);  // probe / insert
+          }
+        uint32_t olds[14];
+#pragma unroll
+        for (int hn = 0; hn < 14; ++hn)
+          olds[hn] = (tmask[hn] && slot[hn] != 0xFFFFFFFFu) ? atomicXor(&W.hmask[slot[hn]], tmask[hn]) : 1u;
+#pragma unroll
+        for (int hn = 0; hn < 14; ++hn)
+          if (olds[hn] == 0) {
+            if (nnew < kNewPerLane) mynew[nnew++] = __ldg(c.rank + (uint32_t)((int32_t)v + c.nd.d[hn]));
+            else overflow = true;
+          }
       }
     }
     if (__any_sync(0xFFFFFFFFu, overflow)) {
       failed = true;
       break;
     }
+    long long c1 = clock64();
+    tv += (unsigned long long)(c1 - c0);
     // outputs of this round
     int otot;
     int ooff = warp_exscan(myout, otot);
@@ -754,6 +777,8 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
         }
         __syncwarp();
       }
+    long long c2 = clock64();
+    ts += (unsigned long long)(c2 - c1);
     // merge front[nb..nf) (descending, unique) with stage[0..ntot) (descending)
     int rest = nf - nb;
     if (rest + ntot > kFront) {
@@ -774,6 +799,8 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
       other[k] = (i < rest && (jb >= ntot || front[nb + i] >= stage[jb])) ? front[nb + i] : stage[jb];
     }
     __syncwarp();
+    long long c3 = clock64();
+    tm += (unsigned long long)(c3 - c2);
     // unique (keep the first of equal neighbours)
     int keep_total = 0;
     for (int base = 0; base < total; base += 32) {
@@ -789,6 +816,7 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
     }
     nf = keep_total;
     __syncwarp();
+    tu += (unsigned long long)(clock64() - c3);
   }
   // fallback for this column, or the sorted, mod-2 reduced output
   int vsum = visits;
@@ -832,6 +860,11 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
     atomicMax(&W.stats[1], (unsigned long long)vsum);
     atomicAdd(&W.stats[2], (unsigned long long)rounds);
     atomicMax(&W.stats[3], (unsigned long long)rounds);
+    atomicAdd(&W.stats[4], tv);
+    atomicAdd(&W.stats[5], ts);
+    atomicAdd(&W.stats[6], tm);
+    atomicAdd(&W.stats[7], tu);
+    atomicAdd(&W.stats[8], fsum);
   }
 }
 
@@ -919,7 +952,7 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.L = L;
   c.d0_killed = P.d0_killed;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
-  cudaMemsetAsync(W.stats, 0, 32, st);
+  cudaMemsetAsync(W.stats, 0, 72, st);
   k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();
   k_d1_morse_warp<<<ncols, 32, 0, st>>>(c, W, ncols, status); note_launch();
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();

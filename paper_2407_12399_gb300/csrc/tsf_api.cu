@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -388,7 +389,7 @@ int compute_diagram(tsf_field* F, bool incremental) {
     F->W.pool_cap = F->pool_cap;
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
-    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 4));
+    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 9));
     uint32_t hwant = 1u << 20;
     while (hwant < (uint32_t)std::min<int64_t>((int64_t)256 * std::max(F->n2, 1), (int64_t)1 << 28)) hwant <<= 1;
     hwant = (uint32_t)std::min<int64_t>((int64_t)hwant << attempt, (int64_t)1 << 29);
@@ -409,6 +410,12 @@ int compute_diagram(tsf_field* F, bool incremental) {
     if (F->d1_cols > 0) {
       ck(cudaMemcpyAsync(F->d1_stats, F->W.stats, 32, cudaMemcpyDeviceToHost, st));
       ck(cudaStreamSynchronize(st));
+      if (std::getenv("TSF_DEBUG_D1")) {
+        unsigned long long x[9];
+        ck(cudaMemcpy(x, F->W.stats, sizeof(x), cudaMemcpyDeviceToHost));
+        std::fprintf(stderr, "d1: visits %llu max %llu rounds %llu max %llu | cycles visit %llu sort %llu merge %llu "
+                     "unique %llu | frontier sum %llu\n", x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], x[8]);
+      }
     } else {
       F->d1_stats[0] = F->d1_stats[1] = F->d1_stats[2] = F->d1_stats[3] = 0;
     }
