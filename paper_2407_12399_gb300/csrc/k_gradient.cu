@@ -12,6 +12,8 @@ namespace tsf {
 __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint8_t* __restrict__ dirty,
                            Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
                            uint32_t* status, unsigned long long* n_recomputed) {
+  __shared__ Geo sg;
+  geo_to_shared(sg);
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool work = v < d.nv;
   if (work && dirty) {
@@ -33,9 +35,9 @@ __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint
   Star s;
   star_load(s, d, (uint32_t)v, rank);
   Fwd f;
-  star_forward(s, f);
+  star_forward(s, f, sg);
   Dual du;
-  star_dual(s, f, du);
+  star_dual(s, f, du, sg);
   if (du.inconsistent) atomicOr(status, kErrInconsistent);
   Rec r = star_record(s, f, du);
   uint4* dst = reinterpret_cast<uint4*>(rec + v);
@@ -45,7 +47,7 @@ __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint
   if (tab) {
     int8_t y_of[14];
     uint64_t path_of[14];
-    star_chains(s, y_of, path_of);
+    star_chains(s, y_of, path_of, sg);
     D1Tab t;
     unsigned long long bp = 0, yy = 0;
     for (int p = 0; p < 14; ++p) bp |= (unsigned long long)((p < s.nl ? s.by_pos[p] : 15) & 15) << (4 * p);
@@ -170,6 +172,8 @@ __global__ void k_crit_write(Dims d, const uint32_t* __restrict__ order, const u
                              const Rec* __restrict__ rec, const int4* __restrict__ tile_off, CritLists L,
                              uint32_t* __restrict__ cidx, uint32_t* __restrict__ c1base,
                              uint32_t* __restrict__ c2base, uint32_t* status) {
+  __shared__ Geo sg;
+  geo_to_shared(sg);
   int4 t = tile_off[blockIdx.x];
   Cnt4 run = {t.x, t.y, t.z, t.w};
   int64_t base = (int64_t)blockIdx.x * kCTile;
@@ -232,7 +236,7 @@ __global__ void k_crit_write(Dims d, const uint32_t* __restrict__ order, const u
             uint64_t bk = 0;
             for (uint64_t mm = m; mm; mm &= mm - 1) {
               int e = __ffsll((long long)mm) - 1;
-              uint32_t ra = nr[c_geo.edge[e][0]], rb = nr[c_geo.edge[e][1]];
+              uint32_t ra = nr[sg.edge[e][0]], rb = nr[sg.edge[e][1]];
               uint64_t kk = ((uint64_t)max(ra, rb) << 32) | min(ra, rb);
               if (best < 0 || kk < bk) {
                 best = e;
@@ -254,21 +258,23 @@ __global__ void k_crit_write(Dims d, const uint32_t* __restrict__ order, const u
 // cell).  Test support: lets the local pairing be checked cell by cell.
 __global__ void k_zero_pairs(Dims d, const uint32_t* __restrict__ rank, unsigned long long* __restrict__ out,
                              int64_t cap, unsigned long long* __restrict__ count, uint32_t* status) {
+  __shared__ Geo sg;
+  geo_to_shared(sg);
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= d.nv) return;
   Star s;
   star_load(s, d, (uint32_t)v, rank);
   Fwd f;
-  star_forward(s, f);
+  star_forward(s, f, sg);
   Dual du;
-  star_dual(s, f, du);
+  star_dual(s, f, du, sg);
   if (du.inconsistent) atomicOr(status, kErrInconsistent);
   int x, y, z;
   vxyz(d, (uint32_t)v, x, y, z);
   auto P = [&](int k, int* o) {
-    o[0] = x + c_geo.off[k][0];
-    o[1] = y + c_geo.off[k][1];
-    o[2] = z + c_geo.off[k][2];
+    o[0] = x + sg.off[k][0];
+    o[1] = y + sg.off[k][1];
+    o[2] = z + sg.off[k][2];
   };
   auto emit = [&](uint64_t a, uint64_t b) {
     unsigned long long i = atomicAdd(count, 1ull);
@@ -288,19 +294,19 @@ __global__ void k_zero_pairs(Dims d, const uint32_t* __restrict__ rank, unsigned
     if (e < 0) continue;
     P(a, xs[1]);
     uint64_t cb = cell_id_of(d, 2, xs);
-    P(c_geo.edge[e][0], xs[1]);
-    P(c_geo.edge[e][1], xs[2]);
+    P(sg.edge[e][0], xs[1]);
+    P(sg.edge[e][1], xs[2]);
     emit(cb, cell_id_of(d, 3, xs));
   }
   for (int t = 0; t < 24; ++t) {
     int e = du.killer[t];
     if (e < 0) continue;
-    P(c_geo.edge[e][0], xs[1]);
-    P(c_geo.edge[e][1], xs[2]);
+    P(sg.edge[e][0], xs[1]);
+    P(sg.edge[e][1], xs[2]);
     uint64_t cb = cell_id_of(d, 3, xs);
-    P(c_geo.tri[t][0], xs[1]);
-    P(c_geo.tri[t][1], xs[2]);
-    P(c_geo.tri[t][2], xs[3]);
+    P(sg.tri[t][0], xs[1]);
+    P(sg.tri[t][1], xs[2]);
+    P(sg.tri[t][2], xs[3]);
     emit(cb, cell_id_of(d, 4, xs));
   }
 }

@@ -62,7 +62,7 @@ __device__ __forceinline__ Rec ld_rec(const Rec* rec, uint32_t v) {
 // Ascending integral line in the dual: from tetrahedron (w, tau) follow the
 // record codes to a maximum (its index) or to the outside (returns n3).
 __device__ int32_t trace_up(uint32_t w, int tau, const Rec* __restrict__ rec, const uint32_t* __restrict__ cidx,
-                            const NbrDelta& nd, int n3) {
+                            const int32_t* nd, int n3, const Geo& G) {
   Rec r = ld_rec(rec, w);
   for (int s = 0; s < kTraceLimit; ++s) {
     int code = rec_tet_code(r, tau);
@@ -74,17 +74,17 @@ __device__ int32_t trace_up(uint32_t w, int tau, const Rec* __restrict__ rec, co
     }
     if (code >= 96) return -1;
     int t2 = (code - 24) / 3, j = (code - 24) % 3;
-    int c = c_geo.tri[t2][j];
-    int p = c_geo.tri[t2][(j + 1) % 3], q = c_geo.tri[t2][(j + 2) % 3];
-    int i0 = nbr_index(-c_geo.off[c][0], -c_geo.off[c][1], -c_geo.off[c][2]);
-    int i1 = nbr_index(c_geo.off[p][0] - c_geo.off[c][0], c_geo.off[p][1] - c_geo.off[c][1],
-                       c_geo.off[p][2] - c_geo.off[c][2]);
-    int i2 = nbr_index(c_geo.off[q][0] - c_geo.off[c][0], c_geo.off[q][1] - c_geo.off[c][1],
-                       c_geo.off[q][2] - c_geo.off[c][2]);
+    int c = G.tri[t2][j];
+    int p = G.tri[t2][(j + 1) % 3], q = G.tri[t2][(j + 2) % 3];
+    int i0 = nbr_index(G, -G.off[c][0], -G.off[c][1], -G.off[c][2]);
+    int i1 = nbr_index(G, G.off[p][0] - G.off[c][0], G.off[p][1] - G.off[c][1],
+                       G.off[p][2] - G.off[c][2]);
+    int i2 = nbr_index(G, G.off[q][0] - G.off[c][0], G.off[q][1] - G.off[c][1],
+                       G.off[q][2] - G.off[c][2]);
     if (i0 < 0 || i1 < 0 || i2 < 0) return -1;
-    tau = c_geo.tri_of3[i0][i1][i2];
+    tau = G.tri_of3[i0][i1][i2];
     if (tau < 0) return -1;
-    w = (uint32_t)((int32_t)w + nd.d[c]);
+    w = (uint32_t)((int32_t)w + nd[c]);
     r = ld_rec(rec, w);
   }
   return -1;
@@ -93,20 +93,24 @@ __device__ int32_t trace_up(uint32_t w, int tau, const Rec* __restrict__ rec, co
 __global__ void k_d2_trace(Dims d, int n2, int n3, CritLists L, const uint32_t* __restrict__ rank,
                            const Rec* __restrict__ rec, const uint32_t* __restrict__ cidx, NbrDelta nd,
                            int32_t* __restrict__ ends, uint32_t* status) {
+  __shared__ Geo sg;
+  __shared__ int32_t snd[14];
+  if (threadIdx.x < 14) snd[threadIdx.x] = nd.d[threadIdx.x];
+  geo_to_shared(sg);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n2) return;
   uint32_t ve = L.c2_ve[i];
   uint32_t v = ve >> 6;
   int e = (int)(ve & 63u);
-  int a = c_geo.edge[e][0], b = c_geo.edge[e][1];
+  int a = sg.edge[e][0], b = sg.edge[e][1];
   int x, y, z;
   vxyz(d, v, x, y, z);
   uint32_t rv = rank[v];
   for (int k = 0; k < 2; ++k) {
-    int t = c_geo.edge_tri[e][k];
+    int t = sg.edge_tri[e][k];
     int j = 0;
-    while (c_geo.tri[t][j] == a || c_geo.tri[t][j] == b) ++j;
-    int c = c_geo.tri[t][j];
+    while (sg.tri[t][j] == a || sg.tri[t][j] == b) ++j;
+    int c = sg.tri[t][j];
     int nx, ny, nz;
     int32_t res;
     if (!nbr_xyz(d, x, y, z, c, nx, ny, nz)) {
@@ -114,15 +118,15 @@ __global__ void k_d2_trace(Dims d, int n2, int n3, CritLists L, const uint32_t* 
     } else {
       uint32_t wc = vid(d, nx, ny, nz);
       if (rank[wc] < rv) {
-        res = trace_up(v, t, rec, cidx, nd, n3);
+        res = trace_up(v, t, rec, cidx, snd, n3, sg);
       } else {
-        int i0 = nbr_index(-c_geo.off[c][0], -c_geo.off[c][1], -c_geo.off[c][2]);
-        int i1 = nbr_index(c_geo.off[a][0] - c_geo.off[c][0], c_geo.off[a][1] - c_geo.off[c][1],
-                           c_geo.off[a][2] - c_geo.off[c][2]);
-        int i2 = nbr_index(c_geo.off[b][0] - c_geo.off[c][0], c_geo.off[b][1] - c_geo.off[c][1],
-                           c_geo.off[b][2] - c_geo.off[c][2]);
-        int tau = (i0 >= 0 && i1 >= 0 && i2 >= 0) ? c_geo.tri_of3[i0][i1][i2] : -1;
-        res = tau < 0 ? -1 : trace_up(wc, tau, rec, cidx, nd, n3);
+        int i0 = nbr_index(sg, -sg.off[c][0], -sg.off[c][1], -sg.off[c][2]);
+        int i1 = nbr_index(sg, sg.off[a][0] - sg.off[c][0], sg.off[a][1] - sg.off[c][1],
+                           sg.off[a][2] - sg.off[c][2]);
+        int i2 = nbr_index(sg, sg.off[b][0] - sg.off[c][0], sg.off[b][1] - sg.off[c][1],
+                           sg.off[b][2] - sg.off[c][2]);
+        int tau = (i0 >= 0 && i1 >= 0 && i2 >= 0) ? sg.tri_of3[i0][i1][i2] : -1;
+        res = tau < 0 ? -1 : trace_up(wc, tau, rec, cidx, snd, n3, sg);
       }
     }
     if (res < 0) {
@@ -304,6 +308,12 @@ __device__ __forceinline__ int nbr_of_pair(const Dims& d, uint32_t hi, uint32_t 
   vxyz(d, lo, lx, ly, lz);
   return nbr_index(lx - hx, ly - hy, lz - hz);
 }
+__device__ __forceinline__ int nbr_of_pair(const Dims& d, uint32_t hi, uint32_t lo, const Geo& G) {
+  int hx, hy, hz, lx, ly, lz;
+  vxyz(d, hi, hx, hy, hz);
+  vxyz(d, lo, lx, ly, lz);
+  return nbr_index(G, lx - hx, ly - hy, lz - hz);
+}
 
 __device__ int crit_edge_index(const D1Ctx& c, uint32_t hi, const Rec& r, int k) {
   int cnt = __popc(rec_crit_edges(r));
@@ -473,6 +483,8 @@ constexpr int kD1StepLimit = 1 << 24;
 // column, largest first, one lower star at a time.  Output: the critical
 // edges left (C1 indices), in decreasing lexicographic order.
 __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
+  __shared__ Geo sg;
+  geo_to_shared(sg);
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ncols) return;
   if (W.redo && !W.redo[j]) return;
@@ -513,7 +525,7 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
     star_load(s, c.d, v, c.rank);
     int8_t y_of[14];
     uint64_t path_of[14];
-    star_chains(s, y_of, path_of);
+    star_chains(s, y_of, path_of, sg);
     for (int p = s.nl - 1; p >= 1; --p) {
       int x = s.by_pos[p];
       if (!((m >> x) & 1u)) continue;
@@ -591,6 +603,10 @@ __device__ __forceinline__ int warp_exscan(int v, int& total) {
 constexpr int kNewPerLane = 48;
 
 __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
+  __shared__ Geo sg;
+  __shared__ int32_t snd[14];
+  if (threadIdx.x < 14) snd[threadIdx.x] = c.nd.d[threadIdx.x];
+  geo_to_shared(sg);
   __shared__ uint32_t fa[kFront], fb[kFront];
   __shared__ uint32_t stage[2048];  // >= next power of two of 32 * kNewPerLane
   __shared__ unsigned long long outv[256];
@@ -608,17 +624,17 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
     uint32_t ve = c.L.c2_ve[W.cols[j]];
     uint32_t v0 = ve >> 6;
     int e0 = (int)(ve & 63u);
-    uint32_t ends[3][2] = {{v0, (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][0]])},
-                           {v0, (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][1]])},
-                           {(uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][0]]),
-                            (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][1]])}};
+    uint32_t ends[3][2] = {{v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]])},
+                           {v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])},
+                           {(uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]]),
+                            (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])}};
     for (int k = 0; k < 3; ++k) {
       uint32_t p = ends[k][0], q = ends[k][1];
       uint32_t rp = c.rank[p], rq = c.rank[q];
       uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
       uint32_t h = hslot(W, colkey | hi, status);
       if (h == 0xFFFFFFFFu) continue;
-      uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo));
+      uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo, sg));
       if (old == 0) {
         // insert rank(hi) into the (tiny) front, kept descending and unique
         uint32_t r = max(rp, rq);
@@ -699,11 +715,11 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
         for (int k = 0; k < 14; ++k) tmask[k] = 0;
         for (uint64_t pm = path; pm; pm &= pm - 1) {
           int le = __ffsll((long long)pm) - 1;
-          int na = c_geo.edge[le][0], nbv = c_geo.edge[le][1];
+          int na = sg.edge[le][0], nbv = sg.edge[le][1];
           bool a_hi = pos[na] > pos[nbv];
           int hn = a_hi ? na : nbv, ln = a_hi ? nbv : na;
-          int dir = nbr_index(c_geo.off[ln][0] - c_geo.off[hn][0], c_geo.off[ln][1] - c_geo.off[hn][1],
-                              c_geo.off[ln][2] - c_geo.off[hn][2]);
+          int dir = nbr_index(sg, sg.off[ln][0] - sg.off[hn][0], sg.off[ln][1] - sg.off[hn][1],
+                              sg.off[ln][2] - sg.off[hn][2]);
           tmask[hn] ^= 1u << dir;
         }
         // the (at most 13) target stars are independent: issue each phase's
@@ -714,7 +730,7 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
         for (int hn = 0; hn < 14; ++hn) {
           slot[hn] = 0xFFFFFFFFu;
           if (tmask[hn]) {
-            unsigned long long key = colkey | (uint32_t)((int32_t)v + c.nd.d[hn]);
+            unsigned long long key = colkey | (uint32_t)((int32_t)v + snd[hn]);
             slot[hn] = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
             seen[hn] = W.hkeys[slot[hn]];
           }
@@ -722,7 +738,7 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
 #pragma unroll
         for (int hn = 0; hn < 14; ++hn)
           if (tmask[hn]) {
-            unsigned long long key = colkey | (uint32_t)((int32_t)v + c.nd.d[hn]);
+            unsigned long long key = colkey | (uint32_t)((int32_t)v + snd[hn]);
             if (seen[hn] != key) slot[hn] = hslot(W, key, status);  // probe / insert
           }
         uint32_t olds[14];
@@ -732,7 +748,7 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
 #pragma unroll
         for (int hn = 0; hn < 14; ++hn)
           if (olds[hn] == 0) {
-            if (nnew < kNewPerLane) mynew[nnew++] = __ldg(c.rank + (uint32_t)((int32_t)v + c.nd.d[hn]));
+            if (nnew < kNewPerLane) mynew[nnew++] = __ldg(c.rank + (uint32_t)((int32_t)v + snd[hn]));
             else overflow = true;
           }
       }

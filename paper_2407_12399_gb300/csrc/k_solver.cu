@@ -62,6 +62,8 @@ __global__ void k_build_points(Dims d, NbrDelta nd, CritLists L, int n1, int n2,
                                const int32_t* __restrict__ d1_edge, const int32_t* __restrict__ d2_max,
                                const uint32_t* __restrict__ order, const float* __restrict__ f, Pt* __restrict__ pts,
                                int* __restrict__ count, int cap) {
+  __shared__ Geo sg;
+  geo_to_shared(sg);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int xs[4][3];
   auto put = [&](Pt& p) {
@@ -96,8 +98,8 @@ __global__ void k_build_points(Dims d, NbrDelta nd, CritLists L, int n1, int n2,
     uint32_t v = ve >> 6;
     int e = (int)(ve & 63u);
     xyz_of(d, v, xs[0]);
-    xyz_of(d, (uint32_t)((int32_t)v + nd.d[c_geo.edge[e][0]]), xs[1]);
-    xyz_of(d, (uint32_t)((int32_t)v + nd.d[c_geo.edge[e][1]]), xs[2]);
+    xyz_of(d, (uint32_t)((int32_t)v + nd.d[sg.edge[e][0]]), xs[1]);
+    xyz_of(d, (uint32_t)((int32_t)v + nd.d[sg.edge[e][1]]), xs[2]);
     uint64_t tri = cell_id_of(d, 3, xs);
     int ce = d1_edge[i], mx = d2_max[i];
     if (ce >= 0) {  // D1: (critical edge, critical triangle)
@@ -125,7 +127,7 @@ __global__ void k_build_points(Dims d, NbrDelta nd, CritLists L, int n1, int n2,
       int tau = (int)(c3 & 31u);
       int ys[4][3];
       xyz_of(d, w, ys[0]);
-      for (int k = 0; k < 3; ++k) xyz_of(d, (uint32_t)((int32_t)w + nd.d[c_geo.tri[tau][k]]), ys[k + 1]);
+      for (int k = 0; k < 3; ++k) xyz_of(d, (uint32_t)((int32_t)w + nd.d[sg.tri[tau][k]]), ys[k + 1]);
       p.cb = tri;
       p.cd = cell_id_of(d, 4, ys);
       p.vb = v;

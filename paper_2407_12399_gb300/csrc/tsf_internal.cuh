@@ -111,6 +111,19 @@ __device__ __forceinline__ uint32_t vid(const Dims& d, int x, int y, int z) {
 __device__ __forceinline__ int nbr_index(int dx, int dy, int dz) {
   return c_geo.nbr_of[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
 }
+__device__ __forceinline__ int nbr_index(const Geo& G, int dx, int dy, int dz) {
+  return G.nbr_of[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+}
+
+// The geometry tables are read with lane-dependent indices in the lower-star
+// kernels; constant memory serialises such reads, shared memory does not.
+// Every thread of the block must call this (it ends with a barrier).
+__device__ inline void geo_to_shared(Geo& sg) {
+  const unsigned char* src = reinterpret_cast<const unsigned char*>(&c_geo);
+  unsigned char* dst = reinterpret_cast<unsigned char*>(&sg);
+  for (int i = threadIdx.x; i < (int)sizeof(Geo); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
 
 // Monotone float -> uint32 key for the vertex order (Section 2.1: ties are
 // broken by vertex id; -0.0 and +0.0 are the same value).

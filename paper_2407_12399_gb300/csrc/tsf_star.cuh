@@ -83,7 +83,7 @@ struct Fwd {
   int8_t killer[14];     // link edge that killed neighbour a's component, -1
 };
 
-__device__ inline void star_forward(const Star& s, Fwd& f) {
+__device__ inline void star_forward(const Star& s, Fwd& f, const Geo& G) {
   int8_t par[14];
   f.lower_edges = 0;
   f.link_pos = 0;
@@ -94,11 +94,11 @@ __device__ inline void star_forward(const Star& s, Fwd& f) {
   }
   for (int p = 1; p < s.nl; ++p) {
     int a = s.by_pos[p];
-    uint32_t nb = c_geo.adj[a] & s.lower;
+    uint32_t nb = G.adj[a] & s.lower;
     for (int q = 0; q < p; ++q) {
       int b = s.by_pos[q];
       if (!((nb >> b) & 1u)) continue;
-      int e = c_geo.edge_idx[a][b];
+      int e = G.edge_idx[a][b];
       f.lower_edges |= 1ull << e;
       int ra = uf_find(par, p), rb = uf_find(par, q);
       if (ra == rb) {
@@ -116,8 +116,8 @@ __device__ inline void star_forward(const Star& s, Fwd& f) {
 
 // Key of a link triangle for the backward sweep (larger = later in the
 // filtration = older in the backward sweep).
-__device__ __forceinline__ int star_tri_key(const Star& s, int tau) {
-  int p0 = s.pos[c_geo.tri[tau][0]], p1 = s.pos[c_geo.tri[tau][1]], p2 = s.pos[c_geo.tri[tau][2]];
+__device__ __forceinline__ int star_tri_key(const Star& s, int tau, const Geo& G) {
+  int p0 = s.pos[G.tri[tau][0]], p1 = s.pos[G.tri[tau][1]], p2 = s.pos[G.tri[tau][2]];
   int hi = max(p0, max(p1, p2)), lo = min(p0, min(p1, p2));
   int mid = p0 + p1 + p2 - hi - lo;
   return hi * 196 + mid * 14 + lo;
@@ -131,7 +131,7 @@ struct Dual {
   bool inconsistent;
 };
 
-__device__ inline void star_dual(const Star& s, const Fwd& f, Dual& du) {
+__device__ inline void star_dual(const Star& s, const Fwd& f, Dual& du, const Geo& G) {
   const int OUT = 24;
   int8_t par[25];
   int key[24];
@@ -141,26 +141,26 @@ __device__ inline void star_dual(const Star& s, const Fwd& f, Dual& du) {
   for (int t = 0; t < 24; ++t) {
     par[t] = (int8_t)t;
     du.killer[t] = -1;
-    uint32_t m = (1u << c_geo.tri[t][0]) | (1u << c_geo.tri[t][1]) | (1u << c_geo.tri[t][2]);
+    uint32_t m = (1u << G.tri[t][0]) | (1u << G.tri[t][1]) | (1u << G.tri[t][2]);
     bool low = (s.lower & m) == m;
     du.code[t] = low ? (uint8_t)kCodeMax : (uint8_t)kCodeNone;
-    key[t] = low ? star_tri_key(s, t) : 0;
+    key[t] = low ? star_tri_key(s, t, G) : 0;
   }
   par[OUT] = OUT;
   for (int p = s.nl - 1; p >= 1; --p) {
     int a = s.by_pos[p];
-    uint32_t nb = c_geo.adj[a] & s.lower;
+    uint32_t nb = G.adj[a] & s.lower;
     for (int q = p - 1; q >= 0; --q) {
       int b = s.by_pos[q];
       if (!((nb >> b) & 1u)) continue;
-      int e = c_geo.edge_idx[a][b];
+      int e = G.edge_idx[a][b];
       int node[2], tcode[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        int t = c_geo.edge_tri[e][k];
+        int t = G.edge_tri[e][k];
         int j = 0;
-        while (c_geo.tri[t][j] == a || c_geo.tri[t][j] == b) ++j;
-        int c = c_geo.tri[t][j];
+        while (G.tri[t][j] == a || G.tri[t][j] == b) ++j;
+        int c = G.tri[t][j];
         if (!((s.valid >> c) & 1u)) {
           node[k] = OUT;
           tcode[k] = kCodeOut;
@@ -204,8 +204,8 @@ __device__ inline Rec star_record(const Star& s, const Fwd& f, const Dual& du) {
 
 // Lexicographic key of a link edge (a, b) of the lower link: (higher rank
 // position, lower rank position).
-__device__ __forceinline__ int star_edge_key(const Star& s, int e) {
-  int pa = s.pos[c_geo.edge[e][0]], pb = s.pos[c_geo.edge[e][1]];
+__device__ __forceinline__ int star_edge_key(const Star& s, int e, const Geo& G) {
+  int pa = s.pos[G.edge[e][0]], pb = s.pos[G.edge[e][1]];
   return max(pa, pb) * 14 + min(pa, pb);
 }
 
@@ -219,7 +219,7 @@ namespace tsf {
 // y being the older representative e' merged x's component with.  Writes the
 // path's link edges (as neighbour index pairs) and returns their number, or
 // -1 if x is not killed.  The column is w*x + w*y + (path edges).
-__device__ inline int star_chain(const Star& s, int x, int8_t* pa, int8_t* pb, int& y) {
+__device__ inline int star_chain(const Star& s, int x, int8_t* pa, int8_t* pb, int& y, const Geo& G) {
   int8_t par[14];
   uint32_t tadj[14];
   for (int i = 0; i < 14; ++i) {
@@ -228,7 +228,7 @@ __device__ inline int star_chain(const Star& s, int x, int8_t* pa, int8_t* pb, i
   }
   for (int p = 1; p < s.nl; ++p) {
     int a = s.by_pos[p];
-    uint32_t nb = c_geo.adj[a] & s.lower;
+    uint32_t nb = G.adj[a] & s.lower;
     for (int q = 0; q < p; ++q) {
       int b = s.by_pos[q];
       if (!((nb >> b) & 1u)) continue;
@@ -292,7 +292,7 @@ namespace tsf {
 // older representative its component merged with, path_of[x] = the link
 // edges (bitmask) of the forest path x ... y through the killing edge.  The
 // reduced column of the triangle paired with w*x is w*x + w*y + path.
-__device__ inline void star_chains(const Star& s, int8_t* y_of, uint64_t* path_of) {
+__device__ inline void star_chains(const Star& s, int8_t* y_of, uint64_t* path_of, const Geo& G) {
   int8_t par[14];
   uint32_t tadj[14];
   for (int i = 0; i < 14; ++i) {
@@ -320,12 +320,12 @@ __device__ inline void star_chains(const Star& s, int8_t* y_of, uint64_t* path_o
       frontier = nf;
     }
     uint64_t bits = 0;
-    for (int c = dst; c != src && prev[c] >= 0; c = prev[c]) bits ^= 1ull << c_geo.edge_idx[c][prev[c]];
+    for (int c = dst; c != src && prev[c] >= 0; c = prev[c]) bits ^= 1ull << G.edge_idx[c][prev[c]];
     return bits;
   };
   for (int p = 1; p < s.nl; ++p) {
     int a = s.by_pos[p];
-    uint32_t nb = c_geo.adj[a] & s.lower;
+    uint32_t nb = G.adj[a] & s.lower;
     for (int q = 0; q < p; ++q) {
       int b = s.by_pos[q];
       if (!((nb >> b) & 1u)) continue;
@@ -337,7 +337,7 @@ __device__ inline void star_chains(const Star& s, int8_t* y_of, uint64_t* path_o
       int other = (ra == young) ? b : a;
       int y = s.by_pos[old];
       y_of[x] = (int8_t)y;
-      path_of[x] = tree_path(x, in_x) ^ (1ull << c_geo.edge_idx[a][b]) ^ tree_path(other, y);
+      path_of[x] = tree_path(x, in_x) ^ (1ull << G.edge_idx[a][b]) ^ tree_path(other, y);
       par[young] = (int8_t)old;
       tadj[a] |= 1u << b;
       tadj[b] |= 1u << a;
