@@ -12,8 +12,7 @@ namespace tsf {
 __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint8_t* __restrict__ dirty,
                            Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
                            uint32_t* status, unsigned long long* n_recomputed) {
-  __shared__ Geo sg;
-  geo_to_shared(sg);
+  const Geo& sg = c_geo;
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool work = v < d.nv;
   if (work && dirty) {
@@ -172,8 +171,7 @@ __global__ void k_crit_write(Dims d, const uint32_t* __restrict__ order, const u
                              const Rec* __restrict__ rec, const int4* __restrict__ tile_off, CritLists L,
                              uint32_t* __restrict__ cidx, uint32_t* __restrict__ c1base,
                              uint32_t* __restrict__ c2base, uint32_t* status) {
-  __shared__ Geo sg;
-  geo_to_shared(sg);
+  const Geo& sg = c_geo;
   int4 t = tile_off[blockIdx.x];
   Cnt4 run = {t.x, t.y, t.z, t.w};
   int64_t base = (int64_t)blockIdx.x * kCTile;
@@ -258,8 +256,7 @@ __global__ void k_crit_write(Dims d, const uint32_t* __restrict__ order, const u
 // cell).  Test support: lets the local pairing be checked cell by cell.
 __global__ void k_zero_pairs(Dims d, const uint32_t* __restrict__ rank, unsigned long long* __restrict__ out,
                              int64_t cap, unsigned long long* __restrict__ count, uint32_t* status) {
-  __shared__ Geo sg;
-  geo_to_shared(sg);
+  const Geo& sg = c_geo;
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= d.nv) return;
   Star s;

@@ -416,6 +416,35 @@ __global__ void k_cand_keep(int nc, const int32_t* __restrict__ idx, const Cand*
 
 constexpr int kHT = 1024;
 
+__device__ __forceinline__ int block_exscan_int1024(int v, int& total) {
+  __shared__ int sw[33];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) sw[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0;
+    int si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xFFFFFFFFu, si, o);
+      if (lane >= o) si += t;
+    }
+    sw[lane] = si - s;
+    if (lane == 31) sw[32] = si;
+  }
+  __syncthreads();
+  int res = sw[wid] + inc - v;
+  total = sw[32];
+  __syncthreads();
+  return res;
+}
+
 // Shortest augmenting path (Hungarian algorithm with potentials): rows =
 // targets in target order, columns = candidate points (point order) and one
 // private diagonal column per target; ties go to the lowest column index.
@@ -580,6 +609,347 @@ static uint32_t read_tail(const uint32_t* flag, const uint32_t* pos, int n, cuda
   return tail[0] + tail[1];
 }
 
+// ---------------------------------------------------------------------------
+// Reduced assignment without host round-trips (used when every target's
+// candidate list fits a shared-memory tile; otherwise `assign_groups` runs).
+// ---------------------------------------------------------------------------
+constexpr int kCandTile = 2048;
+
+
+
+// one block: stable partition of the non-still points and the free targets by
+// group (finite dimension 0/1/2, essential = 3); the essential group is
+// matched in order here
+__global__ void __launch_bounds__(1024) k_asg_partition(int np, const Pt* __restrict__ pts, int nt,
+                                                        const Tg* __restrict__ T, const uint8_t* __restrict__ taken,
+                                                        AsgDev A, Pt* __restrict__ pw) {
+  __shared__ int cnt[8], base[8], run[8];
+  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < np; i += blockDim.x)
+    if (!pts[i].still) atomicAdd(&cnt[pts[i].ess ? 3 : pts[i].dim], 1);
+  for (int t = threadIdx.x; t < nt; t += blockDim.x)
+    if (!taken[t]) atomicAdd(&cnt[4 + (T[t].ess ? 3 : T[t].dim)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int b = 0, c = 0;
+    for (int g = 0; g < 4; ++g) {
+      base[g] = b;
+      b += cnt[g];
+      base[4 + g] = c;
+      c += cnt[4 + g];
+      A.counts[g] = cnt[g];
+      A.counts[4 + g] = cnt[4 + g];
+    }
+    A.counts[8] = 0;
+    A.counts[9] = 0;
+    for (int g = 0; g < 8; ++g) run[g] = base[g];
+  }
+  __syncthreads();
+  // order-preserving compaction: chunks of blockDim, warp ballots per group
+  __shared__ int wc[32][8];
+  for (int pass = 0; pass < 2; ++pass) {
+    int n = pass == 0 ? np : nt;
+    for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+      int i = b0 + threadIdx.x;
+      int g = -1;
+      if (i < n) {
+        if (pass == 0) {
+          if (!pts[i].still) g = pts[i].ess ? 3 : pts[i].dim;
+        } else if (!taken[i]) {
+          g = T[i].ess ? 3 : T[i].dim;
+        }
+      }
+      int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      int myoff = 0;
+      for (int gg = 0; gg < 4; ++gg) {
+        unsigned m = __ballot_sync(0xFFFFFFFFu, g == gg);
+        if (lane == 0) wc[w][gg] = __popc(m);
+        if (g == gg) myoff = __popc(m & ((1u << lane) - 1u));
+      }
+      __syncthreads();
+      if (g >= 0) {
+        int o = run[pass * 4 + g] + myoff;
+        for (int ww = 0; ww < w; ++ww) o += wc[ww][g];
+        if (pass == 0) A.plist[o] = i;
+        else A.tlist[o] = i;
+      }
+      __syncthreads();
+      if (threadIdx.x < 4) {
+        int add = 0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) add += wc[ww][threadIdx.x];
+        run[pass * 4 + threadIdx.x] += add;
+      }
+      __syncthreads();
+    }
+  }
+  // essential class: infinite points only match infinite targets, in order
+  if (threadIdx.x == 0) {
+    int n3 = min(cnt[3], cnt[7]);
+    for (int i = 0; i < n3; ++i) pw[A.plist[base[3] + i]].tgt = A.tlist[base[7] + i];
+  }
+}
+
+__device__ __forceinline__ void group_of_target(const int32_t* counts, int t, int& g, int& local, int& pbase,
+                                                int& tbase) {
+  int tb = 0, pb = 0;
+  g = -1;
+  for (int gg = 0; gg < 3; ++gg) {
+    int k = counts[4 + gg];
+    if (t < tb + k) {
+      g = gg;
+      local = t - tb;
+      tbase = tb;
+      pbase = pb;
+      return;
+    }
+    tb += k;
+    pb += counts[gg];
+  }
+}
+
+// one block per free finite target: candidates p with w(p,t) < diag(t),
+// bitonic-sorted by (w, point index) in shared memory, the k cheapest kept
+__global__ void __launch_bounds__(512) k_asg_candidates(const Pt* __restrict__ pts, const Tg* __restrict__ T,
+                                                        AsgDev A) {
+  __shared__ double sw[kCandTile];
+  __shared__ int sp[kCandTile];
+  __shared__ int fill;
+  int g, local, pbase, tbase;
+  group_of_target(A.counts, blockIdx.x, g, local, pbase, tbase);
+  if (g < 0) return;
+  int npg = A.counts[g], k = A.counts[4 + g];
+  const Tg tg = T[A.tlist[tbase + local]];
+  double dt = cost_diag(tg.b, tg.d);
+  if (threadIdx.x == 0) fill = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < npg; i += blockDim.x) {
+    const Pt& p = pts[A.plist[pbase + i]];
+    double w = __dsub_rn(cost_pt(p.b, p.d, tg.b, tg.d), cost_diag(p.b, p.d));
+    if (w < dt) {
+      int s = atomicAdd(&fill, 1);
+      if (s < kCandTile) {
+        sw[s] = w;
+        sp[s] = i;
+      }
+    }
+  }
+  __syncthreads();
+  int n = fill;
+  if (n > kCandTile) {
+    if (threadIdx.x == 0) A.counts[8] = 1;  // too many: the general path takes over
+    return;
+  }
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = n + threadIdx.x; i < n2; i += blockDim.x) {
+    sw[i] = __longlong_as_double(0x7FF0000000000000ll);
+    sp[i] = 0x7FFFFFFF;
+  }
+  __syncthreads();
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        int j = i ^ stride;
+        if (j > i) {
+          bool up = (i & size) == 0;
+          bool gt = sw[i] > sw[j] || (sw[i] == sw[j] && sp[i] > sp[j]);
+          if (gt == up) {
+            double tw = sw[i];
+            sw[i] = sw[j];
+            sw[j] = tw;
+            int tp = sp[i];
+            sp[i] = sp[j];
+            sp[j] = tp;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  int keep = min(n, k);
+  __shared__ uint32_t off;
+  if (threadIdx.x == 0) {
+    off = (uint32_t)atomicAdd(&A.counts[9], keep);
+    A.kept_off[tbase + local] = off;
+    A.nkept[tbase + local] = (uint32_t)keep;
+    if ((int)off + keep > A.cap_kept) A.counts[8] = 1;
+  }
+  __syncthreads();
+  if ((int)off + keep > A.cap_kept) return;
+  for (int i = threadIdx.x; i < keep; i += blockDim.x) {
+    Cand c;
+    c.w = sw[i];
+    c.p = sp[i];
+    c.t = local;
+    A.kept[off + i] = c;
+    A.is_col[pbase + sp[i]] = 1u;
+  }
+}
+
+// one block per finite group: column map (candidate points in point order,
+// then one private diagonal column per target) and the shortest augmenting
+// path solve, exactly as k_hungarian
+__global__ void __launch_bounds__(kHT) k_asg_solve(AsgDev A, Pt* __restrict__ pts, const Tg* __restrict__ T,
+                                                   uint32_t* status) {
+  const int g = blockIdx.x;
+  if (A.counts[8]) return;
+  int npg = A.counts[g], k = A.counts[4 + g];
+  if (k == 0 || npg == 0) return;
+  int pbase = 0, tbase = 0, wbase = 0;
+  for (int gg = 0; gg < g; ++gg) {
+    pbase += A.counts[gg];
+    tbase += A.counts[4 + gg];
+    wbase += A.counts[gg] + A.counts[4 + gg] + 2;
+  }
+  // column positions of the candidate points of this group
+  __shared__ int s_mc;
+  {
+    int run = 0;
+    for (int b0 = 0; b0 < npg; b0 += kHT) {
+      int i = b0 + threadIdx.x;
+      int f = (i < npg && A.is_col[pbase + i]) ? 1 : 0;
+      int tot;
+      int ex = block_exscan_int1024(f, tot);
+      if (i < npg) A.colpos[pbase + i] = (uint32_t)(run + ex);
+      if (f) A.col_point[wbase + run + ex] = i;
+      run += tot;
+    }
+    if (threadIdx.x == 0) s_mc = run;
+    __syncthreads();
+  }
+  int mc = s_mc;
+  const int m = mc + k;
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+  HungWork H;
+  H.u = A.H.u + wbase;
+  H.v = A.H.v + wbase;
+  H.minv = A.H.minv + wbase;
+  H.row = A.H.row + wbase;
+  H.pm = A.H.pm + wbase;
+  H.way = A.H.way + wbase;
+  H.used = A.H.used + wbase;
+  double* diag_t = A.diag_t + tbase;
+  for (int t = threadIdx.x; t < k; t += kHT) diag_t[t] = cost_diag(T[A.tlist[tbase + t]].b, T[A.tlist[tbase + t]].d);
+  __shared__ int s_j0;
+  __shared__ double s_val[kHT / 32];
+  __shared__ int s_idx[kHT / 32];
+  __shared__ double s_delta;
+  __shared__ int s_j1;
+  for (int j = threadIdx.x; j <= m; j += kHT) {
+    H.v[j] = 0.0;
+    H.pm[j] = 0;
+    H.way[j] = 0;
+  }
+  for (int i = threadIdx.x; i <= k; i += kHT) H.u[i] = 0.0;
+  __syncthreads();
+  for (int i = 1; i <= k; ++i) {
+    for (int j = threadIdx.x; j <= m; j += kHT) {
+      H.minv[j] = INF;
+      H.used[j] = 0;
+    }
+    if (threadIdx.x == 0) {
+      H.pm[0] = i;
+      s_j0 = 0;
+    }
+    __syncthreads();
+    for (int guard = 0;; ++guard) {
+      if (guard > m + 2) {
+        if (threadIdx.x == 0) atomicOr(status, kErrRounds);
+        return;
+      }
+      int j0 = s_j0;
+      if (threadIdx.x == 0) H.used[j0] = 1;
+      int i0 = H.pm[j0];
+      for (int j = 1 + threadIdx.x; j <= m; j += kHT) H.row[j] = INF;
+      __syncthreads();
+      uint32_t ko = A.kept_off[tbase + i0 - 1], kn = A.nkept[tbase + i0 - 1];
+      for (uint32_t c = threadIdx.x; c < kn; c += kHT) {
+        const Cand& cd = A.kept[ko + c];
+        H.row[1 + A.colpos[pbase + cd.p]] = cd.w;
+      }
+      if (threadIdx.x == 0) H.row[1 + mc + (i0 - 1)] = diag_t[i0 - 1];
+      __syncthreads();
+      double ui0 = H.u[i0];
+      double bv = INF;
+      int bj = 0x7FFFFFFF;
+      for (int j = 1 + threadIdx.x; j <= m; j += kHT) {
+        if (H.used[j]) continue;
+        double cur = __dsub_rn(__dsub_rn(H.row[j], ui0), H.v[j]);
+        double mv = H.minv[j];
+        if (cur < mv) {
+          mv = cur;
+          H.minv[j] = cur;
+          H.way[j] = j0;
+        }
+        if (mv < bv || (mv == bv && j < bj)) {
+          bv = mv;
+          bj = j;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        double ov = __shfl_down_sync(0xFFFFFFFFu, bv, o);
+        int oj = __shfl_down_sync(0xFFFFFFFFu, bj, o);
+        if (ov < bv || (ov == bv && oj < bj)) {
+          bv = ov;
+          bj = oj;
+        }
+      }
+      if ((threadIdx.x & 31) == 0) {
+        s_val[threadIdx.x >> 5] = bv;
+        s_idx[threadIdx.x >> 5] = bj;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double v0 = s_val[0];
+        int j1 = s_idx[0];
+        for (int w = 1; w < kHT / 32; ++w)
+          if (s_val[w] < v0 || (s_val[w] == v0 && s_idx[w] < j1)) {
+            v0 = s_val[w];
+            j1 = s_idx[w];
+          }
+        s_delta = v0;
+        s_j1 = j1;
+      }
+      __syncthreads();
+      double delta = s_delta;
+      int j1 = s_j1;
+      if (j1 == 0x7FFFFFFF) {
+        if (threadIdx.x == 0) atomicOr(status, kErrInconsistent);
+        return;
+      }
+      for (int j = threadIdx.x; j <= m; j += kHT) {
+        if (H.used[j]) {
+          int r = H.pm[j];
+          H.u[r] = __dadd_rn(H.u[r], delta);
+          H.v[j] = __dsub_rn(H.v[j], delta);
+        } else {
+          H.minv[j] = __dsub_rn(H.minv[j], delta);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_j0 = j1;
+      __syncthreads();
+      if (H.pm[j1] == 0) break;
+    }
+    if (threadIdx.x == 0) {
+      int j0 = s_j0;
+      do {
+        int j1 = H.way[j0];
+        H.pm[j0] = H.pm[j1];
+        j0 = j1;
+      } while (j0);
+    }
+    __syncthreads();
+  }
+  for (int j = 1 + threadIdx.x; j <= mc; j += kHT) {
+    int r = H.pm[j] - 1;
+    if (r >= 0) pts[A.plist[pbase + A.col_point[wbase + j - 1]]].tgt = A.tlist[tbase + r];
+  }
+}
+
+int assign_groups(int np, Pt* pts, int nt, const Tg* T, SolverBufs& B, uint32_t* status, AssignStats* as,
+                  cudaStream_t st);
+
 // Assignment phi*_j.  `ref` is the previous diagram (or the targets at j = 0,
 // each assigned to itself).  Returns 0, or a negative value when a scratch
 // buffer is too small (the caller grows it and retries).
@@ -591,6 +961,23 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBu
   int32_t* rk = nr > 0 ? merge_sort(nr, B.idxC, B.idxD, KeyLess{ref}, st) : B.idxC;
   k_still<<<(np + 255) / 256, 256, 0, st>>>(np, pts, ck, nr, ref, rk, B.tmp_pts, B.taken); note_launch();
   cudaMemcpyAsync(pts, B.tmp_pts, sizeof(Pt) * (size_t)np, cudaMemcpyDeviceToDevice, st);
+  // 2) reduced problems: three launches, no host round-trip; the general
+  // group-by-group path runs only when a candidate list overflows its tile
+  cudaMemsetAsync(B.A.is_col, 0, sizeof(uint32_t) * (size_t)np, st);
+  k_asg_partition<<<1, 1024, 0, st>>>(np, pts, nt, T, B.taken, B.A, pts); note_launch();
+  k_asg_candidates<<<max(nt, 1), 512, 0, st>>>(pts, T, B.A); note_launch();
+  k_asg_solve<<<3, kHT, 0, st>>>(B.A, pts, T, status); note_launch();
+  int32_t hc[10];
+  cudaMemcpyAsync(hc, B.A.counts, sizeof(hc), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  for (int g = 0; g < 4; ++g) as->k[g] = hc[4 + g];
+  if (!hc[8]) return 0;
+  return assign_groups(np, pts, nt, T, B, status, as, st);
+}
+
+// General path: group by group with host-sized buffers.
+int assign_groups(int np, Pt* pts, int nt, const Tg* T, SolverBufs& B, uint32_t* status, AssignStats* as,
+                  cudaStream_t st) {
   // 2) reduced problems, group by group
   as->k[0] = as->k[1] = as->k[2] = as->k[3] = 0;
   for (int g = 0; g < 4; ++g) {

@@ -272,6 +272,40 @@ void grow_solver(tsf_field* F, int np, int nt) {
   ck(dev_alloc(&B.diag_t, ctt));
   ck(dev_alloc(&B.terms, (size_t)cp + ctt));
   ck(dev_alloc(&B.contrib, 2 * (size_t)cp));
+  {
+    AsgDev& A = B.A;
+    dev_free(A.counts);
+    dev_free(A.kept);
+    dev_free(A.kept_off);
+    dev_free(A.col_point);
+    dev_free(A.H.u);
+    dev_free(A.H.v);
+    dev_free(A.H.minv);
+    dev_free(A.H.row);
+    dev_free(A.H.pm);
+    dev_free(A.H.way);
+    dev_free(A.H.used);
+    size_t w = (size_t)cp + ctt + 8;
+    A.cap_kept = (int)std::min<int64_t>((int64_t)ctt * 2048, std::max<int64_t>((int64_t)16 * cp, 1 << 18));
+    ck(dev_alloc(&A.counts, 16));
+    ck(dev_alloc(&A.kept, (size_t)A.cap_kept));
+    ck(dev_alloc(&A.kept_off, ctt));
+    ck(dev_alloc(&A.col_point, w));
+    ck(dev_alloc(&A.H.u, w));
+    ck(dev_alloc(&A.H.v, w));
+    ck(dev_alloc(&A.H.minv, w));
+    ck(dev_alloc(&A.H.row, w));
+    ck(dev_alloc(&A.H.pm, w));
+    ck(dev_alloc(&A.H.way, w));
+    ck(dev_alloc(&A.H.used, w));
+    A.plist = B.plist;
+    A.tlist = B.tlist;
+    A.nkept = B.nkept;
+    A.is_col = B.is_col;
+    A.colpos = B.colpos;
+    A.diag_t = B.diag_t;
+    A.col_to_row = nullptr;
+  }
   if (!B.count) ck(dev_alloc(&B.count, 4));
   if (!B.dsum) ck(dev_alloc(&B.dsum, 1));
   if (!B.counters) ck(dev_alloc(&B.counters, 4));
@@ -390,8 +424,10 @@ int compute_diagram(tsf_field* F, bool incremental) {
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
     if (!F->W.stats) ck(dev_alloc(&F->W.stats, 9));
-    uint32_t hwant = 1u << 20;
-    while (hwant < (uint32_t)std::min<int64_t>((int64_t)256 * std::max(F->n2, 1), (int64_t)1 << 28)) hwant <<= 1;
+    // (column, vertex) table: the lower stars the saddle-saddle columns visit
+    // number about half the vertices; keep the load factor at or below ~1/4
+    uint32_t hwant = 1u << 22;
+    while ((int64_t)hwant < std::min<int64_t>(2 * F->d.nv, (int64_t)1 << 28)) hwant <<= 1;
     hwant = (uint32_t)std::min<int64_t>((int64_t)hwant << attempt, (int64_t)1 << 29);
     if (hwant > F->W.hash_cap) {
       dev_free(F->W.hkeys);
@@ -665,6 +701,17 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(B.dsum);
   dev_free(B.counters);
   dev_free(B.contrib);
+  dev_free(B.A.counts);
+  dev_free(B.A.kept);
+  dev_free(B.A.kept_off);
+  dev_free(B.A.col_point);
+  dev_free(B.A.H.u);
+  dev_free(B.A.H.v);
+  dev_free(B.A.H.minv);
+  dev_free(B.A.H.row);
+  dev_free(B.A.H.pm);
+  dev_free(B.A.H.way);
+  dev_free(B.A.H.used);
   if (F->h_flags) cudaFreeHost(F->h_flags);
   for (auto e : F->ev_pool) cudaEventDestroy(e);
   delete F;

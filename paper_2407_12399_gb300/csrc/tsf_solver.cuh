@@ -45,6 +45,23 @@ struct HungWork {
   uint8_t* used;
 };
 
+// Device-side buffers of the reduced assignment.
+struct AsgDev {
+  int32_t* plist;      // non-still points, grouped: group g at [pbase[g], pbase[g]+np[g])
+  int32_t* tlist;      // free targets, grouped the same way
+  int32_t* counts;     // [0..3] np per group, [4..7] k per group, [8] overflow flag, [9] kept head
+  Cand* kept;          // candidate lists, per target at kept_off[t], nkept[t] entries
+  uint32_t* kept_off;  // per position in tlist
+  uint32_t* nkept;
+  uint32_t* is_col;    // per position in plist
+  uint32_t* colpos;
+  int32_t* col_point;
+  int32_t* col_to_row;
+  double* diag_t;
+  HungWork H;          // arrays of np + nt + 8 entries, split per group
+  int cap_kept;
+};
+
 struct SolverBufs {
   Pt* tmp_pts;
   int32_t *idxA, *idxB, *idxC, *idxD;
@@ -67,6 +84,7 @@ struct SolverBufs {
   Contrib* contrib;
   int cap_k, cap_cand, cap_cols;
   int64_t cap_kept;
+  AsgDev A;
 };
 
 struct AssignStats {
