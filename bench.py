@@ -92,6 +92,19 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def replica_throughput(total_ms, steps, world, device=None):
+    """Whole-job iterations/s for `world` independent replicas: every rank ran
+    `steps` iterations; the job took as long as the slowest rank (max-reduce,
+    the only collective; the path itself exchanges nothing)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def make_field():
     from paper_2407_12399_gb300 import synthetic
     return synthetic.filament_field(SHAPE, seed=1)
@@ -197,10 +210,8 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
     prof = tsf.tsf_profile_read(fld._h)
+    value, total_ms = replica_throughput(total_ms, args.steps, world, device="cuda")
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     fld.close()
 
@@ -237,7 +248,6 @@ def run_gpu(args):
     sort_bytes = nv * 80.0  # 4 radix passes (hist read + scatter read/write) + rank scatter
     shares = {k: round(v[0] / max(total_ms, 1e-9), 4) for k, v in prof.items()}
     top = max(prof, key=lambda k: prof[k][0])
-    value = world * args.steps / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
