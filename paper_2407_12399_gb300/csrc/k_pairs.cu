@@ -266,6 +266,14 @@ __global__ void k_mark_d0(int n1, const int32_t* __restrict__ kill, uint8_t* __r
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n1) killed[i] = kill[i] >= 0 ? 1 : 0;
 }
+__global__ void k_d0mask_clear(int n1, CritLists L, uint32_t* __restrict__ d0mask) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n1) d0mask[L.c1_vn[i] >> 4] = 0u;
+}
+__global__ void k_d0mask_set(int n1, CritLists L, const int32_t* __restrict__ kill, uint32_t* __restrict__ d0mask) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n1 && kill[i] >= 0) atomicOr(&d0mask[L.c1_vn[i] >> 4], 1u << (L.c1_vn[i] & 15u));
+}
 
 void launch_d0(const Dims& d, const NbrDelta& nd, const CritLists& L, int n0, int n1, const uint8_t* vnext8,
                const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status, cudaStream_t st) {
@@ -274,6 +282,8 @@ void launch_d0(const Dims& d, const NbrDelta& nd, const CritLists& L, int n0, in
     k_uf_rounds<<<1, kUFT, 0, st>>>(n1, n0, false, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
                                     P.d0_min, status); note_launch();
     k_mark_d0<<<(n1 + 255) / 256, 256, 0, st>>>(n1, P.d0_min, P.d0_killed); note_launch();
+    k_d0mask_clear<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, P.d0mask); note_launch();
+    k_d0mask_set<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, P.d0_min, P.d0mask); note_launch();
   }
 }
 
@@ -300,6 +310,7 @@ struct D1Ctx {
   const uint32_t* c1base;
   CritLists L;
   const uint8_t* d0_killed;
+  const uint32_t* d0mask;
 };
 
 __device__ __forceinline__ int nbr_of_pair(const Dims& d, uint32_t hi, uint32_t lo) {
@@ -684,6 +695,7 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
           for (int k = 0; k < 5; ++k) d4[k] = __ldg(s4 + k);
         }
         uint32_t crit = rec_crit_edges(rc);
+        uint32_t negcrit = ((crit >> 0) != 0) ? __ldg(c.d0mask + v) : 0u;
         int nl = (int)((t.q[0] >> 56) & 15ull);
         int8_t pos[14];
 #pragma unroll
@@ -698,8 +710,9 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
           if (!((m >> x) & 1u)) continue;
           m &= ~(1u << x);
           if ((crit >> x) & 1u) {
-            int ci = crit_edge_index(c, v, rc, x);
-            if (ci >= 0 && !c.d0_killed[ci]) myouts[myout++] = (unsigned long long)ci;
+            // positive critical edge v*x: part of the Morse boundary (its C1
+            // index is looked up once, when the column is finished)
+            if (!((negcrit >> x) & 1u)) myouts[myout++] = ((unsigned long long)v << 4) | (unsigned)x;
             continue;
           }
           int y = (int)((t.q[1] >> (4 * x)) & 15ull);
@@ -726,13 +739,16 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
         // memory operations for all of them back to back
         uint32_t slot[14];
         unsigned long long seen[14];
+        uint32_t trank[14];
 #pragma unroll
         for (int hn = 0; hn < 14; ++hn) {
           slot[hn] = 0xFFFFFFFFu;
           if (tmask[hn]) {
-            unsigned long long key = colkey | (uint32_t)((int32_t)v + snd[hn]);
+            uint32_t hv = (uint32_t)((int32_t)v + snd[hn]);
+            unsigned long long key = colkey | hv;
             slot[hn] = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
             seen[hn] = W.hkeys[slot[hn]];
+            trank[hn] = __ldg(c.rank + hv);
           }
         }
 #pragma unroll
@@ -748,7 +764,7 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
 #pragma unroll
         for (int hn = 0; hn < 14; ++hn)
           if (olds[hn] == 0) {
-            if (nnew < kNewPerLane) mynew[nnew++] = __ldg(c.rank + (uint32_t)((int32_t)v + snd[hn]));
+            if (nnew < kNewPerLane) mynew[nnew++] = trank[hn];
             else overflow = true;
           }
       }
@@ -845,6 +861,19 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
     }
     return;
   }
+  // (v, x) -> index of the critical edge v*x in C1 (lexicographic order)
+  for (int i = lane; i < nout; i += 32) {
+    uint32_t v = (uint32_t)(outv[i] >> 4);
+    int x = (int)(outv[i] & 15ull);
+    int cnt = __popc(rec_crit_edges(ld_rec(c.rec, v)));
+    uint32_t base = c.c1base[v];
+    int ci = -1;
+    for (int k2 = 0; k2 < cnt; ++k2)
+      if ((int)(c.L.c1_vn[base + k2] & 15u) == x) ci = (int)(base + k2);
+    outv[i] = (unsigned long long)(ci < 0 ? 0 : ci);
+    if (ci < 0) atomicOr(status, kErrInconsistent);
+  }
+  __syncwarp();
   if (lane == 0) {
     // insertion sort descending, then cancel equal pairs
     for (int i = 1; i < nout; ++i) {
@@ -967,6 +996,7 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   c.c1base = c1base;
   c.L = L;
   c.d0_killed = P.d0_killed;
+  c.d0mask = P.d0mask;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, 72, st);
   k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();

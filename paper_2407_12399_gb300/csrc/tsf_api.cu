@@ -650,6 +650,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->PS.reserve);
   dev_free(F->PO.d0_min);
   dev_free(F->PO.d0_killed);
+  dev_free(F->PO.d0mask);
   dev_free(F->PO.d2_max);
   dev_free(F->PO.d1_edge);
   dev_free(F->W.cols);
@@ -745,6 +746,7 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
     ck(dev_alloc(&F->cidx, nv));
     ck(dev_alloc(&F->c1base, nv));
     ck(dev_alloc(&F->c2base, nv));
+    ck(dev_alloc(&F->PO.d0mask, nv));
     ck(dev_alloc(&F->tile_counts, crit_tiles(nv)));
     ck(dev_alloc(&F->totals, 1));
     ck(dev_alloc(&F->status, 1));

@@ -36,6 +36,7 @@ struct PairOut {
   int32_t* d2_max;     // per critical triangle: index of the maximum it kills, -1
   int32_t* d1_edge;    // per critical triangle: critical edge paired (D1), -1
   uint8_t* d0_killed;  // per critical edge: 1 if it is a D0 death (negative)
+  uint32_t* d0mask;    // per vertex: bit a set if the critical edge v*a is a D0 death
 };
 
 // ---- k_sort.cu -----------------------------------------------------------
