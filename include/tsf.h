@@ -200,7 +200,7 @@ int64_t tsf_kernel_launches(void);
  * number of pairs, TSF_ECAPACITY when it exceeds cap_pairs.  lx*ly*lz above
  * TSF_STATIC_MAX_VERTICES is rejected with TSF_EINVAL.
  *
- * All intermediate data lives in one fixed device array of about 6.4 MB
+ * All intermediate data lives in one fixed device array of about 6.6 MB
  * (sized for TSF_STATIC_MAX_VERTICES vertices) that every GPU loading this
  * library holds until the process exits.  Every call shares that array and
  * finds the previous call's contents in it; calls that overlap on the GPU

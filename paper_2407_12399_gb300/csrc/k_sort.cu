@@ -2,6 +2,8 @@
 // radix sort of (value key, vertex id), 4 passes of 8 bits, then the rank
 // scatter.  Stability of every pass keeps equal values in id order, which is
 // the id tie-break of the vertex order.
+#include <algorithm>
+
 #include "tsf_kernels.cuh"
 
 namespace tsf {
@@ -187,35 +189,171 @@ void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
   k_scan_apply<<<nb, kST, 0, st>>>(in, n, sums, out); note_launch();
 }
 
+// ---------------------------------------------------------------------------
+// Onesweep: one histogram pass for the four digits, then one kernel per digit
+// that ranks a tile, publishes its digit counts and finds its global offsets
+// by a decoupled look-back over the earlier tiles (tile ids come from an
+// atomic counter, so a block only waits for tiles that started before it).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kLbAgg = 1u << 30, kLbInc = 2u << 30, kLbVal = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 24;
+
+__global__ void k_os_hist(int64_t n, const float* __restrict__ f, uint32_t* __restrict__ hist, uint32_t* status) {
+  __shared__ uint32_t h[4][256];
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float x = __ldg(f + i);
+    bad |= !isfinite(x);
+    uint32_t k = value_key(x);
+    atomicAdd(&h[0][k & 255u], 1u);
+    atomicAdd(&h[1][(k >> 8) & 255u], 1u);
+    atomicAdd(&h[2][(k >> 16) & 255u], 1u);
+    atomicAdd(&h[3][k >> 24], 1u);
+  }
+  if (bad) atomicOr(status, kErrNaN);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+    uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(hist + i, c);
+  }
+}
+
+// exclusive scan of each digit's 256 counts (one block of 256 threads)
+__global__ void k_os_bases(uint32_t* __restrict__ hist) {
+  __shared__ uint32_t t[256];
+  for (int pass = 0; pass < 4; ++pass) {
+    uint32_t v = hist[pass * 256 + threadIdx.x];
+    t[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+      uint32_t a = threadIdx.x >= o ? t[threadIdx.x - o] : 0u;
+      __syncthreads();
+      t[threadIdx.x] += a;
+      __syncthreads();
+    }
+    hist[pass * 256 + threadIdx.x] = t[threadIdx.x] - v;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kRT) k_os_pass(int64_t n, int shift, bool first, bool last,
+                                                 const float* __restrict__ f, const uint32_t* __restrict__ keys_in,
+                                                 const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+                                                 uint32_t* __restrict__ vals_out, const uint32_t* __restrict__ bases,
+                                                 uint32_t* lookback, uint32_t* tile_counter, uint32_t* status) {
+  __shared__ uint32_t whist[kRW][256];
+  __shared__ uint32_t s_off[256];
+  __shared__ uint32_t s_tile;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+  for (int i = threadIdx.x; i < kRW * 256; i += kRT) (&whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t wbase = (int64_t)tile * kRTile + (int64_t)w * kRWarpItems;
+  uint32_t key[kRI], val[kRI];
+#pragma unroll
+  for (int c = 0; c < kRI; ++c) {
+    int64_t i = wbase + c * 32 + lane;
+    key[c] = 0xFFFFFFFFu;
+    val[c] = 0;
+    if (i < n) {
+      key[c] = first ? value_key(__ldg(f + i)) : __ldg(keys_in + i);
+      val[c] = first ? (uint32_t)i : __ldg(vals_in + i);
+    }
+  }
+  // per-warp digit counts (the warp's 512 items are contiguous and in order)
+#pragma unroll
+  for (int c = 0; c < kRI; ++c) {
+    int64_t i = wbase + c * 32 + lane;
+    uint32_t dg = i < n ? (key[c] >> shift) & 255u : 256u;
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+    if (dg < 256 && lane == __ffs(peers) - 1) whist[w][dg] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // tile count per digit; per-warp bases inside the tile
+  const uint32_t d = threadIdx.x;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int ww = 0; ww < kRW; ++ww) {
+    uint32_t c = whist[ww][d];
+    whist[ww][d] = cnt;
+    cnt += c;
+  }
+  volatile uint32_t* lb = lookback;
+  uint32_t excl = 0;
+  if (tile == 0) {
+    lb[d] = kLbInc | cnt;
+  } else {
+    lb[(int64_t)tile * 256 + d] = kLbAgg | cnt;
+    int64_t t = (int64_t)tile - 1;
+    int spins = 0;
+    while (t >= 0) {
+      uint32_t word = lb[t * 256 + d];
+      uint32_t flag = word & ~kLbVal;
+      if (flag == 0) {
+        if (++spins > kSpinLimit) {
+          atomicOr(status, kErrSpin);
+          break;
+        }
+        continue;
+      }
+      excl += word & kLbVal;
+      if (flag == kLbInc) break;
+      --t;
+    }
+    lb[(int64_t)tile * 256 + d] = kLbInc | (excl + cnt);
+  }
+  s_off[d] = bases[d] + excl;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int c = 0; c < kRI; ++c) {
+    int64_t i = wbase + c * 32 + lane;
+    uint32_t dg = i < n ? (key[c] >> shift) & 255u : 256u;
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+    uint32_t pos = 0;
+    if (dg < 256) pos = s_off[dg] + whist[w][dg] + __popc(peers & lt);
+    __syncwarp();
+    if (dg < 256) {
+      if (!last) keys_out[pos] = key[c];
+      vals_out[pos] = val[c];
+      if (lane == __ffs(peers) - 1) whist[w][dg] += __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
 int64_t sort_scratch_words(int64_t n) {
   int64_t ntiles = (n + kRTile - 1) / kRTile;
-  int64_t counts = 256 * ntiles;
-  int64_t sums = (counts + kSTile - 1) / kSTile + 1;
-  return 4 * n + 2 * counts + sums + 64;
+  // keys/ids ping-pong, 4 digit histograms, 4 tile counters, 4 look-back tables
+  return 4 * n + 1024 + 64 + 4 * 256 * ntiles + 64;
 }
 
 // Vertex order: order[r] = id of the r-th vertex, rank[id] = r.
 void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, uint32_t* scratch, uint32_t* status,
                   cudaStream_t st) {
   int ntiles = (int)((n + kRTile - 1) / kRTile);
-  int64_t ncounts = 256 * (int64_t)ntiles;
   uint32_t* kA = scratch;
   uint32_t* vA = kA + n;
   uint32_t* kB = vA + n;
   uint32_t* vB = kB + n;
-  uint32_t* counts = vB + n;
-  uint32_t* offs = counts + ncounts;
-  uint32_t* sums = offs + ncounts;
+  uint32_t* hist = vB + n;
+  uint32_t* counters = hist + 1024;
+  uint32_t* lookback = counters + 64;
+  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (1024 + 64 + 4 * 256 * (size_t)ntiles), st);
+  k_os_hist<<<std::min(ntiles, 1216), 256, 0, st>>>(n, f, hist, status); note_launch();
+  k_os_bases<<<1, 256, 0, st>>>(hist); note_launch();
   const uint32_t* kin = nullptr;
   const uint32_t* vin = nullptr;
   for (int pass = 0; pass < 4; ++pass) {
     bool first = pass == 0, last = pass == 3;
-    int shift = 8 * pass;
     uint32_t* kout = (pass & 1) ? kB : kA;
     uint32_t* vout = last ? order : ((pass & 1) ? vB : vA);
-    k_rs_hist<<<ntiles, kRT, 0, st>>>(n, shift, first, f, kin, counts, ntiles, status); note_launch();
-    exclusive_scan_u32(counts, offs, ncounts, sums, st);
-    k_rs_scatter<<<ntiles, kRT, 0, st>>>(n, shift, first, last, f, kin, vin, kout, vout, offs, ntiles); note_launch();
+    k_os_pass<<<ntiles, kRT, 0, st>>>(n, 8 * pass, first, last, f, kin, vin, kout, vout, hist + 256 * pass,
+                                      lookback + (size_t)pass * 256 * ntiles, counters + pass, status); note_launch();
     kin = kout;
     vin = vout;
   }

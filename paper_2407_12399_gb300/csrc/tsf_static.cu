@@ -19,7 +19,7 @@ namespace {
 
 constexpr int64_t kMaxV = TSF_STATIC_MAX_VERTICES;
 // counter (2 words) + status (1) padding to 64 words, order, rank, sort scratch
-constexpr int64_t kSortWords = 4 * kMaxV + 2 * 256 * (kMaxV / 4096 + 1) + (256 * (kMaxV / 4096 + 1)) / 4096 + 1 + 64;
+constexpr int64_t kSortWords = 4 * kMaxV + 1024 + 64 + 4 * 256 * (kMaxV / 4096 + 1) + 64;
 constexpr int64_t kWords = 64 + 2 * kMaxV + kSortWords;
 
 static __device__ __align__(256) uint32_t g_scratch[kWords];
