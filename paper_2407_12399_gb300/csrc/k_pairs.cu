@@ -611,192 +611,267 @@ __device__ __forceinline__ int warp_exscan(int v, int& total) {
   return inc - v;
 }
 
-constexpr int kNewPerLane = 48;
+// One lower-star visit of a column: take the star's pending parity mask,
+// eliminate its gradient-paired edges (largest first; partners y stay in the
+// star), emit positive critical edges as (v << 4 | x), and xor the link-path
+// edges into the target stars' masks (returns the targets that became
+// pending, by rank).
+template <int KNEW>
+__device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned long long colkey, uint32_t r,
+                                         const int32_t* snd, const Geo& sg, uint32_t* status,
+                                         unsigned long long* myouts, int& myout, uint32_t* mynew, int& nnew,
+                                         bool& overflow, int& visits) {
+  uint32_t v = c.order[r];
+  uint32_t h = hslot(W, colkey | v, status);
+  uint32_t m = h == 0xFFFFFFFFu ? 0u : atomicExch(&W.hmask[h], 0u);
+  if (!m) return;
+  ++visits;
+  Rec rc = ld_rec(c.rec, v);
+  D1Tab t;
+  {
+    const uint4* s4 = reinterpret_cast<const uint4*>(c.tab + v);
+    uint4* d4 = reinterpret_cast<uint4*>(&t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) d4[k] = __ldg(s4 + k);
+  }
+  uint32_t crit = rec_crit_edges(rc);
+  uint32_t negcrit = crit ? __ldg(c.d0mask + v) : 0u;
+  int nl = (int)((t.q[0] >> 56) & 15ull);
+  int8_t pos[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) pos[k] = -1;
+  for (int p = 0; p < nl; ++p) pos[(t.q[0] >> (4 * p)) & 15ull] = (int8_t)p;
+  int lowest = (int)(t.q[0] & 15ull);
+  uint64_t path = 0;
+  for (int p = nl - 1; p >= 1; --p) {
+    int x = (int)((t.q[0] >> (4 * p)) & 15ull);
+    if (!((m >> x) & 1u)) continue;
+    m &= ~(1u << x);
+    if ((crit >> x) & 1u) {
+      if (!((negcrit >> x) & 1u)) myouts[myout++] = ((unsigned long long)v << 4) | (unsigned)x;
+      continue;
+    }
+    int y = (int)((t.q[1] >> (4 * x)) & 15ull);
+    if (y == 15) {
+      atomicOr(status, kErrInconsistent);
+      continue;
+    }
+    if (y != lowest) m ^= 1u << y;
+    path ^= tab_path(t, x);
+  }
+  uint32_t tmask[14];
+#pragma unroll
+  for (int k = 0; k < 14; ++k) tmask[k] = 0;
+  for (uint64_t pm = path; pm; pm &= pm - 1) {
+    int le = __ffsll((long long)pm) - 1;
+    int na = sg.edge[le][0], nbv = sg.edge[le][1];
+    bool a_hi = pos[na] > pos[nbv];
+    int hn = a_hi ? na : nbv, ln = a_hi ? nbv : na;
+    int dir = nbr_index(sg, sg.off[ln][0] - sg.off[hn][0], sg.off[ln][1] - sg.off[hn][1], sg.off[ln][2] - sg.off[hn][2]);
+    tmask[hn] ^= 1u << dir;
+  }
+  uint32_t slot[14];
+  unsigned long long seen[14];
+  uint32_t trank[14];
+#pragma unroll
+  for (int hn = 0; hn < 14; ++hn) {
+    slot[hn] = 0xFFFFFFFFu;
+    if (tmask[hn]) {
+      uint32_t hv = (uint32_t)((int32_t)v + snd[hn]);
+      unsigned long long key = colkey | hv;
+      slot[hn] = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
+      seen[hn] = W.hkeys[slot[hn]];
+      trank[hn] = __ldg(c.rank + hv);
+    }
+  }
+#pragma unroll
+  for (int hn = 0; hn < 14; ++hn)
+    if (tmask[hn]) {
+      unsigned long long key = colkey | (uint32_t)((int32_t)v + snd[hn]);
+      if (seen[hn] != key) slot[hn] = hslot(W, key, status);
+    }
+  uint32_t olds[14];
+#pragma unroll
+  for (int hn = 0; hn < 14; ++hn)
+    olds[hn] = (tmask[hn] && slot[hn] != 0xFFFFFFFFu) ? atomicXor(&W.hmask[slot[hn]], tmask[hn]) : 1u;
+#pragma unroll
+  for (int hn = 0; hn < 14; ++hn)
+    if (olds[hn] == 0) {
+      if (nnew < KNEW) mynew[nnew++] = trank[hn];
+      else overflow = true;
+    }
+}
 
-__global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
-  __shared__ Geo sg;
-  __shared__ int32_t snd[14];
+// Group-wide (NT threads: one warp or one block) helpers.
+template <int NT>
+__device__ __forceinline__ void gsync() {
+  if (NT == 32) __syncwarp();
+  else __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive; sm: >= NT/32 + 1 ints
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (NT == 32) {
+    total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    return inc - v;
+  }
+  if (lane == 31) sm[w] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < NT / 32; ++k) {
+      int t = sm[k];
+      sm[k] = run;
+      run += t;
+    }
+    sm[NT / 32] = run;
+  }
+  __syncthreads();
+  int res = sm[w] + inc - v;
+  total = sm[NT / 32];
+  __syncthreads();
+  return res;
+}
+
+// Round loop of one column.  Phase A (NT = 32, max_rounds > 0): every column,
+// one warp; a column still open after max_rounds saves its frontier and is
+// listed for phase B (NT = 256, one block per listed column).
+template <int NT, int FCAP, int SCAP, int KNEW>
+__global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int ncols, int max_rounds,
+                                                       uint32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Geo& sg = *reinterpret_cast<Geo*>(smem);
+  int32_t* snd = reinterpret_cast<int32_t*>(smem + ((sizeof(Geo) + 15) & ~15));
+  int* scan_sm = snd + 16;  // NT/32 + 1 <= 16
+  uint32_t* front = reinterpret_cast<uint32_t*>(scan_sm + 16);
+  uint32_t* other = front + FCAP;
+  uint32_t* stage = other + FCAP;
+  __shared__ int s_nf, s_flag;
+  __shared__ Vec s_out;
   if (threadIdx.x < 14) snd[threadIdx.x] = c.nd.d[threadIdx.x];
   geo_to_shared(sg);
-  __shared__ uint32_t fa[kFront], fb[kFront];
-  __shared__ uint32_t stage[2048];  // >= next power of two of 32 * kNewPerLane
-  __shared__ unsigned long long outv[256];
-  const int lane = threadIdx.x;
-  const int j = blockIdx.x;
-  if (j >= ncols) return;
+  const bool phase_b = max_rounds <= 0;
+  int j;
+  if (phase_b) {
+    if ((int)blockIdx.x >= *W.nbig) return;
+    j = W.big[blockIdx.x];
+  } else {
+    j = blockIdx.x;
+    if (j >= ncols) return;
+  }
+  const int tid = threadIdx.x;
   unsigned long long colkey = (unsigned long long)j << 32;
-  uint32_t* front = fa;
-  uint32_t* other = fb;
-  int nf = 0;
-  int nout = 0;
-  bool failed = false;
-  // seed: the boundary of the critical triangle, as parity masks
-  if (lane == 0) {
-    uint32_t ve = c.L.c2_ve[W.cols[j]];
-    uint32_t v0 = ve >> 6;
-    int e0 = (int)(ve & 63u);
-    uint32_t ends[3][2] = {{v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]])},
-                           {v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])},
-                           {(uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]]),
-                            (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])}};
-    for (int k = 0; k < 3; ++k) {
-      uint32_t p = ends[k][0], q = ends[k][1];
-      uint32_t rp = c.rank[p], rq = c.rank[q];
-      uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
-      uint32_t h = hslot(W, colkey | hi, status);
-      if (h == 0xFFFFFFFFu) continue;
-      uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo, sg));
-      if (old == 0) {
-        // insert rank(hi) into the (tiny) front, kept descending and unique
-        uint32_t r = max(rp, rq);
-        int pos = 0;
-        while (pos < nf && front[pos] > r) ++pos;
-        if (pos == nf || front[pos] != r) {
-          for (int t = nf; t > pos; --t) front[t] = front[t - 1];
-          front[pos] = r;
-          ++nf;
+  if (tid == 0) {
+    s_flag = 0;
+    if (phase_b) {
+      uint4 cs = W.cont[j];
+      s_nf = (int)cs.y;
+      s_out.off = cs.z;
+      s_out.size = cs.w;
+      s_out.cap = W.cont_cap[j];
+      s_out.h = W.pool + s_out.off;
+    } else {
+      s_nf = 0;
+      if (!vec_alloc(W, s_out, 64, status)) s_flag = 1;
+      // seed: the boundary of the critical triangle, as parity masks
+      uint32_t ve = c.L.c2_ve[W.cols[j]];
+      uint32_t v0 = ve >> 6;
+      int e0 = (int)(ve & 63u);
+      uint32_t ends[3][2] = {{v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]])},
+                             {v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])},
+                             {(uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]]),
+                              (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])}};
+      for (int k = 0; k < 3; ++k) {
+        uint32_t p = ends[k][0], q = ends[k][1];
+        uint32_t rp = c.rank[p], rq = c.rank[q];
+        uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
+        uint32_t h = hslot(W, colkey | hi, status);
+        if (h == 0xFFFFFFFFu) continue;
+        uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo, sg));
+        if (old == 0) {
+          uint32_t r = max(rp, rq);
+          int ps = 0;
+          while (ps < s_nf && front[ps] > r) ++ps;
+          if (ps == s_nf || front[ps] != r) {
+            for (int t = s_nf; t > ps; --t) front[t] = front[t - 1];
+            front[ps] = r;
+            ++s_nf;
+          }
         }
       }
     }
   }
-  nf = __shfl_sync(0xFFFFFFFFu, nf, 0);
-  __syncwarp();
-  int visits = 0;
-  int rounds = 0;
-  unsigned long long tv = 0, ts = 0, tm = 0, tu = 0, fsum = 0;
-  for (int round = 0; nf > 0; ++round) {
-    ++rounds;
-    fsum += (unsigned long long)nf;
-    long long c0 = clock64();
-    if (round > kD1StepLimit) {
-      if (lane == 0) atomicOr(status, kErrRounds);
+  gsync<NT>();
+  if (phase_b) {
+    uint4 cs = W.cont[j];
+    for (int i = tid; i < (int)cs.y; i += NT) front[i] = (uint32_t)W.pool[cs.x + i];
+  }
+  gsync<NT>();
+  int visits = 0, rounds = 0;
+  bool failed = s_flag != 0;
+  while (!failed) {
+    int nf = s_nf;
+    if (nf == 0) break;
+    if (!phase_b && rounds >= max_rounds) break;
+    if (rounds > kD1StepLimit) {
+      if (tid == 0) atomicOr(status, kErrRounds);
       failed = true;
       break;
     }
-    int nb = min(32, nf);
-    int nnew = 0;
-    uint32_t mynew[kNewPerLane];
-    int myout = 0;
+    ++rounds;
+    int nb = min(NT, nf);
+    int nnew = 0, myout = 0;
+    uint32_t mynew[KNEW];
     unsigned long long myouts[14];
     bool overflow = false;
-    if (lane < nb) {
-      uint32_t r = front[lane];
-      uint32_t v = c.order[r];
-      uint32_t h = hslot(W, colkey | v, status);
-      uint32_t m = h == 0xFFFFFFFFu ? 0u : atomicExch(&W.hmask[h], 0u);
-      if (m) {
-        ++visits;
-        Rec rc = ld_rec(c.rec, v);
-        D1Tab t;
-        {
-          const uint4* s4 = reinterpret_cast<const uint4*>(c.tab + v);
-          uint4* d4 = reinterpret_cast<uint4*>(&t);
-#pragma unroll
-          for (int k = 0; k < 5; ++k) d4[k] = __ldg(s4 + k);
-        }
-        uint32_t crit = rec_crit_edges(rc);
-        uint32_t negcrit = ((crit >> 0) != 0) ? __ldg(c.d0mask + v) : 0u;
-        int nl = (int)((t.q[0] >> 56) & 15ull);
-        int8_t pos[14];
-#pragma unroll
-        for (int k = 0; k < 14; ++k) pos[k] = -1;
-        for (int p = 0; p < nl; ++p) pos[(t.q[0] >> (4 * p)) & 15ull] = (int8_t)p;
-        int lowest = (int)(t.q[0] & 15ull);
-        // the link edges pushed to lower stars, accumulated per target star
-        // (every target is a lower neighbour of v) before touching the table
-        uint64_t path = 0;
-        for (int p = nl - 1; p >= 1; --p) {
-          int x = (int)((t.q[0] >> (4 * p)) & 15ull);
-          if (!((m >> x) & 1u)) continue;
-          m &= ~(1u << x);
-          if ((crit >> x) & 1u) {
-            // positive critical edge v*x: part of the Morse boundary (its C1
-            // index is looked up once, when the column is finished)
-            if (!((negcrit >> x) & 1u)) myouts[myout++] = ((unsigned long long)v << 4) | (unsigned)x;
-            continue;
-          }
-          int y = (int)((t.q[1] >> (4 * x)) & 15ull);
-          if (y == 15) {
-            atomicOr(status, kErrInconsistent);
-            continue;
-          }
-          if (y != lowest) m ^= 1u << y;
-          path ^= tab_path(t, x);
-        }
-        uint32_t tmask[14];
-#pragma unroll
-        for (int k = 0; k < 14; ++k) tmask[k] = 0;
-        for (uint64_t pm = path; pm; pm &= pm - 1) {
-          int le = __ffsll((long long)pm) - 1;
-          int na = sg.edge[le][0], nbv = sg.edge[le][1];
-          bool a_hi = pos[na] > pos[nbv];
-          int hn = a_hi ? na : nbv, ln = a_hi ? nbv : na;
-          int dir = nbr_index(sg, sg.off[ln][0] - sg.off[hn][0], sg.off[ln][1] - sg.off[hn][1],
-                              sg.off[ln][2] - sg.off[hn][2]);
-          tmask[hn] ^= 1u << dir;
-        }
-        // the (at most 13) target stars are independent: issue each phase's
-        // memory operations for all of them back to back
-        uint32_t slot[14];
-        unsigned long long seen[14];
-        uint32_t trank[14];
-#pragma unroll
-        for (int hn = 0; hn < 14; ++hn) {
-          slot[hn] = 0xFFFFFFFFu;
-          if (tmask[hn]) {
-            uint32_t hv = (uint32_t)((int32_t)v + snd[hn]);
-            unsigned long long key = colkey | hv;
-            slot[hn] = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
-            seen[hn] = W.hkeys[slot[hn]];
-            trank[hn] = __ldg(c.rank + hv);
-          }
-        }
-#pragma unroll
-        for (int hn = 0; hn < 14; ++hn)
-          if (tmask[hn]) {
-            unsigned long long key = colkey | (uint32_t)((int32_t)v + snd[hn]);
-            if (seen[hn] != key) slot[hn] = hslot(W, key, status);  // probe / insert
-          }
-        uint32_t olds[14];
-#pragma unroll
-        for (int hn = 0; hn < 14; ++hn)
-          olds[hn] = (tmask[hn] && slot[hn] != 0xFFFFFFFFu) ? atomicXor(&W.hmask[slot[hn]], tmask[hn]) : 1u;
-#pragma unroll
-        for (int hn = 0; hn < 14; ++hn)
-          if (olds[hn] == 0) {
-            if (nnew < kNewPerLane) mynew[nnew++] = trank[hn];
-            else overflow = true;
-          }
+    if (tid < nb) d1_visit<KNEW>(c, W, colkey, front[tid], snd, sg, status, myouts, myout, mynew, nnew, overflow, visits);
+    if (overflow) atomicOr(&s_flag, 1);
+    // outputs: append to the column's list in the pool
+    int otot;
+    int ooff = gscan<NT>(myout, otot, scan_sm);
+    if (tid == 0 && otot > 0 && s_out.size + otot > s_out.cap) {
+      Vec n;
+      uint32_t cap = s_out.cap;
+      while (cap < s_out.size + otot) cap *= 2;
+      if (vec_alloc(W, n, cap, status)) {
+        for (uint32_t i = 0; i < s_out.size; ++i) n.h[i] = s_out.h[i];
+        n.size = s_out.size;
+        s_out = n;
+      } else {
+        s_flag = 1;
       }
     }
-    if (__any_sync(0xFFFFFFFFu, overflow)) {
+    gsync<NT>();
+    if (s_flag) {
       failed = true;
       break;
     }
-    long long c1 = clock64();
-    tv += (unsigned long long)(c1 - c0);
-    // outputs of this round
-    int otot;
-    int ooff = warp_exscan(myout, otot);
-    if (otot > 0) {
-      if (nout + otot > 256) {
-        failed = true;
-        break;
-      }
-      for (int k = 0; k < myout; ++k) outv[nout + ooff + k] = myouts[k];
-      nout += otot;
-    }
-    // new ranks: stage, sort descending (bitonic), merge with front[nb:]
+    for (int k = 0; k < myout; ++k) s_out.h[s_out.size + ooff + k] = myouts[k];
+    gsync<NT>();
+    if (tid == 0) s_out.size += otot;
+    // new ranks: stage, sort descending (bitonic), merge with front[nb..nf)
     int ntot;
-    int noff = warp_exscan(nnew, ntot);
+    int noff = gscan<NT>(nnew, ntot, scan_sm);
+    int rest = nf - nb;
+    if (ntot > SCAP || rest + ntot > FCAP) {
+      failed = true;
+      break;
+    }
     for (int k = 0; k < nnew; ++k) stage[noff + k] = mynew[k];
     int n2 = 1;
     while (n2 < ntot) n2 <<= 1;
-    for (int k = ntot + lane; k < n2; k += 32) stage[k] = 0;
-    __syncwarp();
+    for (int k = ntot + tid; k < n2; k += NT) stage[k] = 0;
+    gsync<NT>();
     for (int size = 2; size <= n2; size <<= 1)
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int i = lane; i < n2; i += 32) {
+        for (int i = tid; i < n2; i += NT) {
           int jx = i ^ stride;
           if (jx > i) {
             bool desc = (i & size) == 0;
@@ -807,20 +882,10 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
             }
           }
         }
-        __syncwarp();
+        gsync<NT>();
       }
-    long long c2 = clock64();
-    ts += (unsigned long long)(c2 - c1);
-    // merge front[nb..nf) (descending, unique) with stage[0..ntot) (descending)
-    int rest = nf - nb;
-    if (rest + ntot > kFront) {
-      failed = true;
-      break;
-    }
-    // output position k takes i elements from A = front[nb..nf) and k-i from
-    // B = stage[0..ntot), both descending (merge path, A first on ties)
     int total = rest + ntot;
-    for (int k = lane; k < total; k += 32) {
+    for (int k = tid; k < total; k += NT) {
       int lo = max(0, k - ntot), hi = min(k, rest);
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -830,87 +895,139 @@ __global__ void __launch_bounds__(32) k_d1_morse_warp(D1Ctx c, D1Work W, int nco
       int i = lo, jb = k - lo;
       other[k] = (i < rest && (jb >= ntot || front[nb + i] >= stage[jb])) ? front[nb + i] : stage[jb];
     }
-    __syncwarp();
-    long long c3 = clock64();
-    tm += (unsigned long long)(c3 - c2);
-    // unique (keep the first of equal neighbours)
+    gsync<NT>();
     int keep_total = 0;
-    for (int base = 0; base < total; base += 32) {
-      int k = base + lane;
+    for (int base = 0; base < total; base += NT) {
+      int k = base + tid;
       int keep = (k < total) && (k == 0 || other[k] != other[k - 1]);
       uint32_t val = k < total ? other[k] : 0;
       int t;
-      int off = warp_exscan(keep, t);
-      __syncwarp();
+      int off = gscan<NT>(keep, t, scan_sm);
       if (keep) front[keep_total + off] = val;
       keep_total += t;
-      __syncwarp();
+      gsync<NT>();
     }
-    nf = keep_total;
-    __syncwarp();
-    tu += (unsigned long long)(clock64() - c3);
+    if (tid == 0) s_nf = keep_total;
+    gsync<NT>();
   }
-  // fallback for this column, or the sorted, mod-2 reduced output
-  int vsum = visits;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) vsum += __shfl_down_sync(0xFFFFFFFFu, vsum, o);
+  // visits of the whole group
+  int vtot;
+  gscan<NT>(visits, vtot, scan_sm);
   if (failed) {
-    if (lane == 0) {
+    if (tid == 0) {
       W.redo[j] = 1;
       W.hsize[j] = 0;
     }
     return;
   }
-  // (v, x) -> index of the critical edge v*x in C1 (lexicographic order)
-  for (int i = lane; i < nout; i += 32) {
-    uint32_t v = (uint32_t)(outv[i] >> 4);
-    int x = (int)(outv[i] & 15ull);
+  if (!phase_b && s_nf > 0) {
+    // still open: save the frontier for phase B
+    __shared__ Vec s_fr;
+    if (tid == 0) {
+      if (!vec_alloc(W, s_fr, (uint32_t)max(s_nf, 1), status)) s_flag = 1;
+    }
+    gsync<NT>();
+    if (s_flag) {
+      if (tid == 0) {
+        W.redo[j] = 1;
+        W.hsize[j] = 0;
+      }
+      return;
+    }
+    for (int i = tid; i < s_nf; i += NT) s_fr.h[i] = front[i];
+    gsync<NT>();
+    if (tid == 0) {
+      W.cont[j] = make_uint4(s_fr.off, (uint32_t)s_nf, s_out.off, s_out.size);
+      W.cont_cap[j] = s_out.cap;
+      W.big[atomicAdd(W.nbig, 1)] = j;
+      W.redo[j] = 0;
+      W.hsize[j] = 0;
+      atomicAdd(&W.stats[0], (unsigned long long)vtot);
+      atomicAdd(&W.stats[2], (unsigned long long)rounds);
+    }
+    return;
+  }
+  // finished: (v, x) -> C1 index, sort descending, cancel equal pairs (Z/2)
+  uint32_t nout = s_out.size;
+  for (uint32_t i = tid; i < nout; i += NT) {
+    uint32_t v = (uint32_t)(s_out.h[i] >> 4);
+    int x = (int)(s_out.h[i] & 15ull);
     int cnt = __popc(rec_crit_edges(ld_rec(c.rec, v)));
     uint32_t base = c.c1base[v];
     int ci = -1;
     for (int k2 = 0; k2 < cnt; ++k2)
       if ((int)(c.L.c1_vn[base + k2] & 15u) == x) ci = (int)(base + k2);
-    outv[i] = (unsigned long long)(ci < 0 ? 0 : ci);
     if (ci < 0) atomicOr(status, kErrInconsistent);
+    s_out.h[i] = (unsigned long long)(ci < 0 ? 0 : ci);
   }
-  __syncwarp();
-  if (lane == 0) {
-    // insertion sort descending, then cancel equal pairs
-    for (int i = 1; i < nout; ++i) {
-      unsigned long long t = outv[i];
-      int k = i - 1;
-      while (k >= 0 && outv[k] < t) {
-        outv[k + 1] = outv[k];
+  gsync<NT>();
+  if ((int)nout <= SCAP) {
+    int n2 = 1;
+    while (n2 < (int)nout) n2 <<= 1;
+    for (int k = tid; k < n2; k += NT) stage[k] = k < (int)nout ? (uint32_t)s_out.h[k] : 0u;
+    gsync<NT>();
+    for (int size = 2; size <= n2; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = tid; i < n2; i += NT) {
+          int jx = i ^ stride;
+          if (jx > i) {
+            bool desc = (i & size) == 0;
+            uint32_t a = stage[i], b = stage[jx];
+            if ((a < b) == desc) {
+              stage[i] = b;
+              stage[jx] = a;
+            }
+          }
+        }
+        gsync<NT>();
+      }
+    if (tid == 0) {
+      int m = 0;
+      for (int i = 0; i < (int)nout;) {
+        int k = i;
+        while (k < (int)nout && stage[k] == stage[i]) ++k;
+        if ((k - i) & 1) s_out.h[m++] = stage[i];
+        i = k;
+      }
+      s_out.size = (uint32_t)m;
+    }
+  } else if (tid == 0) {
+    unsigned long long* o = s_out.h;
+    for (uint32_t i = 1; i < nout; ++i) {
+      unsigned long long t = o[i];
+      int k = (int)i - 1;
+      while (k >= 0 && o[k] < t) {
+        o[k + 1] = o[k];
         --k;
       }
-      outv[k + 1] = t;
+      o[k + 1] = t;
     }
     int m = 0;
-    for (int i = 0; i < nout;) {
+    for (int i = 0; i < (int)nout;) {
       int k = i;
-      while (k < nout && outv[k] == outv[i]) ++k;
-      if ((k - i) & 1) outv[m++] = outv[i];
+      while (k < (int)nout && o[k] == o[i]) ++k;
+      if ((k - i) & 1) o[m++] = o[i];
       i = k;
     }
-    Vec o2;
-    if (vec_alloc(W, o2, max(m, 1), status)) {
-      for (int i = 0; i < m; ++i) o2.h[i] = outv[i];
-      W.hoff[j] = o2.off;
-      W.hsize[j] = m;
-    } else {
-      W.hsize[j] = 0;
-    }
+    s_out.size = (uint32_t)m;
+  }
+  gsync<NT>();
+  if (tid == 0) {
+    W.hoff[j] = s_out.off;
+    W.hsize[j] = s_out.size;
     W.redo[j] = 0;
-    atomicAdd(&W.stats[0], (unsigned long long)vsum);
-    atomicMax(&W.stats[1], (unsigned long long)vsum);
+    atomicAdd(&W.stats[0], (unsigned long long)vtot);
+    atomicMax(&W.stats[1], (unsigned long long)vtot);
     atomicAdd(&W.stats[2], (unsigned long long)rounds);
     atomicMax(&W.stats[3], (unsigned long long)rounds);
-    atomicAdd(&W.stats[4], tv);
-    atomicAdd(&W.stats[5], ts);
-    atomicAdd(&W.stats[6], tm);
-    atomicAdd(&W.stats[7], tu);
-    atomicAdd(&W.stats[8], fsum);
   }
+}
+
+constexpr int kFrontA = 4096, kStageA = 2048, kNewA = 48;
+constexpr int kFrontB = 8192, kStageB = 4096, kNewB = 16;
+
+static size_t d1_group_smem(int fcap, int scap) {
+  return ((sizeof(Geo) + 15) & ~(size_t)15) + 32 * sizeof(int32_t) + (2 * (size_t)fcap + scap) * sizeof(uint32_t);
 }
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
@@ -1000,7 +1117,20 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, 72, st);
   k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();
-  k_d1_morse_warp<<<ncols, 32, 0, st>>>(c, W, ncols, status); note_launch();
+  cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
+  {
+    static bool attr = false;
+    size_t sa = d1_group_smem(kFrontA, kStageA), sb = d1_group_smem(kFrontB, kStageB);
+    if (!attr) {
+      cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, kNewA>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+      cudaFuncSetAttribute(k_d1_morse_group<256, kFrontB, kStageB, kNewB>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+      attr = true;
+    }
+    k_d1_morse_group<32, kFrontA, kStageA, kNewA><<<ncols, 32, sa, st>>>(c, W, ncols, 48, status); note_launch();
+    k_d1_morse_group<256, kFrontB, kStageB, kNewB><<<ncols, 256, sb, st>>>(c, W, ncols, 0, status); note_launch();
+  }
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
   k_d1_reduce<<<1, kUFT, 0, st>>>(W, ncols, n1, P.d1_edge, status); note_launch();
 }

@@ -168,6 +168,13 @@ void grow_crit(tsf_field* F, int n0, int n1, int n2, int n3) {
     dev_free(F->W.hsize);
     dev_free(F->W.lowc);
     dev_free(F->W.redo);
+  dev_free(F->W.cont);
+  dev_free(F->W.cont_cap);
+  dev_free(F->W.big);
+  dev_free(F->W.nbig);
+    dev_free(F->W.cont);
+    dev_free(F->W.cont_cap);
+    dev_free(F->W.big);
     ck(dev_alloc(&F->L.c2_ve, c2));
     ck(dev_alloc(&F->PO.d2_max, c2));
     ck(dev_alloc(&F->PO.d1_edge, c2));
@@ -178,6 +185,10 @@ void grow_crit(tsf_field* F, int n0, int n1, int n2, int n3) {
     ck(dev_alloc(&F->W.hsize, c2));
     ck(dev_alloc(&F->W.lowc, c2));
     ck(dev_alloc(&F->W.redo, c2));
+    ck(dev_alloc(&F->W.cont, c2));
+    ck(dev_alloc(&F->W.cont_cap, c2));
+    ck(dev_alloc(&F->W.big, c2));
+    if (!F->W.nbig) ck(dev_alloc(&F->W.nbig, 1));
     F->cap_c2 = c2;
   }
   if (c3 != F->cap_c3) {
@@ -667,6 +678,10 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->W.hkeys);
   dev_free(F->W.hmask);
   dev_free(F->W.redo);
+  dev_free(F->W.cont);
+  dev_free(F->W.cont_cap);
+  dev_free(F->W.big);
+  dev_free(F->W.nbig);
   SolverBufs& B = F->B;
   dev_free(F->pts);
   dev_free(F->prev);

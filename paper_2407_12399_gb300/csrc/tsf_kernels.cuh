@@ -91,6 +91,10 @@ struct D1Work {
   uint32_t* hmask;
   uint32_t hash_cap;      // power of two
   int32_t* redo;          // columns whose warp frontier overflowed
+  uint4* cont;            // open columns after phase A: frontier off/size, output off/size
+  uint32_t* cont_cap;     // ... output capacity
+  int32_t* big;           // list of open columns
+  int32_t* nbig;
 };
 // returns 0 on success, otherwise a status bit (kErrPool: retry with a larger pool)
 void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
