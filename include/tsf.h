@@ -175,11 +175,12 @@ int tsf_zero_pairs(tsf_field* field, uint64_t* out, int64_t cap_pairs, int64_t* 
  * CUDA events on the field's stream and its device time accumulated (this
  * adds a stream synchronisation per stage).  Stages, in pipeline order:
  * 0 vertex order (sort + ranks), 1 lower-star gradient, 2 critical cells,
- * 3 D0 pairs, 4 D2 pairs, 5 D1 pairs, 6 diagram points, 7 assignment,
- * 8 loss, 9 gradient step.  tsf_profile_read fills ms[] and calls[] (cap >=
+ * 3 D0 pairs, 4 D2 pairs, 5 D1 candidate columns, 6 diagram points,
+ * 7 assignment, 8 loss, 9 gradient step, 10 D1 Morse boundaries, 11 D1
+ * column reduction.  tsf_profile_read fills ms[] and calls[] (cap >=
  * TSF_NSTAGES entries each) with the totals since profiling was enabled;
  * enabling again resets them. */
-#define TSF_NSTAGES 10
+#define TSF_NSTAGES 12
 int tsf_profile_enable(tsf_field* field, int enable);
 int tsf_profile_read(tsf_field* field, double* ms, int64_t* calls, int cap);
 const char* tsf_stage_name(int stage);

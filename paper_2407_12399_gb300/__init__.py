@@ -67,7 +67,7 @@ EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_
            "tsf_set_signal_pairs", "tsf_solver_step", "tsf_simplify", "tsf_get_field", "tsf_set_field",
            "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
            "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static")
-TSF_NSTAGES = 10
+TSF_NSTAGES = 12
 
 _lib = None
 

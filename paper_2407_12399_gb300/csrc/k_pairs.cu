@@ -574,7 +574,6 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
 // lower stars, one per lane.  The projection is linear, so a lower star that
 // receives entries after it was processed simply comes back.
 // ---------------------------------------------------------------------------
-constexpr int kFront = 4096;
 
 __device__ __forceinline__ uint32_t hslot(const D1Work& W, unsigned long long key, uint32_t* status) {
   uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
@@ -1085,10 +1084,8 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int ncols, int n1,
     d1_edge[W.cols[j]] = W.hsize[j] > 0 ? (int)W.pool[W.hoff[j]] : -1;
 }
 
-void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
-               const uint32_t* order, const Rec* rec, const D1Tab* tab, const uint32_t* c1base, D1Work& W,
-               PairOut& P, uint32_t* status, int32_t* h_flags, cudaStream_t st) {
-  if (n2 == 0) return;
+int launch_d1_prepare(int n2, D1Work& W, PairOut& P, int32_t* h_flags, cudaStream_t st) {
+  if (n2 == 0) return 0;
   // candidate columns, in increasing triangle order
   uint32_t* flag = reinterpret_cast<uint32_t*>(W.lowc);  // scratch (n2 entries available)
   uint32_t* pos = reinterpret_cast<uint32_t*>(W.hsize);
@@ -1102,6 +1099,12 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   cudaStreamSynchronize(st);
   int ncols = (int)(tail[0] + tail[1]);
   h_flags[1] = ncols;
+  return ncols;
+}
+
+void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int ncols, const uint32_t* rank,
+                     const uint32_t* order, const Rec* rec, const D1Tab* tab, const uint32_t* c1base, D1Work& W,
+                     PairOut& P, uint32_t* status, cudaStream_t st) {
   if (ncols == 0) return;
   D1Ctx c;
   c.d = d;
@@ -1118,20 +1121,22 @@ void launch_d1(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, in
   cudaMemsetAsync(W.stats, 0, 72, st);
   k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();
   cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
-  {
-    static bool attr = false;
-    size_t sa = d1_group_smem(kFrontA, kStageA), sb = d1_group_smem(kFrontB, kStageB);
-    if (!attr) {
-      cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, kNewA>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
-      cudaFuncSetAttribute(k_d1_morse_group<256, kFrontB, kStageB, kNewB>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-      attr = true;
-    }
-    k_d1_morse_group<32, kFrontA, kStageA, kNewA><<<ncols, 32, sa, st>>>(c, W, ncols, 48, status); note_launch();
-    k_d1_morse_group<256, kFrontB, kStageB, kNewB><<<ncols, 256, sb, st>>>(c, W, ncols, 0, status); note_launch();
+  static bool attr = false;
+  size_t sa = d1_group_smem(kFrontA, kStageA), sb = d1_group_smem(kFrontB, kStageB);
+  if (!attr) {
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, kNewA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sa);
+    cudaFuncSetAttribute(k_d1_morse_group<256, kFrontB, kStageB, kNewB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sb);
+    attr = true;
   }
+  k_d1_morse_group<32, kFrontA, kStageA, kNewA><<<ncols, 32, sa, st>>>(c, W, ncols, 48, status); note_launch();
+  k_d1_morse_group<256, kFrontB, kStageB, kNewB><<<ncols, 256, sb, st>>>(c, W, ncols, 0, status); note_launch();
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
+}
+
+void launch_d1_reduce(int n1, int ncols, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st) {
+  if (ncols == 0) return;
   k_d1_reduce<<<1, kUFT, 0, st>>>(W, ncols, n1, P.d1_edge, status); note_launch();
 }
 

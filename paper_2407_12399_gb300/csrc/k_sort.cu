@@ -19,82 +19,6 @@ __device__ __forceinline__ uint32_t rs_key(bool first, const float* __restrict__
   return first ? value_key(__ldg(f + i)) : __ldg(keys + i);
 }
 
-__global__ void k_rs_hist(int64_t n, int shift, bool first, const float* __restrict__ f,
-                          const uint32_t* __restrict__ keys, uint32_t* __restrict__ counts, int ntiles,
-                          uint32_t* status) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  int64_t base = (int64_t)blockIdx.x * kRTile;
-  bool bad = false;
-#pragma unroll 4
-  for (int k = 0; k < kRI; ++k) {
-    int64_t i = base + (int64_t)k * kRT + threadIdx.x;
-    if (i < n) {
-      if (first) bad |= !isfinite(__ldg(f + i));
-      uint32_t key = rs_key(first, f, keys, i);
-      atomicAdd(&h[(key >> shift) & 255u], 1u);
-    }
-  }
-  if (bad) atomicOr(status, kErrNaN);
-  __syncthreads();
-  counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-__global__ void k_rs_scatter(int64_t n, int shift, bool first, bool last, const float* __restrict__ f,
-                             const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                             uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                             const uint32_t* __restrict__ offsets, int ntiles) {
-  __shared__ uint32_t whist[kRW][256];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kRW * 256; i += kRT) (&whist[0][0])[i] = 0;
-  __syncthreads();
-  int64_t wbase_item = (int64_t)blockIdx.x * kRTile + (int64_t)w * kRWarpItems;
-  // 1) per-warp digit histogram of the warp's contiguous 512 items
-  for (int c = 0; c < kRWarpItems / 32; ++c) {
-    int64_t i = wbase_item + c * 32 + lane;
-    uint32_t dg = 256;
-    if (i < n) dg = (rs_key(first, f, keys_in, i) >> shift) & 255u;
-    unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
-    int leader = __ffs(peers) - 1;
-    if (lane == leader && dg < 256) whist[w][dg] += __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  // 2) warp bases: global tile offset + counts of earlier warps
-  {
-    uint32_t d = threadIdx.x;
-    uint32_t run = offsets[(int64_t)d * ntiles + blockIdx.x];
-    for (int ww = 0; ww < kRW; ++ww) {
-      uint32_t c = whist[ww][d];
-      whist[ww][d] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  // 3) stable scatter, warp by warp, 32 items at a time
-  unsigned lt = (1u << lane) - 1u;
-  for (int c = 0; c < kRWarpItems / 32; ++c) {
-    int64_t i = wbase_item + c * 32 + lane;
-    uint32_t key = 0, dg = 256, val = 0;
-    if (i < n) {
-      key = rs_key(first, f, keys_in, i);
-      dg = (key >> shift) & 255u;
-      val = first ? (uint32_t)i : __ldg(vals_in + i);
-    }
-    unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
-    uint32_t pos = 0;
-    if (dg < 256) pos = whist[w][dg] + __popc(peers & lt);
-    __syncwarp();
-    if (dg < 256) {
-      if (!last) keys_out[pos] = key;
-      vals_out[pos] = val;
-      if (lane == __ffs(peers) - 1) whist[w][dg] += __popc(peers);
-    }
-    __syncwarp();
-  }
-}
-
 __global__ void k_rank_scatter(int64_t n, const uint32_t* __restrict__ order, uint32_t* __restrict__ rank) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) rank[__ldg(order + i)] = (uint32_t)i;
@@ -203,14 +127,24 @@ __global__ void k_os_hist(int64_t n, const float* __restrict__ f, uint32_t* __re
   for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   bool bad = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float x = __ldg(f + i);
-    bad |= !isfinite(x);
-    uint32_t k = value_key(x);
-    atomicAdd(&h[0][k & 255u], 1u);
-    atomicAdd(&h[1][(k >> 8) & 255u], 1u);
-    atomicAdd(&h[2][(k >> 16) & 255u], 1u);
-    atomicAdd(&h[3][k >> 24], 1u);
+  const int lane = threadIdx.x & 31;
+  // whole warps iterate together so that equal digits are added once per warp
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    int64_t i = i0 + threadIdx.x;
+    uint32_t k = 0;
+    bool in = i < n;
+    if (in) {
+      float x = __ldg(f + i);
+      bad |= !isfinite(x);
+      k = value_key(x);
+    }
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      uint32_t dg = in ? (k >> (8 * d)) & 255u : 256u;
+      unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+      if (dg < 256 && lane == __ffs(peers) - 1) atomicAdd(&h[d][dg], (uint32_t)__popc(peers));
+    }
   }
   if (bad) atomicOr(status, kErrNaN);
   __syncthreads();

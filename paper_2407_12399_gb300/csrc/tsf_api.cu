@@ -104,7 +104,7 @@ struct tsf_field {
 
 namespace {
 
-enum Stage { kSort, kGrad, kCrit, kD0, kD2, kD1, kPoints, kAssign, kLoss, kStep };
+enum Stage { kSort, kGrad, kCrit, kD0, kD2, kD1, kPoints, kAssign, kLoss, kStep, kD1Morse, kD1Reduce };
 
 void stage_begin(tsf_field* F, int s) {
   if (!F->prof) return;
@@ -449,9 +449,16 @@ int compute_diagram(tsf_field* F, bool incremental) {
     }
     ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
-    launch_d1(F->d, F->nd, F->L, F->n1, F->n2, F->rank, F->order, F->rec, F->tab, F->c1base, F->W, F->PO,
-              F->status, F->h_flags, st);
+    int ncols = launch_d1_prepare(F->n2, F->W, F->PO, F->h_flags, st);
     stage_end(F, kD1);
+    if (F->n2 == 0) F->h_flags[1] = 0;
+    stage_begin(F, kD1Morse);
+    launch_d1_morse(F->d, F->nd, F->L, F->n1, ncols, F->rank, F->order, F->rec, F->tab, F->c1base, F->W, F->PO,
+                    F->status, st);
+    stage_end(F, kD1Morse);
+    stage_begin(F, kD1Reduce);
+    launch_d1_reduce(F->n1, ncols, F->W, F->PO, F->status, st);
+    stage_end(F, kD1Reduce);
     s = read_status(F);
     F->d1_cols = F->n2 > 0 ? F->h_flags[1] : 0;
     if (F->d1_cols > 0) {
@@ -1031,8 +1038,9 @@ int tsf_profile_read(tsf_field* F, double* ms, int64_t* calls, int cap) {
 }
 
 const char* tsf_stage_name(int s) {
-  static const char* names[TSF_NSTAGES] = {"vertex_order", "gradient", "critical_cells", "pairs_d0", "pairs_d2",
-                                           "pairs_d1", "diagram_points", "assignment", "loss", "gradient_step"};
+  static const char* names[TSF_NSTAGES] = {"vertex_order", "gradient",      "critical_cells", "pairs_d0",
+                                           "pairs_d2",     "pairs_d1_prep", "diagram_points", "assignment",
+                                           "loss",         "gradient_step", "pairs_d1_morse", "pairs_d1_reduce"};
   return (s >= 0 && s < TSF_NSTAGES) ? names[s] : "unknown";
 }
 
