@@ -250,7 +250,10 @@ def run_gpu(args):
     visits = float(np.mean([s["d1_blocks_total"] for s in stats]))
     bytes_grad = nv * 1.0 + n_grad * (4.0 + 32.0 + 1.0 + 80.0)   # dirty flags; rank, record, vnext, D1 table
     bytes_sort = nv * 80.0                                        # 4 radix passes + rank scatter
-    bytes_d1 = visits * 192.0                                     # per lower-star visit
+    updates = float(np.mean([s["d1_star_updates"] for s in stats]))
+    # per lower-star visit: vertex id 4, table 80, own hash key 8 + mask 4;
+    # per target-star update: hash key 8, mask 4, rank 4
+    bytes_d1 = visits * 96.0 + updates * 16.0
     g_grad, ms_grad = gbs(bytes_grad, "gradient")
     g_sort, ms_sort = gbs(bytes_sort, "vertex_order")
     g_d1, ms_d1 = gbs(bytes_d1, "pairs_d1_morse")
@@ -266,7 +269,8 @@ def run_gpu(args):
         "roofline": {"kernel": "k_d1_morse_group (saddle-saddle Morse boundaries; latency-bound)", "bound": "hbm",
                      "achieved": g_d1, "peak": hbm, "unit": "GB/s", "frac": g_d1 / hbm, "traffic": None,
                      "peak_kind": peak_kind, "avg_launch_ms": ms_d1, "algorithmic_bytes_per_launch": bytes_d1,
-                     "units_per_launch": visits, "bytes_per_unit": 192},
+                     "units_per_launch": visits, "bytes_per_unit": bytes_d1 / max(visits, 1.0),
+                     "target_updates_per_launch": updates},
         "streaming_kernels": {
             "vertex_order": {"achieved": g_sort, "unit": "GB/s", "frac": g_sort / hbm, "avg_ms": ms_sort,
                              "algorithmic_bytes": bytes_sort},

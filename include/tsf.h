@@ -103,6 +103,7 @@ typedef struct {
   int64_t d1_blocks_max;      /* ... by the largest column */
   int64_t d1_rounds_total;    /* rounds (32 lower stars at most each) over all columns */
   int64_t d1_rounds_max;      /* ... of the longest column */
+  int64_t d1_star_updates;    /* parity-mask updates of target lower stars by those visits */
   double ms_diagram, ms_assign, ms_step; /* host wall time of the three stages */
 } tsf_stats;
 

@@ -52,7 +52,8 @@ class tsf_stats(ctypes.Structure):
                 ("n_nonstill_matched", ctypes.c_int64), ("n_updated_vertices", ctypes.c_int64),
                 ("n_gradient_vertices", ctypes.c_int64), ("d1_columns", ctypes.c_int64),
                 ("d1_blocks_total", ctypes.c_int64), ("d1_blocks_max", ctypes.c_int64),
-                ("d1_rounds_total", ctypes.c_int64), ("d1_rounds_max", ctypes.c_int64), ("ms_diagram", ctypes.c_double),
+                ("d1_rounds_total", ctypes.c_int64), ("d1_rounds_max", ctypes.c_int64),
+                ("d1_star_updates", ctypes.c_int64), ("ms_diagram", ctypes.c_double),
                 ("ms_assign", ctypes.c_double), ("ms_step", ctypes.c_double)]
 
     def as_dict(self):

@@ -47,19 +47,47 @@ __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint
     int8_t y_of[14];
     uint64_t path_of[14];
     star_chains(s, y_of, path_of, sg);
+    // closures by increasing rank position: v*y (pos(y) < pos(x)) is done
+    // before the v*x whose chain continues there
+    uint32_t crit = rec_crit_edges(r);
+    uint64_t cl[14];
+    int8_t end[14];
     D1Tab t;
-    unsigned long long bp = 0, yy = 0;
-    for (int p = 0; p < 14; ++p) bp |= (unsigned long long)((p < s.nl ? s.by_pos[p] : 15) & 15) << (4 * p);
-    bp |= (unsigned long long)s.nl << 56;
-    for (int x = 0; x < 14; ++x) yy |= (unsigned long long)((y_of[x] < 0 ? 15 : y_of[x]) & 15) << (4 * x);
-    t.q[0] = bp;
-    t.q[1] = yy;
-    for (int k = 2; k < 10; ++k) t.q[k] = 0;
-    for (int x = 0; x < 14; ++x) {
-      int off = 36 * x, wi = off >> 6, bi = off & 63;
-      t.q[2 + wi] |= path_of[x] << bi;
-      if (bi > 28) t.q[2 + wi + 1] |= path_of[x] >> (64 - bi);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) t.q[k] = 0;
+    unsigned long long ends = ~0ull;
+    for (int p = 0; p < s.nl; ++p) {
+      int x = s.by_pos[p];
+      uint64_t c = 0;
+      int e = 15;
+      if (p > 0) {
+        if ((crit >> x) & 1u) {
+          e = x;
+        } else {
+          int y = y_of[x];
+          if (y < 0) {
+            atomicOr(status, kErrInconsistent);
+          } else {
+            c = path_of[x];
+            if (y != s.by_pos[0]) {
+              c ^= cl[y];
+              e = end[y];
+            }
+          }
+        }
+      }
+      cl[x] = c;
+      end[x] = (int8_t)e;
+      tab_set_closure(t, x, c);
+      ends = (ends & ~(15ull << (4 * x))) | ((unsigned long long)e << (4 * x));
     }
+    unsigned long long orient = 0;
+    for (int le = 0; le < 36; ++le) {
+      int a = sg.edge[le][0], b = sg.edge[le][1];
+      if (((s.lower >> a) & (s.lower >> b) & 1u) && s.pos[a] > s.pos[b]) orient |= 1ull << le;
+    }
+    t.q[8] = ends;
+    t.q[9] = orient;
     uint4* dst4 = reinterpret_cast<uint4*>(tab + v);
     const uint4* src4 = reinterpret_cast<const uint4*>(&t);
 #pragma unroll

@@ -15,6 +15,8 @@
 // The union-find runs in rounds of deterministic reservations: an item
 // commits when no earlier item touches the component that would die, which
 // gives exactly the sequential elder-rule result whatever the schedule.
+#include <utility>
+
 #include "tsf_kernels.cuh"
 #include "tsf_star.cuh"
 
@@ -610,65 +612,67 @@ __device__ __forceinline__ int warp_exscan(int v, int& total) {
   return inc - v;
 }
 
+// Target stars of the link edges left by a visit, with compile-time
+// geometry: edge (a, b) goes to the lower star of whichever endpoint ranks
+// higher (P: a, Q: b), as the direction towards the other endpoint.
+template <int LE>
+__device__ __forceinline__ void link_edge_target(uint64_t P, uint64_t Q, uint32_t (&tm)[14]) {
+  constexpr int a = geo_edge(LE, 0), b = geo_edge(LE, 1);
+  constexpr int dab = geo_dir(a, b), dba = geo_dir(b, a);
+  tm[a] ^= (uint32_t)((P >> LE) & 1ull) << dab;
+  tm[b] ^= (uint32_t)((Q >> LE) & 1ull) << dba;
+}
+template <int... LE>
+__device__ __forceinline__ void link_targets(uint64_t P, uint64_t Q, uint32_t (&tm)[14],
+                                             std::integer_sequence<int, LE...>) {
+  (link_edge_target<LE>(P, Q, tm), ...);
+}
+template <int X>
+__device__ __forceinline__ void closure_of(const D1Tab& t, uint32_t m, uint64_t& path, uint32_t& em) {
+  if ((m >> X) & 1u) {
+    path ^= tab_closure<X>(t);
+    em ^= 1u << tab_end(t, X);
+  }
+}
+template <int... X>
+__device__ __forceinline__ void closures(const D1Tab& t, uint32_t m, uint64_t& path, uint32_t& em,
+                                         std::integer_sequence<int, X...>) {
+  (closure_of<X>(t, m, path, em), ...);
+}
+
 // One lower-star visit of a column: take the star's pending parity mask,
-// eliminate its gradient-paired edges (largest first; partners y stay in the
-// star), emit positive critical edges as (v << 4 | x), and xor the link-path
-// edges into the target stars' masks (returns the targets that became
-// pending, by rank).
+// apply the closures of its edges (linear over Z/2), emit the positive
+// critical edges left as (v << 4 | x), and xor the link edges left into the
+// target stars' masks (returns the targets that became pending, by rank).
 template <int KNEW>
 __device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned long long colkey, uint32_t r,
-                                         const int32_t* snd, const Geo& sg, uint32_t* status,
-                                         unsigned long long* myouts, int& myout, uint32_t* mynew, int& nnew,
-                                         bool& overflow, int& visits) {
+                                         const int32_t* snd, uint32_t* status, unsigned long long* myouts,
+                                         int& myout, uint32_t* mynew, int& nnew, bool& overflow, int& visits,
+                                         int& updates) {
   uint32_t v = c.order[r];
-  uint32_t h = hslot(W, colkey | v, status);
-  uint32_t m = h == 0xFFFFFFFFu ? 0u : atomicExch(&W.hmask[h], 0u);
-  if (!m) return;
-  ++visits;
-  Rec rc = ld_rec(c.rec, v);
-  D1Tab t;
+  D1Tab t;  // independent of the hash probe: issued first
   {
     const uint4* s4 = reinterpret_cast<const uint4*>(c.tab + v);
     uint4* d4 = reinterpret_cast<uint4*>(&t);
 #pragma unroll
     for (int k = 0; k < 5; ++k) d4[k] = __ldg(s4 + k);
   }
-  uint32_t crit = rec_crit_edges(rc);
-  uint32_t negcrit = crit ? __ldg(c.d0mask + v) : 0u;
-  int nl = (int)((t.q[0] >> 56) & 15ull);
-  int8_t pos[14];
-#pragma unroll
-  for (int k = 0; k < 14; ++k) pos[k] = -1;
-  for (int p = 0; p < nl; ++p) pos[(t.q[0] >> (4 * p)) & 15ull] = (int8_t)p;
-  int lowest = (int)(t.q[0] & 15ull);
+  uint32_t h = hslot(W, colkey | v, status);
+  uint32_t m = h == 0xFFFFFFFFu ? 0u : atomicExch(&W.hmask[h], 0u);
+  if (!m) return;
+  ++visits;
   uint64_t path = 0;
-  for (int p = nl - 1; p >= 1; --p) {
-    int x = (int)((t.q[0] >> (4 * p)) & 15ull);
-    if (!((m >> x) & 1u)) continue;
-    m &= ~(1u << x);
-    if ((crit >> x) & 1u) {
-      if (!((negcrit >> x) & 1u)) myouts[myout++] = ((unsigned long long)v << 4) | (unsigned)x;
-      continue;
-    }
-    int y = (int)((t.q[1] >> (4 * x)) & 15ull);
-    if (y == 15) {
-      atomicOr(status, kErrInconsistent);
-      continue;
-    }
-    if (y != lowest) m ^= 1u << y;
-    path ^= tab_path(t, x);
+  uint32_t em = 0;
+  closures(t, m, path, em, std::make_integer_sequence<int, 14>{});
+  em &= 0x3FFFu;
+  if (em) {
+    em &= ~__ldg(c.d0mask + v);  // negative critical edges are not rows
+    for (; em; em &= em - 1) myouts[myout++] = ((unsigned long long)v << 4) | (unsigned)(__ffs(em) - 1);
   }
   uint32_t tmask[14];
 #pragma unroll
   for (int k = 0; k < 14; ++k) tmask[k] = 0;
-  for (uint64_t pm = path; pm; pm &= pm - 1) {
-    int le = __ffsll((long long)pm) - 1;
-    int na = sg.edge[le][0], nbv = sg.edge[le][1];
-    bool a_hi = pos[na] > pos[nbv];
-    int hn = a_hi ? na : nbv, ln = a_hi ? nbv : na;
-    int dir = nbr_index(sg, sg.off[ln][0] - sg.off[hn][0], sg.off[ln][1] - sg.off[hn][1], sg.off[ln][2] - sg.off[hn][2]);
-    tmask[hn] ^= 1u << dir;
-  }
+  link_targets(path & t.q[9], path & ~t.q[9], tmask, std::make_integer_sequence<int, 36>{});
   uint32_t slot[14];
   unsigned long long seen[14];
   uint32_t trank[14];
@@ -691,8 +695,13 @@ __device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned lon
     }
   uint32_t olds[14];
 #pragma unroll
-  for (int hn = 0; hn < 14; ++hn)
-    olds[hn] = (tmask[hn] && slot[hn] != 0xFFFFFFFFu) ? atomicXor(&W.hmask[slot[hn]], tmask[hn]) : 1u;
+  for (int hn = 0; hn < 14; ++hn) {
+    olds[hn] = 1u;
+    if (tmask[hn] && slot[hn] != 0xFFFFFFFFu) {
+      olds[hn] = atomicXor(&W.hmask[slot[hn]], tmask[hn]);
+      ++updates;
+    }
+  }
 #pragma unroll
   for (int hn = 0; hn < 14; ++hn)
     if (olds[hn] == 0) {
@@ -740,22 +749,22 @@ __device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive
 }
 
 // Round loop of one column.  Phase A (NT = 32, max_rounds > 0): every column,
-// one warp; a column still open after max_rounds saves its frontier and is
-// listed for phase B (NT = 256, one block per listed column).
+// one warp; a column still open after max_rounds (or whose frontier could
+// outgrow the warp's buffers) saves its frontier and is listed for phase B
+// (NT = 128, one block per listed column).
 template <int NT, int FCAP, int SCAP, int KNEW>
 __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int ncols, int max_rounds,
                                                        uint32_t* status) {
+  static_assert(SCAP >= NT * KNEW, "one round's new entries fit the stage");
   extern __shared__ __align__(16) unsigned char smem[];
-  Geo& sg = *reinterpret_cast<Geo*>(smem);
-  int32_t* snd = reinterpret_cast<int32_t*>(smem + ((sizeof(Geo) + 15) & ~15));
-  int* scan_sm = snd + 16;  // NT/32 + 1 <= 16
-  uint32_t* front = reinterpret_cast<uint32_t*>(scan_sm + 16);
+  uint32_t* front = reinterpret_cast<uint32_t*>(smem);
   uint32_t* other = front + FCAP;
   uint32_t* stage = other + FCAP;
+  __shared__ int32_t snd[16];
+  __shared__ int scan_sm[16];  // NT/32 + 1 <= 16
   __shared__ int s_nf, s_flag;
   __shared__ Vec s_out;
   if (threadIdx.x < 14) snd[threadIdx.x] = c.nd.d[threadIdx.x];
-  geo_to_shared(sg);
   const bool phase_b = max_rounds <= 0;
   int j;
   if (phase_b) {
@@ -783,17 +792,16 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
       uint32_t ve = c.L.c2_ve[W.cols[j]];
       uint32_t v0 = ve >> 6;
       int e0 = (int)(ve & 63u);
-      uint32_t ends[3][2] = {{v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]])},
-                             {v0, (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])},
-                             {(uint32_t)((int32_t)v0 + snd[sg.edge[e0][0]]),
-                              (uint32_t)((int32_t)v0 + snd[sg.edge[e0][1]])}};
+      uint32_t ea = (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][0]]);
+      uint32_t eb = (uint32_t)((int32_t)v0 + c.nd.d[c_geo.edge[e0][1]]);
+      uint32_t ends[3][2] = {{v0, ea}, {v0, eb}, {ea, eb}};
       for (int k = 0; k < 3; ++k) {
         uint32_t p = ends[k][0], q = ends[k][1];
         uint32_t rp = c.rank[p], rq = c.rank[q];
         uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
         uint32_t h = hslot(W, colkey | hi, status);
         if (h == 0xFFFFFFFFu) continue;
-        uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo, sg));
+        uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo));
         if (old == 0) {
           uint32_t r = max(rp, rq);
           int ps = 0;
@@ -813,13 +821,17 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     for (int i = tid; i < (int)cs.y; i += NT) front[i] = (uint32_t)W.pool[cs.x + i];
   }
   gsync<NT>();
-  int visits = 0, rounds = 0;
+  int visits = 0, updates = 0, rounds = 0;
   bool failed = s_flag != 0;
   while (!failed) {
     int nf = s_nf;
     if (nf == 0) break;
     if (!phase_b && rounds >= max_rounds) break;
-    if (rounds > kD1StepLimit) {
+    // phase A hands a column whose frontier could outgrow FCAP to phase B
+    if (!phase_b && nf - min(NT, nf) + min(NT, nf) * KNEW > FCAP) break;
+    // every target is a lower neighbour of the visited vertex, so the
+    // frontier's highest rank drops each round: at most nv rounds
+    if (rounds > c.d.nv) {
       if (tid == 0) atomicOr(status, kErrRounds);
       failed = true;
       break;
@@ -830,7 +842,8 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     uint32_t mynew[KNEW];
     unsigned long long myouts[14];
     bool overflow = false;
-    if (tid < nb) d1_visit<KNEW>(c, W, colkey, front[tid], snd, sg, status, myouts, myout, mynew, nnew, overflow, visits);
+    if (tid < nb)
+      d1_visit<KNEW>(c, W, colkey, front[tid], snd, status, myouts, myout, mynew, nnew, overflow, visits, updates);
     if (overflow) atomicOr(&s_flag, 1);
     // outputs: append to the column's list in the pool
     int otot;
@@ -909,9 +922,10 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     if (tid == 0) s_nf = keep_total;
     gsync<NT>();
   }
-  // visits of the whole group
-  int vtot;
+  // visits and target updates of the whole group
+  int vtot, utot;
   gscan<NT>(visits, vtot, scan_sm);
+  gscan<NT>(updates, utot, scan_sm);
   if (failed) {
     if (tid == 0) {
       W.redo[j] = 1;
@@ -943,6 +957,7 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
       W.hsize[j] = 0;
       atomicAdd(&W.stats[0], (unsigned long long)vtot);
       atomicAdd(&W.stats[2], (unsigned long long)rounds);
+      atomicAdd(&W.stats[4], (unsigned long long)utot);
     }
     return;
   }
@@ -1019,15 +1034,17 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     atomicMax(&W.stats[1], (unsigned long long)vtot);
     atomicAdd(&W.stats[2], (unsigned long long)rounds);
     atomicMax(&W.stats[3], (unsigned long long)rounds);
+    atomicAdd(&W.stats[4], (unsigned long long)utot);
   }
 }
 
-constexpr int kFrontA = 4096, kStageA = 2048, kNewA = 48;
-constexpr int kFrontB = 8192, kStageB = 4096, kNewB = 16;
+// A visit makes at most 14 stars pending (one per neighbour).  Phase A keeps
+// its shared memory small so that every column's warp is resident at once.
+constexpr int kNewA = 14, kNewB = 14, kThreadsB = 128;
+constexpr int kFrontA = 1024, kStageA = 512;
+constexpr int kFrontB = 4096, kStageB = 2048;
 
-static size_t d1_group_smem(int fcap, int scap) {
-  return ((sizeof(Geo) + 15) & ~(size_t)15) + 32 * sizeof(int32_t) + (2 * (size_t)fcap + scap) * sizeof(uint32_t);
-}
+static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + scap) * sizeof(uint32_t); }
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
 // each low; every addition is of an earlier column.
@@ -1126,12 +1143,12 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   if (!attr) {
     cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, kNewA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sa);
-    cudaFuncSetAttribute(k_d1_morse_group<256, kFrontB, kStageB, kNewB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_d1_morse_group<kThreadsB, kFrontB, kStageB, kNewB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
     attr = true;
   }
   k_d1_morse_group<32, kFrontA, kStageA, kNewA><<<ncols, 32, sa, st>>>(c, W, ncols, 48, status); note_launch();
-  k_d1_morse_group<256, kFrontB, kStageB, kNewB><<<ncols, 256, sb, st>>>(c, W, ncols, 0, status); note_launch();
+  k_d1_morse_group<kThreadsB, kFrontB, kStageB, kNewB><<<ncols, kThreadsB, sb, st>>>(c, W, ncols, 0, status); note_launch();
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
 }
 

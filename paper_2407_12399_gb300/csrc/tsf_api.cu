@@ -89,7 +89,7 @@ struct tsf_field {
   double loss = 0, loss0 = 0;
   unsigned long long counts[4] = {0, 0, 0, 0};
   int64_t n_updated = 0, n_gradient = 0;
-  unsigned long long d1_stats[4] = {0, 0, 0, 0};
+  unsigned long long d1_stats[5] = {0, 0, 0, 0, 0};
   int d1_cols = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
@@ -462,16 +462,10 @@ int compute_diagram(tsf_field* F, bool incremental) {
     s = read_status(F);
     F->d1_cols = F->n2 > 0 ? F->h_flags[1] : 0;
     if (F->d1_cols > 0) {
-      ck(cudaMemcpyAsync(F->d1_stats, F->W.stats, 32, cudaMemcpyDeviceToHost, st));
+      ck(cudaMemcpyAsync(F->d1_stats, F->W.stats, sizeof(F->d1_stats), cudaMemcpyDeviceToHost, st));
       ck(cudaStreamSynchronize(st));
-      if (std::getenv("TSF_DEBUG_D1")) {
-        unsigned long long x[9];
-        ck(cudaMemcpy(x, F->W.stats, sizeof(x), cudaMemcpyDeviceToHost));
-        std::fprintf(stderr, "d1: visits %llu max %llu rounds %llu max %llu | cycles visit %llu sort %llu merge %llu "
-                     "unique %llu | frontier sum %llu\n", x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7], x[8]);
-      }
     } else {
-      F->d1_stats[0] = F->d1_stats[1] = F->d1_stats[2] = F->d1_stats[3] = 0;
+      for (auto& x : F->d1_stats) x = 0;
     }
     if ((s & kErrPool) && attempt < 6) continue;
     break;
@@ -536,6 +530,7 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
   out->d1_blocks_max = (int64_t)F->d1_stats[1];
   out->d1_rounds_total = (int64_t)F->d1_stats[2];
   out->d1_rounds_max = (int64_t)F->d1_stats[3];
+  out->d1_star_updates = (int64_t)F->d1_stats[4];
   out->ms_diagram = F->ms_diag;
   out->ms_assign = F->ms_assign;
   out->ms_step = F->ms_step;

@@ -90,6 +90,21 @@ constexpr Geo make_geo() {
 
 constexpr Geo kGeo = make_geo();
 
+// Compile-time lookups for fully unrolled device code: link edge `le`'s
+// endpoints, and the neighbour index of b - a as seen from neighbour a.
+__host__ __device__ constexpr int geo_edge(int le, int k) { return kGeo.edge[le][k]; }
+__host__ __device__ constexpr int geo_dir(int a, int b) {
+  return kGeo.nbr_of[(kGeo.off[b][0] - kGeo.off[a][0] + 1) + 3 * (kGeo.off[b][1] - kGeo.off[a][1] + 1) +
+                     9 * (kGeo.off[b][2] - kGeo.off[a][2] + 1)];
+}
+
+constexpr bool geo_link_dirs_valid() {
+  for (int e = 0; e < 36; ++e)
+    if (geo_dir(geo_edge(e, 0), geo_edge(e, 1)) < 0 || geo_dir(geo_edge(e, 1), geo_edge(e, 0)) < 0) return false;
+  return true;
+}
+static_assert(geo_link_dirs_valid(), "the endpoints of a link edge are neighbours of each other");
+
 constexpr int geo_count_edges() {
   int n = 0;
   for (int i = 0; i < 14; ++i)

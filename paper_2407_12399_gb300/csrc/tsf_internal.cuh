@@ -67,25 +67,37 @@ __host__ __device__ inline uint64_t rec_crit_tris(const Rec& r) {
 __host__ __device__ inline bool rec_has_max(const Rec& r) { return (r.w[1] >> 22) & 1u; }
 __host__ __device__ inline int rec_tet_code(const Rec& r, int tau) { return (int)rec_bits(r, 56 + 7 * tau, 7); }
 
-// Per-vertex expansion table for the saddle-saddle reduction (80 bytes):
-//   q[0] bits 0..55  lower neighbours by increasing rank (4-bit neighbour
-//                    indices, position p at bits 4p), bits 56..59 their count
-//   q[1]             y of each killed neighbour x (4 bits at 4x, 15 = none):
-//                    the older representative x's link component merged into
-//   q[2..9]          link path x..y of each killed x (36 bits at 36x): the
-//                    reduced column of the triangle paired with edge v*x is
-//                    v*x + v*y + these link edges
+// Per-vertex expansion table for the saddle-saddle reduction (80 bytes).
+// Eliminating the gradient-paired edges of one lower star is linear over
+// Z/2, so the table holds the effect of each lower-star edge v*x eliminated
+// alone, its *closure*: v*x paired with triangle v*(x, ..) is replaced by
+// v*y + (link path x..y), v*y in turn by its own closure, until the chain
+// reaches a critical edge (kept) or the lowest edge v*x0 (negative: not a
+// row of the reduction).  Layout:
+//   q[0..7]   bits 36x .. 36x+35: link edges (36-bit mask over v's link
+//             edges) that the closure of v*x leaves in lower stars below v
+//   q[8]      bits 4x .. 4x+3: the critical edge v*c the closure of v*x ends
+//             at (c = x when v*x itself is critical), 15 = none
+//   q[9]      bits 0..35: orientation of the link edges (a, b), a < b as
+//             neighbour indices: 1 when a ranks above b (edge a*b then lies
+//             in the lower star of v + off[a])
 struct __align__(16) D1Tab {
   unsigned long long q[10];
 };
 
-__host__ __device__ inline uint64_t tab_path(const D1Tab& t, int x) {
-  int off = 36 * x;
-  int wi = off >> 6, bi = off & 63;
-  unsigned long long lo = t.q[2 + wi] >> bi;
-  unsigned long long hi = (bi > 28 && wi + 1 < 8) ? (t.q[2 + wi + 1] << (64 - bi)) : 0ull;
-  return (lo | hi) & ((1ull << 36) - 1);
+template <int X>
+__host__ __device__ __forceinline__ uint64_t tab_closure(const D1Tab& t) {
+  constexpr int off = 36 * X, wi = off >> 6, bi = off & 63;
+  uint64_t lo = t.q[wi] >> bi;
+  if constexpr (bi > 28) lo |= t.q[wi + 1] << (64 - bi);
+  return lo & ((1ull << 36) - 1);
 }
+__host__ __device__ inline void tab_set_closure(D1Tab& t, int x, uint64_t path) {
+  int off = 36 * x, wi = off >> 6, bi = off & 63;
+  t.q[wi] |= path << bi;
+  if (bi > 28) t.q[wi + 1] |= path >> (64 - bi);
+}
+__host__ __device__ __forceinline__ int tab_end(const D1Tab& t, int x) { return (int)((t.q[8] >> (4 * x)) & 15ull); }
 
 // Grid helpers -------------------------------------------------------------
 struct Dims {

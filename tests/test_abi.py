@@ -58,7 +58,35 @@ def test_status_strings_and_argument_checks_need_no_gpu(libpath):
     assert L.tsf_destroy_field(None) == 0
 
 
-def test_struct_layouts():
-    assert ctypes.sizeof(tsf.tsf_pair) == 40
-    assert ctypes.sizeof(tsf.tsf_params) == 24
-    assert ctypes.sizeof(tsf.tsf_stats) == 192
+def _c_layout(struct, fields):
+    """sizeof and offsetof as the C compiler sees them in include/tsf.h."""
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src = f"""#include <stddef.h>
+#include <stdio.h>
+#include "tsf.h"
+int main(void) {{
+  printf("%zu\\n", sizeof({struct}));
+{body}  return 0;
+}}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.run([cc, "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return [int(x) for x in out]
+
+
+@pytest.mark.parametrize("name", ["tsf_pair", "tsf_params", "tsf_stats"])
+def test_struct_layouts_match_the_header(name):
+    S = getattr(tsf, name)
+    fields = [f for f, _ in S._fields_]
+    got = _c_layout(name, fields)
+    assert got[0] == ctypes.sizeof(S)
+    assert got[1:] == [getattr(S, f).offset for f in fields]
