@@ -569,47 +569,53 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
 }
 
 // ---------------------------------------------------------------------------
-// Phase 1, warp per column.  Pending entries are kept as (column, vertex) ->
-// parity mask over the 14 edge directions of the vertex's lower star, in a
-// hash table; the frontier is the descending list of ranks with a pending
-// mask, in shared memory.  Each round the warp takes the 32 highest pending
-// lower stars, one per lane.  The projection is linear, so a lower star that
-// receives entries after it was processed simply comes back.
+// Phase 1, one group of threads per column.  Pending entries are kept as
+// (column, vertex) -> parity mask over the 14 edge directions of the vertex's
+// lower star, one 64-bit word per entry of an open-addressing table:
+//   bits 63..14  key (column << vbits | vertex), bits 13..0  the mask.
+// The frontier is the descending list of (rank << 32 | slot) of the lower
+// stars with a pending mask, in shared memory.  Each round the group takes
+// the NT highest, one per thread.  The projection is linear, so a lower star
+// that receives entries after it was processed simply comes back.
 // ---------------------------------------------------------------------------
+constexpr unsigned long long kHEmpty = ~0ull, kHBits = 0x3FFFull;
 
-__device__ __forceinline__ uint32_t hslot(const D1Work& W, unsigned long long key, uint32_t* status) {
-  uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
+__device__ __forceinline__ unsigned long long hkey(const D1Work& W, uint32_t j, uint32_t v) {
+  return (((unsigned long long)j << W.vbits) | v) << 14;
+}
+__device__ __forceinline__ uint32_t hhome(const D1Work& W, unsigned long long key) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> W.hshift);
+}
+
+// xor `bits` into entry `key`, inserting it when absent, probing on from slot
+// h whose word was read as w.  Returns the entry's previous mask (0 when it
+// was absent) and its slot; on a full table sets kErrPool, slot = ~0.
+__device__ uint32_t hxor_probe(D1Work& W, unsigned long long key, uint32_t bits, uint32_t h, unsigned long long w,
+                               uint32_t& slot, uint32_t* status) {
   for (uint32_t probe = 0; probe < W.hash_cap; ++probe) {
-    unsigned long long k = W.hkeys[h];
-    if (k == key) return h;
-    if (k == ~0ull) {
-      unsigned long long old = atomicCAS(&W.hkeys[h], ~0ull, key);
-      if (old == ~0ull || old == key) return h;
+    if (w == kHEmpty) {
+      unsigned long long old = atomicCAS(&W.htab[h], kHEmpty, key | bits);
+      if (old == kHEmpty) {
+        slot = h;
+        return 0u;
+      }
+      w = old;
+    }
+    if ((w & ~kHBits) == key) {
+      slot = h;
+      return (uint32_t)(atomicXor(&W.htab[h], (unsigned long long)bits) & kHBits);
     }
     h = (h + 1) & (W.hash_cap - 1);
+    w = W.htab[h];
   }
   atomicOr(status, kErrPool);
-  return 0xFFFFFFFFu;
+  slot = 0xFFFFFFFFu;
+  return 1u;
 }
 
 __global__ void k_hash_clear(D1Work W) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < W.hash_cap) {
-    W.hkeys[i] = ~0ull;
-    W.hmask[i] = 0;
-  }
-}
-
-__device__ __forceinline__ int warp_exscan(int v, int& total) {
-  int lane = threadIdx.x & 31;
-  int inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-    if (lane >= o) inc += t;
-  }
-  total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-  return inc - v;
+  if (i < W.hash_cap) W.htab[i] = kHEmpty;
 }
 
 // Target stars of the link edges left by a visit, with compile-time
@@ -640,27 +646,29 @@ __device__ __forceinline__ void closures(const D1Tab& t, uint32_t m, uint64_t& p
   (closure_of<X>(t, m, path, em), ...);
 }
 
-// One lower-star visit of a column: take the star's pending parity mask,
-// apply the closures of its edges (linear over Z/2), emit the positive
-// critical edges left as (v << 4 | x), and xor the link edges left into the
-// target stars' masks (returns the targets that became pending, by rank).
+// One lower-star visit of a column (frontier entry fe = rank << 32 | slot):
+// take the star's pending mask, apply the closures of its edges (linear over
+// Z/2), emit the positive critical edges left as (v << 4 | x), and xor the
+// link edges left into the target stars' masks.  Returns the targets that
+// became pending as frontier entries.  Four dependent memory steps: the
+// take, the table, the targets' words and ranks, the targets' updates.
 template <int KNEW>
-__device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned long long colkey, uint32_t r,
+__device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned long long colkey, unsigned long long fe,
                                          const int32_t* snd, uint32_t* status, unsigned long long* myouts,
-                                         int& myout, uint32_t* mynew, int& nnew, bool& overflow, int& visits,
-                                         int& updates) {
-  uint32_t v = c.order[r];
-  D1Tab t;  // independent of the hash probe: issued first
+                                         int& myout, unsigned long long* mynew, int& nnew, bool& overflow,
+                                         int& visits, int& updates) {
+  unsigned long long w0 = atomicAnd(&W.htab[(uint32_t)fe], ~kHBits);
+  uint32_t m = (uint32_t)(w0 & kHBits);
+  if (!m) return;
+  ++visits;
+  uint32_t v = (uint32_t)((w0 >> 14) & ((1ull << W.vbits) - 1));
+  D1Tab t;
   {
     const uint4* s4 = reinterpret_cast<const uint4*>(c.tab + v);
     uint4* d4 = reinterpret_cast<uint4*>(&t);
 #pragma unroll
     for (int k = 0; k < 5; ++k) d4[k] = __ldg(s4 + k);
   }
-  uint32_t h = hslot(W, colkey | v, status);
-  uint32_t m = h == 0xFFFFFFFFu ? 0u : atomicExch(&W.hmask[h], 0u);
-  if (!m) return;
-  ++visits;
   uint64_t path = 0;
   uint32_t em = 0;
   closures(t, m, path, em, std::make_integer_sequence<int, 14>{});
@@ -673,41 +681,53 @@ __device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned lon
 #pragma unroll
   for (int k = 0; k < 14; ++k) tmask[k] = 0;
   link_targets(path & t.q[9], path & ~t.q[9], tmask, std::make_integer_sequence<int, 36>{});
-  uint32_t slot[14];
-  unsigned long long seen[14];
-  uint32_t trank[14];
+  // the targets' home words and ranks, all loads in flight together
+  unsigned long long w[14];
+  uint32_t home[14], trank[14];
 #pragma unroll
   for (int hn = 0; hn < 14; ++hn) {
-    slot[hn] = 0xFFFFFFFFu;
     if (tmask[hn]) {
       uint32_t hv = (uint32_t)((int32_t)v + snd[hn]);
-      unsigned long long key = colkey | hv;
-      slot[hn] = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & (W.hash_cap - 1);
-      seen[hn] = W.hkeys[slot[hn]];
+      home[hn] = hhome(W, colkey | ((unsigned long long)hv << 14));
+      w[hn] = W.htab[home[hn]];
       trank[hn] = __ldg(c.rank + hv);
     }
   }
-#pragma unroll
-  for (int hn = 0; hn < 14; ++hn)
-    if (tmask[hn]) {
-      unsigned long long key = colkey | (uint32_t)((int32_t)v + snd[hn]);
-      if (seen[hn] != key) slot[hn] = hslot(W, key, status);
-    }
-  uint32_t olds[14];
+  // first attempt, all atomics in flight together: xor into the entry when
+  // the home slot holds it, insert it when the home slot is empty
+  uint32_t present = 0, empty = 0;
 #pragma unroll
   for (int hn = 0; hn < 14; ++hn) {
-    olds[hn] = 1u;
-    if (tmask[hn] && slot[hn] != 0xFFFFFFFFu) {
-      olds[hn] = atomicXor(&W.hmask[slot[hn]], tmask[hn]);
-      ++updates;
+    if (tmask[hn]) {
+      unsigned long long key = colkey | ((unsigned long long)(uint32_t)((int32_t)v + snd[hn]) << 14);
+      if ((w[hn] & ~kHBits) == key) {
+        present |= 1u << hn;
+        w[hn] = atomicXor(&W.htab[home[hn]], (unsigned long long)tmask[hn]);
+      } else if (w[hn] == kHEmpty) {
+        empty |= 1u << hn;
+        w[hn] = atomicCAS(&W.htab[home[hn]], kHEmpty, key | tmask[hn]);
+      }
     }
   }
 #pragma unroll
-  for (int hn = 0; hn < 14; ++hn)
-    if (olds[hn] == 0) {
-      if (nnew < KNEW) mynew[nnew++] = trank[hn];
-      else overflow = true;
+  for (int hn = 0; hn < 14; ++hn) {
+    if (tmask[hn]) {
+      uint32_t old, slot = home[hn];
+      if ((present >> hn) & 1u) {
+        old = (uint32_t)(w[hn] & kHBits);
+      } else if (((empty >> hn) & 1u) && w[hn] == kHEmpty) {
+        old = 0u;  // inserted
+      } else {     // the home slot holds another key, or the insert lost a race: probe on
+        unsigned long long key = colkey | ((unsigned long long)(uint32_t)((int32_t)v + snd[hn]) << 14);
+        old = hxor_probe(W, key, tmask[hn], home[hn], w[hn], slot, status);
+      }
+      ++updates;
+      if (old == 0u && slot != 0xFFFFFFFFu) {
+        if (nnew < KNEW) mynew[nnew++] = ((unsigned long long)trank[hn] << 32) | slot;
+        else overflow = true;
+      }
     }
+  }
 }
 
 // Group-wide (NT threads: one warp or one block) helpers.
@@ -748,6 +768,27 @@ __device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive
   return res;
 }
 
+// Descending bitonic sort of a[0..n2), n2 a power of two (shared or global
+// memory of the group; the group's barrier orders both).
+template <int NT>
+__device__ void group_sort_desc(unsigned long long* a, int n2) {
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += NT) {
+        int jx = i ^ stride;
+        if (jx > i) {
+          bool desc = (i & size) == 0;
+          unsigned long long x = a[i], y = a[jx];
+          if ((x < y) == desc) {
+            a[i] = y;
+            a[jx] = x;
+          }
+        }
+      }
+      gsync<NT>();
+    }
+}
+
 // Round loop of one column.  Phase A (NT = 32, max_rounds > 0): every column,
 // one warp; a column still open after max_rounds (or whose frontier could
 // outgrow the warp's buffers) saves its frontier and is listed for phase B
@@ -757,13 +798,13 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
                                                        uint32_t* status) {
   static_assert(SCAP >= NT * KNEW, "one round's new entries fit the stage");
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* front = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* other = front + FCAP;
-  uint32_t* stage = other + FCAP;
+  unsigned long long* front = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* other = front + FCAP;
+  unsigned long long* stage = other + FCAP;
   __shared__ int32_t snd[16];
   __shared__ int scan_sm[16];  // NT/32 + 1 <= 16
   __shared__ int s_nf, s_flag;
-  __shared__ Vec s_out;
+  __shared__ Vec s_out, s_grow;
   if (threadIdx.x < 14) snd[threadIdx.x] = c.nd.d[threadIdx.x];
   const bool phase_b = max_rounds <= 0;
   int j;
@@ -773,9 +814,16 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
   } else {
     j = blockIdx.x;
     if (j >= ncols) return;
+    if ((unsigned long long)j >> (50 - W.vbits)) {  // beyond the key's column field
+      if (threadIdx.x == 0) {
+        W.redo[j] = 1;
+        W.hsize[j] = 0;
+      }
+      return;
+    }
   }
   const int tid = threadIdx.x;
-  unsigned long long colkey = (unsigned long long)j << 32;
+  const unsigned long long colkey = hkey(W, (uint32_t)j, 0u);
   if (tid == 0) {
     s_flag = 0;
     if (phase_b) {
@@ -799,16 +847,16 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
         uint32_t p = ends[k][0], q = ends[k][1];
         uint32_t rp = c.rank[p], rq = c.rank[q];
         uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
-        uint32_t h = hslot(W, colkey | hi, status);
-        if (h == 0xFFFFFFFFu) continue;
-        uint32_t old = atomicXor(&W.hmask[h], 1u << nbr_of_pair(c.d, hi, lo));
-        if (old == 0) {
-          uint32_t r = max(rp, rq);
+        unsigned long long key = colkey | ((unsigned long long)hi << 14);
+        uint32_t h = hhome(W, key), slot;
+        uint32_t old = hxor_probe(W, key, 1u << nbr_of_pair(c.d, hi, lo), h, W.htab[h], slot, status);
+        if (old == 0u && slot != 0xFFFFFFFFu) {
+          unsigned long long e = ((unsigned long long)max(rp, rq) << 32) | slot;
           int ps = 0;
-          while (ps < s_nf && front[ps] > r) ++ps;
-          if (ps == s_nf || front[ps] != r) {
+          while (ps < s_nf && front[ps] > e) ++ps;
+          if (ps == s_nf || front[ps] != e) {
             for (int t = s_nf; t > ps; --t) front[t] = front[t - 1];
-            front[ps] = r;
+            front[ps] = e;
             ++s_nf;
           }
         }
@@ -818,7 +866,7 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
   gsync<NT>();
   if (phase_b) {
     uint4 cs = W.cont[j];
-    for (int i = tid; i < (int)cs.y; i += NT) front[i] = (uint32_t)W.pool[cs.x + i];
+    for (int i = tid; i < (int)cs.y; i += NT) front[i] = W.pool[cs.x + i];
   }
   gsync<NT>();
   int visits = 0, updates = 0, rounds = 0;
@@ -839,25 +887,24 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     ++rounds;
     int nb = min(NT, nf);
     int nnew = 0, myout = 0;
-    uint32_t mynew[KNEW];
+    unsigned long long mynew[KNEW];
     unsigned long long myouts[14];
     bool overflow = false;
     if (tid < nb)
       d1_visit<KNEW>(c, W, colkey, front[tid], snd, status, myouts, myout, mynew, nnew, overflow, visits, updates);
     if (overflow) atomicOr(&s_flag, 1);
-    // outputs: append to the column's list in the pool
+    // outputs: append to the column's list in the pool (grown by the group)
     int otot;
     int ooff = gscan<NT>(myout, otot, scan_sm);
-    if (tid == 0 && otot > 0 && s_out.size + otot > s_out.cap) {
-      Vec n;
-      uint32_t cap = s_out.cap;
-      while (cap < s_out.size + otot) cap *= 2;
-      if (vec_alloc(W, n, cap, status)) {
-        for (uint32_t i = 0; i < s_out.size; ++i) n.h[i] = s_out.h[i];
-        n.size = s_out.size;
-        s_out = n;
-      } else {
-        s_flag = 1;
+    if (tid == 0) {
+      s_grow.h = nullptr;
+      if (otot > 0 && s_out.size + otot > s_out.cap) {
+        uint32_t cap = s_out.cap;
+        while (cap < s_out.size + otot) cap *= 2;
+        if (!vec_alloc(W, s_grow, cap, status)) {
+          s_grow.h = nullptr;
+          s_flag = 1;
+        }
       }
     }
     gsync<NT>();
@@ -865,14 +912,23 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
       failed = true;
       break;
     }
+    if (s_grow.h) {
+      for (uint32_t i = tid; i < s_out.size; i += NT) s_grow.h[i] = s_out.h[i];
+      gsync<NT>();
+      if (tid == 0) {
+        s_grow.size = s_out.size;
+        s_out = s_grow;
+      }
+      gsync<NT>();
+    }
     for (int k = 0; k < myout; ++k) s_out.h[s_out.size + ooff + k] = myouts[k];
     gsync<NT>();
     if (tid == 0) s_out.size += otot;
-    // new ranks: stage, sort descending (bitonic), merge with front[nb..nf)
+    // new entries: stage, sort descending, merge with front[nb..nf)
     int ntot;
     int noff = gscan<NT>(nnew, ntot, scan_sm);
     int rest = nf - nb;
-    if (ntot > SCAP || rest + ntot > FCAP) {
+    if (rest + ntot > FCAP) {
       failed = true;
       break;
     }
@@ -881,21 +937,7 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     while (n2 < ntot) n2 <<= 1;
     for (int k = ntot + tid; k < n2; k += NT) stage[k] = 0;
     gsync<NT>();
-    for (int size = 2; size <= n2; size <<= 1)
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int i = tid; i < n2; i += NT) {
-          int jx = i ^ stride;
-          if (jx > i) {
-            bool desc = (i & size) == 0;
-            uint32_t a = stage[i], b = stage[jx];
-            if ((a < b) == desc) {
-              stage[i] = b;
-              stage[jx] = a;
-            }
-          }
-        }
-        gsync<NT>();
-      }
+    group_sort_desc<NT>(stage, n2);
     int total = rest + ntot;
     for (int k = tid; k < total; k += NT) {
       int lo = max(0, k - ntot), hi = min(k, rest);
@@ -912,7 +954,7 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     for (int base = 0; base < total; base += NT) {
       int k = base + tid;
       int keep = (k < total) && (k == 0 || other[k] != other[k - 1]);
-      uint32_t val = k < total ? other[k] : 0;
+      unsigned long long val = k < total ? other[k] : 0ull;
       int t;
       int off = gscan<NT>(keep, t, scan_sm);
       if (keep) front[keep_total + off] = val;
@@ -961,74 +1003,63 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     }
     return;
   }
-  // finished: (v, x) -> C1 index, sort descending, cancel equal pairs (Z/2)
+  // finished: (v, x) -> C1 index, sort descending, keep the entries present
+  // an odd number of times (Z/2)
   uint32_t nout = s_out.size;
-  for (uint32_t i = tid; i < nout; i += NT) {
-    uint32_t v = (uint32_t)(s_out.h[i] >> 4);
-    int x = (int)(s_out.h[i] & 15ull);
-    int cnt = __popc(rec_crit_edges(ld_rec(c.rec, v)));
-    uint32_t base = c.c1base[v];
-    int ci = -1;
-    for (int k2 = 0; k2 < cnt; ++k2)
-      if ((int)(c.L.c1_vn[base + k2] & 15u) == x) ci = (int)(base + k2);
-    if (ci < 0) atomicOr(status, kErrInconsistent);
-    s_out.h[i] = (unsigned long long)(ci < 0 ? 0 : ci);
+  int n2 = 1;
+  while (n2 < (int)nout) n2 <<= 1;
+  unsigned long long* a = stage;
+  if (n2 > SCAP) {  // too long for shared memory: sort in the pool
+    if (tid == 0 && !vec_alloc(W, s_grow, (uint32_t)n2, status)) s_flag = 1;
+    gsync<NT>();
+    if (s_flag) {
+      if (tid == 0) {
+        W.redo[j] = 1;
+        W.hsize[j] = 0;
+      }
+      return;
+    }
+    a = s_grow.h;
+  }
+  for (int i = tid; i < n2; i += NT) {
+    unsigned long long ci = 0;
+    if (i < (int)nout) {
+      uint32_t v = (uint32_t)(s_out.h[i] >> 4);
+      int x = (int)(s_out.h[i] & 15ull);
+      int cnt = __popc(rec_crit_edges(ld_rec(c.rec, v)));
+      uint32_t base = c.c1base[v];
+      int found = -1;
+      for (int k2 = 0; k2 < cnt; ++k2)
+        if ((int)(c.L.c1_vn[base + k2] & 15u) == x) found = (int)(base + k2);
+      if (found < 0) atomicOr(status, kErrInconsistent);
+      ci = (unsigned long long)(found < 0 ? 0 : found);
+    }
+    a[i] = ci;
   }
   gsync<NT>();
-  if ((int)nout <= SCAP) {
-    int n2 = 1;
-    while (n2 < (int)nout) n2 <<= 1;
-    for (int k = tid; k < n2; k += NT) stage[k] = k < (int)nout ? (uint32_t)s_out.h[k] : 0u;
-    gsync<NT>();
-    for (int size = 2; size <= n2; size <<= 1)
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int i = tid; i < n2; i += NT) {
-          int jx = i ^ stride;
-          if (jx > i) {
-            bool desc = (i & size) == 0;
-            uint32_t a = stage[i], b = stage[jx];
-            if ((a < b) == desc) {
-              stage[i] = b;
-              stage[jx] = a;
-            }
-          }
-        }
-        gsync<NT>();
+  group_sort_desc<NT>(a, n2);
+  int kept = 0;
+  for (int base = 0; base < (int)nout; base += NT) {
+    int k = base + tid;
+    int keep = 0;
+    unsigned long long x = 0;
+    if (k < (int)nout) {
+      x = a[k];
+      if (k == 0 || a[k - 1] != x) {
+        int e = k + 1;
+        while (e < (int)nout && a[e] == x) ++e;
+        keep = (e - k) & 1;
       }
-    if (tid == 0) {
-      int m = 0;
-      for (int i = 0; i < (int)nout;) {
-        int k = i;
-        while (k < (int)nout && stage[k] == stage[i]) ++k;
-        if ((k - i) & 1) s_out.h[m++] = stage[i];
-        i = k;
-      }
-      s_out.size = (uint32_t)m;
     }
-  } else if (tid == 0) {
-    unsigned long long* o = s_out.h;
-    for (uint32_t i = 1; i < nout; ++i) {
-      unsigned long long t = o[i];
-      int k = (int)i - 1;
-      while (k >= 0 && o[k] < t) {
-        o[k + 1] = o[k];
-        --k;
-      }
-      o[k + 1] = t;
-    }
-    int m = 0;
-    for (int i = 0; i < (int)nout;) {
-      int k = i;
-      while (k < (int)nout && o[k] == o[i]) ++k;
-      if ((k - i) & 1) o[m++] = o[i];
-      i = k;
-    }
-    s_out.size = (uint32_t)m;
+    int t;
+    int off = gscan<NT>(keep, t, scan_sm);
+    if (keep) s_out.h[kept + off] = x;
+    kept += t;
   }
   gsync<NT>();
   if (tid == 0) {
     W.hoff[j] = s_out.off;
-    W.hsize[j] = s_out.size;
+    W.hsize[j] = (uint32_t)kept;
     W.redo[j] = 0;
     atomicAdd(&W.stats[0], (unsigned long long)vtot);
     atomicMax(&W.stats[1], (unsigned long long)vtot);
@@ -1042,9 +1073,9 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
 // its shared memory small so that every column's warp is resident at once.
 constexpr int kNewA = 14, kNewB = 14, kThreadsB = 128;
 constexpr int kFrontA = 1024, kStageA = 512;
-constexpr int kFrontB = 4096, kStageB = 2048;
+constexpr int kFrontB = 2048, kStageB = 2048;
 
-static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + scap) * sizeof(uint32_t); }
+static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + scap) * sizeof(unsigned long long); }
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
 // each low; every addition is of an earlier column.
@@ -1134,6 +1165,8 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   c.L = L;
   c.d0_killed = P.d0_killed;
   c.d0mask = P.d0mask;
+  W.vbits = 64 - __builtin_clzll((unsigned long long)d.nv);
+  W.hshift = 64 - __builtin_ctz(W.hash_cap);
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, 72, st);
   k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();

@@ -441,10 +441,8 @@ int compute_diagram(tsf_field* F, bool incremental) {
     while ((int64_t)hwant < std::min<int64_t>(2 * F->d.nv, (int64_t)1 << 28)) hwant <<= 1;
     hwant = (uint32_t)std::min<int64_t>((int64_t)hwant << attempt, (int64_t)1 << 29);
     if (hwant > F->W.hash_cap) {
-      dev_free(F->W.hkeys);
-      dev_free(F->W.hmask);
-      ck(dev_alloc(&F->W.hkeys, hwant));
-      ck(dev_alloc(&F->W.hmask, hwant));
+      dev_free(F->W.htab);
+      ck(dev_alloc(&F->W.htab, hwant));
       F->W.hash_cap = hwant;
     }
     ck(cudaMemsetAsync(F->status, 0, 4, st));
@@ -677,8 +675,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->W.pool_head);
   dev_free(F->W.flags);
   dev_free(F->W.stats);
-  dev_free(F->W.hkeys);
-  dev_free(F->W.hmask);
+  dev_free(F->W.htab);
   dev_free(F->W.redo);
   dev_free(F->W.cont);
   dev_free(F->W.cont_cap);

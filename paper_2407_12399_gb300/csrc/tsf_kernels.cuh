@@ -86,10 +86,12 @@ struct D1Work {
   uint32_t* pool_head;
   int32_t* flags;         // [0] changed, [1] number of candidate columns
   unsigned long long* stats;  // [0] lower stars visited, [1] max per column
-  // (column, vertex) -> parity mask of pending entries, open addressing
-  unsigned long long* hkeys;
-  uint32_t* hmask;
+  // (column, vertex) -> parity mask of pending entries, open addressing:
+  // word = (column << vbits | vertex) << 14 | mask, ~0 = empty
+  unsigned long long* htab;
   uint32_t hash_cap;      // power of two
+  int vbits;              // bits of a vertex id (nv < 2^vbits)
+  int hshift;             // 64 - log2(hash_cap): home slot = top bits of key * golden ratio
   int32_t* redo;          // columns whose warp frontier overflowed
   uint4* cont;            // open columns after phase A: frontier off/size, output off/size
   uint32_t* cont_cap;     // ... output capacity
