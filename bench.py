@@ -248,12 +248,12 @@ def run_gpu(args):
     # algorithmic bytes per launch (per-unit figures in the design doc)
     n_grad = float(np.mean([s["n_gradient_vertices"] for s in stats]))
     visits = float(np.mean([s["d1_blocks_total"] for s in stats]))
-    bytes_grad = nv * 1.0 + n_grad * (4.0 + 32.0 + 1.0 + 80.0)   # dirty flags; rank, record, vnext, D1 table
+    bytes_grad = nv * 1.0 + n_grad * (4.0 + 32.0 + 1.0 + 144.0)  # dirty flags; rank, record, vnext, D1 table
     bytes_sort = nv * 80.0                                        # 4 radix passes + rank scatter
     updates = float(np.mean([s["d1_star_updates"] for s in stats]))
-    # per lower-star visit: vertex id 4, table 80, own hash key 8 + mask 4;
-    # per target-star update: hash key 8, mask 4, rank 4
-    bytes_d1 = visits * 96.0 + updates * 16.0
+    # per lower-star visit: its 144-byte table row (the pending masks live in
+    # shared memory); updates of target stars touch no global memory
+    bytes_d1 = visits * 144.0
     g_grad, ms_grad = gbs(bytes_grad, "gradient")
     g_sort, ms_sort = gbs(bytes_sort, "vertex_order")
     g_d1, ms_d1 = gbs(bytes_d1, "pairs_d1_morse")

@@ -9,9 +9,9 @@ namespace tsf {
 // star holds a vertex updated by the last gradient step are recomputed
 // (Section 4.2, fast persistence update); the others keep last iteration's
 // record, which stays exact because their lower stars did not change.
-__global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint8_t* __restrict__ dirty,
-                           Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
-                           uint32_t* status, unsigned long long* n_recomputed) {
+__global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
+                           const uint8_t* __restrict__ dirty, Rec* __restrict__ rec, uint8_t* __restrict__ vnext8,
+                           D1Tab* __restrict__ tab, uint32_t* status, unsigned long long* n_recomputed) {
   const Geo& sg = c_geo;
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool work = v < d.nv;
@@ -88,10 +88,20 @@ __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const uint
     }
     t.q[8] = ends;
     t.q[9] = orient;
+    {
+      int x, y, z;
+      vxyz(d, (uint32_t)v, x, y, z);
+#pragma unroll
+      for (int i = 0; i < 14; ++i) {
+        int nx, ny, nz;
+        t.nkey[i] = nbr_xyz(d, x, y, z, i, nx, ny, nz) ? value_key(__ldg(values + vid(d, nx, ny, nz))) : 0u;
+      }
+      t.pad[0] = t.pad[1] = 0;
+    }
     uint4* dst4 = reinterpret_cast<uint4*>(tab + v);
     const uint4* src4 = reinterpret_cast<const uint4*>(&t);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) dst4[k] = src4[k];
+    for (int k = 0; k < 9; ++k) dst4[k] = src4[k];
   }
 }
 
@@ -340,10 +350,10 @@ __global__ void k_zero_pairs(Dims d, const uint32_t* __restrict__ rank, unsigned
 
 namespace tsf {
 
-void launch_gradient(const Dims& d, const uint32_t* rank, const uint8_t* dirty, Rec* rec, uint8_t* vnext8,
-                     D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st) {
+void launch_gradient(const Dims& d, const uint32_t* rank, const float* f, const uint8_t* dirty, Rec* rec,
+                     uint8_t* vnext8, D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st) {
   unsigned nb = (unsigned)((d.nv + 127) / 128);
-  k_gradient<<<nb, 128, 0, st>>>(d, rank, dirty, rec, vnext8, tab, status, n_recomputed); note_launch();
+  k_gradient<<<nb, 128, 0, st>>>(d, rank, f, dirty, rec, vnext8, tab, status, n_recomputed); note_launch();
 }
 
 int crit_tiles(int64_t nv) { return (int)((nv + kCTile - 1) / kCTile); }

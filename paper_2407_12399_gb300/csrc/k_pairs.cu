@@ -313,6 +313,7 @@ struct D1Ctx {
   CritLists L;
   const uint8_t* d0_killed;
   const uint32_t* d0mask;
+  const float* f;
 };
 
 __device__ __forceinline__ int nbr_of_pair(const Dims& d, uint32_t hi, uint32_t lo) {
@@ -569,53 +570,38 @@ __global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
 }
 
 // ---------------------------------------------------------------------------
-// Phase 1, one group of threads per column.  Pending entries are kept as
-// (column, vertex) -> parity mask over the 14 edge directions of the vertex's
-// lower star, one 64-bit word per entry of an open-addressing table:
-//   bits 63..14  key (column << vbits | vertex), bits 13..0  the mask.
-// The frontier is the descending list of (rank << 32 | slot) of the lower
-// stars with a pending mask, in shared memory.  Each round the group takes
-// the NT highest, one per thread.  The projection is linear, so a lower star
-// that receives entries after it was processed simply comes back.
+// Phase 1, one group of threads per column.  The pending entries of a column
+// are lower stars with a parity mask over their 14 edge directions.  All of
+// a column's updates come from its own group, so they live in the group's
+// shared memory: the frontier, sorted by descending key = value_key << 32 |
+// vertex (the rank order), one entry per star.  Each round the group takes
+// the NT highest entries, one per thread; every visit appends its updates of
+// target stars to a stage; the stage is sorted, merged into the rest of the
+// frontier and equal keys are combined (xor of masks, zero masks dropped).
+// The projection is linear, so a star that receives entries after it was
+// processed simply comes back, and the order only decides how often.
 // ---------------------------------------------------------------------------
-constexpr unsigned long long kHEmpty = ~0ull, kHBits = 0x3FFFull;
+struct __align__(16) FEnt {
+  unsigned long long key;  // value_key << 32 | vertex; 0 never occurs (NaN is rejected)
+  uint32_t mask;
+  uint32_t pad;
+};
 
-__device__ __forceinline__ unsigned long long hkey(const D1Work& W, uint32_t j, uint32_t v) {
-  return (((unsigned long long)j << W.vbits) | v) << 14;
+// Entries saved in the pool (8-byte aligned) are two 64-bit words.
+__device__ __forceinline__ void fent_save(unsigned long long* p, const FEnt& e) {
+  p[0] = e.key;
+  p[1] = e.mask;
 }
-__device__ __forceinline__ uint32_t hhome(const D1Work& W, unsigned long long key) {
-  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> W.hshift);
-}
-
-// xor `bits` into entry `key`, inserting it when absent, probing on from slot
-// h whose word was read as w.  Returns the entry's previous mask (0 when it
-// was absent) and its slot; on a full table sets kErrPool, slot = ~0.
-__device__ uint32_t hxor_probe(D1Work& W, unsigned long long key, uint32_t bits, uint32_t h, unsigned long long w,
-                               uint32_t& slot, uint32_t* status) {
-  for (uint32_t probe = 0; probe < W.hash_cap; ++probe) {
-    if (w == kHEmpty) {
-      unsigned long long old = atomicCAS(&W.htab[h], kHEmpty, key | bits);
-      if (old == kHEmpty) {
-        slot = h;
-        return 0u;
-      }
-      w = old;
-    }
-    if ((w & ~kHBits) == key) {
-      slot = h;
-      return (uint32_t)(atomicXor(&W.htab[h], (unsigned long long)bits) & kHBits);
-    }
-    h = (h + 1) & (W.hash_cap - 1);
-    w = W.htab[h];
-  }
-  atomicOr(status, kErrPool);
-  slot = 0xFFFFFFFFu;
-  return 1u;
+__device__ __forceinline__ FEnt fent_restore(const unsigned long long* p) {
+  FEnt e;
+  e.key = p[0];
+  e.mask = (uint32_t)p[1];
+  e.pad = 0u;
+  return e;
 }
 
-__global__ void k_hash_clear(D1Work W) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < W.hash_cap) W.htab[i] = kHEmpty;
+__device__ __forceinline__ unsigned long long star_key(uint32_t vkey, uint32_t v) {
+  return ((unsigned long long)vkey << 32) | v;
 }
 
 // Target stars of the link edges left by a visit, with compile-time
@@ -646,28 +632,21 @@ __device__ __forceinline__ void closures(const D1Tab& t, uint32_t m, uint64_t& p
   (closure_of<X>(t, m, path, em), ...);
 }
 
-// One lower-star visit of a column (frontier entry fe = rank << 32 | slot):
-// take the star's pending mask, apply the closures of its edges (linear over
-// Z/2), emit the positive critical edges left as (v << 4 | x), and xor the
-// link edges left into the target stars' masks.  Returns the targets that
-// became pending as frontier entries.  Four dependent memory steps: the
-// take, the table, the targets' words and ranks, the targets' updates.
-template <int KNEW>
-__device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned long long colkey, unsigned long long fe,
-                                         const int32_t* snd, uint32_t* status, unsigned long long* myouts,
-                                         int& myout, unsigned long long* mynew, int& nnew, bool& overflow,
-                                         int& visits, int& updates) {
-  unsigned long long w0 = atomicAnd(&W.htab[(uint32_t)fe], ~kHBits);
-  uint32_t m = (uint32_t)(w0 & kHBits);
-  if (!m) return;
-  ++visits;
-  uint32_t v = (uint32_t)((w0 >> 14) & ((1ull << W.vbits) - 1));
+// One lower-star visit: apply the closures of the star's pending edges
+// (linear over Z/2), keep the positive critical edges left as (v << 4 | x),
+// and append the link edges left to the stage as updates of the target
+// stars.  One dependent global load: the star's table row.
+template <int SCAP>
+__device__ __forceinline__ void d1_visit(const D1Ctx& c, FEnt fe, const int32_t* snd, FEnt* stage, int* s_ntot,
+                                         int* s_flag, unsigned long long* myouts, int& myout, int& updates) {
+  uint32_t v = (uint32_t)fe.key;
+  uint32_t m = fe.mask;
   D1Tab t;
   {
     const uint4* s4 = reinterpret_cast<const uint4*>(c.tab + v);
     uint4* d4 = reinterpret_cast<uint4*>(&t);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) d4[k] = __ldg(s4 + k);
+    for (int k = 0; k < 9; ++k) d4[k] = __ldg(s4 + k);
   }
   uint64_t path = 0;
   uint32_t em = 0;
@@ -681,51 +660,29 @@ __device__ __forceinline__ void d1_visit(const D1Ctx& c, D1Work& W, unsigned lon
 #pragma unroll
   for (int k = 0; k < 14; ++k) tmask[k] = 0;
   link_targets(path & t.q[9], path & ~t.q[9], tmask, std::make_integer_sequence<int, 36>{});
-  // the targets' home words and ranks, all loads in flight together
-  unsigned long long w[14];
-  uint32_t home[14], trank[14];
+  int cnt = 0;
+#pragma unroll
+  for (int hn = 0; hn < 14; ++hn) cnt += tmask[hn] != 0u;
+  if (!cnt) return;
+  int off = atomicAdd(s_ntot, cnt);
+  if (off + cnt > SCAP) {
+    atomicOr(s_flag, 1);
+    return;
+  }
+  updates += cnt;
 #pragma unroll
   for (int hn = 0; hn < 14; ++hn) {
     if (tmask[hn]) {
       uint32_t hv = (uint32_t)((int32_t)v + snd[hn]);
-      home[hn] = hhome(W, colkey | ((unsigned long long)hv << 14));
-      w[hn] = W.htab[home[hn]];
-      trank[hn] = __ldg(c.rank + hv);
-    }
-  }
-  // first attempt, all atomics in flight together: xor into the entry when
-  // the home slot holds it, insert it when the home slot is empty
-  uint32_t present = 0, empty = 0;
-#pragma unroll
-  for (int hn = 0; hn < 14; ++hn) {
-    if (tmask[hn]) {
-      unsigned long long key = colkey | ((unsigned long long)(uint32_t)((int32_t)v + snd[hn]) << 14);
-      if ((w[hn] & ~kHBits) == key) {
-        present |= 1u << hn;
-        w[hn] = atomicXor(&W.htab[home[hn]], (unsigned long long)tmask[hn]);
-      } else if (w[hn] == kHEmpty) {
-        empty |= 1u << hn;
-        w[hn] = atomicCAS(&W.htab[home[hn]], kHEmpty, key | tmask[hn]);
-      }
-    }
-  }
-#pragma unroll
-  for (int hn = 0; hn < 14; ++hn) {
-    if (tmask[hn]) {
-      uint32_t old, slot = home[hn];
-      if ((present >> hn) & 1u) {
-        old = (uint32_t)(w[hn] & kHBits);
-      } else if (((empty >> hn) & 1u) && w[hn] == kHEmpty) {
-        old = 0u;  // inserted
-      } else {     // the home slot holds another key, or the insert lost a race: probe on
-        unsigned long long key = colkey | ((unsigned long long)(uint32_t)((int32_t)v + snd[hn]) << 14);
-        old = hxor_probe(W, key, tmask[hn], home[hn], w[hn], slot, status);
-      }
-      ++updates;
-      if (old == 0u && slot != 0xFFFFFFFFu) {
-        if (nnew < KNEW) mynew[nnew++] = ((unsigned long long)trank[hn] << 32) | slot;
-        else overflow = true;
-      }
+      FEnt e;
+      e.key = star_key(t.nkey[hn], hv);
+      e.mask = tmask[hn];
+      e.pad = 0;
+      stage[off++] = e;
+      // the star is likely visited in a later round: bring its row to L2
+      const char* row = reinterpret_cast<const char*>(c.tab + hv);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(row + 128));
     }
   }
 }
@@ -768,8 +725,8 @@ __device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive
   return res;
 }
 
-// Descending bitonic sort of a[0..n2), n2 a power of two (shared or global
-// memory of the group; the group's barrier orders both).
+// Descending bitonic sort of a[0..n2) (n2 a power of two) by key, 64-bit
+// values (shared or global memory of the group; its barrier orders both).
 template <int NT>
 __device__ void group_sort_desc(unsigned long long* a, int n2) {
   for (int size = 2; size <= n2; size <<= 1)
@@ -788,22 +745,87 @@ __device__ void group_sort_desc(unsigned long long* a, int n2) {
       gsync<NT>();
     }
 }
+template <int NT>
+__device__ void group_sort_desc(FEnt* a, int n2) {
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += NT) {
+        int jx = i ^ stride;
+        if (jx > i) {
+          bool desc = (i & size) == 0;
+          FEnt x = a[i], y = a[jx];
+          if ((x.key < y.key) == desc) {
+            a[i] = y;
+            a[jx] = x;
+          }
+        }
+      }
+      gsync<NT>();
+    }
+}
+
+// New frontier from the untaken rest (front[nb..nf), descending) and the
+// stage (ntot updates, any order): sort the stage, merge, combine equal keys.
+// Returns the new frontier size.  All threads of the group call it.
+template <int NT>
+__device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* stage, int ntot, int* scan_sm) {
+  const int tid = threadIdx.x;
+  int rest = nf - nb;
+  int n2 = 1;
+  while (n2 < ntot) n2 <<= 1;
+  for (int k = ntot + tid; k < n2; k += NT) stage[k].key = 0ull;
+  gsync<NT>();
+  group_sort_desc<NT>(stage, n2);
+  int total = rest + ntot;
+  for (int k = tid; k < total; k += NT) {  // merge path
+    int lo = max(0, k - ntot), hi = min(k, rest);
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (front[nb + mid].key >= stage[k - mid - 1].key) lo = mid + 1;
+      else hi = mid;
+    }
+    int i = lo, jb = k - lo;
+    other[k] = (i < rest && (jb >= ntot || front[nb + i].key >= stage[jb].key)) ? front[nb + i] : stage[jb];
+  }
+  gsync<NT>();
+  int kept = 0;
+  for (int base = 0; base < total; base += NT) {
+    int k = base + tid;
+    int keep = 0;
+    FEnt e;
+    e.key = 0ull;
+    e.mask = 0u;
+    e.pad = 0u;
+    if (k < total) {
+      e = other[k];
+      if (k == 0 || other[k - 1].key != e.key) {
+        for (int q = k + 1; q < total && other[q].key == e.key; ++q) e.mask ^= other[q].mask;
+        keep = e.mask != 0u;
+      }
+    }
+    int t;
+    int off = gscan<NT>(keep, t, scan_sm);
+    if (keep) front[kept + off] = e;
+    kept += t;
+  }
+  gsync<NT>();
+  return kept;
+}
 
 // Round loop of one column.  Phase A (NT = 32, max_rounds > 0): every column,
-// one warp; a column still open after max_rounds (or whose frontier could
-// outgrow the warp's buffers) saves its frontier and is listed for phase B
-// (NT = 128, one block per listed column).
-template <int NT, int FCAP, int SCAP, int KNEW>
+// one warp; a column still open after max_rounds, or whose frontier outgrows
+// the warp's buffers, saves its entries and is listed for phase B (NT = 128,
+// one block per listed column).
+template <int NT, int FCAP, int SCAP>
 __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int ncols, int max_rounds,
                                                        uint32_t* status) {
-  static_assert(SCAP >= NT * KNEW, "one round's new entries fit the stage");
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long* front = reinterpret_cast<unsigned long long*>(smem);
-  unsigned long long* other = front + FCAP;
-  unsigned long long* stage = other + FCAP;
+  FEnt* front = reinterpret_cast<FEnt*>(smem);
+  FEnt* other = front + FCAP;
+  FEnt* stage = other + FCAP;
   __shared__ int32_t snd[16];
   __shared__ int scan_sm[16];  // NT/32 + 1 <= 16
-  __shared__ int s_nf, s_flag;
+  __shared__ int s_nf, s_flag, s_ntot, s_otot;
   __shared__ Vec s_out, s_grow;
   if (threadIdx.x < 14) snd[threadIdx.x] = c.nd.d[threadIdx.x];
   const bool phase_b = max_rounds <= 0;
@@ -814,29 +836,24 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
   } else {
     j = blockIdx.x;
     if (j >= ncols) return;
-    if ((unsigned long long)j >> (50 - W.vbits)) {  // beyond the key's column field
-      if (threadIdx.x == 0) {
-        W.redo[j] = 1;
-        W.hsize[j] = 0;
-      }
-      return;
-    }
   }
   const int tid = threadIdx.x;
-  const unsigned long long colkey = hkey(W, (uint32_t)j, 0u);
   if (tid == 0) {
     s_flag = 0;
+    s_nf = 0;
+    s_ntot = 0;
+    s_otot = 0;
     if (phase_b) {
       uint4 cs = W.cont[j];
-      s_nf = (int)cs.y;
+      s_ntot = (int)cs.y;  // saved entries, combined below like a stage
       s_out.off = cs.z;
       s_out.size = cs.w;
       s_out.cap = W.cont_cap[j];
       s_out.h = W.pool + s_out.off;
     } else {
-      s_nf = 0;
       if (!vec_alloc(W, s_out, 64, status)) s_flag = 1;
-      // seed: the boundary of the critical triangle, as parity masks
+      // seed: the boundary of the critical triangle, each edge an entry of
+      // the lower star of its higher endpoint
       uint32_t ve = c.L.c2_ve[W.cols[j]];
       uint32_t v0 = ve >> 6;
       int e0 = (int)(ve & 63u);
@@ -847,38 +864,37 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
         uint32_t p = ends[k][0], q = ends[k][1];
         uint32_t rp = c.rank[p], rq = c.rank[q];
         uint32_t hi = rp > rq ? p : q, lo = rp > rq ? q : p;
-        unsigned long long key = colkey | ((unsigned long long)hi << 14);
-        uint32_t h = hhome(W, key), slot;
-        uint32_t old = hxor_probe(W, key, 1u << nbr_of_pair(c.d, hi, lo), h, W.htab[h], slot, status);
-        if (old == 0u && slot != 0xFFFFFFFFu) {
-          unsigned long long e = ((unsigned long long)max(rp, rq) << 32) | slot;
-          int ps = 0;
-          while (ps < s_nf && front[ps] > e) ++ps;
-          if (ps == s_nf || front[ps] != e) {
-            for (int t = s_nf; t > ps; --t) front[t] = front[t - 1];
-            front[ps] = e;
-            ++s_nf;
-          }
-        }
+        FEnt e;
+        e.key = star_key(value_key(c.f[hi]), hi);
+        e.mask = 1u << nbr_of_pair(c.d, hi, lo);
+        e.pad = 0u;
+        stage[s_ntot++] = e;
       }
     }
   }
   gsync<NT>();
   if (phase_b) {
     uint4 cs = W.cont[j];
-    for (int i = tid; i < (int)cs.y; i += NT) front[i] = W.pool[cs.x + i];
+    for (int i = tid; i < (int)cs.y; i += NT) stage[i] = fent_restore(W.pool + cs.x + 2 * (size_t)i);
   }
   gsync<NT>();
+  {
+    int n0 = group_combine<NT>(front, 0, 0, other, stage, s_ntot, scan_sm);
+    if (tid == 0) {
+      s_nf = n0;
+      s_ntot = 0;
+    }
+    gsync<NT>();
+  }
   int visits = 0, updates = 0, rounds = 0;
   bool failed = s_flag != 0;
+  bool handoff = false;
   while (!failed) {
     int nf = s_nf;
     if (nf == 0) break;
     if (!phase_b && rounds >= max_rounds) break;
-    // phase A hands a column whose frontier could outgrow FCAP to phase B
-    if (!phase_b && nf - min(NT, nf) + min(NT, nf) * KNEW > FCAP) break;
     // every target is a lower neighbour of the visited vertex, so the
-    // frontier's highest rank drops each round: at most nv rounds
+    // frontier's highest key drops each round: at most nv rounds
     if (rounds > c.d.nv) {
       if (tid == 0) atomicOr(status, kErrRounds);
       failed = true;
@@ -886,115 +902,110 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     }
     ++rounds;
     int nb = min(NT, nf);
-    int nnew = 0, myout = 0;
-    unsigned long long mynew[KNEW];
+    int myout = 0;
     unsigned long long myouts[14];
-    bool overflow = false;
-    if (tid < nb)
-      d1_visit<KNEW>(c, W, colkey, front[tid], snd, status, myouts, myout, mynew, nnew, overflow, visits, updates);
-    if (overflow) atomicOr(&s_flag, 1);
+    if (tid < nb) {
+      ++visits;
+      d1_visit<SCAP>(c, front[tid], snd, stage, &s_ntot, &s_flag, myouts, myout, updates);
+    }
+    int ooff = myout ? atomicAdd(&s_otot, myout) : 0;
+    gsync<NT>();
+    if (s_flag) {  // stage overflow: updates were dropped, recompute the column
+      failed = true;
+      break;
+    }
     // outputs: append to the column's list in the pool (grown by the group)
-    int otot;
-    int ooff = gscan<NT>(myout, otot, scan_sm);
-    if (tid == 0) {
-      s_grow.h = nullptr;
-      if (otot > 0 && s_out.size + otot > s_out.cap) {
-        uint32_t cap = s_out.cap;
-        while (cap < s_out.size + otot) cap *= 2;
-        if (!vec_alloc(W, s_grow, cap, status)) {
-          s_grow.h = nullptr;
-          s_flag = 1;
+    int otot = s_otot;
+    if (otot > 0) {
+      if (tid == 0) {
+        s_grow.h = nullptr;
+        if (s_out.size + otot > s_out.cap) {
+          uint32_t cap = s_out.cap;
+          while (cap < s_out.size + otot) cap *= 2;
+          if (!vec_alloc(W, s_grow, cap, status)) {
+            s_grow.h = nullptr;
+            s_flag = 1;
+          }
         }
       }
-    }
-    gsync<NT>();
-    if (s_flag) {
-      failed = true;
-      break;
-    }
-    if (s_grow.h) {
-      for (uint32_t i = tid; i < s_out.size; i += NT) s_grow.h[i] = s_out.h[i];
+      gsync<NT>();
+      if (s_flag) {
+        failed = true;
+        break;
+      }
+      if (s_grow.h) {
+        for (uint32_t i = tid; i < s_out.size; i += NT) s_grow.h[i] = s_out.h[i];
+        gsync<NT>();
+        if (tid == 0) {
+          s_grow.size = s_out.size;
+          s_out = s_grow;
+        }
+        gsync<NT>();
+      }
+      for (int k = 0; k < myout; ++k) s_out.h[s_out.size + ooff + k] = myouts[k];
       gsync<NT>();
       if (tid == 0) {
-        s_grow.size = s_out.size;
-        s_out = s_grow;
+        s_out.size += otot;
+        s_otot = 0;
       }
-      gsync<NT>();
     }
-    for (int k = 0; k < myout; ++k) s_out.h[s_out.size + ooff + k] = myouts[k];
-    gsync<NT>();
-    if (tid == 0) s_out.size += otot;
-    // new entries: stage, sort descending, merge with front[nb..nf)
-    int ntot;
-    int noff = gscan<NT>(nnew, ntot, scan_sm);
-    int rest = nf - nb;
-    if (rest + ntot > FCAP) {
+    int ntot = s_ntot;
+    if (nf - nb + ntot > FCAP) {  // the new frontier would not fit
+      handoff = !phase_b;
       failed = true;
+      if (handoff) {  // phase A: the rest and the stage go to phase B as they are
+        __shared__ Vec s_fr;
+        int rest = nf - nb;
+        if (tid == 0 && !vec_alloc(W, s_fr, 2u * (uint32_t)(rest + ntot), status)) s_flag = 1;
+        gsync<NT>();
+        if (!s_flag) {
+          for (int i = tid; i < rest; i += NT) fent_save(s_fr.h + 2 * i, front[nb + i]);
+          for (int i = tid; i < ntot; i += NT) fent_save(s_fr.h + 2 * (rest + i), stage[i]);
+          gsync<NT>();
+          if (tid == 0) {
+            W.cont[j] = make_uint4(s_fr.off, (uint32_t)(rest + ntot), s_out.off, s_out.size);
+            W.cont_cap[j] = s_out.cap;
+            W.big[atomicAdd(W.nbig, 1)] = j;
+          }
+        } else {
+          handoff = false;
+        }
+      }
       break;
     }
-    for (int k = 0; k < nnew; ++k) stage[noff + k] = mynew[k];
-    int n2 = 1;
-    while (n2 < ntot) n2 <<= 1;
-    for (int k = ntot + tid; k < n2; k += NT) stage[k] = 0;
     gsync<NT>();
-    group_sort_desc<NT>(stage, n2);
-    int total = rest + ntot;
-    for (int k = tid; k < total; k += NT) {
-      int lo = max(0, k - ntot), hi = min(k, rest);
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (front[nb + mid] >= stage[k - mid - 1]) lo = mid + 1;
-        else hi = mid;
-      }
-      int i = lo, jb = k - lo;
-      other[k] = (i < rest && (jb >= ntot || front[nb + i] >= stage[jb])) ? front[nb + i] : stage[jb];
+    int nn = group_combine<NT>(front, nb, nf, other, stage, ntot, scan_sm);
+    if (tid == 0) {
+      s_nf = nn;
+      s_ntot = 0;
     }
-    gsync<NT>();
-    int keep_total = 0;
-    for (int base = 0; base < total; base += NT) {
-      int k = base + tid;
-      int keep = (k < total) && (k == 0 || other[k] != other[k - 1]);
-      unsigned long long val = k < total ? other[k] : 0ull;
-      int t;
-      int off = gscan<NT>(keep, t, scan_sm);
-      if (keep) front[keep_total + off] = val;
-      keep_total += t;
-      gsync<NT>();
-    }
-    if (tid == 0) s_nf = keep_total;
     gsync<NT>();
   }
   // visits and target updates of the whole group
   int vtot, utot;
   gscan<NT>(visits, vtot, scan_sm);
   gscan<NT>(updates, utot, scan_sm);
-  if (failed) {
-    if (tid == 0) {
-      W.redo[j] = 1;
-      W.hsize[j] = 0;
-    }
-    return;
-  }
-  if (!phase_b && s_nf > 0) {
-    // still open: save the frontier for phase B
-    __shared__ Vec s_fr;
-    if (tid == 0) {
-      if (!vec_alloc(W, s_fr, (uint32_t)max(s_nf, 1), status)) s_flag = 1;
-    }
-    gsync<NT>();
-    if (s_flag) {
-      if (tid == 0) {
-        W.redo[j] = 1;
-        W.hsize[j] = 0;
+  if (handoff || (!failed && !phase_b && s_nf > 0)) {
+    if (!handoff) {  // still open after max_rounds: save the frontier for phase B
+      __shared__ Vec s_fr2;
+      if (tid == 0 && !vec_alloc(W, s_fr2, 2u * (uint32_t)s_nf, status)) s_flag = 1;
+      gsync<NT>();
+      if (s_flag) {
+        if (tid == 0) {
+          W.redo[j] = 1;
+          W.hsize[j] = 0;
+        }
+        return;
       }
-      return;
+      for (int i = tid; i < s_nf; i += NT) fent_save(s_fr2.h + 2 * i, front[i]);
+      gsync<NT>();
+      if (tid == 0) {
+        W.cont[j] = make_uint4(s_fr2.off, (uint32_t)s_nf, s_out.off, s_out.size);
+        W.cont_cap[j] = s_out.cap;
+        W.big[atomicAdd(W.nbig, 1)] = j;
+      }
     }
-    for (int i = tid; i < s_nf; i += NT) s_fr.h[i] = front[i];
-    gsync<NT>();
     if (tid == 0) {
-      W.cont[j] = make_uint4(s_fr.off, (uint32_t)s_nf, s_out.off, s_out.size);
-      W.cont_cap[j] = s_out.cap;
-      W.big[atomicAdd(W.nbig, 1)] = j;
       W.redo[j] = 0;
       W.hsize[j] = 0;
       atomicAdd(&W.stats[0], (unsigned long long)vtot);
@@ -1003,13 +1014,20 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
     }
     return;
   }
+  if (failed) {
+    if (tid == 0) {
+      W.redo[j] = 1;
+      W.hsize[j] = 0;
+    }
+    return;
+  }
   // finished: (v, x) -> C1 index, sort descending, keep the entries present
   // an odd number of times (Z/2)
   uint32_t nout = s_out.size;
   int n2 = 1;
   while (n2 < (int)nout) n2 <<= 1;
-  unsigned long long* a = stage;
-  if (n2 > SCAP) {  // too long for shared memory: sort in the pool
+  unsigned long long* a = reinterpret_cast<unsigned long long*>(stage);
+  if (n2 > 2 * SCAP) {  // too long for shared memory: sort in the pool
     if (tid == 0 && !vec_alloc(W, s_grow, (uint32_t)n2, status)) s_flag = 1;
     gsync<NT>();
     if (s_flag) {
@@ -1069,13 +1087,14 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
   }
 }
 
-// A visit makes at most 14 stars pending (one per neighbour).  Phase A keeps
-// its shared memory small so that every column's warp is resident at once.
-constexpr int kNewA = 14, kNewB = 14, kThreadsB = 128;
-constexpr int kFrontA = 1024, kStageA = 512;
-constexpr int kFrontB = 2048, kStageB = 2048;
+// Phase A keeps its shared memory small so that every column's warp is
+// resident at once; a visit appends 1.1 updates on average, 14 at most.
+constexpr int kThreadsB = 128;
+constexpr int kFrontA = 256, kStageA = 512;
+constexpr int kFrontB = 1024, kStageB = 1024;
+static_assert(kFrontA + kStageA <= kStageB, "a phase A handoff fits phase B's stage");
 
-static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + scap) * sizeof(unsigned long long); }
+static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + scap) * sizeof(FEnt); }
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
 // each low; every addition is of an earlier column.
@@ -1151,8 +1170,8 @@ int launch_d1_prepare(int n2, D1Work& W, PairOut& P, int32_t* h_flags, cudaStrea
 }
 
 void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int ncols, const uint32_t* rank,
-                     const uint32_t* order, const Rec* rec, const D1Tab* tab, const uint32_t* c1base, D1Work& W,
-                     PairOut& P, uint32_t* status, cudaStream_t st) {
+                     const uint32_t* order, const float* f, const Rec* rec, const D1Tab* tab, const uint32_t* c1base,
+                     D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st) {
   if (ncols == 0) return;
   D1Ctx c;
   c.d = d;
@@ -1165,23 +1184,22 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   c.L = L;
   c.d0_killed = P.d0_killed;
   c.d0mask = P.d0mask;
-  W.vbits = 64 - __builtin_clzll((unsigned long long)d.nv);
-  W.hshift = 64 - __builtin_ctz(W.hash_cap);
+  c.f = f;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, 72, st);
-  k_hash_clear<<<(W.hash_cap + 255) / 256, 256, 0, st>>>(W); note_launch();
   cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
-  static bool attr = false;
   size_t sa = d1_group_smem(kFrontA, kStageA), sb = d1_group_smem(kFrontB, kStageB);
-  if (!attr) {
-    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, kNewA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sa);
-    cudaFuncSetAttribute(k_d1_morse_group<kThreadsB, kFrontB, kStageB, kNewB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static bool attr[64] = {};
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+    cudaFuncSetAttribute(k_d1_morse_group<kThreadsB, kFrontB, kStageB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
-    attr = true;
+    attr[dev] = true;
   }
-  k_d1_morse_group<32, kFrontA, kStageA, kNewA><<<ncols, 32, sa, st>>>(c, W, ncols, 48, status); note_launch();
-  k_d1_morse_group<kThreadsB, kFrontB, kStageB, kNewB><<<ncols, kThreadsB, sb, st>>>(c, W, ncols, 0, status); note_launch();
+  k_d1_morse_group<32, kFrontA, kStageA><<<ncols, 32, sa, st>>>(c, W, ncols, 48, status); note_launch();
+  k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<ncols, kThreadsB, sb, st>>>(c, W, ncols, 0, status); note_launch();
   k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
 }
 

@@ -395,7 +395,8 @@ int compute_diagram(tsf_field* F, bool incremental) {
   bool inc = incremental && F->records_valid && F->dirty_valid;
   ck(cudaMemsetAsync(F->counter, 0, 8, st));
   stage_begin(F, kGrad);
-  launch_gradient(F->d, F->rank, inc ? F->dirty : nullptr, F->rec, F->vnext8, F->tab, F->status, F->counter, st);
+  launch_gradient(F->d, F->rank, F->f, inc ? F->dirty : nullptr, F->rec, F->vnext8, F->tab, F->status, F->counter,
+                  st);
   stage_end(F, kGrad);
   unsigned long long ngrad = 0;
   ck(cudaMemcpyAsync(&ngrad, F->counter, 8, cudaMemcpyDeviceToHost, st));
@@ -435,24 +436,14 @@ int compute_diagram(tsf_field* F, bool incremental) {
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
     if (!F->W.stats) ck(dev_alloc(&F->W.stats, 9));
-    // (column, vertex) table: the lower stars the saddle-saddle columns visit
-    // number about half the vertices; keep the load factor at or below ~1/4
-    uint32_t hwant = 1u << 22;
-    while ((int64_t)hwant < std::min<int64_t>(2 * F->d.nv, (int64_t)1 << 28)) hwant <<= 1;
-    hwant = (uint32_t)std::min<int64_t>((int64_t)hwant << attempt, (int64_t)1 << 29);
-    if (hwant > F->W.hash_cap) {
-      dev_free(F->W.htab);
-      ck(dev_alloc(&F->W.htab, hwant));
-      F->W.hash_cap = hwant;
-    }
     ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
     int ncols = launch_d1_prepare(F->n2, F->W, F->PO, F->h_flags, st);
     stage_end(F, kD1);
     if (F->n2 == 0) F->h_flags[1] = 0;
     stage_begin(F, kD1Morse);
-    launch_d1_morse(F->d, F->nd, F->L, F->n1, ncols, F->rank, F->order, F->rec, F->tab, F->c1base, F->W, F->PO,
-                    F->status, st);
+    launch_d1_morse(F->d, F->nd, F->L, F->n1, ncols, F->rank, F->order, F->f, F->rec, F->tab, F->c1base, F->W,
+                    F->PO, F->status, st);
     stage_end(F, kD1Morse);
     stage_begin(F, kD1Reduce);
     launch_d1_reduce(F->n1, ncols, F->W, F->PO, F->status, st);
@@ -675,7 +666,6 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->W.pool_head);
   dev_free(F->W.flags);
   dev_free(F->W.stats);
-  dev_free(F->W.htab);
   dev_free(F->W.redo);
   dev_free(F->W.cont);
   dev_free(F->W.cont_cap);

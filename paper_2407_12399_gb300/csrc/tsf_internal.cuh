@@ -67,7 +67,7 @@ __host__ __device__ inline uint64_t rec_crit_tris(const Rec& r) {
 __host__ __device__ inline bool rec_has_max(const Rec& r) { return (r.w[1] >> 22) & 1u; }
 __host__ __device__ inline int rec_tet_code(const Rec& r, int tau) { return (int)rec_bits(r, 56 + 7 * tau, 7); }
 
-// Per-vertex expansion table for the saddle-saddle reduction (80 bytes).
+// Per-vertex expansion table for the saddle-saddle reduction (144 bytes).
 // Eliminating the gradient-paired edges of one lower star is linear over
 // Z/2, so the table holds the effect of each lower-star edge v*x eliminated
 // alone, its *closure*: v*x paired with triangle v*(x, ..) is replaced by
@@ -81,9 +81,14 @@ __host__ __device__ inline int rec_tet_code(const Rec& r, int tau) { return (int
 //   q[9]      bits 0..35: orientation of the link edges (a, b), a < b as
 //             neighbour indices: 1 when a ranks above b (edge a*b then lies
 //             in the lower star of v + off[a])
+//   nkey[i]   value_key of neighbour i (0 outside the grid): with the vertex
+//             id it orders lower stars exactly as their ranks do
 struct __align__(16) D1Tab {
   unsigned long long q[10];
+  uint32_t nkey[14];
+  uint32_t pad[2];
 };
+static_assert(sizeof(D1Tab) == 144, "nine 16-byte loads per row");
 
 template <int X>
 __host__ __device__ __forceinline__ uint64_t tab_closure(const D1Tab& t) {

@@ -46,8 +46,8 @@ void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, ui
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t st);
 
 // ---- k_gradient.cu -------------------------------------------------------
-void launch_gradient(const Dims& d, const uint32_t* rank, const uint8_t* dirty, Rec* rec, uint8_t* vnext8,
-                     D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st);
+void launch_gradient(const Dims& d, const uint32_t* rank, const float* f, const uint8_t* dirty, Rec* rec,
+                     uint8_t* vnext8, D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st);
 int crit_tiles(int64_t nv);
 void launch_crit_count(const Dims& d, const uint32_t* order, const Rec* rec, int4* tile_counts, int4* totals,
                        cudaStream_t st);
@@ -86,12 +86,6 @@ struct D1Work {
   uint32_t* pool_head;
   int32_t* flags;         // [0] changed, [1] number of candidate columns
   unsigned long long* stats;  // [0] lower stars visited, [1] max per column
-  // (column, vertex) -> parity mask of pending entries, open addressing:
-  // word = (column << vbits | vertex) << 14 | mask, ~0 = empty
-  unsigned long long* htab;
-  uint32_t hash_cap;      // power of two
-  int vbits;              // bits of a vertex id (nv < 2^vbits)
-  int hshift;             // 64 - log2(hash_cap): home slot = top bits of key * golden ratio
   int32_t* redo;          // columns whose warp frontier overflowed
   uint4* cont;            // open columns after phase A: frontier off/size, output off/size
   uint32_t* cont_cap;     // ... output capacity
@@ -101,8 +95,8 @@ struct D1Work {
 // D1: candidate columns (returns their number), Morse boundaries, reduction.
 int launch_d1_prepare(int n2, D1Work& W, PairOut& P, int32_t* h_flags, cudaStream_t st);
 void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int ncols, const uint32_t* rank,
-                     const uint32_t* order, const Rec* rec, const D1Tab* tab, const uint32_t* c1base, D1Work& W,
-                     PairOut& P, uint32_t* status, cudaStream_t st);
+                     const uint32_t* order, const float* f, const Rec* rec, const D1Tab* tab, const uint32_t* c1base,
+                     D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st);
 void launch_d1_reduce(int n1, int ncols, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st);
 
 }  // namespace tsf
