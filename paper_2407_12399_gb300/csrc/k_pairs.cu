@@ -745,37 +745,117 @@ __device__ void group_sort_desc(unsigned long long* a, int n2) {
       gsync<NT>();
     }
 }
-template <int NT>
-__device__ void group_sort_desc(FEnt* a, int n2) {
-  for (int size = 2; size <= n2; size <<= 1)
+// Descending bitonic sort of a[0..n) (n <= NT * E) by key, E entries per
+// thread in registers (entry i = thread * E + e): strides below E swap
+// registers, strides below 32 E exchange with a lane by shuffles, longer
+// strides (blocks of several warps only) go through a[] in shared memory.
+// Equal keys may stay in either order.  All threads of the group call it.
+template <int NT, int E>
+__device__ void group_sort_reg(FEnt* a, int n) {
+  constexpr int N = NT * E;
+  const int tid = threadIdx.x, lane = tid & 31;
+  unsigned long long k[E];
+  uint32_t m[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    int i = tid * E + e;
+    k[e] = 0ull;
+    m[e] = 0u;
+    if (i < n) {
+      k[e] = a[i].key;
+      m[e] = a[i].mask;
+    }
+  }
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += NT) {
-        int jx = i ^ stride;
-        if (jx > i) {
-          bool desc = (i & size) == 0;
-          FEnt x = a[i], y = a[jx];
-          if ((x.key < y.key) == desc) {
-            a[i] = y;
-            a[jx] = x;
+      if (stride < E) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          int p = e ^ stride;
+          if (p > e) {
+            bool desc = ((tid * E + e) & size) == 0;
+            if ((k[e] < k[p]) == desc) {
+              unsigned long long tk = k[e];
+              k[e] = k[p];
+              k[p] = tk;
+              uint32_t tm = m[e];
+              m[e] = m[p];
+              m[p] = tm;
+            }
+          }
+        }
+      } else if (stride < 32 * E) {
+        const int lx = stride / E;
+        const bool lower = (lane & lx) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          unsigned long long ok = __shfl_xor_sync(0xFFFFFFFFu, k[e], lx);
+          uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, m[e], lx);
+          bool desc = ((tid * E + e) & size) == 0;
+          bool take = lower == desc ? ok > k[e] : ok < k[e];
+          if (take) {
+            k[e] = ok;
+            m[e] = om;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          a[tid * E + e].key = k[e];
+          a[tid * E + e].mask = m[e];
+        }
+        __syncthreads();
+        const bool lower = ((tid * E) & stride) == 0;
+        unsigned long long ok[E];
+        uint32_t om[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          int jx = (tid * E + e) ^ stride;
+          ok[e] = a[jx].key;
+          om[e] = a[jx].mask;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          bool desc = ((tid * E + e) & size) == 0;
+          bool take = lower == desc ? ok[e] > k[e] : ok[e] < k[e];
+          if (take) {
+            k[e] = ok[e];
+            m[e] = om[e];
           }
         }
       }
-      gsync<NT>();
     }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    a[tid * E + e].key = k[e];
+    a[tid * E + e].mask = m[e];
+  }
+  gsync<NT>();
+}
+
+// Sorts a stage of n <= SCAP entries (a[] holds SCAP entries).
+template <int NT, int SCAP>
+__device__ void group_sort_stage(FEnt* a, int n) {
+  static_assert(SCAP % NT == 0 && SCAP <= 16 * NT, "a stage fits the register sort");
+  if (n <= NT) group_sort_reg<NT, 1>(a, n);
+  else if (n <= 2 * NT) group_sort_reg<NT, (SCAP >= 2 * NT ? 2 : 1)>(a, n);
+  else if (n <= 4 * NT) group_sort_reg<NT, (SCAP >= 4 * NT ? 4 : 1)>(a, n);
+  else if (n <= 8 * NT) group_sort_reg<NT, (SCAP >= 8 * NT ? 8 : 1)>(a, n);
+  else group_sort_reg<NT, (SCAP >= 16 * NT ? 16 : 1)>(a, n);
 }
 
 // New frontier from the untaken rest (front[nb..nf), descending) and the
 // stage (ntot updates, any order): sort the stage, merge, combine equal keys.
 // Returns the new frontier size.  All threads of the group call it.
-template <int NT>
+template <int NT, int SCAP>
 __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* stage, int ntot, int* scan_sm) {
   const int tid = threadIdx.x;
   int rest = nf - nb;
-  int n2 = 1;
-  while (n2 < ntot) n2 <<= 1;
-  for (int k = ntot + tid; k < n2; k += NT) stage[k].key = 0ull;
-  gsync<NT>();
-  group_sort_desc<NT>(stage, n2);
+  group_sort_stage<NT, SCAP>(stage, ntot);
   int total = rest + ntot;
   for (int k = tid; k < total; k += NT) {  // merge path
     int lo = max(0, k - ntot), hi = min(k, rest);
@@ -879,7 +959,7 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
   }
   gsync<NT>();
   {
-    int n0 = group_combine<NT>(front, 0, 0, other, stage, s_ntot, scan_sm);
+    int n0 = group_combine<NT, SCAP>(front, 0, 0, other, stage, s_ntot, scan_sm);
     if (tid == 0) {
       s_nf = n0;
       s_ntot = 0;
@@ -974,7 +1054,7 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int nc
       break;
     }
     gsync<NT>();
-    int nn = group_combine<NT>(front, nb, nf, other, stage, ntot, scan_sm);
+    int nn = group_combine<NT, SCAP>(front, nb, nf, other, stage, ntot, scan_sm);
     if (tid == 0) {
       s_nf = nn;
       s_ntot = 0;
