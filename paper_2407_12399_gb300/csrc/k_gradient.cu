@@ -1,36 +1,19 @@
 // k_gradient.cu -- lower-star discrete gradient (Section 4.2) and compaction
 // of the critical cells in lexicographic order.
+#include <algorithm>
+
 #include "tsf_kernels.cuh"
 #include "tsf_star.cuh"
 
 namespace tsf {
 
-// One record per vertex.  With `dirty` non-null only vertices whose closed
-// star holds a vertex updated by the last gradient step are recomputed
-// (Section 4.2, fast persistence update); the others keep last iteration's
-// record, which stays exact because their lower stars did not change.
-__global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
-                           const uint8_t* __restrict__ dirty, Rec* __restrict__ rec, uint8_t* __restrict__ vnext8,
-                           D1Tab* __restrict__ tab, uint32_t* status, unsigned long long* n_recomputed) {
+// The lower star of v (Section 4.2): its gradient record, the byte naming
+// the edge v is paired with, and (tab non-null) the saddle-saddle table row.
+__device__ __forceinline__ void gradient_star(const Dims& d, const uint32_t* __restrict__ rank,
+                                              const float* __restrict__ values, int64_t v, Rec* __restrict__ rec,
+                                              uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
+                                              uint32_t* status) {
   const Geo& sg = c_geo;
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool work = v < d.nv;
-  if (work && dirty) {
-    int x, y, z;
-    vxyz(d, (uint32_t)v, x, y, z);
-    bool any = dirty[v] != 0;
-#pragma unroll
-    for (int i = 0; i < 14; ++i) {
-      int nx, ny, nz;
-      if (nbr_xyz(d, x, y, z, i, nx, ny, nz)) any |= dirty[vid(d, nx, ny, nz)] != 0;
-    }
-    work = any;
-  }
-  if (n_recomputed) {
-    unsigned m = __ballot_sync(0xFFFFFFFFu, work);
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(n_recomputed, (unsigned long long)__popc(m));
-  }
-  if (!work) return;
   Star s;
   star_load(s, d, (uint32_t)v, rank);
   Fwd f;
@@ -103,6 +86,43 @@ __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const floa
 #pragma unroll
     for (int k = 0; k < 9; ++k) dst4[k] = src4[k];
   }
+}
+
+// Every lower star (the first diagram of a field, or without the fast update).
+__global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
+                           Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
+                           uint32_t* status) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < d.nv) gradient_star(d, rank, values, v, rec, vnext8, tab, status);
+}
+
+// Section 4.2, fast persistence update: only the lower stars whose closed
+// star holds a vertex the last gradient step updated can change (the vertex
+// itself and its 14 neighbours); the others keep their records, which stay
+// exact.  Each such star is listed once (a generation mark, so the marks are
+// never cleared), then recomputed by one thread of a dense launch.
+__global__ void k_gradient_expand(Dims d, const uint32_t* __restrict__ upd, int64_t nu, uint32_t* __restrict__ mark,
+                                  uint32_t gen, uint32_t* __restrict__ list, unsigned long long* count) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nu * 15) return;
+  uint32_t u = upd[t / 15];
+  int i = (int)(t % 15);
+  uint32_t w = u;
+  if (i < 14) {
+    int x, y, z, nx, ny, nz;
+    vxyz(d, u, x, y, z);
+    if (!nbr_xyz(d, x, y, z, i, nx, ny, nz)) return;
+    w = vid(d, nx, ny, nz);
+  }
+  if (atomicExch(mark + w, gen) != gen) list[atomicAdd(count, 1ull)] = w;
+}
+
+__global__ void k_gradient_list(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
+                                const uint32_t* __restrict__ list, const unsigned long long* __restrict__ count,
+                                Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
+                                uint32_t* status) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (int64_t)*count) gradient_star(d, rank, values, list[i], rec, vnext8, tab, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,10 +370,21 @@ __global__ void k_zero_pairs(Dims d, const uint32_t* __restrict__ rank, unsigned
 
 namespace tsf {
 
-void launch_gradient(const Dims& d, const uint32_t* rank, const float* f, const uint8_t* dirty, Rec* rec,
-                     uint8_t* vnext8, D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st) {
+void launch_gradient(const Dims& d, const uint32_t* rank, const float* f, Rec* rec, uint8_t* vnext8, D1Tab* tab,
+                     uint32_t* status, cudaStream_t st) {
   unsigned nb = (unsigned)((d.nv + 127) / 128);
-  k_gradient<<<nb, 128, 0, st>>>(d, rank, f, dirty, rec, vnext8, tab, status, n_recomputed); note_launch();
+  k_gradient<<<nb, 128, 0, st>>>(d, rank, f, rec, vnext8, tab, status); note_launch();
+}
+
+void launch_gradient_incremental(const Dims& d, const uint32_t* rank, const float* f, const uint32_t* upd, int64_t nu,
+                                 uint32_t* mark, uint32_t gen, uint32_t* list, unsigned long long* count, Rec* rec,
+                                 uint8_t* vnext8, D1Tab* tab, uint32_t* status, cudaStream_t st) {
+  cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (nu <= 0) return;
+  unsigned nb = (unsigned)((nu * 15 + 255) / 256);
+  k_gradient_expand<<<nb, 256, 0, st>>>(d, upd, nu, mark, gen, list, count); note_launch();
+  unsigned nl = (unsigned)((std::min<int64_t>(nu * 15, d.nv) + 127) / 128);
+  k_gradient_list<<<nl, 128, 0, st>>>(d, rank, f, list, count, rec, vnext8, tab, status); note_launch();
 }
 
 int crit_tiles(int64_t nv) { return (int)((nv + kCTile - 1) / kCTile); }

@@ -1118,7 +1118,7 @@ struct ContribLess {
 
 // one thread per vertex segment: acc = +0, acc += c in increasing value order
 __global__ void k_apply_step(int nc, const int32_t* __restrict__ idx, const Contrib* __restrict__ C,
-                             float* __restrict__ f, uint8_t* __restrict__ dirty, unsigned long long* __restrict__ nupd) {
+                             float* __restrict__ f, uint32_t* __restrict__ upd, unsigned long long* __restrict__ nupd) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nc) return;
   uint32_t v = C[idx[r]].v;
@@ -1129,12 +1129,12 @@ __global__ void k_apply_step(int nc, const int32_t* __restrict__ idx, const Cont
   float nw = __fsub_rn(old, acc);
   if (__float_as_uint(nw) != __float_as_uint(old)) {
     f[v] = nw;
-    if (dirty) dirty[v] = 1;
-    atomicAdd(nupd, 1ull);
+    unsigned long long k = atomicAdd(nupd, 1ull);
+    if (upd) upd[k] = v;
   }
 }
 
-int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float alpha_d, float* f, uint8_t* dirty,
+int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float alpha_d, float* f, uint32_t* upd,
                       SolverBufs& B, cudaStream_t st) {
   cudaMemsetAsync(B.count, 0, sizeof(int), st);
   cudaMemsetAsync(B.counters, 0, sizeof(unsigned long long), st);
@@ -1144,7 +1144,7 @@ int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float a
   cudaMemcpyAsync(&nc, B.count, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   int32_t* idx = merge_sort(nc, B.idxA, B.idxB, ContribLess{B.contrib}, st);
-  k_apply_step<<<(nc + 255) / 256, 256, 0, st>>>(nc, idx, B.contrib, f, dirty, B.counters); note_launch();
+  k_apply_step<<<(nc + 255) / 256, 256, 0, st>>>(nc, idx, B.contrib, f, upd, B.counters); note_launch();
   unsigned long long nupd = 0;
   cudaMemcpyAsync(&nupd, B.counters, sizeof(nupd), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);

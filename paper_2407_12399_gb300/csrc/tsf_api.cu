@@ -61,7 +61,11 @@ struct tsf_field {
   uint32_t *order = nullptr, *rank = nullptr, *sort_scratch = nullptr;
   Rec* rec = nullptr;
   D1Tab* tab = nullptr;
-  uint8_t *vnext8 = nullptr, *dirty = nullptr;
+  uint8_t* vnext8 = nullptr;
+  // fast persistence update (Section 4.2): vertices the last step updated,
+  // the lower stars to recompute (listed once each by generation marks)
+  uint32_t *upd = nullptr, *gmark = nullptr, *glist = nullptr;
+  uint32_t ggen = 0;
   uint32_t *cidx = nullptr, *c1base = nullptr, *c2base = nullptr;
   int4 *tile_counts = nullptr, *totals = nullptr;
   uint32_t* status = nullptr;
@@ -84,7 +88,7 @@ struct tsf_field {
   int np = 0, nprev = 0;
   Tg* T = nullptr;
   int nt = 0;
-  bool have_targets = false, diagram_current = false, records_valid = false, dirty_valid = false;
+  bool have_targets = false, diagram_current = false, records_valid = false, upd_valid = false;
   int iter = 0;
   double loss = 0, loss0 = 0;
   unsigned long long counts[4] = {0, 0, 0, 0};
@@ -392,14 +396,21 @@ int compute_diagram(tsf_field* F, bool incremental) {
   stage_end(F, kSort);
   uint32_t s = read_status(F);
   if (s & kErrNaN) return TSF_ENAN;
-  bool inc = incremental && F->records_valid && F->dirty_valid;
-  ck(cudaMemsetAsync(F->counter, 0, 8, st));
+  bool inc = incremental && F->records_valid && F->upd_valid;
+  unsigned long long ngrad = (unsigned long long)F->d.nv;
   stage_begin(F, kGrad);
-  launch_gradient(F->d, F->rank, F->f, inc ? F->dirty : nullptr, F->rec, F->vnext8, F->tab, F->status, F->counter,
-                  st);
+  if (inc) {
+    if (++F->ggen == 0) {  // the marks wrapped around: start over
+      ck(cudaMemsetAsync(F->gmark, 0, sizeof(uint32_t) * (size_t)F->d.nv, st));
+      F->ggen = 1;
+    }
+    launch_gradient_incremental(F->d, F->rank, F->f, F->upd, F->n_updated, F->gmark, F->ggen, F->glist, F->counter,
+                                F->rec, F->vnext8, F->tab, F->status, st);
+    ck(cudaMemcpyAsync(&ngrad, F->counter, 8, cudaMemcpyDeviceToHost, st));
+  } else {
+    launch_gradient(F->d, F->rank, F->f, F->rec, F->vnext8, F->tab, F->status, st);
+  }
   stage_end(F, kGrad);
-  unsigned long long ngrad = 0;
-  ck(cudaMemcpyAsync(&ngrad, F->counter, 8, cudaMemcpyDeviceToHost, st));
   F->records_valid = true;
   stage_begin(F, kCrit);
   launch_crit_count(F->d, F->order, F->rec, F->tile_counts, F->totals, st);
@@ -565,10 +576,9 @@ int step(tsf_field* F, const tsf_params* p, tsf_stats* stats) {
   double t0 = now_ms();
   bool fast = p->fast_gradient_update != 0;
   stage_begin(F, kStep);
-  if (fast) ck(cudaMemsetAsync(F->dirty, 0, (size_t)F->d.nv, st));
-  F->n_updated = gradient_step(F->np, F->pts, F->T, p->alpha_b, p->alpha_d, F->f, fast ? F->dirty : nullptr, F->B, st);
+  F->n_updated = gradient_step(F->np, F->pts, F->T, p->alpha_b, p->alpha_d, F->f, fast ? F->upd : nullptr, F->B, st);
   stage_end(F, kStep);
-  F->dirty_valid = fast;
+  F->upd_valid = fast;
   F->ms_step = now_ms() - t0;
   // previous diagram (with its assignment) becomes the still-pair reference
   std::swap(F->pts, F->prev);
@@ -631,7 +641,9 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->rec);
   dev_free(F->tab);
   dev_free(F->vnext8);
-  dev_free(F->dirty);
+  dev_free(F->upd);
+  dev_free(F->gmark);
+  dev_free(F->glist);
   dev_free(F->cidx);
   dev_free(F->c1base);
   dev_free(F->c2base);
@@ -746,7 +758,10 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
     ck(dev_alloc(&F->rec, nv));
     ck(dev_alloc(&F->tab, nv));
     ck(dev_alloc(&F->vnext8, nv));
-    ck(dev_alloc(&F->dirty, nv));
+    ck(dev_alloc(&F->upd, nv));
+    ck(dev_alloc(&F->gmark, nv));
+    ck(dev_alloc(&F->glist, nv));
+    ck(cudaMemsetAsync(F->gmark, 0, sizeof(uint32_t) * (size_t)nv, F->st));
     ck(dev_alloc(&F->cidx, nv));
     ck(dev_alloc(&F->c1base, nv));
     ck(dev_alloc(&F->c2base, nv));
@@ -925,7 +940,7 @@ int tsf_set_field(tsf_field* F, const float* values, int values_on_device) {
     ck(cudaStreamSynchronize(F->st));
     F->diagram_current = false;
     F->records_valid = false;
-    F->dirty_valid = false;
+    F->upd_valid = false;
     F->have_targets = false;
     return TSF_OK;
   });

@@ -46,8 +46,13 @@ void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, ui
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t st);
 
 // ---- k_gradient.cu -------------------------------------------------------
-void launch_gradient(const Dims& d, const uint32_t* rank, const float* f, const uint8_t* dirty, Rec* rec,
-                     uint8_t* vnext8, D1Tab* tab, uint32_t* status, unsigned long long* n_recomputed, cudaStream_t st);
+void launch_gradient(const Dims& d, const uint32_t* rank, const float* f, Rec* rec, uint8_t* vnext8, D1Tab* tab,
+                     uint32_t* status, cudaStream_t st);
+// Recomputes the lower stars of the nu updated vertices upd[] and of their
+// neighbours; *count receives how many (listed in list[], nv entries).
+void launch_gradient_incremental(const Dims& d, const uint32_t* rank, const float* f, const uint32_t* upd, int64_t nu,
+                                 uint32_t* mark, uint32_t gen, uint32_t* list, unsigned long long* count, Rec* rec,
+                                 uint8_t* vnext8, D1Tab* tab, uint32_t* status, cudaStream_t st);
 int crit_tiles(int64_t nv);
 void launch_crit_count(const Dims& d, const uint32_t* order, const Rec* rec, int4* tile_counts, int4* totals,
                        cudaStream_t st);

@@ -99,7 +99,9 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBu
            AssignStats* as, cudaStream_t st);
 void loss_and_counts(int np, const Pt* pts, int nt, const Tg* T, float cancel_eps, SolverBufs& B, double* h_loss,
                      unsigned long long* h_counts, cudaStream_t st);
-int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float alpha_d, float* f, uint8_t* dirty,
+// One gradient step (Eq. 3); returns the number of vertices whose value
+// changed and, with upd non-null, lists them there.
+int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float alpha_d, float* f, uint32_t* upd,
                       SolverBufs& B, cudaStream_t st);
 
 }  // namespace tsf
