@@ -189,6 +189,11 @@ const char* tsf_stage_name(int stage);
 /* Number of kernels this library has launched in this process. */
 int64_t tsf_kernel_launches(void);
 
+/* After a step that changed at most this many vertex values, the next
+ * diagram merges the changed vertices into the previous vertex order instead
+ * of sorting all values again (the result is the same order). */
+#define TSF_INCREMENTAL_ORDER_MAX 8192
+
 /* Zero-persistence pairs without device allocation.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc,
  * e.g. code running inside a framework that owns all device memory through

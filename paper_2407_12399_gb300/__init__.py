@@ -69,6 +69,7 @@ EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_
            "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
            "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static")
 TSF_NSTAGES = 12
+INCREMENTAL_ORDER_MAX = 8192  # TSF_INCREMENTAL_ORDER_MAX
 
 _lib = None
 

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kRT) k_os_pass(int64_t n, int shift, bool firs
     if (dg < 256) pos = s_off[dg] + whist[w][dg] + __popc(peers & lt);
     __syncwarp();
     if (dg < 256) {
-      if (!last) keys_out[pos] = key[c];
+      if (keys_out) keys_out[pos] = key[c];
       vals_out[pos] = val[c];
       if (lane == __ffs(peers) - 1) whist[w][dg] += __popc(peers);
     }
@@ -267,8 +267,8 @@ int64_t sort_scratch_words(int64_t n) {
 }
 
 // Vertex order: order[r] = id of the r-th vertex, rank[id] = r.
-void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, uint32_t* scratch, uint32_t* status,
-                  cudaStream_t st) {
+void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, uint32_t* skey, uint32_t* scratch,
+                  uint32_t* status, cudaStream_t st) {
   int ntiles = (int)((n + kRTile - 1) / kRTile);
   uint32_t* kA = scratch;
   uint32_t* vA = kA + n;
@@ -284,7 +284,7 @@ void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, ui
   const uint32_t* vin = nullptr;
   for (int pass = 0; pass < 4; ++pass) {
     bool first = pass == 0, last = pass == 3;
-    uint32_t* kout = (pass & 1) ? kB : kA;
+    uint32_t* kout = last ? skey : ((pass & 1) ? kB : kA);
     uint32_t* vout = last ? order : ((pass & 1) ? vB : vA);
     k_os_pass<<<ntiles, kRT, 0, st>>>(n, 8 * pass, first, last, f, kin, vin, kout, vout, hist + 256 * pass,
                                       lookback + (size_t)pass * 256 * ntiles, counters + pass, status); note_launch();

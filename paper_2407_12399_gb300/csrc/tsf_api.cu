@@ -59,6 +59,11 @@ struct tsf_field {
   // vertex-sized
   float* f = nullptr;
   uint32_t *order = nullptr, *rank = nullptr, *sort_scratch = nullptr;
+  // value keys in order (skey[i] = value_key of order[i]), the buffers the
+  // incremental order update writes, and its scratch
+  uint32_t *skey = nullptr, *order2 = nullptr, *skey2 = nullptr, *ubits = nullptr, *ucnt = nullptr;
+  unsigned long long* ordB = nullptr;
+  bool order_valid = false;  // order/skey/rank are those of the current values
   Rec* rec = nullptr;
   D1Tab* tab = nullptr;
   uint8_t* vnext8 = nullptr;
@@ -392,10 +397,23 @@ int compute_diagram(tsf_field* F, bool incremental) {
   double t0 = now_ms();
   ck(cudaMemsetAsync(F->status, 0, 4, st));
   stage_begin(F, kSort);
-  vertex_order(F->f, F->d.nv, F->order, F->rank, F->sort_scratch, F->status, st);
+  if (incremental && F->order_valid && F->upd_valid && F->n_updated <= kIncOrderMax) {
+    if (F->n_updated > 0) {
+      vertex_order_incremental(F->f, F->d.nv, F->upd, (int)F->n_updated, F->order, F->skey, F->order2, F->skey2,
+                               F->rank, F->ubits, F->ucnt, F->ordB, F->status, st);
+      std::swap(F->order, F->order2);
+      std::swap(F->skey, F->skey2);
+    }
+  } else {
+    vertex_order(F->f, F->d.nv, F->order, F->rank, F->skey, F->sort_scratch, F->status, st);
+  }
+  F->order_valid = true;
   stage_end(F, kSort);
   uint32_t s = read_status(F);
-  if (s & kErrNaN) return TSF_ENAN;
+  if (s & kErrNaN) {
+    F->order_valid = false;
+    return TSF_ENAN;
+  }
   bool inc = incremental && F->records_valid && F->upd_valid;
   unsigned long long ngrad = (unsigned long long)F->d.nv;
   stage_begin(F, kGrad);
@@ -641,6 +659,12 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->rec);
   dev_free(F->tab);
   dev_free(F->vnext8);
+  dev_free(F->skey);
+  dev_free(F->order2);
+  dev_free(F->skey2);
+  dev_free(F->ubits);
+  dev_free(F->ucnt);
+  dev_free(F->ordB);
   dev_free(F->upd);
   dev_free(F->gmark);
   dev_free(F->glist);
@@ -755,6 +779,12 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
     ck(dev_alloc(&F->order, nv));
     ck(dev_alloc(&F->rank, nv));
     ck(dev_alloc(&F->sort_scratch, sort_scratch_words(nv)));
+    ck(dev_alloc(&F->skey, nv));
+    ck(dev_alloc(&F->order2, nv));
+    ck(dev_alloc(&F->skey2, nv));
+    ck(dev_alloc(&F->ubits, (size_t)(nv / 32 + 1)));
+    ck(dev_alloc(&F->ucnt, (size_t)order_count_words(nv)));
+    ck(dev_alloc(&F->ordB, kIncOrderMax));
     ck(dev_alloc(&F->rec, nv));
     ck(dev_alloc(&F->tab, nv));
     ck(dev_alloc(&F->vnext8, nv));
@@ -941,6 +971,7 @@ int tsf_set_field(tsf_field* F, const float* values, int values_on_device) {
     F->diagram_current = false;
     F->records_valid = false;
     F->upd_valid = false;
+    F->order_valid = false;
     F->have_targets = false;
     return TSF_OK;
   });
@@ -988,8 +1019,9 @@ int tsf_zero_pairs(tsf_field* F, uint64_t* out, int64_t cap_pairs, int64_t* n_ou
   if (!F || !n_out || cap_pairs < 0) return TSF_EINVAL;
   return guarded([&]() {
     ck(cudaMemsetAsync(F->status, 0, 4, F->st));
-    vertex_order(F->f, F->d.nv, F->order, F->rank, F->sort_scratch, F->status, F->st);
+    vertex_order(F->f, F->d.nv, F->order, F->rank, F->skey, F->sort_scratch, F->status, F->st);
     uint32_t s = read_status(F);
+    F->order_valid = !(s & kErrNaN);
     if (s & kErrNaN) return TSF_ENAN;
     unsigned long long* dout = nullptr;
     int64_t cap = std::max<int64_t>(cap_pairs, 1);

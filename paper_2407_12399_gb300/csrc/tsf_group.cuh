@@ -1,0 +1,169 @@
+// tsf_group.cuh -- cooperative helpers of a thread group (one warp or one
+// block): barrier, exclusive scan, and a descending bitonic sort of keyed
+// entries held in registers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tsf {
+
+// A keyed entry: 64-bit sort key and a 32-bit payload (the parity mask of
+// a frontier entry of the saddle-saddle reduction).
+struct __align__(16) FEnt {
+  unsigned long long key;
+  uint32_t mask;
+  uint32_t pad;
+};
+
+// Group-wide (NT threads: one warp or one block) helpers.
+template <int NT>
+__device__ __forceinline__ void gsync() {
+  if (NT == 32) __syncwarp();
+  else __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive; sm: >= NT/32 + 1 ints
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (NT == 32) {
+    total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    return inc - v;
+  }
+  if (lane == 31) sm[w] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < NT / 32; ++k) {
+      int t = sm[k];
+      sm[k] = run;
+      run += t;
+    }
+    sm[NT / 32] = run;
+  }
+  __syncthreads();
+  int res = sm[w] + inc - v;
+  total = sm[NT / 32];
+  __syncthreads();
+  return res;
+}
+
+// Descending bitonic sort of a[0..n2) (n2 a power of two) by key, 64-bit
+// values (shared or global memory of the group; its barrier orders both).
+template <int NT>
+__device__ void group_sort_desc(unsigned long long* a, int n2) {
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += NT) {
+        int jx = i ^ stride;
+        if (jx > i) {
+          bool desc = (i & size) == 0;
+          unsigned long long x = a[i], y = a[jx];
+          if ((x < y) == desc) {
+            a[i] = y;
+            a[jx] = x;
+          }
+        }
+      }
+      gsync<NT>();
+    }
+}
+// Descending bitonic sort of a[0..n) (n <= NT * E) by key, E entries per
+// thread in registers (entry i = thread * E + e): strides below E swap
+// registers, strides below 32 E exchange with a lane by shuffles, longer
+// strides (blocks of several warps only) go through a[] in shared memory.
+// Equal keys may stay in either order.  All threads of the group call it.
+template <int NT, int E>
+__device__ void group_sort_reg(FEnt* a, int n) {
+  constexpr int N = NT * E;
+  const int tid = threadIdx.x, lane = tid & 31;
+  unsigned long long k[E];
+  uint32_t m[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    int i = tid * E + e;
+    k[e] = 0ull;
+    m[e] = 0u;
+    if (i < n) {
+      k[e] = a[i].key;
+      m[e] = a[i].mask;
+    }
+  }
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < E) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          int p = e ^ stride;
+          if (p > e) {
+            bool desc = ((tid * E + e) & size) == 0;
+            if ((k[e] < k[p]) == desc) {
+              unsigned long long tk = k[e];
+              k[e] = k[p];
+              k[p] = tk;
+              uint32_t tm = m[e];
+              m[e] = m[p];
+              m[p] = tm;
+            }
+          }
+        }
+      } else if (stride < 32 * E) {
+        const int lx = stride / E;
+        const bool lower = (lane & lx) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          unsigned long long ok = __shfl_xor_sync(0xFFFFFFFFu, k[e], lx);
+          uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, m[e], lx);
+          bool desc = ((tid * E + e) & size) == 0;
+          bool take = lower == desc ? ok > k[e] : ok < k[e];
+          if (take) {
+            k[e] = ok;
+            m[e] = om;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          a[tid * E + e].key = k[e];
+          a[tid * E + e].mask = m[e];
+        }
+        __syncthreads();
+        const bool lower = ((tid * E) & stride) == 0;
+        unsigned long long ok[E];
+        uint32_t om[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          int jx = (tid * E + e) ^ stride;
+          ok[e] = a[jx].key;
+          om[e] = a[jx].mask;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          bool desc = ((tid * E + e) & size) == 0;
+          bool take = lower == desc ? ok[e] > k[e] : ok[e] < k[e];
+          if (take) {
+            k[e] = ok[e];
+            m[e] = om[e];
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    a[tid * E + e].key = k[e];
+    a[tid * E + e].mask = m[e];
+  }
+  gsync<NT>();
+}
+
+}  // namespace tsf

@@ -41,8 +41,22 @@ struct PairOut {
 
 // ---- k_sort.cu -----------------------------------------------------------
 int64_t sort_scratch_words(int64_t n);
-void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, uint32_t* scratch, uint32_t* status,
-                  cudaStream_t st);
+// Full vertex order: order[] (vertex ids by (value, id)), rank[] its inverse
+// and, with skey non-null, skey[i] = value_key of order[i].
+void vertex_order(const float* f, int64_t n, uint32_t* order, uint32_t* rank, uint32_t* skey, uint32_t* scratch,
+                  uint32_t* status, cudaStream_t st);
+
+// ---- k_order.cu ----------------------------------------------------------
+// Largest number of updated vertices the incremental order update takes.
+constexpr int kIncOrderMax = 8192;
+// New order2/skey2/rank from the old order/skey/rank and the nu vertices upd[]
+// whose values changed.  Scratch: ubits (n/32 + 1 words), ucnt
+// (order_count_words(n) words), B (kIncOrderMax double words).
+void vertex_order_incremental(const float* f, int64_t n, const uint32_t* upd, int nu, const uint32_t* order,
+                              const uint32_t* skey, uint32_t* order2, uint32_t* skey2, uint32_t* rank,
+                              uint32_t* ubits, uint32_t* ucnt, unsigned long long* B, uint32_t* status,
+                              cudaStream_t st);
+int64_t order_count_words(int64_t n);
 void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* sums, cudaStream_t st);
 
 // ---- k_gradient.cu -------------------------------------------------------

@@ -62,7 +62,7 @@ extern "C" int tsf_zero_pairs_static(int lx, int ly, int lz, const float* values
   uint32_t* sort = rank + nv;
   // the array keeps the previous call's contents: clear what must start at zero
   if (cudaMemsetAsync(base, 0, 64 * sizeof(uint32_t), st) != cudaSuccess) return TSF_ECUDA;
-  tsf::vertex_order(values, nv, order, rank, sort, status, st);
+  tsf::vertex_order(values, nv, order, rank, nullptr, sort, status, st);
   tsf::Dims d;
   d.lx = lx;
   d.ly = ly;

@@ -90,3 +90,13 @@ def test_struct_layouts_match_the_header(name):
     got = _c_layout(name, fields)
     assert got[0] == ctypes.sizeof(S)
     assert got[1:] == [getattr(S, f).offset for f in fields]
+
+
+def test_binding_constants_match_the_header():
+    text = open(os.path.join(ROOT, "include", "tsf.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(TSF_\w+)\s+\(?(-?\d+)\)?", text)}
+    assert tsf.INCREMENTAL_ORDER_MAX == defs["TSF_INCREMENTAL_ORDER_MAX"]
+    assert tsf.TSF_NSTAGES == defs["TSF_NSTAGES"]
+    for name in ("TSF_OK", "TSF_EINVAL", "TSF_ENAN", "TSF_ENOMEM", "TSF_ECUDA", "TSF_ETIMEOUT", "TSF_ENOTARGET",
+                 "TSF_ECAPACITY", "TSF_EINTERNAL"):
+        assert getattr(tsf, name) == defs[name], name

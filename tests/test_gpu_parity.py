@@ -185,3 +185,29 @@ def test_simplify_reaches_the_loss_rule():
     ref.run(stop_s=0.01)
     assert st["iters"] == ref.stats()["iter"]
     assert np.array_equal(bits(g), bits(ref.field()))
+
+
+@pytest.mark.parametrize("shape,tau,many", [((40, 40, 40), 0.9, True), ((20, 22, 24), 0.05, False)],
+                         ids=["many-updates", "few-updates"])
+def test_incremental_order_matches_full_recompute(shape, tau, many):
+    """The vertex order after a step: merged incrementally when few values
+    changed, sorted again when many did; both must equal the full recompute
+    and the diagram must equal the oracle's.  (Uniform noise with a high
+    threshold: few signal targets, nearly every pair moves.)"""
+    import paper_2407_12399_gb300 as tsf
+    f0 = S.random_field(shape, seed=11, kind="uniform")
+    a, b = gpu_field(f0), gpu_field(f0)
+    a.set_threshold(tau)
+    b.set_threshold(tau)
+    upd = []
+    for _ in range(3):
+        sa = a.step(fast_gradient_update=1, stop_s=0.0)
+        sb = b.step(fast_gradient_update=0, stop_s=0.0)
+        upd.append(sa["n_updated_vertices"])
+        assert sa["n_updated_vertices"] == sb["n_updated_vertices"]
+        assert np.array_equal(bits(a.values()), bits(b.values()))
+        assert gpu_rows(a.diagram()) == gpu_rows(b.diagram())
+    limit = tsf.INCREMENTAL_ORDER_MAX
+    assert (max(upd) > limit) if many else (0 < max(upd) <= limit)
+    g = a.values()
+    assert gpu_rows(a.diagram()) == oracle_rows(g, oracle.diagram(g)["pairs"])
