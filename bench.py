@@ -248,8 +248,14 @@ def run_gpu(args):
     # algorithmic bytes per launch (per-unit figures in the design doc)
     n_grad = float(np.mean([s["n_gradient_vertices"] for s in stats]))
     visits = float(np.mean([s["d1_blocks_total"] for s in stats]))
-    bytes_grad = nv * 1.0 + n_grad * (4.0 + 32.0 + 1.0 + 144.0)  # dirty flags; rank, record, vnext, D1 table
-    bytes_sort = nv * 80.0                                        # 4 radix passes + rank scatter
+    n_upd = float(np.mean([s["n_updated_vertices"] for s in stats]))
+    # per recomputed lower star: 15 ranks + 14 values read; record, vnext,
+    # table row written
+    bytes_grad = n_grad * (60.0 + 56.0 + 32.0 + 1.0 + 144.0)
+    # incremental merge (order, skey read; order2, skey2, rank written), or
+    # the full radix sort (histogram, 4 passes, rank scatter)
+    incremental_order = n_upd <= tsf.INCREMENTAL_ORDER_MAX
+    bytes_sort = nv * (20.0 if incremental_order else 84.0)
     updates = float(np.mean([s["d1_star_updates"] for s in stats]))
     # per lower-star visit: its 144-byte table row (the pending masks live in
     # shared memory); updates of target stars touch no global memory
@@ -273,7 +279,8 @@ def run_gpu(args):
                      "target_updates_per_launch": updates},
         "streaming_kernels": {
             "vertex_order": {"achieved": g_sort, "unit": "GB/s", "frac": g_sort / hbm, "avg_ms": ms_sort,
-                             "algorithmic_bytes": bytes_sort},
+                             "algorithmic_bytes": bytes_sort,
+                             "path": "incremental merge" if incremental_order else "full radix sort"},
             "gradient": {"achieved": g_grad, "unit": "GB/s", "frac": g_grad / hbm, "avg_ms": ms_grad,
                          "algorithmic_bytes": bytes_grad}},
         "stage_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
