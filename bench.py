@@ -273,7 +273,7 @@ def run_gpu(args):
                    "fast_gradient_update": 1, "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"kernel": "k_d1_morse_group (saddle-saddle Morse boundaries; latency-bound)", "bound": "hbm",
-                     "achieved": g_d1, "peak": hbm, "unit": "GB/s", "frac": g_d1 / hbm, "traffic": None,
+                     "achieved": g_d1, "peak": hbm, "unit": "GB/s", "frac": g_d1 / hbm, "traffic": D1_TRAFFIC,
                      "peak_kind": peak_kind, "avg_launch_ms": ms_d1, "algorithmic_bytes_per_launch": bytes_d1,
                      "units_per_launch": visits, "bytes_per_unit": bytes_d1 / max(visits, 1.0),
                      "target_updates_per_launch": updates},
@@ -307,6 +307,13 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# DRAM bytes (read + written) of both k_d1_morse_group launches of one
+# diagram of this workload, from an ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum: 36.17 MB + 22.53 MB).
+# Set to None whenever the kernel changes until it is captured again.
+D1_TRAFFIC = 58.72e6
 
 
 def main():
