@@ -443,11 +443,12 @@ __global__ void k_d1_select(int n2, const int32_t* __restrict__ d2_max, uint32_t
   if (i < n2) flag[i] = d2_max[i] < 0 ? 1u : 0u;
 }
 __global__ void k_d1_gather(int n2, const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
-                            int32_t* __restrict__ cols, int32_t* __restrict__ d1_edge) {
+                            int32_t* __restrict__ cols, int32_t* __restrict__ d1_edge, int32_t* __restrict__ ncols) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n2) {
     d1_edge[i] = -1;
     if (flag[i]) cols[pos[i]] = i;
+    if (i == n2 - 1) *ncols = (int32_t)(pos[i] + flag[i]);
   }
 }
 
@@ -497,7 +498,8 @@ constexpr int kD1StepLimit = 1 << 24;
 // edges) with every gradient-paired edge eliminated by its triangle's reduced
 // column, largest first, one lower star at a time.  Output: the critical
 // edges left (C1 indices), in decreasing lexicographic order.
-__global__ void k_d1_morse(D1Ctx c, D1Work W, int ncols, uint32_t* status) {
+__global__ void k_d1_morse(D1Ctx c, D1Work W, uint32_t* status) {
+  const int ncols = W.flags[1];
   __shared__ Geo sg;
   geo_to_shared(sg);
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -744,8 +746,8 @@ __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* sta
 // the warp's buffers, saves its entries and is listed for phase B (NT = 128,
 // one block per listed column).
 template <int NT, int FCAP, int SCAP>
-__global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int ncols, int max_rounds,
-                                                       uint32_t* status) {
+__global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int max_rounds, uint32_t* status) {
+  const int ncols = W.flags[1];
   extern __shared__ __align__(16) unsigned char smem[];
   FEnt* front = reinterpret_cast<FEnt*>(smem);
   FEnt* other = front + FCAP;
@@ -1025,7 +1027,8 @@ static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + sca
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
 // each low; every addition is of an earlier column.
-__global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int ncols, int n1, int32_t* d1_edge, uint32_t* status) {
+__global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d1_edge, uint32_t* status) {
+  const int ncols = W.flags[1];
   __shared__ int changed;
   for (int k = threadIdx.x; k < n1; k += kUFT) W.owner[k] = 0x7FFFFFFF;
   __syncthreads();
@@ -1078,28 +1081,25 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int ncols, int n1,
     d1_edge[W.cols[j]] = W.hsize[j] > 0 ? (int)W.pool[W.hoff[j]] : -1;
 }
 
-int launch_d1_prepare(int n2, D1Work& W, PairOut& P, int32_t* h_flags, cudaStream_t st) {
-  if (n2 == 0) return 0;
-  // candidate columns, in increasing triangle order
+// Candidate columns in increasing triangle order; their number stays on the
+// device (W.flags[1]), the later D1 launches are sized by n2.
+void launch_d1_prepare(int n2, D1Work& W, PairOut& P, cudaStream_t st) {
+  if (n2 == 0) {
+    cudaMemsetAsync(W.flags + 1, 0, sizeof(int32_t), st);
+    return;
+  }
   uint32_t* flag = reinterpret_cast<uint32_t*>(W.lowc);  // scratch (n2 entries available)
   uint32_t* pos = reinterpret_cast<uint32_t*>(W.hsize);
   uint32_t* sums = reinterpret_cast<uint32_t*>(W.hcap);
   k_d1_select<<<(n2 + 255) / 256, 256, 0, st>>>(n2, P.d2_max, flag); note_launch();
   exclusive_scan_u32(flag, pos, n2, sums, st);
-  k_d1_gather<<<(n2 + 255) / 256, 256, 0, st>>>(n2, flag, pos, W.cols, P.d1_edge); note_launch();
-  uint32_t tail[2];
-  cudaMemcpyAsync(&tail[0], pos + n2 - 1, 4, cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&tail[1], flag + n2 - 1, 4, cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  int ncols = (int)(tail[0] + tail[1]);
-  h_flags[1] = ncols;
-  return ncols;
+  k_d1_gather<<<(n2 + 255) / 256, 256, 0, st>>>(n2, flag, pos, W.cols, P.d1_edge, W.flags + 1); note_launch();
 }
 
-void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int ncols, const uint32_t* rank,
+void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
                      const uint32_t* order, const float* f, const Rec* rec, const D1Tab* tab, const uint32_t* c1base,
                      D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st) {
-  if (ncols == 0) return;
+  if (n2 == 0) return;
   D1Ctx c;
   c.d = d;
   c.nd = nd;
@@ -1125,14 +1125,14 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
                          (int)sb);
     attr[dev] = true;
   }
-  k_d1_morse_group<32, kFrontA, kStageA><<<ncols, 32, sa, st>>>(c, W, ncols, 48, status); note_launch();
-  k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<ncols, kThreadsB, sb, st>>>(c, W, ncols, 0, status); note_launch();
-  k_d1_morse<<<(ncols + 63) / 64, 64, 0, st>>>(c, W, ncols, status); note_launch();
+  k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, sa, st>>>(c, W, 48, status); note_launch();
+  k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<n2, kThreadsB, sb, st>>>(c, W, 0, status); note_launch();
+  k_d1_morse<<<(n2 + 63) / 64, 64, 0, st>>>(c, W, status); note_launch();
 }
 
-void launch_d1_reduce(int n1, int ncols, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st) {
-  if (ncols == 0) return;
-  k_d1_reduce<<<1, kUFT, 0, st>>>(W, ncols, n1, P.d1_edge, status); note_launch();
+void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st) {
+  if (n2 == 0) return;
+  k_d1_reduce<<<1, kUFT, 0, st>>>(W, n1, P.d1_edge, status); note_launch();
 }
 
 }  // namespace tsf

@@ -8,12 +8,14 @@
 namespace tsf {
 
 // ---------------------------------------------------------------------------
-// Stable merge sort of an index array by a comparator (bottom-up; each pass
+// Merge sort of an index array by a comparator (bottom-up, stable; each pass
 // places every element by a binary search in its partner run).
 // ---------------------------------------------------------------------------
 template <class Less>
-__global__ void k_merge_pass(int n, int width, const int32_t* __restrict__ in, int32_t* __restrict__ out, Less less) {
+__global__ void k_merge_pass(int n, const int* __restrict__ n_dev, int width, const int32_t* __restrict__ in,
+                             int32_t* __restrict__ out, Less less) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n_dev) n = min(*n_dev, n);
   if (i >= n) return;
   int run = i / width;
   int pair_start = (run & ~1) * width;
@@ -35,17 +37,60 @@ __global__ void k_merge_pass(int n, int width, const int32_t* __restrict__ in, i
   out[pair_start + p + lo] = x;
 }
 
-__global__ void k_iota(int n, int32_t* a) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] = i;
+// The first log2(kTile) merge levels run as one launch: every block sorts a
+// tile of kTile indices with a bitonic network in shared memory over
+// (primary key, index).  Each comparator supplies key(i), a 64-bit
+// coarsening of its order (key(a) < key(b) implies a before b); equal keys
+// fall back to the comparator.  The comparators here are total orders, or
+// order equal values only, so the tiles need no stability; the merge passes
+// above them are stable.  With n_dev non-null the count is read on the
+// device and n is only its upper bound.
+constexpr int kTileT = 1024, kTile = 2 * kTileT;
+
+template <class Less>
+__global__ void __launch_bounds__(kTileT) k_tile_sort(int n, const int* __restrict__ n_dev, int32_t* __restrict__ out,
+                                                      Less less) {
+  __shared__ unsigned long long K[kTile];
+  __shared__ int32_t I[kTile];
+  if (n_dev) n = min(*n_dev, n);
+  const int base = blockIdx.x * kTile;
+  const int m = min(kTile, n - base);
+  if (m <= 0) return;
+  int n2 = 1;
+  while (n2 < m) n2 <<= 1;
+  for (int i = threadIdx.x; i < n2; i += kTileT) {
+    K[i] = i < m ? less.key(base + i) : ~0ull;
+    I[i] = i < m ? base + i : -1;  // -1 sorts after everything
+  }
+  __syncthreads();
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += kTileT) {
+        int j = i ^ stride;
+        if (j > i) {
+          bool up = (i & size) == 0;
+          unsigned long long kx = K[i], ky = K[j];
+          int x = I[i], y = I[j];
+          bool x_after_y = kx != ky ? kx > ky : (x < 0 ? y >= 0 : (y >= 0 && less(y, x)));
+          if (x_after_y == up) {
+            K[i] = ky;
+            K[j] = kx;
+            I[i] = y;
+            I[j] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < m; i += kTileT) out[base + i] = I[i];
 }
 
 template <class Less>
-static int32_t* merge_sort(int n, int32_t* a, int32_t* b, Less less, cudaStream_t st) {
+static int32_t* merge_sort(int n, int32_t* a, int32_t* b, Less less, cudaStream_t st, const int* n_dev = nullptr) {
   if (n <= 0) return a;
-  k_iota<<<(n + 255) / 256, 256, 0, st>>>(n, a); note_launch();
-  for (int w = 1; w < n; w *= 2) {
-    k_merge_pass<<<(n + 255) / 256, 256, 0, st>>>(n, w, a, b, less); note_launch();
+  k_tile_sort<<<(n + kTile - 1) / kTile, kTileT, 0, st>>>(n, n_dev, a, less); note_launch();
+  for (int w = kTile; w < n; w *= 2) {
+    k_merge_pass<<<(n + 255) / 256, 256, 0, st>>>(n, n_dev, w, a, b, less); note_launch();
     int32_t* t = a;
     a = b;
     b = t;
@@ -160,6 +205,9 @@ __global__ void k_build_points(Dims d, NbrDelta nd, CritLists L, int n1, int n2,
 
 struct DiagLess {
   const Pt* p;
+  __device__ unsigned long long key(int i) const {
+    return ((unsigned long long)value_key(p[i].b) << 32) | value_key(p[i].d);
+  }
   __device__ bool operator()(int a, int b) const {
     const Pt& x = p[a];
     const Pt& y = p[b];
@@ -175,6 +223,11 @@ struct DiagLess {
 
 struct KeyLess {  // (essential, dim, v_b, v_d, birth cell)
   const Pt* p;
+  __device__ unsigned long long key(int i) const {  // (essential, dim, v_b, v_d >> 3)
+    const Pt& x = p[i];
+    return ((unsigned long long)(x.ess != 0) << 63) | ((unsigned long long)(x.dim & 3) << 61) |
+           ((unsigned long long)x.vb << 29) | (unsigned long long)(x.vd >> 3);
+  }
   __device__ bool operator()(int a, int b) const {
     const Pt& x = p[a];
     const Pt& y = p[b];
@@ -390,6 +443,11 @@ __global__ void k_cand_fill(int npg, const int32_t* __restrict__ plist, const Pt
 
 struct CandLess {
   const Cand* c;
+  __device__ unsigned long long key(int i) const {  // (target, high half of the monotone image of w)
+    unsigned long long u = (unsigned long long)__double_as_longlong(c[i].w);
+    u = (u >> 63) ? ~u : (u | (1ull << 63));
+    return ((unsigned long long)(uint32_t)c[i].t << 32) | (u >> 32);
+  }
   __device__ bool operator()(int a, int b) const {
     const Cand& x = c[a];
     const Cand& y = c[b];
@@ -969,7 +1027,9 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBu
   k_asg_solve<<<3, kHT, 0, st>>>(B.A, pts, T, status); note_launch();
   int32_t hc[10];
   cudaMemcpyAsync(hc, B.A.counts, sizeof(hc), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&as->status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
+  as->status_valid = !hc[8];
   for (int g = 0; g < 4; ++g) as->k[g] = hc[4 + g];
   if (!hc[8]) return 0;
   return assign_groups(np, pts, nt, T, B, status, as, st);
@@ -1108,6 +1168,7 @@ __global__ void k_contrib(int np, const Pt* __restrict__ pts, const Tg* __restri
 
 struct ContribLess {
   const Contrib* c;
+  __device__ unsigned long long key(int i) const { return ((unsigned long long)c[i].v << 32) | c[i].key; }
   __device__ bool operator()(int a, int b) const {
     const Contrib& x = c[a];
     const Contrib& y = c[b];
@@ -1117,9 +1178,11 @@ struct ContribLess {
 };
 
 // one thread per vertex segment: acc = +0, acc += c in increasing value order
-__global__ void k_apply_step(int nc, const int32_t* __restrict__ idx, const Contrib* __restrict__ C,
-                             float* __restrict__ f, uint32_t* __restrict__ upd, unsigned long long* __restrict__ nupd) {
+__global__ void k_apply_step(int nc, const int* __restrict__ nc_dev, const int32_t* __restrict__ idx,
+                             const Contrib* __restrict__ C, float* __restrict__ f, uint32_t* __restrict__ upd,
+                             unsigned long long* __restrict__ nupd) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (nc_dev) nc = min(*nc_dev, nc);
   if (r >= nc) return;
   uint32_t v = C[idx[r]].v;
   if (r > 0 && C[idx[r - 1]].v == v) return;
@@ -1140,11 +1203,10 @@ int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float a
   cudaMemsetAsync(B.counters, 0, sizeof(unsigned long long), st);
   if (np == 0) return 0;
   k_contrib<<<(np + 255) / 256, 256, 0, st>>>(np, pts, T, alpha_b, alpha_d, B.contrib, B.count); note_launch();
-  int nc = 0;
-  cudaMemcpyAsync(&nc, B.count, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  int32_t* idx = merge_sort(nc, B.idxA, B.idxB, ContribLess{B.contrib}, st);
-  k_apply_step<<<(nc + 255) / 256, 256, 0, st>>>(nc, idx, B.contrib, f, upd, B.counters); note_launch();
+  // at most two contributions per point: sized by 2 np, counted on the device
+  int32_t* idx = merge_sort(2 * np, B.idxA, B.idxB, ContribLess{B.contrib}, st, B.count);
+  k_apply_step<<<(2 * np + 255) / 256, 256, 0, st>>>(2 * np, B.count, idx, B.contrib, f, upd, B.counters);
+  note_launch();
   unsigned long long nupd = 0;
   cudaMemcpyAsync(&nupd, B.counters, sizeof(nupd), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);

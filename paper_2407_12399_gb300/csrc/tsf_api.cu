@@ -409,11 +409,9 @@ int compute_diagram(tsf_field* F, bool incremental) {
   }
   F->order_valid = true;
   stage_end(F, kSort);
-  uint32_t s = read_status(F);
-  if (s & kErrNaN) {
-    F->order_valid = false;
-    return TSF_ENAN;
-  }
+  // The status word is read where the host waits anyway (the critical-cell
+  // counts, the end of D1); every kernel in between stays in bounds on any
+  // permutation, so a NaN found late only invalidates the results.
   bool inc = incremental && F->records_valid && F->upd_valid;
   unsigned long long ngrad = (unsigned long long)F->d.nv;
   stage_begin(F, kGrad);
@@ -433,8 +431,16 @@ int compute_diagram(tsf_field* F, bool incremental) {
   stage_begin(F, kCrit);
   launch_crit_count(F->d, F->order, F->rec, F->tile_counts, F->totals, st);
   int4 tot;
+  uint32_t s = 0;
   ck(cudaMemcpyAsync(&tot, F->totals, sizeof(int4), cudaMemcpyDeviceToHost, st));
+  ck(cudaMemcpyAsync(&s, F->status, sizeof(s), cudaMemcpyDeviceToHost, st));
   ck(cudaStreamSynchronize(st));
+  if (s & kErrNaN) {
+    F->order_valid = false;
+    F->records_valid = false;
+    return TSF_ENAN;
+  }
+  if (status_code(s) != TSF_OK) return status_code(s);
   F->n_gradient = (int64_t)ngrad;
   F->n0 = tot.x;
   F->n1 = tot.y;
@@ -450,9 +456,8 @@ int compute_diagram(tsf_field* F, bool incremental) {
   stage_begin(F, kD2);
   launch_d2(F->d, F->nd, F->L, F->n2, F->n3, F->rank, F->rec, F->cidx, F->PS, F->PO, F->status, st);
   stage_end(F, kD2);
-  s = read_status(F);
-  if (status_code(s) != TSF_OK) return status_code(s);
-  // D1, growing the column pool until it suffices
+  // D1, growing the column pool until it suffices (D0 and D2 report through
+  // the same status word, read after the first attempt)
   for (int attempt = 0;; ++attempt) {
     uint32_t want = (uint32_t)std::min<int64_t>(std::max<int64_t>((int64_t)64 * std::max(F->n2, 1), 1 << 20) << attempt,
                                                  (int64_t)1 << 31);
@@ -465,27 +470,27 @@ int compute_diagram(tsf_field* F, bool incremental) {
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
     if (!F->W.stats) ck(dev_alloc(&F->W.stats, 9));
-    ck(cudaMemsetAsync(F->status, 0, 4, st));
+    if (attempt > 0) ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
-    int ncols = launch_d1_prepare(F->n2, F->W, F->PO, F->h_flags, st);
+    launch_d1_prepare(F->n2, F->W, F->PO, st);
     stage_end(F, kD1);
-    if (F->n2 == 0) F->h_flags[1] = 0;
     stage_begin(F, kD1Morse);
-    launch_d1_morse(F->d, F->nd, F->L, F->n1, ncols, F->rank, F->order, F->f, F->rec, F->tab, F->c1base, F->W,
+    launch_d1_morse(F->d, F->nd, F->L, F->n1, F->n2, F->rank, F->order, F->f, F->rec, F->tab, F->c1base, F->W,
                     F->PO, F->status, st);
     stage_end(F, kD1Morse);
     stage_begin(F, kD1Reduce);
-    launch_d1_reduce(F->n1, ncols, F->W, F->PO, F->status, st);
+    launch_d1_reduce(F->n1, F->n2, F->W, F->PO, F->status, st);
     stage_end(F, kD1Reduce);
-    s = read_status(F);
-    F->d1_cols = F->n2 > 0 ? F->h_flags[1] : 0;
-    if (F->d1_cols > 0) {
+    int32_t ncols = 0;
+    for (auto& x : F->d1_stats) x = 0;
+    ck(cudaMemcpyAsync(&s, F->status, sizeof(s), cudaMemcpyDeviceToHost, st));
+    if (F->n2 > 0) {
+      ck(cudaMemcpyAsync(&ncols, F->W.flags + 1, sizeof(ncols), cudaMemcpyDeviceToHost, st));
       ck(cudaMemcpyAsync(F->d1_stats, F->W.stats, sizeof(F->d1_stats), cudaMemcpyDeviceToHost, st));
-      ck(cudaStreamSynchronize(st));
-    } else {
-      for (auto& x : F->d1_stats) x = 0;
     }
-    if ((s & kErrPool) && attempt < 6) continue;
+    ck(cudaStreamSynchronize(st));
+    F->d1_cols = ncols;
+    if ((s & kErrPool) && !(s & ~kErrPool) && attempt < 6) continue;
     break;
   }
   if (status_code(s) != TSF_OK) return status_code(s);
@@ -505,8 +510,9 @@ int compute_diagram(tsf_field* F, bool incremental) {
 
 int run_assign(tsf_field* F, const Pt* ref, int nr) {
   double t0 = now_ms();
-  AssignStats as;
+  AssignStats as{};
   for (int attempt = 0; attempt < 8; ++attempt) {
+    as.status_valid = false;
     ck(cudaMemsetAsync(F->status, 0, 4, F->st));
     stage_begin(F, kAssign);
     int r = assign(F->np, F->pts, nr, ref, F->nt, F->T, F->B, F->status, &as, F->st);
@@ -517,7 +523,7 @@ int run_assign(tsf_field* F, const Pt* ref, int nr) {
     else return TSF_EINTERNAL;
     // the failed pass may have written partial assignments: restart from the still step
   }
-  uint32_t s = read_status(F);
+  uint32_t s = as.status_valid ? as.status : read_status(F);
   if (status_code(s) != TSF_OK) return status_code(s);
   F->ms_assign = now_ms() - t0;
   return TSF_OK;

@@ -111,11 +111,12 @@ struct D1Work {
   int32_t* big;           // list of open columns
   int32_t* nbig;
 };
-// D1: candidate columns (returns their number), Morse boundaries, reduction.
-int launch_d1_prepare(int n2, D1Work& W, PairOut& P, int32_t* h_flags, cudaStream_t st);
-void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int ncols, const uint32_t* rank,
+// D1: candidate columns (their number in W.flags[1]), Morse boundaries,
+// reduction; grids are sized by n2, the kernels read the column count.
+void launch_d1_prepare(int n2, D1Work& W, PairOut& P, cudaStream_t st);
+void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
                      const uint32_t* order, const float* f, const Rec* rec, const D1Tab* tab, const uint32_t* c1base,
                      D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st);
-void launch_d1_reduce(int n1, int ncols, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st);
+void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st);
 
 }  // namespace tsf

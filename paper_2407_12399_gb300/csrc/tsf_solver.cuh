@@ -89,6 +89,8 @@ struct SolverBufs {
 
 struct AssignStats {
   int k[4];
+  uint32_t status;    // the status word, read with the group counts (fast path)
+  bool status_valid;
 };
 
 int build_diagram(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, int n3, const PairOut& P,
