@@ -311,9 +311,9 @@ def run_gpu(args):
 
 # DRAM bytes (read + written) of both k_d1_morse_group launches of one
 # diagram of this workload, from an ncu capture of the current kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum: 36.17 MB + 22.53 MB).
-# Set to None whenever the kernel changes until it is captured again.
-D1_TRAFFIC = 58.72e6
+# (dram__bytes_read.sum + dram__bytes_write.sum), or None while the kernel
+# has changed since the last capture.
+D1_TRAFFIC = None
 
 
 def main():

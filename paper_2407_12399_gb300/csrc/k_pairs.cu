@@ -634,10 +634,15 @@ __device__ __forceinline__ void closures(const D1Tab& t, uint32_t m, uint64_t& p
 // One lower-star visit: apply the closures of the star's pending edges
 // (linear over Z/2), keep the positive critical edges left as (v << 4 | x),
 // and append the link edges left to the stage as updates of the target
-// stars.  One dependent global load: the star's table row.
+// stars.  One dependent global load: the star's table row.  With `chain`
+// set, a visit whose link edges all go to one target star hands that update
+// back in *next instead of staging it, and the caller visits it at once (a
+// star reached again later by another part of its mask is simply visited
+// again: the projection is linear).
 template <int SCAP>
-__device__ __forceinline__ void d1_visit(const D1Ctx& c, FEnt fe, const int32_t* snd, FEnt* stage, int* s_ntot,
-                                         int* s_flag, unsigned long long* myouts, int& myout, int& updates) {
+__device__ __forceinline__ bool d1_visit(const D1Ctx& c, FEnt fe, const int32_t* snd, FEnt* stage, int* s_ntot,
+                                         int* s_flag, unsigned long long* myouts, int& myout, int& updates, bool chain,
+                                         FEnt* next) {
   uint32_t v = (uint32_t)fe.key;
   uint32_t m = fe.mask;
   D1Tab t;
@@ -659,16 +664,27 @@ __device__ __forceinline__ void d1_visit(const D1Ctx& c, FEnt fe, const int32_t*
 #pragma unroll
   for (int k = 0; k < 14; ++k) tmask[k] = 0;
   link_targets(path & t.q[9], path & ~t.q[9], tmask, std::make_integer_sequence<int, 36>{});
-  int cnt = 0;
+  int cnt = 0, only = 0;
 #pragma unroll
-  for (int hn = 0; hn < 14; ++hn) cnt += tmask[hn] != 0u;
-  if (!cnt) return;
+  for (int hn = 0; hn < 14; ++hn)
+    if (tmask[hn]) {
+      ++cnt;
+      only = hn;
+    }
+  if (!cnt) return false;
+  updates += cnt;
+  if (chain && cnt == 1) {
+    uint32_t hv = (uint32_t)((int32_t)v + snd[only]);
+    next->key = star_key(t.nkey[only], hv);
+    next->mask = tmask[only];
+    next->pad = 0;
+    return true;
+  }
   int off = atomicAdd(s_ntot, cnt);
   if (off + cnt > SCAP) {
     atomicOr(s_flag, 1);
-    return;
+    return false;
   }
-  updates += cnt;
 #pragma unroll
   for (int hn = 0; hn < 14; ++hn) {
     if (tmask[hn]) {
@@ -684,6 +700,7 @@ __device__ __forceinline__ void d1_visit(const D1Ctx& c, FEnt fe, const int32_t*
       asm volatile("prefetch.global.L2 [%0];" ::"l"(row + 128));
     }
   }
+  return false;
 }
 
 // Sorts a stage of n <= SCAP entries (a[] holds SCAP entries).
@@ -741,12 +758,20 @@ __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* sta
   return kept;
 }
 
+// Visits one thread makes per round along a chain of single-target updates;
+// room for the critical edges those visits keep.  Rounds of phase A before a
+// column moves to a block.  (Measured on the 128^3 filament field: chains of
+// 2 and 16 warp rounds gave the shortest D1 time; longer chains lengthen
+// every round more than they shorten the longest column.)
+constexpr int kChain = 2, kOutCap = 28, kRoundsA = 16;
+
 // Round loop of one column.  Phase A (NT = 32, max_rounds > 0): every column,
 // one warp; a column still open after max_rounds, or whose frontier outgrows
 // the warp's buffers, saves its entries and is listed for phase B (NT = 128,
 // one block per listed column).
 template <int NT, int FCAP, int SCAP>
-__global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int max_rounds, uint32_t* status) {
+__global__ void __launch_bounds__(NT, NT == 32 ? 12 : 4) k_d1_morse_group(D1Ctx c, D1Work W, int max_rounds,
+                                                                    uint32_t* status) {
   const int ncols = W.flags[1];
   extern __shared__ __align__(16) unsigned char smem[];
   FEnt* front = reinterpret_cast<FEnt*>(smem);
@@ -832,10 +857,16 @@ __global__ void __launch_bounds__(NT) k_d1_morse_group(D1Ctx c, D1Work W, int ma
     ++rounds;
     int nb = min(NT, nf);
     int myout = 0;
-    unsigned long long myouts[14];
+    unsigned long long myouts[kOutCap];
     if (tid < nb) {
-      ++visits;
-      d1_visit<SCAP>(c, front[tid], snd, stage, &s_ntot, &s_flag, myouts, myout, updates);
+      FEnt cur = front[tid];
+      for (int k = 0;; ++k) {
+        ++visits;
+        FEnt nxt;
+        bool more = k + 1 < kChain && myout + 14 <= kOutCap;
+        if (!d1_visit<SCAP>(c, cur, snd, stage, &s_ntot, &s_flag, myouts, myout, updates, more, &nxt)) break;
+        cur = nxt;
+      }
     }
     int ooff = myout ? atomicAdd(&s_otot, myout) : 0;
     gsync<NT>();
@@ -1125,7 +1156,7 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
                          (int)sb);
     attr[dev] = true;
   }
-  k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, sa, st>>>(c, W, 48, status); note_launch();
+  k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, sa, st>>>(c, W, kRoundsA, status); note_launch();
   k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<n2, kThreadsB, sb, st>>>(c, W, 0, status); note_launch();
   k_d1_morse<<<(n2 + 63) / 64, 64, 0, st>>>(c, W, status); note_launch();
 }
