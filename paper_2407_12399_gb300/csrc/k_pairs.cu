@@ -23,15 +23,17 @@
 
 namespace tsf {
 
-constexpr int kTraceLimit = 1 << 26;
 constexpr int kUFT = 1024;
 
 // ---------------------------------------------------------------------------
 // integral lines
 // ---------------------------------------------------------------------------
+// A descending line visits each vertex at most once (ranks decrease), so it
+// has at most nv steps; an ascending dual line crosses into a higher vertex's
+// star at most nv times and takes at most 24 steps inside one star.
 __device__ __forceinline__ int32_t trace_down(uint32_t w, const uint8_t* __restrict__ vnext8,
-                                              const uint32_t* __restrict__ cidx, const NbrDelta& nd) {
-  for (int s = 0; s < kTraceLimit; ++s) {
+                                              const uint32_t* __restrict__ cidx, const NbrDelta& nd, int64_t nv) {
+  for (int64_t s = 0; s <= nv; ++s) {
     int k = vnext8[w];
     if (k == kVnextMin) return (int32_t)cidx[w];
     w = (uint32_t)((int32_t)w + nd.d[k]);
@@ -39,18 +41,18 @@ __device__ __forceinline__ int32_t trace_down(uint32_t w, const uint8_t* __restr
   return -1;
 }
 
-__global__ void k_d0_trace(int n1, CritLists L, const uint8_t* __restrict__ vnext8, const uint32_t* __restrict__ cidx,
-                           NbrDelta nd, int32_t* __restrict__ ends, uint32_t* status) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n1) return;
-  uint32_t vn = L.c1_vn[i];
+// One thread per endpoint of each critical edge.
+__global__ void k_d0_trace(int n1, int64_t nv, CritLists L, const uint8_t* __restrict__ vnext8,
+                           const uint32_t* __restrict__ cidx, NbrDelta nd, int32_t* __restrict__ ends,
+                           uint32_t* status) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * (int64_t)n1) return;
+  uint32_t vn = L.c1_vn[t >> 1];
   uint32_t v = vn >> 4;
-  int k = (int)(vn & 15u);
-  uint32_t u = (uint32_t)((int32_t)v + nd.d[k]);
-  int32_t a = trace_down(v, vnext8, cidx, nd), b = trace_down(u, vnext8, cidx, nd);
-  if (a < 0 || b < 0) atomicOr(status, kErrTrace);
-  ends[2 * i] = a < 0 ? 0 : a;
-  ends[2 * i + 1] = b < 0 ? 0 : b;
+  if (t & 1) v = (uint32_t)((int32_t)v + nd.d[vn & 15u]);
+  int32_t a = trace_down(v, vnext8, cidx, nd, nv);
+  if (a < 0) atomicOr(status, kErrTrace);
+  ends[t] = a < 0 ? 0 : a;
 }
 
 __device__ __forceinline__ Rec ld_rec(const Rec* rec, uint32_t v) {
@@ -65,9 +67,9 @@ __device__ __forceinline__ Rec ld_rec(const Rec* rec, uint32_t v) {
 // Ascending integral line in the dual: from tetrahedron (w, tau) follow the
 // record codes to a maximum (its index) or to the outside (returns n3).
 __device__ int32_t trace_up(uint32_t w, int tau, const Rec* __restrict__ rec, const uint32_t* __restrict__ cidx,
-                            const int32_t* nd, int n3, const Geo& G) {
+                            const int32_t* nd, int n3, const UpStep* up, int64_t nv) {
   Rec r = ld_rec(rec, w);
-  for (int s = 0; s < kTraceLimit; ++s) {
+  for (int64_t s = 0; s <= 25 * nv; ++s) {
     int code = rec_tet_code(r, tau);
     if (code == kCodeMax) return (int32_t)cidx[w];
     if (code == kCodeOut) return n3;
@@ -76,75 +78,68 @@ __device__ int32_t trace_up(uint32_t w, int tau, const Rec* __restrict__ rec, co
       continue;
     }
     if (code >= 96) return -1;
-    int t2 = (code - 24) / 3, j = (code - 24) % 3;
-    int c = G.tri[t2][j];
-    int p = G.tri[t2][(j + 1) % 3], q = G.tri[t2][(j + 2) % 3];
-    int i0 = nbr_index(G, -G.off[c][0], -G.off[c][1], -G.off[c][2]);
-    int i1 = nbr_index(G, G.off[p][0] - G.off[c][0], G.off[p][1] - G.off[c][1],
-                       G.off[p][2] - G.off[c][2]);
-    int i2 = nbr_index(G, G.off[q][0] - G.off[c][0], G.off[q][1] - G.off[c][1],
-                       G.off[q][2] - G.off[c][2]);
-    if (i0 < 0 || i1 < 0 || i2 < 0) return -1;
-    tau = G.tri_of3[i0][i1][i2];
-    if (tau < 0) return -1;
-    w = (uint32_t)((int32_t)w + nd[c]);
+    UpStep u = up[code - 24];
+    tau = u.tau;
+    w = (uint32_t)((int32_t)w + nd[u.c]);
     r = ld_rec(rec, w);
   }
   return -1;
 }
 
+// One thread per (critical triangle, side): the ascending dual line from the
+// tetrahedron on that side to a maximum or the outside.
 __global__ void k_d2_trace(Dims d, int n2, int n3, CritLists L, const uint32_t* __restrict__ rank,
                            const Rec* __restrict__ rec, const uint32_t* __restrict__ cidx, NbrDelta nd,
                            int32_t* __restrict__ ends, uint32_t* status) {
-  __shared__ Geo sg;
+  __shared__ UpStep sup[72];
   __shared__ int32_t snd[14];
   if (threadIdx.x < 14) snd[threadIdx.x] = nd.d[threadIdx.x];
-  geo_to_shared(sg);
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n2) return;
+  if (threadIdx.x < 72) sup[threadIdx.x] = c_up.s[threadIdx.x];
+  __syncthreads();
+  int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= 2 * (int64_t)n2) return;
+  int i = (int)(tt >> 1), k = (int)(tt & 1);
+  const Geo& G = c_geo;
   uint32_t ve = L.c2_ve[i];
   uint32_t v = ve >> 6;
   int e = (int)(ve & 63u);
-  int a = sg.edge[e][0], b = sg.edge[e][1];
+  int a = G.edge[e][0], b = G.edge[e][1];
   int x, y, z;
   vxyz(d, v, x, y, z);
-  uint32_t rv = rank[v];
-  for (int k = 0; k < 2; ++k) {
-    int t = sg.edge_tri[e][k];
-    int j = 0;
-    while (sg.tri[t][j] == a || sg.tri[t][j] == b) ++j;
-    int c = sg.tri[t][j];
-    int nx, ny, nz;
-    int32_t res;
-    if (!nbr_xyz(d, x, y, z, c, nx, ny, nz)) {
-      res = n3;
+  int t = G.edge_tri[e][k];
+  int j = 0;
+  while (G.tri[t][j] == a || G.tri[t][j] == b) ++j;
+  int c = G.tri[t][j];
+  int nx, ny, nz;
+  int32_t res;
+  if (!nbr_xyz(d, x, y, z, c, nx, ny, nz)) {
+    res = n3;
+  } else {
+    uint32_t wc = vid(d, nx, ny, nz);
+    if (rank[wc] < rank[v]) {
+      res = trace_up(v, t, rec, cidx, snd, n3, sup, d.nv);
     } else {
-      uint32_t wc = vid(d, nx, ny, nz);
-      if (rank[wc] < rv) {
-        res = trace_up(v, t, rec, cidx, snd, n3, sg);
-      } else {
-        int i0 = nbr_index(sg, -sg.off[c][0], -sg.off[c][1], -sg.off[c][2]);
-        int i1 = nbr_index(sg, sg.off[a][0] - sg.off[c][0], sg.off[a][1] - sg.off[c][1],
-                           sg.off[a][2] - sg.off[c][2]);
-        int i2 = nbr_index(sg, sg.off[b][0] - sg.off[c][0], sg.off[b][1] - sg.off[c][1],
-                           sg.off[b][2] - sg.off[c][2]);
-        int tau = (i0 >= 0 && i1 >= 0 && i2 >= 0) ? sg.tri_of3[i0][i1][i2] : -1;
-        res = tau < 0 ? -1 : trace_up(wc, tau, rec, cidx, snd, n3, sg);
-      }
+      int i0 = nbr_index(G, -G.off[c][0], -G.off[c][1], -G.off[c][2]);
+      int i1 = nbr_index(G, G.off[a][0] - G.off[c][0], G.off[a][1] - G.off[c][1], G.off[a][2] - G.off[c][2]);
+      int i2 = nbr_index(G, G.off[b][0] - G.off[c][0], G.off[b][1] - G.off[c][1], G.off[b][2] - G.off[c][2]);
+      int tau = (i0 >= 0 && i1 >= 0 && i2 >= 0) ? G.tri_of3[i0][i1][i2] : -1;
+      res = tau < 0 ? -1 : trace_up(wc, tau, rec, cidx, snd, n3, sup, d.nv);
     }
-    if (res < 0) {
-      atomicOr(status, kErrTrace);
-      res = n3;
-    }
-    ends[2 * i + k] = res;
   }
+  if (res < 0) {
+    atomicOr(status, kErrTrace);
+    res = n3;
+  }
+  ends[tt] = res;
 }
 
 // ---------------------------------------------------------------------------
 // elder-rule union-find by rounds of deterministic reservations (one block)
 // ---------------------------------------------------------------------------
+constexpr int kFindLimit = 1 << 26;
+
 __device__ __forceinline__ int uf_root(int32_t* parent, int x) {
-  for (int s = 0; s < kTraceLimit; ++s) {
+  for (int s = 0; s < kFindLimit; ++s) {
     int p = parent[x];
     if (p == x) return x;
     int gp = parent[p];
@@ -281,7 +276,8 @@ __global__ void k_d0mask_set(int n1, CritLists L, const int32_t* __restrict__ ki
 void launch_d0(const Dims& d, const NbrDelta& nd, const CritLists& L, int n0, int n1, const uint8_t* vnext8,
                const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status, cudaStream_t st) {
   if (n1 > 0) {
-    k_d0_trace<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, vnext8, cidx, nd, S.ends, status); note_launch();
+    k_d0_trace<<<(unsigned)((2 * (int64_t)n1 + 255) / 256), 256, 0, st>>>(n1, d.nv, L, vnext8, cidx, nd, S.ends,
+                                                                         status); note_launch();
     k_uf_rounds<<<1, kUFT, 0, st>>>(n1, n0, false, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
                                     P.d0_min, status); note_launch();
     k_mark_d0<<<(n1 + 255) / 256, 256, 0, st>>>(n1, P.d0_min, P.d0_killed); note_launch();
@@ -294,7 +290,8 @@ void launch_d2(const Dims& d, const NbrDelta& nd, const CritLists& L, int n2, in
                const Rec* rec, const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status,
                cudaStream_t st) {
   if (n2 > 0) {
-    k_d2_trace<<<(n2 + 255) / 256, 256, 0, st>>>(d, n2, n3, L, rank, rec, cidx, nd, S.ends, status); note_launch();
+    k_d2_trace<<<(unsigned)((2 * (int64_t)n2 + 127) / 128), 128, 0, st>>>(d, n2, n3, L, rank, rec, cidx, nd, S.ends,
+                                                                         status); note_launch();
     k_uf_rounds<<<1, kUFT, 0, st>>>(n2, n3 + 1, true, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
                                     P.d2_max, status); note_launch();
   }

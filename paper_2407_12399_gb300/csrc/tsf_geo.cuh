@@ -98,6 +98,40 @@ __host__ __device__ constexpr int geo_dir(int a, int b) {
                      9 * (kGeo.off[b][2] - kGeo.off[a][2] + 1)];
 }
 
+// Crossing into the next lower star on an ascending dual line: the
+// tetrahedron v*tau whose record code is 24 + 3 t + j continues as the
+// tetrahedron of neighbour c = tri[t][j]'s star opposite the same triangle:
+// its link triangle there is (v, p, q) seen from c.  up_step[code - 24] =
+// {c, that link triangle}, or {-1, -1} if the geometry has none.
+struct UpStep {
+  int8_t c, tau;
+};
+struct UpSteps {
+  UpStep s[72];
+};
+constexpr UpSteps make_up_steps() {
+  UpSteps u{};
+  for (int code = 0; code < 72; ++code) {
+    int t2 = code / 3, j = code % 3;
+    int c = kGeo.tri[t2][j], p = kGeo.tri[t2][(j + 1) % 3], q = kGeo.tri[t2][(j + 2) % 3];
+    auto idx = [](int dx, int dy, int dz) { return kGeo.nbr_of[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)]; };
+    int i0 = idx(-kGeo.off[c][0], -kGeo.off[c][1], -kGeo.off[c][2]);
+    int i1 = idx(kGeo.off[p][0] - kGeo.off[c][0], kGeo.off[p][1] - kGeo.off[c][1], kGeo.off[p][2] - kGeo.off[c][2]);
+    int i2 = idx(kGeo.off[q][0] - kGeo.off[c][0], kGeo.off[q][1] - kGeo.off[c][1], kGeo.off[q][2] - kGeo.off[c][2]);
+    int tau = (i0 >= 0 && i1 >= 0 && i2 >= 0) ? kGeo.tri_of3[i0][i1][i2] : -1;
+    u.s[code].c = (int8_t)(tau >= 0 ? c : -1);
+    u.s[code].tau = (int8_t)tau;
+  }
+  return u;
+}
+constexpr UpSteps kUpSteps = make_up_steps();
+constexpr bool up_steps_complete() {
+  for (int k = 0; k < 72; ++k)
+    if (kUpSteps.s[k].c < 0) return false;
+  return true;
+}
+static_assert(up_steps_complete(), "every link triangle of a neighbour star continues across the shared face");
+
 constexpr bool geo_link_dirs_valid() {
   for (int e = 0; e < 36; ++e)
     if (geo_dir(geo_edge(e, 0), geo_edge(e, 1)) < 0 || geo_dir(geo_edge(e, 1), geo_edge(e, 0)) < 0) return false;

@@ -20,6 +20,7 @@ enum : uint32_t {
 };
 
 static __constant__ Geo c_geo = make_geo();
+static __constant__ UpSteps c_up = make_up_steps();
 
 // ---------------------------------------------------------------------------
 // Per-vertex gradient record (32 bytes), bit layout:
