@@ -700,15 +700,16 @@ __device__ __forceinline__ bool d1_visit(const D1Ctx& c, FEnt fe, const int32_t*
   return false;
 }
 
-// Sorts a stage of n <= SCAP entries (a[] holds SCAP entries).
+// Sorts a stage of n <= SCAP entries (a[] holds SCAP entries, a power of
+// two): in registers for up to two entries per thread (the usual case),
+// else in shared memory (compact code: the unrolled networks for more
+// entries per thread only crowd the instruction cache).
 template <int NT, int SCAP>
 __device__ void group_sort_stage(FEnt* a, int n) {
-  static_assert(SCAP % NT == 0 && SCAP <= 16 * NT, "a stage fits the register sort");
+  static_assert(SCAP % NT == 0 && (SCAP & (SCAP - 1)) == 0, "a stage is a power of two");
   if (n <= NT) group_sort_reg<NT, 1>(a, n);
-  else if (n <= 2 * NT) group_sort_reg<NT, (SCAP >= 2 * NT ? 2 : 1)>(a, n);
-  else if (n <= 4 * NT) group_sort_reg<NT, (SCAP >= 4 * NT ? 4 : 1)>(a, n);
-  else if (n <= 8 * NT) group_sort_reg<NT, (SCAP >= 8 * NT ? 8 : 1)>(a, n);
-  else group_sort_reg<NT, (SCAP >= 16 * NT ? 16 : 1)>(a, n);
+  else if (n <= 2 * NT && SCAP >= 2 * NT) group_sort_reg<NT, (SCAP >= 2 * NT ? 2 : 1)>(a, n);
+  else group_sort_smem<NT>(a, n);
 }
 
 // New frontier from the untaken rest (front[nb..nf), descending) and the

@@ -74,6 +74,34 @@ __device__ void group_sort_desc(unsigned long long* a, int n2) {
       gsync<NT>();
     }
 }
+// Descending bitonic sort of keyed entries a[0..n) in shared memory (a[]
+// holds the next power of two; compact code for the rare long stages).
+template <int NT>
+__device__ void group_sort_smem(FEnt* a, int n) {
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = n + threadIdx.x; i < n2; i += NT) {
+    a[i].key = 0ull;
+    a[i].mask = 0u;
+  }
+  gsync<NT>();
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += NT) {
+        int jx = i ^ stride;
+        if (jx > i) {
+          bool desc = (i & size) == 0;
+          FEnt x = a[i], y = a[jx];
+          if ((x.key < y.key) == desc) {
+            a[i] = y;
+            a[jx] = x;
+          }
+        }
+      }
+      gsync<NT>();
+    }
+}
+
 // Descending bitonic sort of a[0..n) (n <= NT * E) by key, E entries per
 // thread in registers (entry i = thread * E + e): strides below E swap
 // registers, strides below 32 E exchange with a lane by shuffles, longer
