@@ -639,9 +639,14 @@ __device__ __forceinline__ void closures(const D1Tab& t, uint32_t m, uint64_t& p
 template <int SCAP>
 __device__ __forceinline__ bool d1_visit(const D1Ctx& c, FEnt fe, const int32_t* snd, FEnt* stage, int* s_ntot,
                                          int* s_flag, unsigned long long* myouts, int& myout, int& updates, bool chain,
-                                         FEnt* next) {
+                                         FEnt* next, uint32_t* status) {
   uint32_t v = (uint32_t)fe.key;
   uint32_t m = fe.mask;
+  if ((int64_t)v >= c.d.nv) {  // never for a valid entry: report and let the column be recomputed
+    atomicOr(status, kErrInconsistent);
+    atomicOr(s_flag, 1);
+    return false;
+  }
   D1Tab t;
   {
     const uint4* s4 = reinterpret_cast<const uint4*>(c.tab + v);
@@ -862,7 +867,8 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 12 : 4) k_d1_morse_group(D1Ctx 
         ++visits;
         FEnt nxt;
         bool more = k + 1 < kChain && myout + 14 <= kOutCap;
-        if (!d1_visit<SCAP>(c, cur, snd, stage, &s_ntot, &s_flag, myouts, myout, updates, more, &nxt)) break;
+        if (!d1_visit<SCAP>(c, cur, snd, stage, &s_ntot, &s_flag, myouts, myout, updates, more, &nxt, status))
+          break;
         cur = nxt;
       }
     }
@@ -930,6 +936,19 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 12 : 4) k_d1_morse_group(D1Ctx 
         }
       }
       break;
+    }
+    if (nf == nb && ntot <= NT) {
+      // every entry is taken next round, so neither their order nor
+      // combining equal keys matters (a star listed twice is visited twice
+      // with parts of its mask: the projection is linear)
+      for (int i = tid; i < ntot; i += NT) front[i] = stage[i];
+      gsync<NT>();  // every thread has read s_ntot before it is reset
+      if (tid == 0) {
+        s_nf = ntot;
+        s_ntot = 0;
+      }
+      gsync<NT>();
+      continue;
     }
     gsync<NT>();
     int nn = group_combine<NT, SCAP>(front, nb, nf, other, stage, ntot, scan_sm);
