@@ -12,12 +12,14 @@ namespace tsf {
 __device__ __forceinline__ void gradient_star(const Dims& d, const uint32_t* __restrict__ rank,
                                               const float* __restrict__ values, int64_t v, Rec* __restrict__ rec,
                                               uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
-                                              uint32_t* status) {
-  const Geo& sg = c_geo;
+                                              uint32_t* status, const Geo& sg) {
   Star s;
   star_load(s, d, (uint32_t)v, rank);
   Fwd f;
-  star_forward(s, f, sg);
+  int8_t y_of[14];
+  uint64_t path_of[14];
+  if (tab) star_forward_impl<true>(s, f, sg, y_of, path_of);
+  else star_forward(s, f, sg);
   Dual du;
   star_dual(s, f, du, sg);
   if (du.inconsistent) atomicOr(status, kErrInconsistent);
@@ -27,9 +29,6 @@ __device__ __forceinline__ void gradient_star(const Dims& d, const uint32_t* __r
   dst[1] = make_uint4(r.w[4], r.w[5], r.w[6], r.w[7]);
   vnext8[v] = (uint8_t)(r.w[0] & 15u);
   if (tab) {
-    int8_t y_of[14];
-    uint64_t path_of[14];
-    star_chains(s, y_of, path_of, sg);
     // closures by increasing rank position: v*y (pos(y) < pos(x)) is done
     // before the v*x whose chain continues there
     uint32_t crit = rec_crit_edges(r);
@@ -92,8 +91,10 @@ __device__ __forceinline__ void gradient_star(const Dims& d, const uint32_t* __r
 __global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
                            Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
                            uint32_t* status) {
+  __shared__ Geo sg;
+  geo_to_shared(sg);
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < d.nv) gradient_star(d, rank, values, v, rec, vnext8, tab, status);
+  if (v < d.nv) gradient_star(d, rank, values, v, rec, vnext8, tab, status, sg);
 }
 
 // Section 4.2, fast persistence update: only the lower stars whose closed
@@ -121,8 +122,10 @@ __global__ void k_gradient_list(Dims d, const uint32_t* __restrict__ rank, const
                                 const uint32_t* __restrict__ list, const unsigned long long* __restrict__ count,
                                 Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
                                 uint32_t* status) {
+  __shared__ Geo sg;
+  geo_to_shared(sg);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < (int64_t)*count) gradient_star(d, rank, values, list[i], rec, vnext8, tab, status);
+  if (i < (int64_t)*count) gradient_star(d, rank, values, list[i], rec, vnext8, tab, status, sg);
 }
 
 // ---------------------------------------------------------------------------

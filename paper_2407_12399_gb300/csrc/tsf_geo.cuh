@@ -93,6 +93,7 @@ constexpr Geo kGeo = make_geo();
 // Compile-time lookups for fully unrolled device code: link edge `le`'s
 // endpoints, and the neighbour index of b - a as seen from neighbour a.
 __host__ __device__ constexpr int geo_edge(int le, int k) { return kGeo.edge[le][k]; }
+__host__ __device__ constexpr uint32_t geo_adj(int a) { return kGeo.adj[a]; }
 __host__ __device__ constexpr int geo_dir(int a, int b) {
   return kGeo.nbr_of[(kGeo.off[b][0] - kGeo.off[a][0] + 1) + 3 * (kGeo.off[b][1] - kGeo.off[a][1] + 1) +
                      9 * (kGeo.off[b][2] - kGeo.off[a][2] + 1)];

@@ -19,6 +19,7 @@
 // so the integral lines below follow "the component a cell merges into",
 // not the cell's partner.
 #pragma once
+#include <utility>
 #include "tsf_internal.cuh"
 
 namespace tsf {
@@ -30,8 +31,24 @@ struct Star {
   uint32_t lower;     // neighbours ranked below v
   int8_t pos[14];     // rank position among the lower neighbours, -1
   int8_t by_pos[14];  // inverse of pos
+  uint16_t adjn[14];  // lower neighbour i: bit q = linked to the lower neighbour at position q
   int nl;
 };
+
+// Link adjacency of neighbour I (compile time) in rank-position space.
+template <int I>
+__device__ __forceinline__ void star_adj_of(Star& s) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int j = 0; j < 14; ++j)
+    if ((geo_adj(I) >> j) & 1u)
+      if ((s.lower >> j) & 1u) r |= 1u << s.pos[j];
+  s.adjn[I] = (uint16_t)r;
+}
+template <int... I>
+__device__ __forceinline__ void star_adj(Star& s, std::integer_sequence<int, I...>) {
+  (star_adj_of<I>(s), ...);
+}
 
 __device__ inline void star_load(Star& s, const Dims& d, uint32_t v, const uint32_t* __restrict__ rank) {
   int x, y, z;
@@ -64,6 +81,7 @@ __device__ inline void star_load(Star& s, const Dims& d, uint32_t v, const uint3
       ++s.nl;
     }
   }
+  star_adj(s, std::make_integer_sequence<int, 14>{});
 }
 
 __device__ __forceinline__ int uf_find(int8_t* par, int x) {
@@ -83,21 +101,58 @@ struct Fwd {
   int8_t killer[14];     // link edge that killed neighbour a's component, -1
 };
 
-__device__ inline void star_forward(const Star& s, Fwd& f, const Geo& G) {
+// Path between two link vertices in a forest given by its adjacency masks
+// (the path is unique), as a mask of link edges.
+__device__ inline uint64_t forest_path(const uint32_t* tadj, int src, int dst, const Geo& G) {
+  if (src == dst) return 0ull;
+  int8_t prev[14];
+  uint32_t seen = 1u << src, frontier = 1u << src;
+  while (frontier && !((seen >> dst) & 1u)) {
+    uint32_t nf = 0;
+    for (uint32_t fm = frontier; fm; fm &= fm - 1) {
+      int u = __ffs(fm) - 1;
+      for (uint32_t m = tadj[u] & ~seen; m; m &= m - 1) {
+        int w2 = __ffs(m) - 1;
+        prev[w2] = (int8_t)u;
+        seen |= 1u << w2;
+        nf |= 1u << w2;
+      }
+    }
+    frontier = nf;
+  }
+  uint64_t bits = 0;
+  if (!((seen >> dst) & 1u)) return bits;
+  for (int c = dst; c != src; c = prev[c]) bits ^= 1ull << G.edge_idx[c][prev[c]];
+  return bits;
+}
+
+// The forward sweep; with CHAINS it also gives, for every killed lower
+// neighbour x, y_of[x] = the older representative its component merged
+// with and path_of[x] = the link edges of the forest path x ... y through
+// the killing edge (a forest path never changes as the forest grows, so the
+// paths are taken in the final forest).
+template <bool CHAINS>
+__device__ inline void star_forward_impl(const Star& s, Fwd& f, const Geo& G, int8_t* y_of, uint64_t* path_of) {
   int8_t par[14];
+  uint32_t tadj[14];
+  int8_t in_x[14], other[14];
   f.lower_edges = 0;
   f.link_pos = 0;
   f.crit_edges = 0;
   for (int i = 0; i < 14; ++i) {
     par[i] = (int8_t)i;
     f.killer[i] = -1;
+    if (CHAINS) {
+      tadj[i] = 0;
+      y_of[i] = -1;
+      path_of[i] = 0;
+    }
   }
   for (int p = 1; p < s.nl; ++p) {
     int a = s.by_pos[p];
-    uint32_t nb = G.adj[a] & s.lower;
-    for (int q = 0; q < p; ++q) {
+    for (uint32_t qm = s.adjn[a] & ((1u << p) - 1u); qm; qm &= qm - 1) {
+      int q = __ffs(qm) - 1;
       int b = s.by_pos[q];
-      if (!((nb >> b) & 1u)) continue;
       int e = G.edge_idx[a][b];
       f.lower_edges |= 1ull << e;
       int ra = uf_find(par, p), rb = uf_find(par, q);
@@ -105,13 +160,29 @@ __device__ inline void star_forward(const Star& s, Fwd& f, const Geo& G) {
         f.link_pos |= 1ull << e;
       } else {
         int young = ra > rb ? ra : rb, old = ra > rb ? rb : ra;
+        int x = s.by_pos[young];
         par[young] = (int8_t)old;
-        f.killer[s.by_pos[young]] = (int8_t)e;
+        f.killer[x] = (int8_t)e;
+        if (CHAINS) {
+          y_of[x] = s.by_pos[old];
+          in_x[x] = (int8_t)(ra == young ? a : b);
+          other[x] = (int8_t)(ra == young ? b : a);
+          tadj[a] |= 1u << b;
+          tadj[b] |= 1u << a;
+        }
       }
     }
   }
   for (int p = 1; p < s.nl; ++p)
     if (uf_find(par, p) == p) f.crit_edges |= 1u << s.by_pos[p];
+  if (CHAINS)
+    for (int x = 0; x < 14; ++x)
+      if (y_of[x] >= 0)
+        path_of[x] = forest_path(tadj, x, in_x[x], G) ^ (1ull << f.killer[x]) ^ forest_path(tadj, other[x], y_of[x], G);
+}
+
+__device__ inline void star_forward(const Star& s, Fwd& f, const Geo& G) {
+  star_forward_impl<false>(s, f, G, nullptr, nullptr);
 }
 
 // Key of a link triangle for the backward sweep (larger = later in the
@@ -149,10 +220,10 @@ __device__ inline void star_dual(const Star& s, const Fwd& f, Dual& du, const Ge
   par[OUT] = OUT;
   for (int p = s.nl - 1; p >= 1; --p) {
     int a = s.by_pos[p];
-    uint32_t nb = G.adj[a] & s.lower;
-    for (int q = p - 1; q >= 0; --q) {
+    for (uint32_t qm = s.adjn[a] & ((1u << p) - 1u); qm;) {
+      int q = 31 - __clz(qm);
+      qm ^= 1u << q;
       int b = s.by_pos[q];
-      if (!((nb >> b) & 1u)) continue;
       int e = G.edge_idx[a][b];
       int node[2], tcode[2];
 #pragma unroll
@@ -213,77 +284,6 @@ __device__ __forceinline__ int star_edge_key(const Star& s, int e, const Geo& G)
 
 namespace tsf {
 
-// Reduced column of the triangle paired with the edge w*x (x killed in the
-// forward sweep by link edge e' = (a,b)): in the block's reduction it equals
-// the boundary of the fan of triangles w*(link path from x to y through e'),
-// y being the older representative e' merged x's component with.  Writes the
-// path's link edges (as neighbour index pairs) and returns their number, or
-// -1 if x is not killed.  The column is w*x + w*y + (path edges).
-__device__ inline int star_chain(const Star& s, int x, int8_t* pa, int8_t* pb, int& y, const Geo& G) {
-  int8_t par[14];
-  uint32_t tadj[14];
-  for (int i = 0; i < 14; ++i) {
-    par[i] = (int8_t)i;
-    tadj[i] = 0;
-  }
-  for (int p = 1; p < s.nl; ++p) {
-    int a = s.by_pos[p];
-    uint32_t nb = G.adj[a] & s.lower;
-    for (int q = 0; q < p; ++q) {
-      int b = s.by_pos[q];
-      if (!((nb >> b) & 1u)) continue;
-      int ra = uf_find(par, p), rb = uf_find(par, q);
-      if (ra == rb) continue;
-      int young = ra > rb ? ra : rb, old = ra > rb ? rb : ra;
-      if (s.by_pos[young] == x) {
-        // x's component holds a (ra young) or b (rb young)
-        int in_x = (ra == young) ? a : b;
-        int other = (ra == young) ? b : a;
-        y = s.by_pos[old];
-        int n = 0;
-        // forest path x -> in_x (inside x's component), by BFS over tree edges
-        auto path = [&](int src, int dst, bool reverse_out) {
-          int8_t prev[14];
-          for (int i = 0; i < 14; ++i) prev[i] = -1;
-          uint32_t seen = 1u << src, frontier = 1u << src;
-          prev[src] = (int8_t)src;
-          while (frontier && !((seen >> dst) & 1u)) {
-            uint32_t nf = 0;
-            for (uint32_t fm = frontier; fm; fm &= fm - 1) {
-              int u = __ffs(fm) - 1;
-              for (uint32_t m = tadj[u] & ~seen; m; m &= m - 1) {
-                int w2 = __ffs(m) - 1;
-                prev[w2] = (int8_t)u;
-                seen |= 1u << w2;
-                nf |= 1u << w2;
-              }
-            }
-            frontier = nf;
-          }
-          int c = dst;
-          while (c != src) {
-            pa[n] = (int8_t)c;
-            pb[n] = prev[c];
-            ++n;
-            c = prev[c];
-          }
-          (void)reverse_out;
-        };
-        path(x, in_x, false);
-        pa[n] = (int8_t)in_x;
-        pb[n] = (int8_t)other;
-        ++n;
-        path(other, y, false);
-        return n;
-      }
-      par[young] = (int8_t)old;
-      tadj[a] |= 1u << b;
-      tadj[b] |= 1u << a;
-    }
-  }
-  return -1;
-}
-
 }  // namespace tsf
 
 namespace tsf {
@@ -293,56 +293,8 @@ namespace tsf {
 // edges (bitmask) of the forest path x ... y through the killing edge.  The
 // reduced column of the triangle paired with w*x is w*x + w*y + path.
 __device__ inline void star_chains(const Star& s, int8_t* y_of, uint64_t* path_of, const Geo& G) {
-  int8_t par[14];
-  uint32_t tadj[14];
-  for (int i = 0; i < 14; ++i) {
-    par[i] = (int8_t)i;
-    tadj[i] = 0;
-    y_of[i] = -1;
-    path_of[i] = 0;
-  }
-  auto tree_path = [&](int src, int dst) -> uint64_t {
-    if (src == dst) return 0ull;
-    int8_t prev[14];
-    for (int i = 0; i < 14; ++i) prev[i] = -1;
-    uint32_t seen = 1u << src, frontier = 1u << src;
-    while (frontier && !((seen >> dst) & 1u)) {
-      uint32_t nf = 0;
-      for (uint32_t fm = frontier; fm; fm &= fm - 1) {
-        int u = __ffs(fm) - 1;
-        for (uint32_t m = tadj[u] & ~seen; m; m &= m - 1) {
-          int w2 = __ffs(m) - 1;
-          prev[w2] = (int8_t)u;
-          seen |= 1u << w2;
-          nf |= 1u << w2;
-        }
-      }
-      frontier = nf;
-    }
-    uint64_t bits = 0;
-    for (int c = dst; c != src && prev[c] >= 0; c = prev[c]) bits ^= 1ull << G.edge_idx[c][prev[c]];
-    return bits;
-  };
-  for (int p = 1; p < s.nl; ++p) {
-    int a = s.by_pos[p];
-    uint32_t nb = G.adj[a] & s.lower;
-    for (int q = 0; q < p; ++q) {
-      int b = s.by_pos[q];
-      if (!((nb >> b) & 1u)) continue;
-      int ra = uf_find(par, p), rb = uf_find(par, q);
-      if (ra == rb) continue;
-      int young = ra > rb ? ra : rb, old = ra > rb ? rb : ra;
-      int x = s.by_pos[young];
-      int in_x = (ra == young) ? a : b;
-      int other = (ra == young) ? b : a;
-      int y = s.by_pos[old];
-      y_of[x] = (int8_t)y;
-      path_of[x] = tree_path(x, in_x) ^ (1ull << G.edge_idx[a][b]) ^ tree_path(other, y);
-      par[young] = (int8_t)old;
-      tadj[a] |= 1u << b;
-      tadj[b] |= 1u << a;
-    }
-  }
+  Fwd f;
+  star_forward_impl<true>(s, f, G, y_of, path_of);
 }
 
 }  // namespace tsf
