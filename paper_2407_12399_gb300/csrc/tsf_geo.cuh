@@ -22,6 +22,7 @@ struct Geo {
   int8_t tri[24][3];        // link triangle -> neighbour indices (a < b < c)
   int8_t tri_edge[24][3];   // link triangle -> its three link edges
   int8_t edge_tri[36][2];   // link edge -> the two link triangles containing it
+  int8_t edge_third[36][2]; // ... and the slot (0..2) of each triangle's third vertex
   uint16_t adj[14];         // link adjacency bitmask per neighbour
   int8_t nbr_of[27];        // (dx+1) + 3 (dy+1) + 9 (dz+1) -> neighbour index, -1
   int8_t tri_of3[14][14][14];  // neighbour triple -> link triangle, -1
@@ -79,6 +80,11 @@ constexpr Geo make_geo() {
             else g.edge_tri[es[s]][1] = (int8_t)nt;
           }
           int p[3] = {i, j, k};
+          for (int s2 = 0; s2 < 3; ++s2) {
+            int ee = es[s2], slot = g.edge_tri[ee][1] == nt ? 1 : 0;
+            for (int q = 0; q < 3; ++q)
+              if (p[q] != g.edge[ee][0] && p[q] != g.edge[ee][1]) g.edge_third[ee][slot] = (int8_t)q;
+          }
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
               for (int c = 0; c < 3; ++c)
@@ -153,5 +159,14 @@ constexpr bool geo_edges_have_two_triangles() {
 }
 static_assert(geo_count_edges() == 36, "the link of a Freudenthal vertex has 36 edges");
 static_assert(geo_edges_have_two_triangles(), "the link is a closed surface: 24 triangles, 2 per edge");
+constexpr bool geo_third_vertices_valid() {
+  for (int e = 0; e < 36; ++e)
+    for (int k = 0; k < 2; ++k) {
+      int c = kGeo.tri[kGeo.edge_tri[e][k]][kGeo.edge_third[e][k]];
+      if (c == kGeo.edge[e][0] || c == kGeo.edge[e][1]) return false;
+    }
+  return true;
+}
+static_assert(geo_third_vertices_valid(), "edge_third names the vertex of each triangle off the edge");
 
 }  // namespace tsf

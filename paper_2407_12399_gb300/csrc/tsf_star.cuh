@@ -101,36 +101,11 @@ struct Fwd {
   int8_t killer[14];     // link edge that killed neighbour a's component, -1
 };
 
-// Path between two link vertices in a forest given by its adjacency masks
-// (the path is unique), as a mask of link edges.
-__device__ inline uint64_t forest_path(const uint32_t* tadj, int src, int dst, const Geo& G) {
-  if (src == dst) return 0ull;
-  int8_t prev[14];
-  uint32_t seen = 1u << src, frontier = 1u << src;
-  while (frontier && !((seen >> dst) & 1u)) {
-    uint32_t nf = 0;
-    for (uint32_t fm = frontier; fm; fm &= fm - 1) {
-      int u = __ffs(fm) - 1;
-      for (uint32_t m = tadj[u] & ~seen; m; m &= m - 1) {
-        int w2 = __ffs(m) - 1;
-        prev[w2] = (int8_t)u;
-        seen |= 1u << w2;
-        nf |= 1u << w2;
-      }
-    }
-    frontier = nf;
-  }
-  uint64_t bits = 0;
-  if (!((seen >> dst) & 1u)) return bits;
-  for (int c = dst; c != src; c = prev[c]) bits ^= 1ull << G.edge_idx[c][prev[c]];
-  return bits;
-}
-
 // The forward sweep; with CHAINS it also gives, for every killed lower
 // neighbour x, y_of[x] = the older representative its component merged
 // with and path_of[x] = the link edges of the forest path x ... y through
 // the killing edge (a forest path never changes as the forest grows, so the
-// paths are taken in the final forest).
+// paths are taken in the final forest, as xors of paths to the tree roots).
 template <bool CHAINS>
 __device__ inline void star_forward_impl(const Star& s, Fwd& f, const Geo& G, int8_t* y_of, uint64_t* path_of) {
   int8_t par[14];
@@ -175,10 +150,36 @@ __device__ inline void star_forward_impl(const Star& s, Fwd& f, const Geo& G, in
   }
   for (int p = 1; p < s.nl; ++p)
     if (uf_find(par, p) == p) f.crit_edges |= 1u << s.by_pos[p];
-  if (CHAINS)
+  if (CHAINS) {
+    // link edges from every vertex to the root of its tree (the vertex of
+    // rank position 0 of its component, any root works): the forest path
+    // between two vertices of one tree is the xor of their root paths
+    uint64_t rp[14];
+    uint32_t done = 0;
+    for (int p = 0; p < s.nl; ++p) {
+      int r = s.by_pos[p];
+      if ((done >> r) & 1u) continue;
+      rp[r] = 0;
+      done |= 1u << r;
+      uint32_t frontier = 1u << r;
+      while (frontier) {
+        uint32_t nf = 0;
+        for (uint32_t fm = frontier; fm; fm &= fm - 1) {
+          int u = __ffs(fm) - 1;
+          for (uint32_t m = tadj[u] & ~done; m; m &= m - 1) {
+            int w2 = __ffs(m) - 1;
+            rp[w2] = rp[u] ^ (1ull << G.edge_idx[u][w2]);
+            done |= 1u << w2;
+            nf |= 1u << w2;
+          }
+        }
+        frontier = nf;
+      }
+    }
     for (int x = 0; x < 14; ++x)
       if (y_of[x] >= 0)
-        path_of[x] = forest_path(tadj, x, in_x[x], G) ^ (1ull << f.killer[x]) ^ forest_path(tadj, other[x], y_of[x], G);
+        path_of[x] = rp[x] ^ rp[in_x[x]] ^ (1ull << f.killer[x]) ^ rp[other[x]] ^ rp[y_of[x]];
+  }
 }
 
 __device__ inline void star_forward(const Star& s, Fwd& f, const Geo& G) {
@@ -229,8 +230,7 @@ __device__ inline void star_dual(const Star& s, const Fwd& f, Dual& du, const Ge
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         int t = G.edge_tri[e][k];
-        int j = 0;
-        while (G.tri[t][j] == a || G.tri[t][j] == b) ++j;
+        int j = G.edge_third[e][k];
         int c = G.tri[t][j];
         if (!((s.valid >> c) & 1u)) {
           node[k] = OUT;
