@@ -76,13 +76,18 @@ typedef struct {
  * max_iters: j_max of Algorithm 1 (the paper uses 1000).
  * fast_gradient_update: 1 recomputes the gradient only around vertices the
  *   last step changed (Section 4.2); 0 recomputes it everywhere.  Results are
- *   identical either way. */
+ *   identical either way.
+ * fast_assignment_update: 1 lets still pairs keep their previous assignment
+ *   and matches only the others (Section 4.3); 0 matches every point of the
+ *   new diagram with the exact solver.  The j = 0 assignment is the identity
+ *   either way. */
 typedef struct {
   float alpha_b, alpha_d;
   float stop_s;
   float cancel_eps;
   int32_t max_iters;
   int32_t fast_gradient_update;
+  int32_t fast_assignment_update;
 } tsf_params;
 
 /* Per-iteration statistics. */

@@ -65,6 +65,8 @@ def lib():
                                         ctypes.c_int]
         L.or_solver_done.restype = ctypes.c_int
         L.or_solver_done.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_int]
+        L.or_solver_set_fast_assignment.restype = None
+        L.or_solver_set_fast_assignment.argtypes = [P, ctypes.c_int]
         L.or_solver_field.argtypes = [P, P]
         L.or_solver_num_points.restype = I64
         L.or_solver_num_points.argtypes = [P]
@@ -149,7 +151,7 @@ def assign(pb, pd, tb, td):
 class Solver:
     """Algorithm 1 with Sections 4.1 and 4.3, on the CPU, one iteration at a time."""
 
-    def __init__(self, f0, tau=None, targets=None):
+    def __init__(self, f0, tau=None, targets=None, fast_assignment=True):
         L = lib()
         f0, lx, ly, lz = _field(f0)
         self.shape = f0.shape
@@ -166,6 +168,7 @@ class Solver:
         if not h:
             raise ValueError(f"oracle solver failed (status {st.value})")
         self._h = h
+        L.or_solver_set_fast_assignment(h, 1 if fast_assignment else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -475,6 +475,7 @@ struct or_solver {
   int64_t j;
   double loss, loss0;
   int64_t n_unc, n_still, n_updated, n_nssp;
+  int fast_assign; /* Section 4.3 still-pair reuse after each step (default on) */
 };
 
 /* Diagram order: increasing birth, then death (Section 2.4); the remaining
@@ -949,6 +950,7 @@ static or_solver* solver_alloc(int lx, int ly, int lz, const float* f0, int* sta
 }
 
 static void solver_start(or_solver* s) {
+  s->fast_assign = 1;
   qsort(s->T, s->nt, sizeof(otarget_t), cmp_target);
   /* j = 0: the targets play the previous diagram, each assigned to itself */
   opoint_t* R = (opoint_t*)malloc(sizeof(opoint_t) * (s->nt + 1));
@@ -1074,12 +1076,16 @@ int or_solver_iterate(or_solver* s, float alpha_b, float alpha_d, float stop_s, 
     s->np = nprev;
     return st;
   }
-  assign_points(s, prev, nprev, 0);
+  /* without the Section 4.3 reuse no point of the previous diagram is
+   * consulted: every point is matched by the exact solver */
+  assign_points(s, prev, s->fast_assign ? nprev : 0, 0);
   free(prev);
   s->j += 1;
   eval_loss(s);
   return or_solver_done(s, stop_s, cancel_eps, max_iters);
 }
+
+void or_solver_set_fast_assignment(or_solver* s, int on) { s->fast_assign = on ? 1 : 0; }
 
 void or_solver_field(const or_solver* s, float* out) { memcpy(out, s->f, sizeof(float) * s->g.nv); }
 int64_t or_solver_num_points(const or_solver* s) { return s->np; }

@@ -62,6 +62,11 @@ or_solver* or_solver_create_targets(int lx, int ly, int lz, const float* f0, int
 int or_solver_iterate(or_solver* s, float alpha_b, float alpha_d, float stop_s, float cancel_eps,
                       int max_iters);
 int or_solver_done(or_solver* s, float stop_s, float cancel_eps, int max_iters);
+/* Section 4.3 fast assignment update on (default) or off for the following
+ * iterations: off, every point of the new diagram is matched by the exact
+ * solver instead of still points inheriting their previous assignment.  The
+ * j = 0 assignment is the identity in both modes. */
+void or_solver_set_fast_assignment(or_solver* s, int on);
 void or_solver_field(const or_solver* s, float* out);
 int64_t or_solver_num_points(const or_solver* s);
 int64_t or_solver_num_targets(const or_solver* s);

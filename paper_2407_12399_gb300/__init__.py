@@ -42,7 +42,7 @@ assert PAIR_DTYPE.itemsize == ctypes.sizeof(tsf_pair) == 40
 class tsf_params(ctypes.Structure):
     _fields_ = [("alpha_b", ctypes.c_float), ("alpha_d", ctypes.c_float), ("stop_s", ctypes.c_float),
                 ("cancel_eps", ctypes.c_float), ("max_iters", ctypes.c_int32),
-                ("fast_gradient_update", ctypes.c_int32)]
+                ("fast_gradient_update", ctypes.c_int32), ("fast_assignment_update", ctypes.c_int32)]
 
 
 class tsf_stats(ctypes.Structure):
@@ -222,8 +222,9 @@ def tsf_kernel_launches():
     return int(lib().tsf_kernel_launches())
 
 
-def params(alpha_b=0.5, alpha_d=0.5, stop_s=0.01, cancel_eps=0.0, max_iters=1000, fast_gradient_update=1):
-    return tsf_params(alpha_b, alpha_d, stop_s, cancel_eps, max_iters, fast_gradient_update)
+def params(alpha_b=0.5, alpha_d=0.5, stop_s=0.01, cancel_eps=0.0, max_iters=1000, fast_gradient_update=1,
+           fast_assignment_update=1):
+    return tsf_params(alpha_b, alpha_d, stop_s, cancel_eps, max_iters, fast_gradient_update, fast_assignment_update)
 
 
 def _ptr_of(a):

@@ -609,7 +609,9 @@ int step(tsf_field* F, const tsf_params* p, tsf_stats* stats) {
   F->nprev = F->np;
   int r = compute_diagram(F, fast);
   if (r) return r;
-  r = run_assign(F, F->prev, F->nprev);
+  // without the Section 4.3 reuse no point of the previous diagram is
+  // consulted: every point is matched by the exact solver
+  r = run_assign(F, F->prev, p->fast_assignment_update ? F->nprev : 0);
   if (r) return r;
   F->iter += 1;
   eval(F, p->cancel_eps);

@@ -211,3 +211,22 @@ def test_incremental_order_matches_full_recompute(shape, tau, many):
     assert (max(upd) > limit) if many else (0 < max(upd) <= limit)
     g = a.values()
     assert gpu_rows(a.diagram()) == oracle_rows(g, oracle.diagram(g)["pairs"])
+
+
+@pytest.mark.parametrize("name,tau,iters", [("plain_32", 0.1, 5), ("filament_40", 0.05, 4)])
+def test_trajectory_without_assignment_reuse_is_bit_exact(name, tau, iters):
+    """Section 4.3 reuse off: every point is matched by the exact solver each
+    iteration, on both sides."""
+    f0 = NAMED[name]()
+    fld = gpu_field(f0)
+    fld.set_threshold(tau)
+    ref = oracle.Solver(f0, tau=tau, fast_assignment=False)
+    for j in range(iters):
+        st = fld.step(fast_assignment_update=0, stop_s=0.0)
+        ref.iterate(stop_s=0.0)
+        assert np.array_equal(bits(fld.values()), bits(ref.field())), f"field differs after step {j + 1}"
+        tgt, still = fld.assignment()
+        P = ref.points()
+        assert tgt.tolist() == P["tgt"].tolist()
+        assert not still.any() and st["n_still"] == 0
+        assert st["loss"] == pytest.approx(ref.stats()["loss"], rel=1e-12, abs=1e-300)

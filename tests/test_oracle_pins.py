@@ -318,3 +318,20 @@ def test_small_solve_reaches_the_loss_stop_rule():
     P = s.points()
     # every signal target is still matched
     assert len(set(P["tgt"][P["tgt"] >= 0].tolist())) == len(s.targets()["vb"])
+
+
+@pytest.mark.parametrize("seed", [0, 3, 7])
+def test_fast_assignment_off_is_the_exact_full_matching(seed):
+    """Section 4.3 reuse off: no point is still, and on the same diagram the
+    exact matching of every point costs no more than the matching that lets
+    still pairs keep their previous target (after the first step both modes
+    see the same D(f_1), since both start from the identity at j = 0)."""
+    f0 = S.gaussian_mixture((12, 11, 10), n_bumps=6, seed=seed)
+    on = oracle.Solver(f0, tau=0.05)
+    off = oracle.Solver(f0, tau=0.05, fast_assignment=False)
+    assert on.stats()["loss"] == off.stats()["loss"]
+    on.iterate(stop_s=0.0)
+    off.iterate(stop_s=0.0)
+    assert np.array_equal(on.field(), off.field())
+    assert off.stats()["still"] == 0
+    assert off.stats()["loss"] <= on.stats()["loss"] * (1 + 1e-12)
