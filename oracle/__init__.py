@@ -67,6 +67,8 @@ def lib():
         L.or_solver_done.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_int]
         L.or_solver_set_fast_assignment.restype = None
         L.or_solver_set_fast_assignment.argtypes = [P, ctypes.c_int]
+        L.or_solver_loss_grad.restype = ctypes.c_int
+        L.or_solver_loss_grad.argtypes = [P, P, P, P]
         L.or_solver_field.argtypes = [P, P]
         L.or_solver_num_points.restype = I64
         L.or_solver_num_points.argtypes = [P]
@@ -222,6 +224,18 @@ class Solver:
         lib().or_solver_stats(self._h, _ptr(st), _ptr(loss))
         return {"iter": int(st[0]), "uncancelled": int(st[1]), "still": int(st[2]), "updated": int(st[3]),
                 "nonstill_matched": int(st[4]), "loss": float(loss[0]), "loss0": float(loss[1])}
+
+    def loss_grad(self, values):
+        """(loss, dL/df as float64 of the field's shape) of `values` against the
+        target diagram, every point matched by the exact solver."""
+        v = np.ascontiguousarray(values, np.float32)
+        assert v.shape == self.shape
+        loss = np.zeros(1, np.float64)
+        grad = np.zeros(self.shape, np.float64)
+        r = lib().or_solver_loss_grad(self._h, _ptr(v), _ptr(loss), _ptr(grad))
+        if r < 0:
+            raise ValueError(f"oracle loss failed ({r})")
+        return float(loss[0]), grad
 
     def run(self, alpha_b=0.5, alpha_d=0.5, stop_s=0.01, cancel_eps=0.0, max_iters=1000):
         while not self.done(stop_s, cancel_eps, max_iters):

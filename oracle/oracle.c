@@ -1087,6 +1087,49 @@ int or_solver_iterate(or_solver* s, float alpha_b, float alpha_d, float stop_s, 
 
 void or_solver_set_fast_assignment(or_solver* s, int on) { s->fast_assign = on ? 1 : 0; }
 
+/*
+ * Topological loss of the field `values` against the solver's target
+ * diagram (Eq. 2, q = 2): the diagram of `values`, every point matched by
+ * the exact solver (no still-pair reuse), L, and dL/df in fp64.  Where the
+ * pairing and the matching do not change, L is a sum of squares of vertex
+ * values, so: a point matched to target t adds 2 (b - t_b) at v_b and
+ * 2 (d - t_d) at v_d (the essential class too: its death value is the
+ * global maximum's); a point matched to the diagonal adds b - d at v_b and
+ * d - b at v_d, the derivative of (d - b)^2 / 2.  Contributions are added
+ * in diagram order, birth before death.  The solver's state becomes this
+ * field, its diagram and matching.
+ */
+int or_solver_loss_grad(or_solver* s, const float* values, double* loss, double* grad) {
+  memcpy(s->f, values, sizeof(float) * s->g.nv);
+  opoint_t* prev = s->P;
+  int64_t nprev = s->np;
+  int st = compute_points(&s->g, s->f, &s->P, &s->np);
+  if (st) {
+    s->P = prev;
+    s->np = nprev;
+    return st;
+  }
+  free(prev);
+  assign_points(s, NULL, 0, 0);
+  eval_loss(s);
+  *loss = s->loss;
+  memset(grad, 0, sizeof(double) * s->g.nv);
+  for (int64_t i = 0; i < s->np; ++i) {
+    const opoint_t* p = &s->P[i];
+    double b = (double)p->b, d = (double)p->d, gb, gd;
+    if (p->tgt >= 0) {
+      gb = 2.0 * (b - (double)s->T[p->tgt].b);
+      gd = 2.0 * (d - (double)s->T[p->tgt].d);
+    } else {
+      gb = b - d;
+      gd = d - b;
+    }
+    grad[p->vb] += gb;
+    grad[p->vd] += gd;
+  }
+  return 0;
+}
+
 void or_solver_field(const or_solver* s, float* out) { memcpy(out, s->f, sizeof(float) * s->g.nv); }
 int64_t or_solver_num_points(const or_solver* s) { return s->np; }
 int64_t or_solver_num_targets(const or_solver* s) { return s->nt; }

@@ -67,6 +67,12 @@ int or_solver_done(or_solver* s, float stop_s, float cancel_eps, int max_iters);
  * solver instead of still points inheriting their previous assignment.  The
  * j = 0 assignment is the identity in both modes. */
 void or_solver_set_fast_assignment(or_solver* s, int on);
+/* Topological loss of `values` (nv floats) against the target diagram:
+ * diagram, full exact matching, *loss = Eq. 2 with q = 2, grad[nv] = dL/df
+ * in fp64 (contributions added in diagram order, birth before death; the
+ * essential class contributes at both its vertices).  The solver's state
+ * becomes this field.  Returns 0, or a negative status. */
+int or_solver_loss_grad(or_solver* s, const float* values, double* loss, double* grad);
 void or_solver_field(const or_solver* s, float* out);
 int64_t or_solver_num_points(const or_solver* s);
 int64_t or_solver_num_targets(const or_solver* s);

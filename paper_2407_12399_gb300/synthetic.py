@@ -253,6 +253,12 @@ def plain_32(seed=0):
     return gaussian_mixture((32, 32, 32), n_bumps=8, seed=seed, noise_frac=0.05)
 
 
+def mixture_96(seed=3):
+    """96^3 Gaussian mixture (32 bumps) + 5 % uniform noise: the field of the
+    differentiable-loss workload."""
+    return gaussian_mixture((96, 96, 96), n_bumps=32, seed=seed, noise_frac=0.05)
+
+
 def filament_128(seed=1):
     """128^3 filament-tube field + 4-octave gradient noise at 10 % of range."""
     return filament_field((128, 128, 128), seed=seed)

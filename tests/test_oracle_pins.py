@@ -335,3 +335,43 @@ def test_fast_assignment_off_is_the_exact_full_matching(seed):
     assert np.array_equal(on.field(), off.field())
     assert off.stats()["still"] == 0
     assert off.stats()["loss"] <= on.stats()["loss"] * (1 + 1e-12)
+
+
+def _pairing(s):
+    P = s.points()
+    return list(zip(P["dim"].tolist(), P["vb"].tolist(), P["vd"].tolist(), P["tgt"].tolist()))
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_loss_gradient_matches_central_differences(seed):
+    """dL/df of the topological loss (Eq. 2) against (L(f + d e_v) - L(f - d' e_v)) / (d + d')
+    with d, d' the fp32 perturbations actually applied, at vertices whose
+    perturbation changes neither the pairing nor the matching: there L is
+    quadratic in f(v), so the difference quotient is exact up to h (d - d')."""
+    f0 = S.gaussian_mixture((9, 8, 7), n_bumps=5, seed=seed)
+    s = oracle.Solver(f0, tau=0.1)
+    L0, g = s.loss_grad(f0)
+    base = _pairing(s)
+    flat = f0.ravel()
+    rng = np.random.default_rng(seed)
+    P = s.points()
+    ess = np.concatenate([P["vb"][P["essential"] == 1], P["vd"][P["essential"] == 1]]).astype(np.int64)
+    cand = np.concatenate([ess, np.nonzero(g.ravel())[0], rng.choice(flat.size, 20, replace=False)])
+    checked = 0
+    for v in cand:
+        fp, fm = f0.copy().ravel(), f0.copy().ravel()
+        fp[v] = np.float32(flat[v] + np.float32(1e-3))
+        fm[v] = np.float32(flat[v] - np.float32(1e-3))
+        Lp, _ = s.loss_grad(fp.reshape(f0.shape))
+        if _pairing(s) != base:
+            continue
+        Lm, _ = s.loss_grad(fm.reshape(f0.shape))
+        if _pairing(s) != base:
+            continue
+        d1, d2 = float(fp[v]) - float(flat[v]), float(flat[v]) - float(fm[v])
+        fd = (Lp - Lm) / (d1 + d2)
+        assert fd == pytest.approx(g.ravel()[v], abs=2e-6), v
+        checked += 1
+    assert checked >= 20
+    # back at f0 the loss is unchanged
+    assert s.loss_grad(f0)[0] == L0
