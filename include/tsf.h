@@ -158,6 +158,24 @@ int tsf_simplify(tsf_field* field, const tsf_params* params, float* out_values, 
 /* Copies the current values to out (lx*ly*lz floats, host or device). */
 int tsf_get_field(tsf_field* field, float* out, int out_on_device);
 
+/* Topological loss of a field against the target diagram (Eq. 2 with q = 2:
+ * squared distances of the points matched to targets to those targets, of
+ * the others to the diagonal, plus unmatched targets to the diagonal) and
+ * its gradient with respect to the field values.  values: lx*ly*lz floats
+ * (host or device), which become the field's values (the diagram follows
+ * the vertices they change, Section 4.2); every point of the diagram is
+ * matched by the exact solver (no still-pair reuse).  *loss (host) receives
+ * L in fp64; grad (may be NULL), lx*ly*lz doubles (host or device),
+ * receives dL/df for that diagram and matching: 2 (b - t_b) at v_b and
+ * 2 (d - t_d) at v_d for a point matched to target t (the essential class
+ * included), b - d and d - b for a point matched to the diagonal, added per
+ * vertex in diagram order (Section 4.1's gradient without the step size).
+ * It is the derivative of L wherever a small change of the values changes
+ * neither the pairing nor the matching.
+ * Errors: TSF_EINVAL, TSF_ENOTARGET before a target was set, TSF_ENAN. */
+int tsf_loss_and_gradient(tsf_field* field, const float* values, int values_on_device, double* loss,
+                          double* grad, int grad_on_device);
+
 /* Overwrites the current values (restart from a saved field; the still-pair
  * history is reset, so the next assignment starts cold). */
 int tsf_set_field(tsf_field* field, const float* values, int values_on_device);

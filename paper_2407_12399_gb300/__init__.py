@@ -67,7 +67,8 @@ class tsf_stats(ctypes.Structure):
 EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_set_signal_threshold",
            "tsf_set_signal_pairs", "tsf_solver_step", "tsf_simplify", "tsf_get_field", "tsf_set_field",
            "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
-           "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static")
+           "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static",
+           "tsf_loss_and_gradient")
 TSF_NSTAGES = 12
 INCREMENTAL_ORDER_MAX = 8192  # TSF_INCREMENTAL_ORDER_MAX
 
@@ -98,6 +99,7 @@ def lib():
             "tsf_get_targets": [P, P, I64, ctypes.POINTER(I64)],
             "tsf_zero_pairs": [P, P, I64, ctypes.POINTER(I64)],
             "tsf_zero_pairs_static": [I, I, I, P, P, I64, ctypes.POINTER(I64), P],
+            "tsf_loss_and_gradient": [P, P, I, ctypes.POINTER(ctypes.c_double), P, I],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -203,6 +205,15 @@ def tsf_zero_pairs_static(lx, ly, lz, values_ptr, out_ptr, cap, cuda_stream=0):
     return r, n.value
 
 
+def tsf_loss_and_gradient(h, values_ptr, values_on_device, grad_ptr, grad_on_device):
+    """Loss of the values at values_ptr against the target diagram; dL/df
+    (float64) written at grad_ptr (may be None)."""
+    loss = ctypes.c_double(0.0)
+    _check(lib().tsf_loss_and_gradient(h, values_ptr, values_on_device, ctypes.byref(loss), grad_ptr, grad_on_device),
+           "tsf_loss_and_gradient")
+    return loss.value
+
+
 def tsf_profile_enable(h, enable=1):
     _check(lib().tsf_profile_enable(h, enable), "tsf_profile_enable")
 
@@ -298,6 +309,21 @@ class Field:
         out = np.zeros(self.shape, np.float32)
         tsf_get_field(self._h, out.ctypes.data, 0)
         return out
+
+    def loss_and_grad(self, values, grad_out=None):
+        """Topological loss of `values` (numpy array or tensor of the field's
+        shape) against the target diagram, and dL/df into `grad_out` (float64
+        numpy array or tensor of the same shape, host or device; allocated on
+        the host when None).  The values become the field's values."""
+        if isinstance(values, np.ndarray):
+            values = np.ascontiguousarray(values, np.float32)
+        else:
+            values = values.contiguous()
+        vp, von = _ptr_of(values)
+        if grad_out is None:
+            grad_out = np.zeros(self.shape, np.float64)
+        gp, gon = _ptr_of(grad_out)
+        return tsf_loss_and_gradient(self._h, vp, von, gp, gon), grad_out
 
     def assignment(self):
         r, n = tsf_get_assignment(self._h, None, None, 0)

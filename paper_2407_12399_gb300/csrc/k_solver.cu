@@ -1213,6 +1213,86 @@ int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float a
   return (int64_t)nupd;
 }
 
+// ---------------------------------------------------------------------------
+// Gradient of the topological loss (Eq. 2, q = 2) with respect to the field,
+// for a fixed diagram and matching, in fp64: a point matched to target t
+// contributes 2 (b - t_b) at v_b and 2 (d - t_d) at v_d (the essential class
+// too), a diagonal-matched point b - d at v_b and d - b at v_d.  Per vertex
+// the contributions are added in diagram order, birth before death.
+// ---------------------------------------------------------------------------
+struct Grad64 {
+  uint32_t v;
+  uint32_t idx;  // 2 * point + (0 birth, 1 death)
+  double g;
+};
+static_assert(sizeof(Grad64) == sizeof(Contrib), "gradient entries reuse the contribution buffer");
+
+__global__ void k_loss_grad_contrib(int np, const Pt* __restrict__ pts, const Tg* __restrict__ T,
+                                    Grad64* __restrict__ G) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const Pt& p = pts[i];
+  double b = (double)p.b, d = (double)p.d, gb, gd;
+  if (p.tgt >= 0) {
+    gb = __dmul_rn(2.0, __dsub_rn(b, (double)T[p.tgt].b));
+    gd = __dmul_rn(2.0, __dsub_rn(d, (double)T[p.tgt].d));
+  } else {
+    gb = __dsub_rn(b, d);
+    gd = __dsub_rn(d, b);
+  }
+  G[2 * i].v = p.vb;
+  G[2 * i].idx = 2u * (uint32_t)i;
+  G[2 * i].g = gb;
+  G[2 * i + 1].v = p.vd;
+  G[2 * i + 1].idx = 2u * (uint32_t)i + 1u;
+  G[2 * i + 1].g = gd;
+}
+
+struct Grad64Less {
+  const Grad64* c;
+  __device__ unsigned long long key(int i) const { return ((unsigned long long)c[i].v << 32) | c[i].idx; }
+  __device__ bool operator()(int a, int b) const { return key(a) < key(b); }
+};
+
+__global__ void k_loss_grad_apply(int n, const int32_t* __restrict__ idx, const Grad64* __restrict__ G,
+                                  double* __restrict__ grad) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  uint32_t v = G[idx[r]].v;
+  if (r > 0 && G[idx[r - 1]].v == v) return;
+  double acc = 0.0;
+  for (int s = r; s < n && G[idx[s]].v == v; ++s) acc = __dadd_rn(acc, G[idx[s]].g);
+  grad[v] = acc;
+}
+
+void loss_gradient(int np, const Pt* pts, const Tg* T, SolverBufs& B, double* grad, int64_t nv, cudaStream_t st) {
+  cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)nv, st);
+  if (np == 0) return;
+  Grad64* G = reinterpret_cast<Grad64*>(B.contrib);
+  k_loss_grad_contrib<<<(np + 255) / 256, 256, 0, st>>>(np, pts, T, G); note_launch();
+  int32_t* idx = merge_sort(2 * np, B.idxA, B.idxB, Grad64Less{G}, st);
+  k_loss_grad_apply<<<(2 * np + 255) / 256, 256, 0, st>>>(2 * np, idx, G, grad); note_launch();
+}
+
+// New field values: copies the changed ones and lists their vertices, so
+// that the next diagram can be updated incrementally (Section 4.2).
+__global__ void k_replace_values(int64_t nv, const float* __restrict__ in, float* __restrict__ f,
+                                 uint32_t* __restrict__ upd, unsigned long long* __restrict__ count) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  float x = in[v];
+  if (__float_as_uint(x) != __float_as_uint(f[v])) {
+    f[v] = x;
+    upd[atomicAdd(count, 1ull)] = (uint32_t)v;
+  }
+}
+
+void replace_values(int64_t nv, const float* in, float* f, uint32_t* upd, unsigned long long* count,
+                    cudaStream_t st) {
+  cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  k_replace_values<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(nv, in, f, upd, count); note_launch();
+}
+
 void targets_as_points(int nt, const Tg* T, Pt* R, cudaStream_t st) {
   if (nt > 0) k_targets_as_points<<<(nt + 255) / 256, 256, 0, st>>>(nt, T, R); note_launch();
 }

@@ -70,6 +70,8 @@ struct tsf_field {
   // fast persistence update (Section 4.2): vertices the last step updated,
   // the lower stars to recompute (listed once each by generation marks)
   uint32_t *upd = nullptr, *gmark = nullptr, *glist = nullptr;
+  double* lgrad = nullptr;  // dL/df of the topological loss (allocated on first use)
+  float* lstage = nullptr;  // host values staged on the device for it
   uint32_t ggen = 0;
   uint32_t *cidx = nullptr, *c1base = nullptr, *c2base = nullptr;
   int4 *tile_counts = nullptr, *totals = nullptr;
@@ -673,6 +675,8 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->ubits);
   dev_free(F->ucnt);
   dev_free(F->ordB);
+  dev_free(F->lgrad);
+  dev_free(F->lstage);
   dev_free(F->upd);
   dev_free(F->gmark);
   dev_free(F->glist);
@@ -956,6 +960,46 @@ int tsf_simplify(tsf_field* F, const tsf_params* p, float* out_values, int out_o
       ck(cudaMemcpyAsync(out_values, F->f, sizeof(float) * F->d.nv,
                          out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, F->st));
     ck(cudaStreamSynchronize(F->st));
+    return TSF_OK;
+  });
+}
+
+int tsf_loss_and_gradient(tsf_field* F, const float* values, int values_on_device, double* loss, double* grad,
+                          int grad_on_device) {
+  if (!F || !values || !loss) return TSF_EINVAL;
+  if (!F->have_targets) return TSF_ENOTARGET;
+  return guarded_f(F, [&]() {
+    // the new values replace the field's; the vertices they change are
+    // listed, so the diagram follows them incrementally (Section 4.2) where
+    // the previous order and records are those of the current values
+    const float* in = values;
+    if (!values_on_device) {
+      if (!F->lstage) ck(dev_alloc(&F->lstage, (size_t)F->d.nv));
+      ck(cudaMemcpyAsync(F->lstage, values, sizeof(float) * F->d.nv, cudaMemcpyHostToDevice, F->st));
+      in = F->lstage;
+    }
+    replace_values(F->d.nv, in, F->f, F->upd, F->counter, F->st);
+    unsigned long long nchanged = 0;
+    ck(cudaMemcpyAsync(&nchanged, F->counter, sizeof(nchanged), cudaMemcpyDeviceToHost, F->st));
+    ck(cudaStreamSynchronize(F->st));
+    F->n_updated = (int64_t)nchanged;
+    F->upd_valid = true;
+    std::swap(F->pts, F->prev);  // the previous diagram is not consulted
+    F->nprev = F->np;
+    int r = compute_diagram(F, true);
+    if (r) return r;
+    r = run_assign(F, F->prev, 0);
+    if (r) return r;
+    eval(F, 0.0f);
+    *loss = F->loss;
+    if (grad) {
+      if (!F->lgrad) ck(dev_alloc(&F->lgrad, (size_t)F->d.nv));
+      loss_gradient(F->np, F->pts, F->T, F->B, F->lgrad, F->d.nv, F->st);
+      ck(cudaMemcpyAsync(grad, F->lgrad, sizeof(double) * F->d.nv,
+                         grad_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, F->st));
+    }
+    ck(cudaStreamSynchronize(F->st));
+    ck(cudaGetLastError());
     return TSF_OK;
   });
 }

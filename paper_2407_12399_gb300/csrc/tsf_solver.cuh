@@ -97,6 +97,13 @@ int build_diagram(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1,
                   const uint32_t* order, const float* f, SolverBufs& B, Pt* out, int cap, cudaStream_t st);
 int make_targets(int np, const Pt* pts, float theta, SolverBufs& B, Tg* T, cudaStream_t st);
 void targets_as_points(int nt, const Tg* T, Pt* R, cudaStream_t st);
+// f[v] = in[v] where they differ, the changed vertices listed in upd, their
+// number in *count.
+void replace_values(int64_t nv, const float* in, float* f, uint32_t* upd, unsigned long long* count,
+                    cudaStream_t st);
+// dL/df (fp64, nv entries) of the topological loss for the current points
+// and their matching.
+void loss_gradient(int np, const Pt* pts, const Tg* T, SolverBufs& B, double* grad, int64_t nv, cudaStream_t st);
 int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBufs& B, uint32_t* status,
            AssignStats* as, cudaStream_t st);
 void loss_and_counts(int np, const Pt* pts, int nt, const Tg* T, float cancel_eps, SolverBufs& B, double* h_loss,
