@@ -1074,24 +1074,51 @@ static_assert(kFrontA + kStageA <= kStageB, "a phase A handoff fits phase B's st
 static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + scap) * sizeof(FEnt); }
 
 // Phase 2 (one block): reduce the Morse boundaries, smallest column owning
-// each low; every addition is of an earlier column.
+// each low; every addition is of an earlier column.  Rounds of two phases:
+// every listed column claims its low (atomicMin), then every listed column
+// that does not own its low adds the owner's column (owners do not change in
+// that phase) and is listed again.  A settled owner that a smaller column
+// displaces is listed for the next round; columns not listed own their lows
+// and stay as they are, so a round costs as much as its list.
+__device__ __forceinline__ void d1_list_push(int32_t* next, int* n_next, int32_t* mark, int j, int round) {
+  if (atomicExch(&mark[j], round) != round) next[atomicAdd(n_next, 1)] = j;
+}
+
 __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d1_edge, uint32_t* status) {
   const int ncols = W.flags[1];
-  __shared__ int changed;
+  // free per-column scratch by now: two lists and a "listed in round" mark
+  int32_t* listA = W.lowc;
+  int32_t* listB = reinterpret_cast<int32_t*>(W.hcap);
+  int32_t* mark = W.redo;
+  __shared__ int s_na, s_nb;
   for (int k = threadIdx.x; k < n1; k += kUFT) W.owner[k] = 0x7FFFFFFF;
+  if (threadIdx.x == 0) s_na = 0;
   __syncthreads();
+  for (int j = threadIdx.x; j < ncols; j += kUFT) {
+    mark[j] = -1;
+    if (W.hsize[j] > 0) listA[atomicAdd(&s_na, 1)] = j;
+  }
+  __syncthreads();
+  int32_t* cur = listA;
+  int32_t* nxt = listB;
   for (int round = 0;; ++round) {
+    int na = s_na;
+    if (na == 0) break;
     if (round > ncols + 2) {
       if (threadIdx.x == 0) atomicOr(status, kErrRounds);
       break;
     }
-    if (threadIdx.x == 0) changed = 0;
-    for (int j = threadIdx.x; j < ncols; j += kUFT)
-      if (W.hsize[j] > 0) atomicMin(&W.owner[(int)W.pool[W.hoff[j]]], j);
+    if (threadIdx.x == 0) s_nb = 0;
     __syncthreads();
-    for (int j = threadIdx.x; j < ncols; j += kUFT) {
+    for (int i = threadIdx.x; i < na; i += kUFT) {
+      int j = cur[i];
+      int old = atomicMin(&W.owner[(int)W.pool[W.hoff[j]]], j);
+      if (old > j && old != 0x7FFFFFFF) d1_list_push(nxt, &s_nb, mark, old, round);  // displaced owner
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < na; i += kUFT) {
+      int j = cur[i];
       uint32_t n = W.hsize[j];
-      if (n == 0) continue;
       const unsigned long long* a = W.pool + W.hoff[j];
       int o = W.owner[(int)a[0]];
       if (o == j) continue;
@@ -1104,26 +1131,28 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
         continue;
       }
       unsigned long long* d = W.pool + off;
-      uint32_t i = 0, k = 0, m = 0;
-      while (i < n && k < no) {  // both decreasing: symmetric difference
-        if (a[i] > b[k]) d[m++] = a[i++];
-        else if (b[k] > a[i]) d[m++] = b[k++];
+      uint32_t x = 0, y = 0, m = 0;
+      while (x < n && y < no) {  // both decreasing: symmetric difference
+        if (a[x] > b[y]) d[m++] = a[x++];
+        else if (b[y] > a[x]) d[m++] = b[y++];
         else {
-          ++i;
-          ++k;
+          ++x;
+          ++y;
         }
       }
-      while (i < n) d[m++] = a[i++];
-      while (k < no) d[m++] = b[k++];
-      if (m == 0) atomicOr(status, kErrEmptyColumn);
+      while (x < n) d[m++] = a[x++];
+      while (y < no) d[m++] = b[y++];
       W.hoff[j] = off;
       W.hsize[j] = m;
-      changed = 1;
+      if (m == 0) atomicOr(status, kErrEmptyColumn);
+      else d1_list_push(nxt, &s_nb, mark, j, round);
     }
     __syncthreads();
-    int ch = changed;
+    if (threadIdx.x == 0) s_na = s_nb;
+    int32_t* t = cur;
+    cur = nxt;
+    nxt = t;
     __syncthreads();
-    if (!ch) break;
   }
   for (int j = threadIdx.x; j < ncols; j += kUFT)
     d1_edge[W.cols[j]] = W.hsize[j] > 0 ? (int)W.pool[W.hoff[j]] : -1;
