@@ -110,6 +110,44 @@ def make_field():
     return synthetic.filament_field(SHAPE, seed=1)
 
 
+def differentiable_loss(evals=10):
+    """Differentiable topological loss (96^3 Gaussian mixture, 32 bumps, 5 %
+    noise; signal >= 0.1 of the range; the field is moved by U(-0.005, 0.005)
+    so signal pairs have a non-zero gradient): device time of one
+    tsf_loss_and_gradient call on the whole field, and of a call after one
+    vertex value changed (the diagram follows the change incrementally)."""
+    import torch
+
+    import paper_2407_12399_gb300 as tsf
+    from paper_2407_12399_gb300 import synthetic as S
+    f0 = S.mixture_96()
+    rng = np.random.default_rng(7)
+    f = (f0 + rng.uniform(-0.005, 0.005, f0.shape)).astype(np.float32)
+    fld = tsf.Field(torch.from_numpy(f0).cuda())
+    fld.set_threshold(0.1)
+    ft = torch.from_numpy(f).cuda()
+    gt = torch.empty(f.shape, dtype=torch.float64, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    loss, _ = fld.loss_and_grad(ft, gt)
+    ev1.record()
+    torch.cuda.synchronize()
+    first = ev0.elapsed_time(ev1)
+    flat = ft.view(-1)
+    times = []
+    for k in range(evals):
+        flat[1000 + 37 * k] += 1e-3
+        ev0.record()
+        fld.loss_and_grad(ft, gt)
+        ev1.record()
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+    st = fld.step(stop_s=0.0)
+    return {"workload": "mixture_96", "grid": [96, 96, 96], "signal_threshold": 0.1, "loss": loss,
+            "points": int(st["n_points"]), "ms_full_evaluation": first,
+            "ms_after_one_change": float(np.median(times)), "evaluations_per_s": 1e3 / float(np.median(times))}
+
+
 def cpu_baseline(f0, steps=2):
     """The oracle as it stands, single-threaded, on the 64^3 corner crop."""
     import oracle
@@ -301,6 +339,8 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
     }
+    if not args.no_loss:
+        line["differentiable_loss"] = differentiable_loss()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(f0)
     print(json.dumps(line))
@@ -324,6 +364,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end solve (short profiling runs)")
+    ap.add_argument("--no-loss", action="store_true", help="skip the differentiable-loss measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
