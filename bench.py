@@ -267,9 +267,33 @@ def run_gpu(args):
         tts = time.perf_counter() - t
         tsf.tsf_destroy_field(h)
         iters = max(st.iters, 1)
+        diff = out.astype(np.float64) - host.astype(np.float64)
         e2e = {"value": iters / tts, "unit": UNIT, "h2d_bytes_per_step": int(4 * nv / iters),
                "d2h_bytes_per_step": int(4 * nv / iters), "iterations": int(st.iters),
-               "time_to_simplified_field_s": tts, "stop_rule": "loss <= 0.01 loss_0 (Algorithm 1)"}
+               "time_to_simplified_field_s": tts, "stop_rule": "loss <= 0.01 loss_0 (Algorithm 1)",
+               "loss0": float(st.loss0), "final_loss": float(st.loss),
+               "non_signal_remaining": int(st.n_uncancelled), "still_fraction_last": float(st.n_still) / max(st.n_points, 1),
+               "l2_change": float(np.sqrt((diff ** 2).sum())), "linf_change": float(np.abs(diff).max())}
+
+    # Section 4.2 / 4.3 ablation (the paper's Table 2 analogue): the same
+    # solve with each acceleration on or off
+    ablation = None
+    if rank == 0 and not args.no_e2e and not args.no_ablation:
+        host = np.ascontiguousarray(f0)
+        ablation = {}
+        for fg in (1, 0):
+            for fa in (1, 0):
+                h = tsf.tsf_create_field(SHAPE[2], SHAPE[1], SHAPE[0], host.ctypes.data, 0, stream.cuda_stream)
+                tsf.tsf_set_signal_threshold(h, TAU)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                st = tsf.tsf_simplify(h, tsf.params(stop_s=0.01, fast_gradient_update=fg, fast_assignment_update=fa),
+                                      None, 0)
+                dt = time.perf_counter() - t
+                tsf.tsf_destroy_field(h)
+                ablation[f"gradient_update_{'fast' if fg else 'full'}/assignment_{'reuse' if fa else 'full'}"] = {
+                    "iterations": int(st.iters), "solve_s": dt, "iters_per_s": int(st.iters) / dt,
+                    "final_loss": float(st.loss)}
 
     if rank != 0:
         if world > 1:
@@ -339,6 +363,8 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
     }
+    if ablation is not None:
+        line["ablation"] = ablation
     if not args.no_loss:
         line["differentiable_loss"] = differentiable_loss()
     if not args.no_cpu_baseline:
@@ -353,7 +379,7 @@ def run_gpu(args):
 # diagram of this workload, from an ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum), or None while the kernel
 # has changed since the last capture.
-D1_TRAFFIC = None
+D1_TRAFFIC = 59.46e6  # phase A 23.42 MB + 0.02 MB, phase B 35.93 MB + 0.09 MB
 
 
 def main():
@@ -365,6 +391,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end solve (short profiling runs)")
     ap.add_argument("--no-loss", action="store_true", help="skip the differentiable-loss measurement")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the Section 4.2/4.3 on/off solves")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
