@@ -79,8 +79,13 @@ typedef struct {
  *   identical either way.
  * fast_assignment_update: 1 lets still pairs keep their previous assignment
  *   and matches only the others (Section 4.3); 0 matches every point of the
- *   new diagram with the exact solver.  The j = 0 assignment is the identity
- *   either way. */
+ *   new diagram with the solver.  The j = 0 assignment is the identity
+ *   either way.
+ * assignment_precision: 0 solves each reduced assignment exactly (shortest
+ *   augmenting paths); p > 0 uses the Auction algorithm, as the paper's
+ *   implementation does (Section 5, p = 0.01), whose reduced W2^2 is within
+ *   a factor (1 + p) of the minimum: much faster when many targets compete
+ *   for the same points.  Deterministic either way.  Must be finite, >= 0. */
 typedef struct {
   float alpha_b, alpha_d;
   float stop_s;
@@ -88,6 +93,7 @@ typedef struct {
   int32_t max_iters;
   int32_t fast_gradient_update;
   int32_t fast_assignment_update;
+  float assignment_precision;
 } tsf_params;
 
 /* Per-iteration statistics. */
@@ -175,6 +181,34 @@ int tsf_get_field(tsf_field* field, float* out, int out_on_device);
  * Errors: TSF_EINVAL, TSF_ENOTARGET before a target was set, TSF_ENAN. */
 int tsf_loss_and_gradient(tsf_field* field, const float* values, int values_on_device, double* loss,
                           double* grad, int grad_on_device);
+
+/* A batch of independent fields solved together.  The paper solves one
+ * field at a time (Algorithm 1); a batch runs many such solves at once:
+ * every field gets its own non-blocking CUDA stream and one host thread of
+ * a small pool drives it, so the kernels of different fields run
+ * concurrently.  Each field's iteration is exactly tsf_solver_step /
+ * tsf_simplify on it, so a field's result does not depend on its batch.
+ *
+ * tsf_batch_create: n fields, field i of lx[i]*ly[i]*lz[i] values copied
+ *   from values[i] (host or device); the batch owns fields and streams.
+ *   Errors: TSF_EINVAL, TSF_ENOMEM, TSF_ECUDA, TSF_ENAN.
+ * tsf_batch_field: the i-th field (owned by the batch; use it with the
+ *   single-field calls, but not while a batch call runs).
+ * tsf_batch_set_signal_thresholds: tsf_set_signal_threshold(field i,
+ *   fractions[i]) for every field, concurrently.
+ * tsf_batch_step: one tsf_solver_step of every field; stats (may be NULL)
+ *   has n entries.  tsf_batch_simplify: tsf_simplify of every field (no
+ *   copy-out; read fields with tsf_get_field).  Both return the first
+ *   non-zero status of the fields, after all of them finished. */
+typedef struct tsf_batch tsf_batch;
+int tsf_batch_create(int n, const int* lx, const int* ly, const int* lz, const float* const* values,
+                     int values_on_device, tsf_batch** out);
+int tsf_batch_destroy(tsf_batch* batch);
+int tsf_batch_size(const tsf_batch* batch);
+int tsf_batch_field(tsf_batch* batch, int i, tsf_field** out);
+int tsf_batch_set_signal_thresholds(tsf_batch* batch, const float* fractions);
+int tsf_batch_step(tsf_batch* batch, const tsf_params* params, tsf_stats* stats);
+int tsf_batch_simplify(tsf_batch* batch, const tsf_params* params, tsf_stats* stats);
 
 /* Overwrites the current values (restart from a saved field; the still-pair
  * history is reset, so the next assignment starts cold). */

@@ -67,6 +67,8 @@ def lib():
         L.or_solver_done.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_int]
         L.or_solver_set_fast_assignment.restype = None
         L.or_solver_set_fast_assignment.argtypes = [P, ctypes.c_int]
+        L.or_solver_set_assignment_precision.restype = None
+        L.or_solver_set_assignment_precision.argtypes = [P, ctypes.c_double]
         L.or_solver_loss_grad.restype = ctypes.c_int
         L.or_solver_loss_grad.argtypes = [P, P, P, P]
         L.or_solver_field.argtypes = [P, P]
@@ -80,6 +82,8 @@ def lib():
         L.or_solver_free.argtypes = [P]
         L.or_assign.restype = ctypes.c_double
         L.or_assign.argtypes = [I64, P, P, I64, P, P, P]
+        L.or_assign_prec.restype = ctypes.c_double
+        L.or_assign_prec.argtypes = [I64, P, P, I64, P, P, ctypes.c_double, P]
         _lib = L
     return _lib
 
@@ -138,22 +142,31 @@ def diagram(f, with_zero: bool = False, with_filtration: bool = False):
         L.or_diagram_free(h)
 
 
-def assign(pb, pd, tb, td):
-    """Exact reduced assignment of one finite group; returns (targets, W2^2)."""
+def _prec(p):
+    """The precision as the solver sees it: a float32 parameter widened to fp64."""
+    return float(np.float32(p))
+
+
+def assign(pb, pd, tb, td, precision=0.0):
+    """Reduced assignment of one finite group, exact (precision 0) or by the
+    auction at that relative precision; returns (targets, W2^2)."""
     L = lib()
     pb = np.ascontiguousarray(pb, np.float32)
     pd = np.ascontiguousarray(pd, np.float32)
     tb = np.ascontiguousarray(tb, np.float32)
     td = np.ascontiguousarray(td, np.float32)
     out = np.zeros(len(pb), np.int32)
-    cost = L.or_assign(len(pb), _ptr(pb), _ptr(pd), len(tb), _ptr(tb), _ptr(td), _ptr(out))
+    cost = L.or_assign_prec(len(pb), _ptr(pb), _ptr(pd), len(tb), _ptr(tb), _ptr(td), ctypes.c_double(_prec(precision)),
+                            _ptr(out))
+    if cost < 0:
+        raise RuntimeError("oracle auction did not finish")
     return out, cost
 
 
 class Solver:
     """Algorithm 1 with Sections 4.1 and 4.3, on the CPU, one iteration at a time."""
 
-    def __init__(self, f0, tau=None, targets=None, fast_assignment=True):
+    def __init__(self, f0, tau=None, targets=None, fast_assignment=True, assignment_precision=0.0):
         L = lib()
         f0, lx, ly, lz = _field(f0)
         self.shape = f0.shape
@@ -171,6 +184,7 @@ class Solver:
             raise ValueError(f"oracle solver failed (status {st.value})")
         self._h = h
         L.or_solver_set_fast_assignment(h, 1 if fast_assignment else 0)
+        L.or_solver_set_assignment_precision(h, ctypes.c_double(_prec(assignment_precision)))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -32,6 +32,7 @@
  */
 #include "oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -476,6 +477,7 @@ struct or_solver {
   double loss, loss0;
   int64_t n_unc, n_still, n_updated, n_nssp;
   int fast_assign; /* Section 4.3 still-pair reuse after each step (default on) */
+  double assign_prec; /* 0: exact reduced assignment; > 0: auction at this relative precision */
 };
 
 /* Diagram order: increasing birth, then death (Section 2.4); the remaining
@@ -583,10 +585,14 @@ static int cmp_cand(const void* a, const void* b) {
  * augmenting path method (Hungarian algorithm with potentials), rows in target
  * order, ties to the lowest column index.
  */
-static void assign_group(int64_t np, const float* pb, const float* pd, int64_t nt, const float* tb,
-                         const float* td, int32_t* out) {
+static int auction_rows(int64_t k, int64_t np, const int64_t* cand_p, const double* cand_w, const int64_t* ncand,
+                        const float* pb, const float* pd, const float* tb, const float* td, double prec,
+                        int32_t* out);
+
+static int assign_group(int64_t np, const float* pb, const float* pd, int64_t nt, const float* tb,
+                        const float* td, double prec, int32_t* out) {
   for (int64_t i = 0; i < np; ++i) out[i] = -1;
-  if (nt == 0 || np == 0) return;
+  if (nt == 0 || np == 0) return 0;
   int64_t k = nt;
   cand_t* buf = (cand_t*)malloc(sizeof(cand_t) * np);
   int64_t* cand_p = (int64_t*)malloc(sizeof(int64_t) * k * k);
@@ -612,6 +618,15 @@ static void assign_group(int64_t np, const float* pb, const float* pd, int64_t n
       is_col[buf[i].p] = 1;
     }
     ncand[t] = keep;
+  }
+  if (prec > 0.0) {
+    int st = auction_rows(k, np, cand_p, cand_w, ncand, pb, pd, tb, td, prec, out);
+    free(buf);
+    free(cand_p);
+    free(cand_w);
+    free(ncand);
+    free(is_col);
+    return st;
   }
   /* columns: candidate points in point order, then k private diagonal columns */
   int64_t mc = 0;
@@ -693,11 +708,202 @@ static void assign_group(int64_t np, const float* pb, const float* pd, int64_t n
   free(pm);
   free(way);
   free(used);
+  return 0;
+}
+
+/*
+ * Approximate reduced assignment by the Auction algorithm (Bertsekas; the
+ * paper's implementation, Section 5, runs it at relative precision 0.01),
+ * on the same rows (targets in order) and options (kept candidates, then
+ * the private diagonal column, which comes after every point column) as the
+ * exact solve.  Net cost of an option: w(r,j) + price(j).
+ *
+ * Forward auction in synchronous (Jacobi) rounds:
+ *   - every unassigned row r finds its lowest net cost n1 (ties: lowest
+ *     column) at column j1 and the lowest net cost n2 among its other
+ *     options, and bids price(j1) + ((n2 - n1) + eps) for j1;
+ *   - each point column takes its highest bid (ties: lowest row), its price
+ *     becomes that bid, its previous row is unassigned; a bid for the row's
+ *     own diagonal always wins;
+ * until every row is assigned.  A row with no candidate takes its diagonal.
+ *
+ * eps-scaling: eps starts at max diag(t) / 4 and is divided by 5 per
+ * phase.  Each later phase keeps the previous assignment and prices, except
+ * that (repeatedly, until nothing changes) every column without a row gets
+ * price 0 and every row whose net cost exceeds its lowest one by more than
+ * the new eps is released.  So at the end of a phase every column without a
+ * row has price 0 (a column once bid on keeps a row) and the prices give the
+ * dual bound LB = sum_r min_j (w(r,j) + price(j)) - sum_j price(j) <= the
+ * optimum, with W - LB <= k * eps for the assignment's cost W.  The auction
+ * stops after the first phase with W + D <= (1 + prec) (LB + D), D the sum
+ * of diag(p) over the points (so the reduced W2^2 is within a factor
+ * (1 + prec) of its minimum), or once eps reaches 2^-40 max diag(t).  Sums
+ * run in row order, prices in column order (points, then diagonals).
+ * Returns 0, or -1 if 2^24 rounds did not finish.
+ */
+static int auction_rows(int64_t k, int64_t np, const int64_t* cand_p, const double* cand_w, const int64_t* ncand,
+                        const float* pb, const float* pd, const float* tb, const float* td, double prec,
+                        int32_t* out) {
+  const double INF = HUGE_VAL;
+  double* diag_t = (double*)malloc(sizeof(double) * k);
+  double* price = (double*)calloc(np + k, sizeof(double)); /* point columns, then diagonals */
+  int64_t* owner = (int64_t*)malloc(sizeof(int64_t) * np);
+  int64_t* rowcol = (int64_t*)malloc(sizeof(int64_t) * k);
+  int64_t* bcol = (int64_t*)malloc(sizeof(int64_t) * k);
+  double* bid = (double*)malloc(sizeof(double) * k);
+  int64_t* win = (int64_t*)malloc(sizeof(int64_t) * np);
+  double* best = (double*)malloc(sizeof(double) * np);
+  uint8_t* viol = (uint8_t*)malloc(k);
+  double dsum = 0.0, cmax = 0.0;
+  for (int64_t r = 0; r < k; ++r) {
+    diag_t[r] = cost_diag(tb[r], td[r]);
+    if (diag_t[r] > cmax) cmax = diag_t[r];
+    rowcol[r] = ncand[r] > 0 ? -1 : np + r;
+  }
+  for (int64_t p = 0; p < np; ++p) {
+    dsum += cost_diag(pb[p], pd[p]);
+    owner[p] = -1;
+    win[p] = -1;
+  }
+  double emin = ldexp(cmax, -40);
+  if (!(emin > 0.0)) emin = DBL_MIN;
+  double eps = cmax * 0.25;
+  if (eps < emin) eps = emin;
+  const double onep = 1.0 + prec;
+  int st = 0;
+  int64_t rounds = 0;
+  for (int phase = 0;; ++phase) {
+    if (phase > 0) {
+      for (;;) { /* release the rows that break eps-complementary slackness */
+        for (int64_t p = 0; p < np; ++p)
+          if (owner[p] < 0) price[p] = 0.0;
+        for (int64_t r = 0; r < k; ++r)
+          if (rowcol[r] != np + r) price[np + r] = 0.0;
+        int64_t nviol = 0;
+        for (int64_t r = 0; r < k; ++r) {
+          viol[r] = 0;
+          if (rowcol[r] < 0) continue; /* released earlier in this cascade */
+          double n1 = INF, cur = INF;
+          for (int64_t c = 0; c <= ncand[r]; ++c) {
+            int64_t j = c < ncand[r] ? cand_p[r * k + c] : np + r;
+            double w = c < ncand[r] ? cand_w[r * k + c] : diag_t[r];
+            double n = w + price[j];
+            if (n < n1) n1 = n;
+            if (j == rowcol[r]) cur = n;
+          }
+          double lim = n1 + eps;
+          if (cur > lim) {
+            viol[r] = 1;
+            ++nviol;
+          }
+        }
+        if (nviol == 0) break;
+        for (int64_t r = 0; r < k; ++r) {
+          if (!viol[r]) continue;
+          if (rowcol[r] < np) owner[rowcol[r]] = -1;
+          rowcol[r] = -1;
+        }
+      }
+    }
+    for (;; ++rounds) {
+      if (rounds >= ((int64_t)1 << 24)) {
+        st = -1;
+        break;
+      }
+      int64_t nun = 0;
+      for (int64_t r = 0; r < k; ++r) {
+        bcol[r] = -1;
+        if (rowcol[r] >= 0) continue;
+        ++nun;
+        double n1 = INF, n2 = INF;
+        int64_t j1 = -1;
+        for (int64_t c = 0; c <= ncand[r]; ++c) {
+          int64_t j = c < ncand[r] ? cand_p[r * k + c] : np + r;
+          double w = c < ncand[r] ? cand_w[r * k + c] : diag_t[r];
+          double n = w + price[j];
+          if (n < n1 || (n == n1 && j < j1)) {
+            n2 = n1;
+            n1 = n;
+            j1 = j;
+          } else if (n < n2) {
+            n2 = n;
+          }
+        }
+        double g = n2 - n1;
+        g = g + eps;
+        bid[r] = price[j1] + g;
+        bcol[r] = j1;
+      }
+      if (nun == 0) break;
+      for (int64_t r = 0; r < k; ++r) {
+        int64_t j = bcol[r];
+        if (j < 0) continue;
+        if (j >= np) { /* the row's own diagonal: no competition */
+          price[j] = bid[r];
+          rowcol[r] = j;
+          bcol[r] = -1;
+        } else if (win[j] < 0 || bid[r] > best[j]) { /* rows in increasing order: ties keep the lower */
+          win[j] = r;
+          best[j] = bid[r];
+        }
+      }
+      for (int64_t r = 0; r < k; ++r) {
+        int64_t j = bcol[r];
+        if (j < 0 || win[j] != r) continue;
+        if (owner[j] >= 0) rowcol[owner[j]] = -1;
+        owner[j] = r;
+        rowcol[r] = j;
+        price[j] = bid[r];
+      }
+      for (int64_t r = 0; r < k; ++r)
+        if (bcol[r] >= 0) win[bcol[r]] = -1;
+    }
+    if (st) break;
+    /* phase end: the assignment's cost W and the dual bound LB */
+    double W = 0.0, U = 0.0, P = 0.0;
+    for (int64_t r = 0; r < k; ++r) {
+      double n1 = INF, wcur = INF;
+      for (int64_t c = 0; c <= ncand[r]; ++c) {
+        int64_t j = c < ncand[r] ? cand_p[r * k + c] : np + r;
+        double w = c < ncand[r] ? cand_w[r * k + c] : diag_t[r];
+        double n = w + price[j];
+        if (n < n1) n1 = n;
+        if (j == rowcol[r]) wcur = w;
+      }
+      W += wcur;
+      U += n1;
+    }
+    for (int64_t j = 0; j < np + k; ++j) P += price[j];
+    double lb = U - P;
+    double lhs = W + dsum;
+    double rhs = lb + dsum;
+    rhs = rhs * onep;
+    if (lhs <= rhs || !(eps > emin)) break;
+    eps = eps / 5.0;
+    if (eps < emin) eps = emin;
+  }
+  if (st == 0)
+    for (int64_t p = 0; p < np; ++p) out[p] = owner[p] >= 0 ? (int32_t)owner[p] : -1;
+  free(diag_t);
+  free(price);
+  free(owner);
+  free(rowcol);
+  free(bcol);
+  free(bid);
+  free(win);
+  free(best);
+  free(viol);
+  return st;
 }
 
 double or_assign(int64_t np, const float* pb, const float* pd, int64_t nt, const float* tb, const float* td,
                  int32_t* out_tgt) {
-  assign_group(np, pb, pd, nt, tb, td, out_tgt);
+  return or_assign_prec(np, pb, pd, nt, tb, td, 0.0, out_tgt);
+}
+
+double or_assign_prec(int64_t np, const float* pb, const float* pd, int64_t nt, const float* tb, const float* td,
+                      double prec, int32_t* out_tgt) {
+  if (assign_group(np, pb, pd, nt, tb, td, prec, out_tgt)) return -1.0;
   double total = 0.0;
   uint8_t* taken = (uint8_t*)calloc(nt + 1, 1);
   for (int64_t i = 0; i < np; ++i) {
@@ -750,7 +956,8 @@ static int key_cmp4(int32_t ea, int32_t da, uint32_t ba, uint32_t xa, int32_t eb
  * At j = 0 the reference list is the target diagram itself, each target
  * "assigned" to itself: with a threshold this is the identity (Section 4.3).
  */
-static void assign_points(or_solver* s, const opoint_t* R, int64_t nr, int r_is_targets) {
+static int assign_points(or_solver* s, const opoint_t* R, int64_t nr, int r_is_targets, double prec) {
+  int status = 0;
   int64_t np = s->np;
   opoint_t* P = s->P;
   int64_t* ip = (int64_t*)malloc(sizeof(int64_t) * (np + 1));
@@ -809,7 +1016,7 @@ static void assign_points(or_solver* s, const opoint_t* R, int64_t nr, int r_is_
       for (int64_t i = 0; i < n1 && i < n2; ++i) P[pidx[i]].tgt = (int32_t)tidx[i];
       continue;
     }
-    assign_group(n1, pb, pd, n2, tb, td, res);
+    if (assign_group(n1, pb, pd, n2, tb, td, prec, res)) status = -1;
     for (int64_t i = 0; i < n1; ++i) P[pidx[i]].tgt = res[i] >= 0 ? (int32_t)tidx[res[i]] : -1;
   }
   free(pb);
@@ -822,6 +1029,7 @@ static void assign_points(or_solver* s, const opoint_t* R, int64_t nr, int r_is_
   free(taken);
   free(ip);
   free(ir);
+  return status;
 }
 
 /* W2^2 of the current assignment (Eq. 2) and the stop counters. */
@@ -951,6 +1159,7 @@ static or_solver* solver_alloc(int lx, int ly, int lz, const float* f0, int* sta
 
 static void solver_start(or_solver* s) {
   s->fast_assign = 1;
+  s->assign_prec = 0.0;
   qsort(s->T, s->nt, sizeof(otarget_t), cmp_target);
   /* j = 0: the targets play the previous diagram, each assigned to itself */
   opoint_t* R = (opoint_t*)malloc(sizeof(opoint_t) * (s->nt + 1));
@@ -966,7 +1175,7 @@ static void solver_start(or_solver* s) {
     R[t].tgt = (int32_t)t;
     R[t].still = 0;
   }
-  assign_points(s, R, s->nt, 1);
+  assign_points(s, R, s->nt, 1, 0.0); /* the j = 0 problem is solved exactly */
   free(R);
   s->j = 0;
   eval_loss(s);
@@ -1078,14 +1287,17 @@ int or_solver_iterate(or_solver* s, float alpha_b, float alpha_d, float stop_s, 
   }
   /* without the Section 4.3 reuse no point of the previous diagram is
    * consulted: every point is matched by the exact solver */
-  assign_points(s, prev, s->fast_assign ? nprev : 0, 0);
+  int ast = assign_points(s, prev, s->fast_assign ? nprev : 0, 0, s->assign_prec);
   free(prev);
+  if (ast) return -4;
   s->j += 1;
   eval_loss(s);
   return or_solver_done(s, stop_s, cancel_eps, max_iters);
 }
 
 void or_solver_set_fast_assignment(or_solver* s, int on) { s->fast_assign = on ? 1 : 0; }
+
+void or_solver_set_assignment_precision(or_solver* s, double prec) { s->assign_prec = prec > 0.0 ? prec : 0.0; }
 
 /*
  * Topological loss of the field `values` against the solver's target
@@ -1110,7 +1322,7 @@ int or_solver_loss_grad(or_solver* s, const float* values, double* loss, double*
     return st;
   }
   free(prev);
-  assign_points(s, NULL, 0, 0);
+  assign_points(s, NULL, 0, 0, 0.0);
   eval_loss(s);
   *loss = s->loss;
   memset(grad, 0, sizeof(double) * s->g.nv);

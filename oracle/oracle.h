@@ -14,8 +14,9 @@
  *     plus the essential class at (f(v_min), f(v_max)) (Section 2.2);
  *   - the solver of Algorithm 1 with the direct gradient step (Section 4.1)
  *     and the still-pair reuse of the assignment (Section 4.3); the assignment
- *     itself is an exact minimum-cost matching (the paper uses an approximate
- *     auction; the exact matching is this project's reading).
+ *     itself is an exact minimum-cost matching by default (this project's
+ *     reading), or the paper's approximate auction at a given relative
+ *     precision.
  *
  * Cell ids: (dim << 60) | (base_vertex << 6) | type, where the simplex is the
  * chain base, base+A, base+A+B, base+(1,1,1) with axis masks A, B (x=1, y=2,
@@ -67,6 +68,11 @@ int or_solver_done(or_solver* s, float stop_s, float cancel_eps, int max_iters);
  * solver instead of still points inheriting their previous assignment.  The
  * j = 0 assignment is the identity in both modes. */
 void or_solver_set_fast_assignment(or_solver* s, int on);
+/* Assignment of the following iterations: prec = 0 (default) the exact
+ * reduced assignment; prec > 0 the Auction algorithm at that relative
+ * precision (Section 5), its reduced W2^2 within a factor (1 + prec) of the
+ * optimum.  An iteration returns -4 if an auction did not finish. */
+void or_solver_set_assignment_precision(or_solver* s, double prec);
 /* Topological loss of `values` (nv floats) against the target diagram:
  * diagram, full exact matching, *loss = Eq. 2 with q = 2, grad[nv] = dL/df
  * in fp64 (contributions added in diagram order, birth before death; the
@@ -94,6 +100,10 @@ void or_solver_free(or_solver* s);
  * Returns the total W2^2 cost. */
 double or_assign(int64_t np, const float* pb, const float* pd, int64_t nt, const float* tb,
                  const float* td, int32_t* out_tgt);
+/* The same with the auction at relative precision prec (> 0; 0 is exact).
+ * Returns -1.0 if the auction did not finish. */
+double or_assign_prec(int64_t np, const float* pb, const float* pd, int64_t nt, const float* tb,
+                      const float* td, double prec, int32_t* out_tgt);
 
 #ifdef __cplusplus
 }

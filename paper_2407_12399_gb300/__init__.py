@@ -42,7 +42,8 @@ assert PAIR_DTYPE.itemsize == ctypes.sizeof(tsf_pair) == 40
 class tsf_params(ctypes.Structure):
     _fields_ = [("alpha_b", ctypes.c_float), ("alpha_d", ctypes.c_float), ("stop_s", ctypes.c_float),
                 ("cancel_eps", ctypes.c_float), ("max_iters", ctypes.c_int32),
-                ("fast_gradient_update", ctypes.c_int32), ("fast_assignment_update", ctypes.c_int32)]
+                ("fast_gradient_update", ctypes.c_int32), ("fast_assignment_update", ctypes.c_int32),
+                ("assignment_precision", ctypes.c_float)]
 
 
 class tsf_stats(ctypes.Structure):
@@ -68,7 +69,8 @@ EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_
            "tsf_set_signal_pairs", "tsf_solver_step", "tsf_simplify", "tsf_get_field", "tsf_set_field",
            "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
            "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static",
-           "tsf_loss_and_gradient")
+           "tsf_loss_and_gradient", "tsf_batch_create", "tsf_batch_destroy", "tsf_batch_size", "tsf_batch_field",
+           "tsf_batch_set_signal_thresholds", "tsf_batch_step", "tsf_batch_simplify")
 TSF_NSTAGES = 12
 INCREMENTAL_ORDER_MAX = 8192  # TSF_INCREMENTAL_ORDER_MAX
 
@@ -100,6 +102,13 @@ def lib():
             "tsf_zero_pairs": [P, P, I64, ctypes.POINTER(I64)],
             "tsf_zero_pairs_static": [I, I, I, P, P, I64, ctypes.POINTER(I64), P],
             "tsf_loss_and_gradient": [P, P, I, ctypes.POINTER(ctypes.c_double), P, I],
+            "tsf_batch_create": [I, P, P, P, P, I, ctypes.POINTER(P)],
+            "tsf_batch_destroy": [P],
+            "tsf_batch_size": [P],
+            "tsf_batch_field": [P, I, ctypes.POINTER(P)],
+            "tsf_batch_set_signal_thresholds": [P, P],
+            "tsf_batch_step": [P, ctypes.POINTER(tsf_params), P],
+            "tsf_batch_simplify": [P, ctypes.POINTER(tsf_params), P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -214,6 +223,49 @@ def tsf_loss_and_gradient(h, values_ptr, values_on_device, grad_ptr, grad_on_dev
     return loss.value
 
 
+def tsf_batch_create(shapes, values_ptrs, values_on_device):
+    """shapes: (Lz, Ly, Lx) per field; values_ptrs: one pointer per field."""
+    n = len(shapes)
+    lx = (ctypes.c_int * n)(*[s[2] for s in shapes])
+    ly = (ctypes.c_int * n)(*[s[1] for s in shapes])
+    lz = (ctypes.c_int * n)(*[s[0] for s in shapes])
+    vp = (ctypes.c_void_p * n)(*values_ptrs)
+    h = ctypes.c_void_p()
+    _check(lib().tsf_batch_create(n, lx, ly, lz, vp, values_on_device, ctypes.byref(h)), "tsf_batch_create")
+    return h
+
+
+def tsf_batch_destroy(h):
+    return lib().tsf_batch_destroy(h)
+
+
+def tsf_batch_size(h):
+    return lib().tsf_batch_size(h)
+
+
+def tsf_batch_field(h, i):
+    f = ctypes.c_void_p()
+    _check(lib().tsf_batch_field(h, i, ctypes.byref(f)), "tsf_batch_field")
+    return f
+
+
+def tsf_batch_set_signal_thresholds(h, fractions):
+    a = np.ascontiguousarray(fractions, np.float32)
+    _check(lib().tsf_batch_set_signal_thresholds(h, a.ctypes.data), "tsf_batch_set_signal_thresholds")
+
+
+def tsf_batch_step(h, params, n):
+    st = (tsf_stats * n)()
+    _check(lib().tsf_batch_step(h, ctypes.byref(params), st), "tsf_batch_step")
+    return [s.as_dict() for s in st]
+
+
+def tsf_batch_simplify(h, params, n):
+    st = (tsf_stats * n)()
+    _check(lib().tsf_batch_simplify(h, ctypes.byref(params), st), "tsf_batch_simplify")
+    return [s.as_dict() for s in st]
+
+
 def tsf_profile_enable(h, enable=1):
     _check(lib().tsf_profile_enable(h, enable), "tsf_profile_enable")
 
@@ -234,8 +286,9 @@ def tsf_kernel_launches():
 
 
 def params(alpha_b=0.5, alpha_d=0.5, stop_s=0.01, cancel_eps=0.0, max_iters=1000, fast_gradient_update=1,
-           fast_assignment_update=1):
-    return tsf_params(alpha_b, alpha_d, stop_s, cancel_eps, max_iters, fast_gradient_update, fast_assignment_update)
+           fast_assignment_update=1, assignment_precision=0.0):
+    return tsf_params(alpha_b, alpha_d, stop_s, cancel_eps, max_iters, fast_gradient_update, fast_assignment_update,
+                      assignment_precision)
 
 
 def _ptr_of(a):
@@ -346,3 +399,68 @@ class Field:
         r, n = tsf_zero_pairs(self._h, out.ctypes.data, n)
         _check(r, "tsf_zero_pairs")
         return out[: 2 * n].reshape(-1, 2)
+
+
+class _BatchMember(Field):
+    """A field owned by a Batch: the single-field calls work on it, but the
+    batch frees it."""
+
+    def __init__(self, h, shape):
+        self._h = h
+        self.shape = shape
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """Independent fields solved together (one stream and one host worker
+    per field, all fields' kernels in flight at once).  fields: sequence of
+    (Lz, Ly, Lx) float32 arrays or tensors, all on the host or all on the
+    device.  A field's trajectory is the one it has when solved alone."""
+
+    def __init__(self, fields):
+        shapes, ptrs, on_dev = [], [], set()
+        keep = []
+        for v in fields:
+            if len(v.shape) != 3:
+                raise ValueError("values must be (Lz, Ly, Lx)")
+            v = np.ascontiguousarray(v, np.float32) if isinstance(v, np.ndarray) else v.contiguous()
+            p, dev = _ptr_of(v)
+            keep.append(v)
+            shapes.append(tuple(v.shape))
+            ptrs.append(p)
+            on_dev.add(dev)
+        if len(on_dev) != 1:
+            raise ValueError("batch fields must be all on the host or all on the device")
+        self.shapes = shapes
+        self._h = tsf_batch_create(shapes, ptrs, on_dev.pop())
+        self.fields = [_BatchMember(tsf_batch_field(self._h, i), s) for i, s in enumerate(shapes)]
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for f in self.fields:
+                f.close()
+            tsf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_thresholds(self, fractions):
+        tsf_batch_set_signal_thresholds(self._h, fractions)
+
+    def step(self, **kw):
+        return tsf_batch_step(self._h, params(**kw), len(self))
+
+    def simplify(self, **kw):
+        return tsf_batch_simplify(self._h, params(**kw), len(self))
+
+    def values(self):
+        return [f.values() for f in self.fields]

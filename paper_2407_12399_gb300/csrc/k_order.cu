@@ -10,6 +10,7 @@
 // second count by a binary search, even though the updated vertices' old
 // values are gone.
 #include <algorithm>
+#include <atomic>
 
 #include "../../include/tsf.h"
 #include "tsf_group.cuh"
@@ -192,10 +193,10 @@ void vertex_order_incremental(const float* f, int64_t n, const uint32_t* upd, in
   const size_t smem = sizeof(unsigned long long) * (size_t)kIncOrderMax;
   int dev = 0;
   cudaGetDevice(&dev);
-  static bool attr[64] = {};
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
+  static std::atomic<bool> attr[64] = {};  // fields may be driven from several host threads
+  if (dev >= 0 && dev < 64 && !attr[dev].load(std::memory_order_acquire)) {
     cudaFuncSetAttribute(k_order_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr[dev] = true;
+    attr[dev].store(true, std::memory_order_release);
   }
   cudaMemsetAsync(ubits, 0, sizeof(uint32_t) * (size_t)nw, st);
   k_order_mark<<<(nu + 255) / 256, 256, 0, st>>>(upd, nu, rank, ubits); note_launch();

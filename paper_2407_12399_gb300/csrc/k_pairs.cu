@@ -15,6 +15,7 @@
 // The union-find runs in rounds of deterministic reservations: an item
 // commits when no earlier item touches the component that would die, which
 // gives exactly the sequential elder-rule result whatever the schedule.
+#include <atomic>
 #include <utility>
 
 #include "tsf_group.cuh"
@@ -1195,12 +1196,12 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   size_t sa = d1_group_smem(kFrontA, kStageA), sb = d1_group_smem(kFrontB, kStageB);
   int dev = 0;
   cudaGetDevice(&dev);
-  static bool attr[64] = {};
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
+  static std::atomic<bool> attr[64] = {};  // fields may be driven from several host threads
+  if (dev >= 0 && dev < 64 && !attr[dev].load(std::memory_order_acquire)) {
     cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
     cudaFuncSetAttribute(k_d1_morse_group<kThreadsB, kFrontB, kStageB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
-    attr[dev] = true;
+    attr[dev].store(true, std::memory_order_release);
   }
   k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, sa, st>>>(c, W, kRoundsA, status); note_launch();
   k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<n2, kThreadsB, sb, st>>>(c, W, 0, status); note_launch();

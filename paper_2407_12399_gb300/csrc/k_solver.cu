@@ -506,70 +506,77 @@ __device__ __forceinline__ int block_exscan_int1024(int v, int& total) {
 // Shortest augmenting path (Hungarian algorithm with potentials): rows =
 // targets in target order, columns = candidate points (point order) and one
 // private diagonal column per target; ties go to the lowest column index.
-__global__ void __launch_bounds__(kHT) k_hungarian(int k, int mc, const Cand* __restrict__ kept,
-                                                   const uint32_t* __restrict__ koff,
-                                                   const uint32_t* __restrict__ nkept,
-                                                   const uint32_t* __restrict__ colpos,
-                                                   const double* __restrict__ diag_t, HungWork H,
-                                                   int32_t* __restrict__ col_to_row, uint32_t* status) {
+//
+// A row's search only ever reaches the candidate columns of the rows in its
+// tree and their diagonal columns; every other column keeps minv = +inf
+// (inf - delta = inf) and never takes part in a decision.  So each step works
+// on the list of reached columns instead of all m columns: the same
+// arithmetic on the same columns, O(reached) per step.  Rows: count(r) and
+// get(r, c, j, w) give row r's c-th candidate as 1-based column j, weight w.
+template <class Rows>
+__device__ bool sap_solve(int k, int mc, const Rows& R, const double* __restrict__ diag_t, HungWork H,
+                          uint32_t* status) {
   const int m = mc + k;
   const double INF = __longlong_as_double(0x7FF0000000000000ll);
-  __shared__ int s_j0;
+  __shared__ int s_nl;
   __shared__ double s_val[kHT / 32];
   __shared__ int s_idx[kHT / 32];
-  __shared__ double s_delta;
-  __shared__ int s_j1;
   for (int j = threadIdx.x; j <= m; j += kHT) {
     H.v[j] = 0.0;
     H.pm[j] = 0;
     H.way[j] = 0;
+    H.minv[j] = INF;
+    H.used[j] = 0;
   }
   for (int i = threadIdx.x; i <= k; i += kHT) H.u[i] = 0.0;
+  if (threadIdx.x == 0) s_nl = 0;
   __syncthreads();
   for (int i = 1; i <= k; ++i) {
-    for (int j = threadIdx.x; j <= m; j += kHT) {
-      H.minv[j] = INF;
-      H.used[j] = 0;
-    }
-    if (threadIdx.x == 0) {
-      H.pm[0] = i;
-      s_j0 = 0;
-    }
+    if (threadIdx.x == 0) H.pm[0] = i;
     __syncthreads();
+    int j0 = 0;
     for (int guard = 0;; ++guard) {
       if (guard > m + 2) {
         if (threadIdx.x == 0) atomicOr(status, kErrRounds);
-        return;
+        return false;
       }
-      int j0 = s_j0;
-      if (threadIdx.x == 0) H.used[j0] = 1;
-      int i0 = H.pm[j0];
-      for (int j = 1 + threadIdx.x; j <= m; j += kHT) H.row[j] = INF;
-      __syncthreads();
-      for (int c = threadIdx.x; c < (int)nkept[i0 - 1]; c += kHT) {
-        const Cand& cd = kept[koff[i0 - 1] + c];
-        H.row[1 + colpos[cd.p]] = cd.w;
-      }
-      if (threadIdx.x == 0) H.row[1 + mc + (i0 - 1)] = diag_t[i0 - 1];
-      __syncthreads();
-      double ui0 = H.u[i0];
-      double bv = INF;
-      int bj = 0x7FFFFFFF;
-      for (int j = 1 + threadIdx.x; j <= m; j += kHT) {
-        if (H.used[j]) continue;
-        double cur = __dsub_rn(__dsub_rn(H.row[j], ui0), H.v[j]);
+      // relax the columns of row i0 = pm[j0] (its candidates, then its diagonal)
+      const int i0 = H.pm[j0];
+      const double ui0 = H.u[i0];
+      const int n = R.count(i0 - 1);
+      for (int c = threadIdx.x; c <= n; c += kHT) {
+        int j;
+        double w;
+        if (c < n) {
+          R.get(i0 - 1, c, j, w);
+        } else {
+          j = 1 + mc + (i0 - 1);
+          w = diag_t[i0 - 1];
+        }
+        if (j == j0 || H.used[j]) continue;
+        double cur = __dsub_rn(__dsub_rn(w, ui0), H.v[j]);
         double mv = H.minv[j];
+        if (mv == INF) H.list[atomicAdd(&s_nl, 1)] = j;
         if (cur < mv) {
-          mv = cur;
           H.minv[j] = cur;
           H.way[j] = j0;
         }
+      }
+      if (threadIdx.x == 0) H.used[j0] = 1;
+      __syncthreads();
+      // argmin of minv over the reached unused columns, lowest index on ties
+      const int nl = s_nl;
+      double bv = INF;
+      int bj = 0x7FFFFFFF;
+      for (int q = threadIdx.x; q < nl; q += kHT) {
+        int j = H.list[q];
+        if (H.used[j]) continue;
+        double mv = H.minv[j];
         if (mv < bv || (mv == bv && j < bj)) {
           bv = mv;
           bj = j;
         }
       }
-      // block argmin, lowest index on ties
       for (int o = 16; o; o >>= 1) {
         double ov = __shfl_down_sync(0xFFFFFFFFu, bv, o);
         int oj = __shfl_down_sync(0xFFFFFFFFu, bj, o);
@@ -583,25 +590,26 @@ __global__ void __launch_bounds__(kHT) k_hungarian(int k, int mc, const Cand* __
         s_idx[threadIdx.x >> 5] = bj;
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
-        double v0 = s_val[0];
-        int j1 = s_idx[0];
-        for (int w = 1; w < kHT / 32; ++w)
-          if (s_val[w] < v0 || (s_val[w] == v0 && s_idx[w] < j1)) {
-            v0 = s_val[w];
-            j1 = s_idx[w];
-          }
-        s_delta = v0;
-        s_j1 = j1;
-      }
-      __syncthreads();
-      double delta = s_delta;
-      int j1 = s_j1;
+      double delta = s_val[0];
+      int j1 = s_idx[0];
+      for (int w = 1; w < kHT / 32; ++w)
+        if (s_val[w] < delta || (s_val[w] == delta && s_idx[w] < j1)) {
+          delta = s_val[w];
+          j1 = s_idx[w];
+        }
       if (j1 == 0x7FFFFFFF) {
         if (threadIdx.x == 0) atomicOr(status, kErrInconsistent);
-        return;
+        return false;
       }
-      for (int j = threadIdx.x; j <= m; j += kHT) {
+      // potentials: the tree's columns (the root column 0 and the used
+      // reached ones) and their rows move by delta, the others' minv drop
+      if (threadIdx.x == 0) {
+        int r = H.pm[0];
+        H.u[r] = __dadd_rn(H.u[r], delta);
+        H.v[0] = __dsub_rn(H.v[0], delta);
+      }
+      for (int q = threadIdx.x; q < nl; q += kHT) {
+        int j = H.list[q];
         if (H.used[j]) {
           int r = H.pm[j];
           H.u[r] = __dadd_rn(H.u[r], delta);
@@ -611,21 +619,362 @@ __global__ void __launch_bounds__(kHT) k_hungarian(int k, int mc, const Cand* __
         }
       }
       __syncthreads();
-      if (threadIdx.x == 0) s_j0 = j1;
-      __syncthreads();
+      j0 = j1;
       if (H.pm[j1] == 0) break;
     }
     if (threadIdx.x == 0) {
-      int j0 = s_j0;
+      int j = j0;
       do {
-        int j1 = H.way[j0];
-        H.pm[j0] = H.pm[j1];
-        j0 = j1;
-      } while (j0);
+        int jp = H.way[j];
+        H.pm[j] = H.pm[jp];
+        j = jp;
+      } while (j);
+    }
+    // back to the untouched state for the next row
+    const int nl = s_nl;
+    for (int q = threadIdx.x; q < nl; q += kHT) {
+      int j = H.list[q];
+      H.minv[j] = INF;
+      H.used[j] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      H.used[0] = 0;
+      s_nl = 0;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+struct KeptRows {
+  const Cand* kept;
+  const uint32_t* koff;
+  const uint32_t* nkept;
+  const uint32_t* colpos;
+  __device__ int count(int r) const { return (int)nkept[r]; }
+  __device__ void get(int r, int c, int& j, double& w) const {
+    const Cand& cd = kept[koff[r] + c];
+    j = 1 + (int)colpos[cd.p];
+    w = cd.w;
+  }
+};
+
+__global__ void __launch_bounds__(kHT, 1) k_hungarian(int k, int mc, const Cand* __restrict__ kept,
+                                                   const uint32_t* __restrict__ koff,
+                                                   const uint32_t* __restrict__ nkept,
+                                                   const uint32_t* __restrict__ colpos,
+                                                   const double* __restrict__ diag_t, HungWork H,
+                                                   int32_t* __restrict__ col_to_row, uint32_t* status) {
+  if (!sap_solve(k, mc, KeptRows{kept, koff, nkept, colpos}, diag_t, H, status)) return;
+  for (int j = 1 + threadIdx.x; j <= mc; j += kHT) col_to_row[j - 1] = H.pm[j] - 1;
+}
+
+
+// ---------------------------------------------------------------------------
+// Auction variant of the reduced assignment (the paper's implementation,
+// Section 5, solves it with the Auction algorithm at relative precision
+// 0.01).  Same rows and options as sap_solve; net cost of an option
+// w(r,j) + price(j).  Forward auction in synchronous (Jacobi) rounds: every
+// unassigned row finds its cheapest net cost n1 (ties: lowest column) at j1
+// and the cheapest among its other options n2, and bids
+// price(j1) + ((n2 - n1) + eps); each point column takes its highest bid
+// (ties: lowest row) and its previous row is unassigned; a bid for the row's
+// own diagonal always wins.  eps-scaling: eps = max diag(t) / 4, divided by
+// 5 per phase; a later phase keeps the assignment and prices, except that
+// (until nothing changes) columns without a row get price 0 and rows whose
+// net cost exceeds their cheapest by more than the new eps are released.
+// Phase end: every column without a row has price 0, so
+// LB = sum_r n1_r - sum_j price(j) bounds the optimum from below and
+// W - LB <= k eps for the assignment's cost W; the auction stops once
+// W + D <= (1 + prec)(LB + D), D = sum of diag(p) over the group's points
+// (the reduced W2^2 within a factor (1 + prec) of its minimum), or once eps
+// reaches 2^-40 max diag(t).  The sums run on one thread in row order,
+// prices in column order (points, then diagonals).  Rounds work on the list
+// of rows that bid.  On return H.pm[j] (j < mc) is the row owning point
+// column j, or -1.
+// Scratch: H.v = prices (m), H.minv = a column's highest bid (bits), H.key =
+// its round-tagged winner, H.u = bids / cheapest net costs (k), H.aw = costs
+// of the assigned options (k), H.pm = owners (mc); aux (4 x stride ints) =
+// a row's column, its bid column (-2: released), two row lists.
+// ---------------------------------------------------------------------------
+constexpr int kAuctionRounds = 1 << 24;
+
+// One warp evaluates row r: cheapest net cost n1 and, for the column jr it
+// holds, its net cost and weight (lane 0 has the results).
+template <class Rows>
+__device__ __forceinline__ void auction_eval(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
+                                             const double* price, int jr, double& n1, double& ncur, double& wcur) {
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+  const int lane = threadIdx.x & 31;
+  const int n = R.count(r);
+  n1 = INF;
+  ncur = INF;
+  wcur = INF;
+  for (int c = lane; c <= n; c += 32) {
+    int j;
+    double w;
+    if (c < n) {
+      R.get(r, c, j, w);
+      j -= 1;
+    } else {
+      j = mc + r;
+      w = diag_t[r];
+    }
+    double v = __dadd_rn(w, price[j]);
+    n1 = fmin(n1, v);
+    if (j == jr) {
+      ncur = v;
+      wcur = w;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    n1 = fmin(n1, __shfl_down_sync(0xFFFFFFFFu, n1, o));
+    ncur = fmin(ncur, __shfl_down_sync(0xFFFFFFFFu, ncur, o));
+    wcur = fmin(wcur, __shfl_down_sync(0xFFFFFFFFu, wcur, o));
+  }
+}
+
+template <class Rows>
+__device__ bool auction_solve(int k, int mc, const Rows& R, const double* __restrict__ diag_t, double prec,
+                              const Pt* __restrict__ pts, const int32_t* __restrict__ gpts, int npg, HungWork H,
+                              int32_t* aux, int stride, uint32_t* status) {
+  const int m = mc + k;
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t* rowcol = aux;
+  int32_t* bidcol = aux + stride;
+  int32_t* lists[2] = {aux + 2 * stride, aux + 3 * stride};
+  double* price = H.v;
+  unsigned long long* colbid = reinterpret_cast<unsigned long long*>(H.minv);
+  unsigned long long* colkey = H.key;
+  double* bidval = H.u;
+  double* aw = H.aw;
+  int32_t* owner = H.pm;
+  __shared__ int s_n[2];
+  __shared__ int s_nv;
+  __shared__ int s_stop;
+  __shared__ double s_chunk[kHT];
+  __shared__ double s_eps;
+  if (threadIdx.x == 0) {
+    s_n[0] = 0;
+    s_n[1] = 0;
+  }
+  for (int j = threadIdx.x; j < m; j += kHT) price[j] = 0.0;
+  for (int j = threadIdx.x; j < mc; j += kHT) {
+    owner[j] = -1;
+    colbid[j] = 0ull;
+    colkey[j] = ~0ull;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < k; r += kHT) {
+    bidcol[r] = -1;
+    if (R.count(r) > 0) {
+      rowcol[r] = -1;
+      lists[0][atomicAdd(&s_n[0], 1)] = r;
+    } else {
+      rowcol[r] = mc + r;
+    }
+  }
+  // D = sum of diag(p) in point order; the largest diag(t)
+  double dsum = 0.0, cmax = 0.0;
+  for (int c0 = 0; c0 < npg; c0 += kHT) {
+    int i = c0 + threadIdx.x;
+    if (i < npg) s_chunk[threadIdx.x] = cost_diag(pts[gpts[i]].b, pts[gpts[i]].d);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int n = min(kHT, npg - c0);
+      for (int q = 0; q < n; ++q) dsum = __dadd_rn(dsum, s_chunk[q]);
     }
     __syncthreads();
   }
-  for (int j = 1 + threadIdx.x; j <= mc; j += kHT) col_to_row[j - 1] = H.pm[j] - 1;
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < k; ++r) cmax = fmax(cmax, diag_t[r]);
+    double emin = ldexp(cmax, -40);
+    if (!(emin > 0.0)) emin = 2.2250738585072014e-308;  // smallest normal double
+    double e = __dmul_rn(cmax, 0.25);
+    s_eps = e < emin ? emin : e;
+  }
+  __syncthreads();
+  double eps = s_eps;
+  const double onep = __dadd_rn(1.0, prec);
+  int cur = 0;
+  unsigned round = 0;
+  for (int phase = 0;; ++phase) {
+    if (phase > 0) {
+      for (;;) {  // release the rows that break eps-complementary slackness
+        for (int j = threadIdx.x; j < mc; j += kHT)
+          if (owner[j] < 0) price[j] = 0.0;
+        for (int r = threadIdx.x; r < k; r += kHT)
+          if (rowcol[r] != mc + r) price[mc + r] = 0.0;
+        if (threadIdx.x == 0) s_nv = 0;
+        __syncthreads();
+        for (int r = warp; r < k; r += kHT / 32) {
+          const int jr = rowcol[r];
+          if (jr < 0) continue;
+          double n1, ncur, wcur;
+          auction_eval(R, r, mc, diag_t, price, jr, n1, ncur, wcur);
+          if (lane == 0 && ncur > __dadd_rn(n1, eps)) {
+            bidcol[r] = -2;
+            atomicAdd(&s_nv, 1);
+          }
+        }
+        __syncthreads();
+        if (s_nv == 0) break;
+        for (int r = threadIdx.x; r < k; r += kHT) {
+          if (bidcol[r] != -2) continue;
+          bidcol[r] = -1;
+          if (rowcol[r] < mc) owner[rowcol[r]] = -1;
+          rowcol[r] = -1;
+          lists[cur][atomicAdd(&s_n[cur], 1)] = r;
+        }
+        __syncthreads();
+      }
+    }
+    for (;; ++round) {
+      if (round >= (unsigned)kAuctionRounds) {
+        if (threadIdx.x == 0) atomicOr(status, kErrRounds);
+        return false;
+      }
+      const int ncur = s_n[cur];
+      const int nxt = cur ^ 1;
+      if (ncur == 0) break;
+      const int32_t* L = lists[cur];
+      int32_t* LN = lists[nxt];
+      // bids: one warp per listed row
+      for (int idx = warp; idx < ncur; idx += kHT / 32) {
+        const int r = L[idx];
+        const int n = R.count(r);
+        double n1 = INF, n2 = INF;
+        int j1 = 0x7FFFFFFF;
+        for (int c = lane; c <= n; c += 32) {
+          int j;
+          double w;
+          if (c < n) {
+            R.get(r, c, j, w);
+            j -= 1;  // Rows give 1-based columns
+          } else {
+            j = mc + r;
+            w = diag_t[r];
+          }
+          double v = __dadd_rn(w, price[j]);
+          if (v < n1 || (v == n1 && j < j1)) {
+            n2 = n1;
+            n1 = v;
+            j1 = j;
+          } else if (v < n2) {
+            n2 = v;
+          }
+        }
+        for (int o = 16; o; o >>= 1) {
+          double b1 = __shfl_down_sync(0xFFFFFFFFu, n1, o);
+          int bj = __shfl_down_sync(0xFFFFFFFFu, j1, o);
+          double b2 = __shfl_down_sync(0xFFFFFFFFu, n2, o);
+          if (b1 < n1 || (b1 == n1 && bj < j1)) {
+            n2 = fmin(n1, b2);
+            n1 = b1;
+            j1 = bj;
+          } else {
+            n2 = fmin(n2, b1);
+          }
+        }
+        if (lane == 0) {
+          double g = __dsub_rn(n2, n1);
+          g = __dadd_rn(g, eps);
+          double bid = __dadd_rn(price[j1], g);
+          if (j1 >= mc) {  // the row's own diagonal: nobody else bids for it
+            price[j1] = bid;
+            rowcol[r] = j1;
+          } else {
+            bidcol[r] = j1;
+            bidval[r] = bid;
+            atomicMax(&colbid[j1], (unsigned long long)__double_as_longlong(bid));
+          }
+        }
+      }
+      __syncthreads();
+      // ties: the lowest row among a column's highest bids
+      const unsigned long long tag = (unsigned long long)(0xFFFFFFFFu - round) << 32;
+      for (int idx = threadIdx.x; idx < ncur; idx += kHT) {
+        const int r = L[idx];
+        const int j = bidcol[r];
+        if (j >= 0 && colbid[j] == (unsigned long long)__double_as_longlong(bidval[r]))
+          atomicMin(&colkey[j], tag | (unsigned)r);
+      }
+      __syncthreads();
+      // winners take their column; losers and displaced rows bid again
+      for (int idx = threadIdx.x; idx < ncur; idx += kHT) {
+        const int r = L[idx];
+        const int j = bidcol[r];
+        if (j < 0) continue;
+        bidcol[r] = -1;
+        if (colkey[j] == (tag | (unsigned)r)) {
+          const int old = owner[j];
+          if (old >= 0) {
+            rowcol[old] = -1;
+            LN[atomicAdd(&s_n[nxt], 1)] = old;
+          }
+          owner[j] = r;
+          rowcol[r] = j;
+          price[j] = bidval[r];
+          colbid[j] = 0ull;
+        } else {
+          LN[atomicAdd(&s_n[nxt], 1)] = r;
+        }
+      }
+      if (threadIdx.x == 0) s_n[cur] = 0;
+      __syncthreads();
+      cur = nxt;
+    }
+    // phase end: W, LB and the stop test
+    for (int r = warp; r < k; r += kHT / 32) {
+      double n1, ncur, wcur;
+      auction_eval(R, r, mc, diag_t, price, rowcol[r], n1, ncur, wcur);
+      if (lane == 0) {
+        bidval[r] = n1;
+        aw[r] = wcur;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double W = 0.0, U = 0.0, P = 0.0;
+      for (int r = 0; r < k; ++r) {
+        W = __dadd_rn(W, aw[r]);
+        U = __dadd_rn(U, bidval[r]);
+      }
+      for (int j = 0; j < m; ++j) P = __dadd_rn(P, price[j]);
+      double lb = __dsub_rn(U, P);
+      double lhs = __dadd_rn(W, dsum);
+      double rhs = __dadd_rn(lb, dsum);
+      rhs = __dmul_rn(rhs, onep);
+      double emin = ldexp(cmax, -40);
+      if (!(emin > 0.0)) emin = 2.2250738585072014e-308;
+      int stop = (lhs <= rhs || !(eps > emin)) ? 1 : 0;
+      if (!stop) {
+        double e = __ddiv_rn(eps, 5.0);
+        s_eps = e < emin ? emin : e;
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    eps = s_eps;
+  }
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(kHT, 1) k_auction(int k, int mc, const Cand* __restrict__ kept,
+                                                 const uint32_t* __restrict__ koff, const uint32_t* __restrict__ nkept,
+                                                 const uint32_t* __restrict__ colpos,
+                                                 const double* __restrict__ diag_t, double prec,
+                                                 const Pt* __restrict__ pts, const int32_t* __restrict__ plist,
+                                                 int npg, HungWork H, int32_t* aux, int stride,
+                                                 int32_t* __restrict__ col_to_row, uint32_t* status) {
+  if (!auction_solve(k, mc, KeptRows{kept, koff, nkept, colpos}, diag_t, prec, pts, plist, npg, H, aux, stride,
+                     status))
+    return;
+  for (int j = threadIdx.x; j < mc; j += kHT) col_to_row[j] = H.pm[j];
 }
 
 __global__ void k_colpos(int npg, const uint32_t* __restrict__ is_col, const uint32_t* __restrict__ pos,
@@ -848,7 +1197,7 @@ __global__ void __launch_bounds__(512) k_asg_candidates(const Pt* __restrict__ p
 // then one private diagonal column per target) and the shortest augmenting
 // path solve, exactly as k_hungarian
 __global__ void __launch_bounds__(kHT) k_asg_solve(AsgDev A, Pt* __restrict__ pts, const Tg* __restrict__ T,
-                                                   uint32_t* status) {
+                                                   double prec, uint32_t* status) {
   const int g = blockIdx.x;
   if (A.counts[8]) return;
   int npg = A.counts[g], k = A.counts[4 + g];
@@ -876,143 +1225,46 @@ __global__ void __launch_bounds__(kHT) k_asg_solve(AsgDev A, Pt* __restrict__ pt
     __syncthreads();
   }
   int mc = s_mc;
-  const int m = mc + k;
-  const double INF = __longlong_as_double(0x7FF0000000000000ll);
   HungWork H;
   H.u = A.H.u + wbase;
   H.v = A.H.v + wbase;
   H.minv = A.H.minv + wbase;
-  H.row = A.H.row + wbase;
+  H.list = A.H.list + wbase;
   H.pm = A.H.pm + wbase;
   H.way = A.H.way + wbase;
   H.used = A.H.used + wbase;
+  H.key = A.H.key + wbase;
+  H.aw = A.H.aw + wbase;
   double* diag_t = A.diag_t + tbase;
   for (int t = threadIdx.x; t < k; t += kHT) diag_t[t] = cost_diag(T[A.tlist[tbase + t]].b, T[A.tlist[tbase + t]].d);
-  __shared__ int s_j0;
-  __shared__ double s_val[kHT / 32];
-  __shared__ int s_idx[kHT / 32];
-  __shared__ double s_delta;
-  __shared__ int s_j1;
-  for (int j = threadIdx.x; j <= m; j += kHT) {
-    H.v[j] = 0.0;
-    H.pm[j] = 0;
-    H.way[j] = 0;
-  }
-  for (int i = threadIdx.x; i <= k; i += kHT) H.u[i] = 0.0;
   __syncthreads();
-  for (int i = 1; i <= k; ++i) {
-    for (int j = threadIdx.x; j <= m; j += kHT) {
-      H.minv[j] = INF;
-      H.used[j] = 0;
+  if (prec > 0.0) {
+    const int wg = npg + k + 2;
+    if (!auction_solve(k, mc, KeptRows{A.kept, A.kept_off + tbase, A.nkept + tbase, A.colpos + pbase}, diag_t, prec,
+                       pts, A.plist + pbase, npg, H, A.aux + 4 * wbase, wg, status))
+      return;
+    for (int j = threadIdx.x; j < mc; j += kHT) {
+      int r = H.pm[j];
+      if (r >= 0) pts[A.plist[pbase + A.col_point[wbase + j]]].tgt = A.tlist[tbase + r];
     }
-    if (threadIdx.x == 0) {
-      H.pm[0] = i;
-      s_j0 = 0;
-    }
-    __syncthreads();
-    for (int guard = 0;; ++guard) {
-      if (guard > m + 2) {
-        if (threadIdx.x == 0) atomicOr(status, kErrRounds);
-        return;
-      }
-      int j0 = s_j0;
-      if (threadIdx.x == 0) H.used[j0] = 1;
-      int i0 = H.pm[j0];
-      for (int j = 1 + threadIdx.x; j <= m; j += kHT) H.row[j] = INF;
-      __syncthreads();
-      uint32_t ko = A.kept_off[tbase + i0 - 1], kn = A.nkept[tbase + i0 - 1];
-      for (uint32_t c = threadIdx.x; c < kn; c += kHT) {
-        const Cand& cd = A.kept[ko + c];
-        H.row[1 + A.colpos[pbase + cd.p]] = cd.w;
-      }
-      if (threadIdx.x == 0) H.row[1 + mc + (i0 - 1)] = diag_t[i0 - 1];
-      __syncthreads();
-      double ui0 = H.u[i0];
-      double bv = INF;
-      int bj = 0x7FFFFFFF;
-      for (int j = 1 + threadIdx.x; j <= m; j += kHT) {
-        if (H.used[j]) continue;
-        double cur = __dsub_rn(__dsub_rn(H.row[j], ui0), H.v[j]);
-        double mv = H.minv[j];
-        if (cur < mv) {
-          mv = cur;
-          H.minv[j] = cur;
-          H.way[j] = j0;
-        }
-        if (mv < bv || (mv == bv && j < bj)) {
-          bv = mv;
-          bj = j;
-        }
-      }
-      for (int o = 16; o; o >>= 1) {
-        double ov = __shfl_down_sync(0xFFFFFFFFu, bv, o);
-        int oj = __shfl_down_sync(0xFFFFFFFFu, bj, o);
-        if (ov < bv || (ov == bv && oj < bj)) {
-          bv = ov;
-          bj = oj;
-        }
-      }
-      if ((threadIdx.x & 31) == 0) {
-        s_val[threadIdx.x >> 5] = bv;
-        s_idx[threadIdx.x >> 5] = bj;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double v0 = s_val[0];
-        int j1 = s_idx[0];
-        for (int w = 1; w < kHT / 32; ++w)
-          if (s_val[w] < v0 || (s_val[w] == v0 && s_idx[w] < j1)) {
-            v0 = s_val[w];
-            j1 = s_idx[w];
-          }
-        s_delta = v0;
-        s_j1 = j1;
-      }
-      __syncthreads();
-      double delta = s_delta;
-      int j1 = s_j1;
-      if (j1 == 0x7FFFFFFF) {
-        if (threadIdx.x == 0) atomicOr(status, kErrInconsistent);
-        return;
-      }
-      for (int j = threadIdx.x; j <= m; j += kHT) {
-        if (H.used[j]) {
-          int r = H.pm[j];
-          H.u[r] = __dadd_rn(H.u[r], delta);
-          H.v[j] = __dsub_rn(H.v[j], delta);
-        } else {
-          H.minv[j] = __dsub_rn(H.minv[j], delta);
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) s_j0 = j1;
-      __syncthreads();
-      if (H.pm[j1] == 0) break;
-    }
-    if (threadIdx.x == 0) {
-      int j0 = s_j0;
-      do {
-        int j1 = H.way[j0];
-        H.pm[j0] = H.pm[j1];
-        j0 = j1;
-      } while (j0);
-    }
-    __syncthreads();
+    return;
   }
+  if (!sap_solve(k, mc, KeptRows{A.kept, A.kept_off + tbase, A.nkept + tbase, A.colpos + pbase}, diag_t, H, status))
+    return;
   for (int j = 1 + threadIdx.x; j <= mc; j += kHT) {
     int r = H.pm[j] - 1;
     if (r >= 0) pts[A.plist[pbase + A.col_point[wbase + j - 1]]].tgt = A.tlist[tbase + r];
   }
 }
 
-int assign_groups(int np, Pt* pts, int nt, const Tg* T, SolverBufs& B, uint32_t* status, AssignStats* as,
-                  cudaStream_t st);
+int assign_groups(int np, Pt* pts, int nt, const Tg* T, double prec, SolverBufs& B, uint32_t* status,
+                  AssignStats* as, cudaStream_t st);
 
 // Assignment phi*_j.  `ref` is the previous diagram (or the targets at j = 0,
 // each assigned to itself).  Returns 0, or a negative value when a scratch
 // buffer is too small (the caller grows it and retries).
-int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBufs& B, uint32_t* status,
-           AssignStats* as, cudaStream_t st) {
+int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double prec, SolverBufs& B,
+           uint32_t* status, AssignStats* as, cudaStream_t st) {
   // 1) still pairs
   cudaMemsetAsync(B.taken, 0, (size_t)max(nt, 1), st);
   int32_t* ck = merge_sort(np, B.idxA, B.idxB, KeyLess{pts}, st);
@@ -1024,7 +1276,7 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBu
   cudaMemsetAsync(B.A.is_col, 0, sizeof(uint32_t) * (size_t)np, st);
   k_asg_partition<<<1, 1024, 0, st>>>(np, pts, nt, T, B.taken, B.A, pts); note_launch();
   k_asg_candidates<<<max(nt, 1), 512, 0, st>>>(pts, T, B.A); note_launch();
-  k_asg_solve<<<3, kHT, 0, st>>>(B.A, pts, T, status); note_launch();
+  k_asg_solve<<<3, kHT, 0, st>>>(B.A, pts, T, prec, status); note_launch();
   int32_t hc[10];
   cudaMemcpyAsync(hc, B.A.counts, sizeof(hc), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&as->status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
@@ -1032,12 +1284,12 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBu
   as->status_valid = !hc[8];
   for (int g = 0; g < 4; ++g) as->k[g] = hc[4 + g];
   if (!hc[8]) return 0;
-  return assign_groups(np, pts, nt, T, B, status, as, st);
+  return assign_groups(np, pts, nt, T, prec, B, status, as, st);
 }
 
 // General path: group by group with host-sized buffers.
-int assign_groups(int np, Pt* pts, int nt, const Tg* T, SolverBufs& B, uint32_t* status, AssignStats* as,
-                  cudaStream_t st) {
+int assign_groups(int np, Pt* pts, int nt, const Tg* T, double prec, SolverBufs& B, uint32_t* status,
+                  AssignStats* as, cudaStream_t st) {
   // 2) reduced problems, group by group
   as->k[0] = as->k[1] = as->k[2] = as->k[3] = 0;
   for (int g = 0; g < 4; ++g) {
@@ -1074,7 +1326,12 @@ int assign_groups(int np, Pt* pts, int nt, const Tg* T, SolverBufs& B, uint32_t*
     if (mc + k + 1 > B.cap_cols) return -3;
     k_colpos<<<(npg + 255) / 256, 256, 0, st>>>(npg, B.is_col, B.colpos, B.colpos, B.col_point); note_launch();
     k_diag_t<<<(k + 255) / 256, 256, 0, st>>>(k, B.tlist, T, B.diag_t); note_launch();
-    k_hungarian<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, B.H, B.col_to_row, status); note_launch();
+    if (prec > 0.0) {
+      k_auction<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, prec, pts, B.plist, npg, B.H,
+                                   B.aux, B.cap_cols + 1, B.col_to_row, status); note_launch();
+    } else {
+      k_hungarian<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, B.H, B.col_to_row, status); note_launch();
+    }
     k_apply_assignment<<<(mc + 255) / 256, 256, 0, st>>>(mc, B.col_to_row, B.col_point, B.plist, B.tlist, pts); note_launch();
   }
   return 0;

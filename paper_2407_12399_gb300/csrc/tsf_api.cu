@@ -303,10 +303,13 @@ void grow_solver(tsf_field* F, int np, int nt) {
     dev_free(A.H.u);
     dev_free(A.H.v);
     dev_free(A.H.minv);
-    dev_free(A.H.row);
+    dev_free(A.H.list);
     dev_free(A.H.pm);
     dev_free(A.H.way);
     dev_free(A.H.used);
+    dev_free(A.H.key);
+    dev_free(A.H.aw);
+    dev_free(A.aux);
     size_t w = (size_t)cp + ctt + 8;
     A.cap_kept = (int)std::min<int64_t>((int64_t)ctt * 2048, std::max<int64_t>((int64_t)16 * cp, 1 << 18));
     ck(dev_alloc(&A.counts, 16));
@@ -316,10 +319,13 @@ void grow_solver(tsf_field* F, int np, int nt) {
     ck(dev_alloc(&A.H.u, w));
     ck(dev_alloc(&A.H.v, w));
     ck(dev_alloc(&A.H.minv, w));
-    ck(dev_alloc(&A.H.row, w));
+    ck(dev_alloc(&A.H.list, w));
     ck(dev_alloc(&A.H.pm, w));
     ck(dev_alloc(&A.H.way, w));
     ck(dev_alloc(&A.H.used, w));
+    ck(dev_alloc(&A.H.key, w));
+    ck(dev_alloc(&A.H.aw, w));
+    ck(dev_alloc(&A.aux, 4 * w));
     A.plist = B.plist;
     A.tlist = B.tlist;
     A.nkept = B.nkept;
@@ -361,18 +367,24 @@ void grow_assign(tsf_field* F, int cand, int cols) {
     dev_free(H.u);
     dev_free(H.v);
     dev_free(H.minv);
-    dev_free(H.row);
+    dev_free(H.list);
     dev_free(H.pm);
     dev_free(H.way);
     dev_free(H.used);
+    dev_free(H.key);
+    dev_free(H.aw);
+    dev_free(B.aux);
     dev_free(B.col_to_row);
     ck(dev_alloc(&H.u, c + 1));
     ck(dev_alloc(&H.v, c + 1));
     ck(dev_alloc(&H.minv, c + 1));
-    ck(dev_alloc(&H.row, c + 1));
+    ck(dev_alloc(&H.list, c + 1));
     ck(dev_alloc(&H.pm, c + 1));
     ck(dev_alloc(&H.way, c + 1));
     ck(dev_alloc(&H.used, c + 1));
+    ck(dev_alloc(&H.key, c + 1));
+    ck(dev_alloc(&H.aw, c + 1));
+    ck(dev_alloc(&B.aux, 4 * ((size_t)c + 1)));
     ck(dev_alloc(&B.col_to_row, c + 1));
     B.cap_cols = c;
   }
@@ -510,14 +522,14 @@ int compute_diagram(tsf_field* F, bool incremental) {
   return TSF_OK;
 }
 
-int run_assign(tsf_field* F, const Pt* ref, int nr) {
+int run_assign(tsf_field* F, const Pt* ref, int nr, double prec = 0.0) {
   double t0 = now_ms();
   AssignStats as{};
   for (int attempt = 0; attempt < 8; ++attempt) {
     as.status_valid = false;
     ck(cudaMemsetAsync(F->status, 0, 4, F->st));
     stage_begin(F, kAssign);
-    int r = assign(F->np, F->pts, nr, ref, F->nt, F->T, F->B, F->status, &as, F->st);
+    int r = assign(F->np, F->pts, nr, ref, F->nt, F->T, prec, F->B, F->status, &as, F->st);
     stage_end(F, kAssign);
     if (r == 0) break;
     if (r == -2) grow_assign(F, std::max(2 * F->B.cap_cand, 4096), 0);
@@ -592,7 +604,8 @@ int start_solver(tsf_field* F) {
 
 int check_params(const tsf_params* p) {
   if (!p) return TSF_EINVAL;
-  if (!(p->alpha_b >= 0.0f) || !(p->alpha_d >= 0.0f) || !(p->cancel_eps >= 0.0f) || p->max_iters < 0)
+  if (!(p->alpha_b >= 0.0f) || !(p->alpha_d >= 0.0f) || !(p->cancel_eps >= 0.0f) || p->max_iters < 0 ||
+      !(p->assignment_precision >= 0.0f) || !(p->assignment_precision <= 3.4e38f))
     return TSF_EINVAL;
   return TSF_OK;
 }
@@ -613,7 +626,7 @@ int step(tsf_field* F, const tsf_params* p, tsf_stats* stats) {
   if (r) return r;
   // without the Section 4.3 reuse no point of the previous diagram is
   // consulted: every point is matched by the exact solver
-  r = run_assign(F, F->prev, p->fast_assignment_update ? F->nprev : 0);
+  r = run_assign(F, F->prev, p->fast_assignment_update ? F->nprev : 0, (double)p->assignment_precision);
   if (r) return r;
   F->iter += 1;
   eval(F, p->cancel_eps);
@@ -746,10 +759,13 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(B.H.u);
   dev_free(B.H.v);
   dev_free(B.H.minv);
-  dev_free(B.H.row);
+  dev_free(B.H.list);
   dev_free(B.H.pm);
   dev_free(B.H.way);
   dev_free(B.H.used);
+  dev_free(B.H.key);
+  dev_free(B.H.aw);
+  dev_free(B.aux);
   dev_free(B.terms);
   dev_free(B.dsum);
   dev_free(B.counters);
@@ -761,10 +777,13 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(B.A.H.u);
   dev_free(B.A.H.v);
   dev_free(B.A.H.minv);
-  dev_free(B.A.H.row);
+  dev_free(B.A.H.list);
   dev_free(B.A.H.pm);
   dev_free(B.A.H.way);
   dev_free(B.A.H.used);
+  dev_free(B.A.H.key);
+  dev_free(B.A.H.aw);
+  dev_free(B.A.aux);
   if (F->h_flags) cudaFreeHost(F->h_flags);
   for (auto e : F->ev_pool) cudaEventDestroy(e);
   delete F;

@@ -39,7 +39,9 @@ struct HungWork {
   double* u;
   double* v;
   double* minv;
-  double* row;
+  int32_t* list;  // columns reached by the current row's search
+  unsigned long long* key;  // auction: round-tagged winner of a column
+  double* aw;               // auction: cost of each row's assigned option
   int32_t* pm;
   int32_t* way;
   uint8_t* used;
@@ -59,6 +61,7 @@ struct AsgDev {
   int32_t* col_to_row;
   double* diag_t;
   HungWork H;          // arrays of np + nt + 8 entries, split per group
+  int32_t* aux;        // auction: 4 x (np + nt + 8) ints, split per group
   int cap_kept;
 };
 
@@ -75,6 +78,7 @@ struct SolverBufs {
   uint32_t* is_col;
   uint32_t* colpos;
   int32_t* col_point;
+  int32_t* aux;  // auction scratch of the group-by-group path: 4 x (cap_cols + 1)
   int32_t* col_to_row;
   double* diag_t;
   HungWork H;
@@ -104,7 +108,7 @@ void replace_values(int64_t nv, const float* in, float* f, uint32_t* upd, unsign
 // dL/df (fp64, nv entries) of the topological loss for the current points
 // and their matching.
 void loss_gradient(int np, const Pt* pts, const Tg* T, SolverBufs& B, double* grad, int64_t nv, cudaStream_t st);
-int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, SolverBufs& B, uint32_t* status,
+int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double prec, SolverBufs& B, uint32_t* status,
            AssignStats* as, cudaStream_t st);
 void loss_and_counts(int np, const Pt* pts, int nt, const Tg* T, float cancel_eps, SolverBufs& B, double* h_loss,
                      unsigned long long* h_counts, cudaStream_t st);

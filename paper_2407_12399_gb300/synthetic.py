@@ -262,3 +262,22 @@ def mixture_96(seed=3):
 def filament_128(seed=1):
     """128^3 filament-tube field + 4-octave gradient noise at 10 % of range."""
     return filament_field((128, 128, 128), seed=seed)
+
+
+def uneven_batch_shapes(n=48, seed=2, dims=(48, 64, 96, 128, 160)):
+    """Shapes (Lz, Ly, Lx) of n independent fields, each axis drawn from
+    dims (anisotropic grids allowed), a per-field signal threshold
+    U[0.02, 0.2] (fraction of range), and a per-field generator seed."""
+    rng = np.random.default_rng(seed)
+    shapes = rng.choice(np.asarray(dims), size=(n, 3))
+    thresholds = rng.uniform(0.02, 0.2, size=n).astype(np.float32)
+    seeds = rng.integers(0, 2 ** 31 - 1, size=n)
+    return [tuple(int(d) for d in s) for s in shapes], thresholds, [int(s) for s in seeds]
+
+
+def uneven_batch(n=48, seed=2, dims=(48, 64, 96, 128, 160)):
+    """n independent fields of the shapes above, each a 16-bump Gaussian
+    mixture + 5 % uniform noise.  Returns (fields, thresholds)."""
+    shapes, thresholds, seeds = uneven_batch_shapes(n, seed, dims)
+    fields = [gaussian_mixture(s, n_bumps=16, seed=k, noise_frac=0.05) for s, k in zip(shapes, seeds)]
+    return fields, thresholds

@@ -230,3 +230,50 @@ def test_trajectory_without_assignment_reuse_is_bit_exact(name, tau, iters):
         assert tgt.tolist() == P["tgt"].tolist()
         assert not still.any() and st["n_still"] == 0
         assert st["loss"] == pytest.approx(ref.stats()["loss"], rel=1e-12, abs=1e-300)
+
+
+AUCTION = {
+    "mixture_24": (lambda: S.gaussian_mixture((24, 22, 20), n_bumps=10, seed=4), 0.02, 5),
+    "noise_20": (lambda: S.random_field((20, 20, 20), seed=3), 0.3, 4),
+    "noise_28": (lambda: S.random_field((28, 28, 28), seed=5), 0.3, 2),
+}
+
+
+@pytest.mark.parametrize("name", list(AUCTION))
+def test_auction_trajectory_is_bit_exact(name):
+    """The auction assignment (Section 5's solver, relative precision 0.01)
+    on fields where hundreds of free targets compete for the same points:
+    assignment, field, diagram and loss equal the oracle's at every step."""
+    make, tau, iters = AUCTION[name]
+    f0 = make()
+    fld = gpu_field(f0)
+    fld.set_threshold(tau)
+    ref = oracle.Solver(f0, tau=tau, assignment_precision=0.01)
+    for j in range(iters):
+        st = fld.step(stop_s=0.0, assignment_precision=0.01)
+        ref.iterate(stop_s=0.0)
+        tgt, still = fld.assignment()
+        P = ref.points()
+        assert tgt.tolist() == P["tgt"].tolist(), f"assignment differs at j={j + 1}"
+        assert still.tolist() == P["still"].tolist()
+        assert np.array_equal(bits(fld.values()), bits(ref.field())), f"field differs after step {j + 1}"
+        assert st["loss"] == pytest.approx(ref.stats()["loss"], rel=1e-12, abs=1e-300)
+    assert [(x[0], x[1], x[2], x[3], x[4], x[5]) for x in gpu_rows(fld.diagram())] == _points_rows(ref.points())
+
+
+def test_auction_step_is_within_its_precision_of_the_exact_step():
+    """From the same state (identity at j = 0, the same first step) the
+    auction's loss lies between the exact solver's and (1 + 0.01) times it."""
+    f0 = S.gaussian_mixture((24, 22, 20), n_bumps=10, seed=4)
+    a, b = gpu_field(f0), gpu_field(f0)
+    a.set_threshold(0.02)
+    b.set_threshold(0.02)
+    se = a.step(stop_s=0.0)
+    sa = b.step(stop_s=0.0, assignment_precision=0.01)
+    assert np.array_equal(bits(a.values()), bits(b.values()))
+    assert se["n_still"] == sa["n_still"]
+    assert se["loss"] * (1 - 1e-12) <= sa["loss"] <= 1.01 * se["loss"] * (1 + 1e-12)
+    import paper_2407_12399_gb300 as tsf
+    with pytest.raises(tsf.TsfError) as e:
+        b.step(assignment_precision=-0.5)
+    assert e.value.code == tsf.TSF_EINVAL

@@ -238,6 +238,100 @@ def test_assignment_is_optimal_by_brute_force(seed):
     assert len(used) == len(set(used.tolist()))
 
 
+@pytest.mark.parametrize("prec", [0.5, 0.1, 0.01])
+@pytest.mark.parametrize("seed", range(12))
+def test_auction_is_within_its_precision_of_brute_force(seed, prec):
+    """The auction (Section 5's assignment solver) at relative precision
+    prec: a valid matching whose W2^2 is between the brute-force minimum and
+    (1 + prec) times it."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 8))
+    k = int(rng.integers(1, 5))
+    b = rng.uniform(0, 1, n)
+    pb = b.astype(np.float32)
+    pd = (b + rng.uniform(0, 0.5, n) * (rng.uniform(size=n) < 0.6)).astype(np.float32)
+    tb_ = rng.uniform(0, 1, k)
+    tb = tb_.astype(np.float32)
+    td = (tb_ + rng.uniform(0.1, 0.6, k)).astype(np.float32)
+    if seed % 3 == 0:
+        m = min(n, k)
+        tb[:m], td[:m] = pb[:m] + np.float32(0.01), pd[:m]
+    tgt, cost = oracle.assign(pb, pd, tb, td, precision=prec)
+    ref = _brute_assign(pb, pd, tb, td)
+    assert ref * (1 - 1e-12) <= cost <= (1 + prec) * ref * (1 + 1e-12) + 1e-15
+    used = tgt[tgt >= 0]
+    assert len(used) == len(set(used.tolist()))
+
+
+def _square_w2(pb, pd, tb, td):
+    """Optimal W2^2 by scipy's linear_sum_assignment on the square problem
+    (points + target projections) x (targets + point projections)."""
+    from scipy.optimize import linear_sum_assignment
+    n, k = len(pb), len(tb)
+    pb, pd, tb, td = (np.asarray(x, np.float64) for x in (pb, pd, tb, td))
+    big = 1e6
+    C = np.full((n + k, k + n), big)
+    C[:n, :k] = (pb[:, None] - tb[None, :]) ** 2 + (pd[:, None] - td[None, :]) ** 2
+    C[:n, k:][np.arange(n), np.arange(n)] = 0.5 * (pd - pb) ** 2
+    C[n:, :k][np.arange(k), np.arange(k)] = 0.5 * (td - tb) ** 2
+    C[n:, k:] = 0.0
+    r, c = linear_sum_assignment(C)
+    return float(C[r, c].sum())
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_exact_and_auction_against_a_library_solver_on_crowded_diagrams(seed):
+    """Many targets inside a cloud of low-persistence points (they compete for
+    the same points): the exact assignment reaches scipy's optimum, the
+    auction stays within its precision of it, and a very fine auction finds
+    the same optimum."""
+    rng = np.random.default_rng(seed)
+    n, k = 70, 24
+    pb_ = rng.uniform(0.0, 0.3, n)
+    pb = pb_.astype(np.float32)
+    pd = (pb_ + rng.uniform(0.0, 0.06, n)).astype(np.float32)
+    tb_ = rng.uniform(0.0, 0.3, k)
+    tb = tb_.astype(np.float32)
+    td = (tb_ + rng.uniform(0.02, 0.08, k)).astype(np.float32)
+    ref = _square_w2(pb, pd, tb, td)
+    _, exact = oracle.assign(pb, pd, tb, td)
+    assert exact == pytest.approx(ref, rel=1e-12)
+    for prec in (0.1, 0.01):
+        tgt, cost = oracle.assign(pb, pd, tb, td, precision=prec)
+        assert ref * (1 - 1e-12) <= cost <= (1 + prec) * ref * (1 + 1e-12)
+        used = tgt[tgt >= 0]
+        assert len(used) == len(set(used.tolist()))
+    _, fine = oracle.assign(pb, pd, tb, td, precision=1e-7)
+    assert fine == pytest.approx(ref, rel=1e-6)
+
+
+def test_auction_resolves_a_two_target_contest():
+    """One point (0, 1) and targets (0, 1), (0.1, 1): the first takes the
+    point (W2^2 = 0 + 0.405) rather than the second (0.01 + 0.5); at 1 %
+    precision the auction must find it."""
+    for prec in (0.0, 0.01):
+        tgt, cost = oracle.assign([0.0], [1.0], [0.0, 0.1], [1.0, 1.0], precision=prec)
+        assert tgt.tolist() == [0]
+        assert cost == pytest.approx(0.405, rel=1e-6)
+
+
+def test_auction_solver_step_is_within_its_precision_of_the_exact_one():
+    """Both solvers start from the identity at j = 0 and take the same first
+    step, so they see the same D(f_1) and the same still pairs; the
+    auction's loss lies between the exact one and (1 + prec) times it."""
+    f0 = S.gaussian_mixture((12, 11, 10), n_bumps=6, seed=2)
+    ex = oracle.Solver(f0, tau=0.02)
+    au = oracle.Solver(f0, tau=0.02, assignment_precision=0.01)
+    assert len(ex.targets()["vb"]) > 10
+    ex.iterate(stop_s=0.0)
+    au.iterate(stop_s=0.0)
+    assert np.array_equal(ex.field(), au.field())
+    le, la = ex.stats()["loss"], au.stats()["loss"]
+    assert le * (1 - 1e-12) <= la <= 1.01 * le * (1 + 1e-12)
+    au.run(stop_s=0.01)
+    assert au.stats()["loss"] <= 0.01 * au.stats()["loss0"]
+
+
 def _isolated_pair_field():
     """A linear ramp with one raised interior vertex: one small saddle-max pair."""
     shape = (6, 7, 8)
