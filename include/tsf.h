@@ -116,6 +116,9 @@ typedef struct {
   int64_t d1_rounds_max;      /* ... of the longest column */
   int64_t d1_star_updates;    /* parity-mask updates of target lower stars by those visits */
   double ms_diagram, ms_assign, ms_step; /* host wall time of the three stages */
+  int64_t assign_rounds;      /* auction rounds of the last assignment (0 when exact) */
+  int64_t assign_phases;      /* ... its eps phases */
+  int64_t assign_checks;      /* ... its passes releasing rows off eps-complementary slackness */
 } tsf_stats;
 
 /* Creates a field from lx*ly*lz values (host or device memory, copied).

@@ -2,6 +2,7 @@
 // target diagram (Section 3), still pairs and the reduced assignment
 // (Section 4.3, Eq. 1), the direct gradient step (Section 4.1) and the loss
 // (Eq. 2).
+#include <atomic>
 #include "tsf_kernels.cuh"
 #include "tsf_solver.cuh"
 
@@ -700,47 +701,98 @@ __global__ void __launch_bounds__(kHT, 1) k_hungarian(int k, int mc, const Cand*
 // ---------------------------------------------------------------------------
 constexpr int kAuctionRounds = 1 << 24;
 
-// One warp evaluates row r: cheapest net cost n1 and, for the column jr it
-// holds, its net cost and weight (lane 0 has the results).
+// Options of a row are scanned by one warp in chunks of 32, in the kept
+// list's order (increasing w); prices are >= 0, so once a chunk's largest w
+// exceeds the running second-cheapest net cost no later option can change
+// the cheapest (n1, j1) or the second-cheapest n2, and the scan stops.  The
+// row's own diagonal is the first option.  Lane states merge by a
+// butterfly, so every lane ends with the warp's result.
+struct AucBest {
+  double n1, w1, n2;
+  int j1;
+};
+
+__device__ __forceinline__ void auc_take(AucBest& s, double v, int j, double w) {
+  if (v < s.n1 || (v == s.n1 && j < s.j1)) {
+    s.n2 = s.n1;
+    s.n1 = v;
+    s.j1 = j;
+    s.w1 = w;
+  } else if (v < s.n2) {
+    s.n2 = v;
+  }
+}
+
+__device__ __forceinline__ AucBest auc_warp_merge(AucBest s) {
+  for (int o = 16; o; o >>= 1) {
+    AucBest b;
+    b.n1 = __shfl_xor_sync(0xFFFFFFFFu, s.n1, o);
+    b.w1 = __shfl_xor_sync(0xFFFFFFFFu, s.w1, o);
+    b.n2 = __shfl_xor_sync(0xFFFFFFFFu, s.n2, o);
+    b.j1 = __shfl_xor_sync(0xFFFFFFFFu, s.j1, o);
+    if (b.n1 < s.n1 || (b.n1 == s.n1 && b.j1 < s.j1)) {
+      s.n2 = fmin(s.n1, b.n2);
+      s.n1 = b.n1;
+      s.j1 = b.j1;
+      s.w1 = b.w1;
+    } else {
+      s.n2 = fmin(s.n2, b.n1);
+    }
+  }
+  return s;
+}
+
 template <class Rows>
-__device__ __forceinline__ void auction_eval(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
-                                             const double* price, int jr, double& n1, double& ncur, double& wcur) {
+__device__ __forceinline__ AucBest auction_best(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
+                                                const double* price) {
   const double INF = __longlong_as_double(0x7FF0000000000000ll);
   const int lane = threadIdx.x & 31;
   const int n = R.count(r);
-  n1 = INF;
-  ncur = INF;
-  wcur = INF;
-  for (int c = lane; c <= n; c += 32) {
-    int j;
-    double w;
+  AucBest s{INF, INF, INF, 0x7FFFFFFF};
+  if (lane == 0) auc_take(s, __dadd_rn(diag_t[r], price[mc + r]), mc + r, diag_t[r]);
+  for (int base = 0; base < n; base += 32) {
+    const int c = base + lane;
+    double w = 0.0;
     if (c < n) {
+      int j;
       R.get(r, c, j, w);
-      j -= 1;
-    } else {
-      j = mc + r;
-      w = diag_t[r];
+      auc_take(s, __dadd_rn(w, price[j - 1]), j - 1, w);
     }
-    double v = __dadd_rn(w, price[j]);
-    n1 = fmin(n1, v);
-    if (j == jr) {
-      ncur = v;
-      wcur = w;
+    const double wlast = __shfl_sync(0xFFFFFFFFu, w, min(31, n - 1 - base));
+    const AucBest m = auc_warp_merge(s);
+    if (wlast > m.n2) break;
+  }
+  return auc_warp_merge(s);
+}
+
+// Cheapest net cost of row r (all lanes), with the same early stop.
+template <class Rows>
+__device__ __forceinline__ double auction_min(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
+                                              const double* price) {
+  const int lane = threadIdx.x & 31;
+  const int n = R.count(r);
+  double m = __dadd_rn(diag_t[r], price[mc + r]);
+  for (int base = 0; base < n; base += 32) {
+    const int c = base + lane;
+    double w = 0.0, v = m;
+    if (c < n) {
+      int j;
+      R.get(r, c, j, w);
+      v = __dadd_rn(w, price[j - 1]);
     }
+    for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    m = fmin(m, v);
+    const double wlast = __shfl_sync(0xFFFFFFFFu, w, min(31, n - 1 - base));
+    if (wlast > m) break;
   }
-  for (int o = 16; o; o >>= 1) {
-    n1 = fmin(n1, __shfl_down_sync(0xFFFFFFFFu, n1, o));
-    ncur = fmin(ncur, __shfl_down_sync(0xFFFFFFFFu, ncur, o));
-    wcur = fmin(wcur, __shfl_down_sync(0xFFFFFFFFu, wcur, o));
-  }
+  return m;
 }
 
 template <class Rows>
 __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __restrict__ diag_t, double prec,
                               const Pt* __restrict__ pts, const int32_t* __restrict__ gpts, int npg, HungWork H,
-                              int32_t* aux, int stride, uint32_t* status) {
+                              int32_t* aux, int stride, int32_t* rounds_out, uint32_t* status) {
   const int m = mc + k;
-  const double INF = __longlong_as_double(0x7FF0000000000000ll);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t* rowcol = aux;
   int32_t* bidcol = aux + stride;
@@ -749,6 +801,7 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
   unsigned long long* colbid = reinterpret_cast<unsigned long long*>(H.minv);
   unsigned long long* colkey = H.key;
   double* bidval = H.u;
+  double* bidw = H.bw;
   double* aw = H.aw;
   int32_t* owner = H.pm;
   __shared__ int s_n[2];
@@ -774,6 +827,7 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
       lists[0][atomicAdd(&s_n[0], 1)] = r;
     } else {
       rowcol[r] = mc + r;
+      aw[r] = diag_t[r];
     }
   }
   // D = sum of diag(p) in point order; the largest diag(t)
@@ -800,9 +854,10 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
   const double onep = __dadd_rn(1.0, prec);
   int cur = 0;
   unsigned round = 0;
-  for (int phase = 0;; ++phase) {
+  int phase = 0, checks = 0;
+  for (;; ++phase) {
     if (phase > 0) {
-      for (;;) {  // release the rows that break eps-complementary slackness
+      for (;; ++checks) {  // release the rows that break eps-complementary slackness
         for (int j = threadIdx.x; j < mc; j += kHT)
           if (owner[j] < 0) price[j] = 0.0;
         for (int r = threadIdx.x; r < k; r += kHT)
@@ -812,9 +867,8 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
         for (int r = warp; r < k; r += kHT / 32) {
           const int jr = rowcol[r];
           if (jr < 0) continue;
-          double n1, ncur, wcur;
-          auction_eval(R, r, mc, diag_t, price, jr, n1, ncur, wcur);
-          if (lane == 0 && ncur > __dadd_rn(n1, eps)) {
+          const double n1 = auction_min(R, r, mc, diag_t, price);
+          if (lane == 0 && __dadd_rn(aw[r], price[jr]) > __dadd_rn(n1, eps)) {
             bidcol[r] = -2;
             atomicAdd(&s_nv, 1);
           }
@@ -844,51 +898,20 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
       // bids: one warp per listed row
       for (int idx = warp; idx < ncur; idx += kHT / 32) {
         const int r = L[idx];
-        const int n = R.count(r);
-        double n1 = INF, n2 = INF;
-        int j1 = 0x7FFFFFFF;
-        for (int c = lane; c <= n; c += 32) {
-          int j;
-          double w;
-          if (c < n) {
-            R.get(r, c, j, w);
-            j -= 1;  // Rows give 1-based columns
-          } else {
-            j = mc + r;
-            w = diag_t[r];
-          }
-          double v = __dadd_rn(w, price[j]);
-          if (v < n1 || (v == n1 && j < j1)) {
-            n2 = n1;
-            n1 = v;
-            j1 = j;
-          } else if (v < n2) {
-            n2 = v;
-          }
-        }
-        for (int o = 16; o; o >>= 1) {
-          double b1 = __shfl_down_sync(0xFFFFFFFFu, n1, o);
-          int bj = __shfl_down_sync(0xFFFFFFFFu, j1, o);
-          double b2 = __shfl_down_sync(0xFFFFFFFFu, n2, o);
-          if (b1 < n1 || (b1 == n1 && bj < j1)) {
-            n2 = fmin(n1, b2);
-            n1 = b1;
-            j1 = bj;
-          } else {
-            n2 = fmin(n2, b1);
-          }
-        }
+        const AucBest b = auction_best(R, r, mc, diag_t, price);
         if (lane == 0) {
-          double g = __dsub_rn(n2, n1);
+          double g = __dsub_rn(b.n2, b.n1);
           g = __dadd_rn(g, eps);
-          double bid = __dadd_rn(price[j1], g);
-          if (j1 >= mc) {  // the row's own diagonal: nobody else bids for it
-            price[j1] = bid;
-            rowcol[r] = j1;
+          const double bid = __dadd_rn(price[b.j1], g);
+          if (b.j1 >= mc) {  // the row's own diagonal: nobody else bids for it
+            price[b.j1] = bid;
+            rowcol[r] = b.j1;
+            aw[r] = b.w1;
           } else {
-            bidcol[r] = j1;
+            bidcol[r] = b.j1;
             bidval[r] = bid;
-            atomicMax(&colbid[j1], (unsigned long long)__double_as_longlong(bid));
+            bidw[r] = b.w1;
+            atomicMax(&colbid[b.j1], (unsigned long long)__double_as_longlong(bid));
           }
         }
       }
@@ -916,6 +939,7 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
           }
           owner[j] = r;
           rowcol[r] = j;
+          aw[r] = bidw[r];
           price[j] = bidval[r];
           colbid[j] = 0ull;
         } else {
@@ -928,21 +952,37 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
     }
     // phase end: W, LB and the stop test
     for (int r = warp; r < k; r += kHT / 32) {
-      double n1, ncur, wcur;
-      auction_eval(R, r, mc, diag_t, price, rowcol[r], n1, ncur, wcur);
-      if (lane == 0) {
-        bidval[r] = n1;
-        aw[r] = wcur;
-      }
+      const double n1 = auction_min(R, r, mc, diag_t, price);
+      if (lane == 0) bidval[r] = n1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double W = 0.0, U = 0.0, P = 0.0;
-      for (int r = 0; r < k; ++r) {
-        W = __dadd_rn(W, aw[r]);
-        U = __dadd_rn(U, bidval[r]);
+    // W, U (row order) and P (column order): chunks staged in shared memory,
+    // added by one thread in order
+    __shared__ double s_w[kHT];
+    double W = 0.0, U = 0.0, P = 0.0;
+    for (int c0 = 0; c0 < k; c0 += kHT) {
+      const int r = c0 + threadIdx.x;
+      if (r < k) {
+        s_w[threadIdx.x] = aw[r];
+        s_chunk[threadIdx.x] = bidval[r];
       }
-      for (int j = 0; j < m; ++j) P = __dadd_rn(P, price[j]);
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int i = 0, n = min(kHT, k - c0); i < n; ++i) {
+          W = __dadd_rn(W, s_w[i]);
+          U = __dadd_rn(U, s_chunk[i]);
+        }
+      __syncthreads();
+    }
+    for (int c0 = 0; c0 < m; c0 += kHT) {
+      const int j = c0 + threadIdx.x;
+      if (j < m) s_chunk[threadIdx.x] = price[j];
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int i = 0, n = min(kHT, m - c0); i < n; ++i) P = __dadd_rn(P, s_chunk[i]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
       double lb = __dsub_rn(U, P);
       double lhs = __dadd_rn(W, dsum);
       double rhs = __dadd_rn(lb, dsum);
@@ -960,6 +1000,11 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
     if (s_stop) break;
     eps = s_eps;
   }
+  if (threadIdx.x == 0 && rounds_out) {
+    atomicAdd(rounds_out, (int)round);
+    atomicAdd(rounds_out + 1, phase + 1);
+    atomicAdd(rounds_out + 2, checks);
+  }
   __syncthreads();
   return true;
 }
@@ -970,11 +1015,391 @@ __global__ void __launch_bounds__(kHT, 1) k_auction(int k, int mc, const Cand* _
                                                  const double* __restrict__ diag_t, double prec,
                                                  const Pt* __restrict__ pts, const int32_t* __restrict__ plist,
                                                  int npg, HungWork H, int32_t* aux, int stride,
-                                                 int32_t* __restrict__ col_to_row, uint32_t* status) {
+                                                 int32_t* __restrict__ col_to_row, int32_t* rounds_out,
+                                                 uint32_t* status) {
   if (!auction_solve(k, mc, KeptRows{kept, koff, nkept, colpos}, diag_t, prec, pts, plist, npg, H, aux, stride,
-                     status))
+                     rounds_out, status))
     return;
   for (int j = threadIdx.x; j < mc; j += kHT) col_to_row[j] = H.pm[j];
+}
+
+// ---------------------------------------------------------------------------
+// The same auction over the whole GPU: one cooperative launch of
+// co-resident blocks, the steps of auction_solve separated by a grid
+// barrier instead of a block barrier, rows and columns spread over every
+// warp of the grid.  Identical arithmetic in identical order (the sums still
+// run on one thread); a large reduced problem then bids with thousands of
+// warps instead of 32.  State shared between blocks is read through L2
+// (__ldcg); the barrier gives up after ~2^24 polls, sets kErrSpin and the
+// auction returns false on every block.
+// ---------------------------------------------------------------------------
+constexpr int kGT = 512;        // threads per block of the grid auction
+constexpr int kGridMin = 192;   // fewer rows: the single-block auction
+
+struct AucCtl {
+  unsigned bar[2];  // arrivals, generation
+  int n[2];         // lengths of the two row lists
+  int nv;           // rows released by the current check
+  int stop;
+  int pad[2];
+  double eps;
+};
+
+__device__ __forceinline__ bool grid_barrier(AucCtl* c, unsigned nblocks, uint32_t* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = &c->bar[1];
+    const unsigned gen = *vgen;
+    __threadfence();
+    if (atomicAdd(&c->bar[0], 1u) == nblocks - 1) {
+      atomicExch(&c->bar[0], 0u);
+      __threadfence();
+      atomicAdd(&c->bar[1], 1u);
+    } else {
+      unsigned it = 0;
+      while (*vgen == gen) {
+        if (++it > (1u << 24)) {
+          atomicOr(status, kErrSpin);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <class Rows>
+__device__ __forceinline__ AucBest auction_best_cg(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
+                                                   const double* price) {
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+  const int lane = threadIdx.x & 31;
+  const int n = R.count(r);
+  AucBest s{INF, INF, INF, 0x7FFFFFFF};
+  if (lane == 0) auc_take(s, __dadd_rn(diag_t[r], __ldcg(price + mc + r)), mc + r, diag_t[r]);
+  for (int base = 0; base < n; base += 32) {
+    const int c = base + lane;
+    double w = 0.0;
+    if (c < n) {
+      int j;
+      R.get(r, c, j, w);
+      auc_take(s, __dadd_rn(w, __ldcg(price + j - 1)), j - 1, w);
+    }
+    const double wlast = __shfl_sync(0xFFFFFFFFu, w, min(31, n - 1 - base));
+    const AucBest m = auc_warp_merge(s);
+    if (wlast > m.n2) break;
+  }
+  return auc_warp_merge(s);
+}
+
+template <class Rows>
+__device__ __forceinline__ double auction_min_cg(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
+                                                 const double* price) {
+  const int lane = threadIdx.x & 31;
+  const int n = R.count(r);
+  double m = __dadd_rn(diag_t[r], __ldcg(price + mc + r));
+  for (int base = 0; base < n; base += 32) {
+    const int c = base + lane;
+    double w = 0.0, v = m;
+    if (c < n) {
+      int j;
+      R.get(r, c, j, w);
+      v = __dadd_rn(w, __ldcg(price + j - 1));
+    }
+    for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    m = fmin(m, v);
+    const double wlast = __shfl_sync(0xFFFFFFFFu, w, min(31, n - 1 - base));
+    if (wlast > m) break;
+  }
+  return m;
+}
+
+template <class Rows>
+__device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restrict__ diag_t, double prec,
+                             const Pt* __restrict__ pts, const int32_t* __restrict__ gpts, int npg, HungWork H,
+                             int32_t* aux, int stride, AucCtl* ctl, int32_t* rounds_out, uint32_t* status) {
+  const int m = mc + k;
+  const unsigned nb = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const int gtid = blockIdx.x * kGT + threadIdx.x, gthreads = nb * kGT;
+  const int gwarp = gtid >> 5, gwarps = gthreads >> 5;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  int32_t* rowcol = aux;
+  int32_t* bidcol = aux + stride;
+  int32_t* lists[2] = {aux + 2 * stride, aux + 3 * stride};
+  double* price = H.v;
+  unsigned long long* colbid = reinterpret_cast<unsigned long long*>(H.minv);
+  unsigned long long* colkey = H.key;
+  double* bidval = H.u;
+  double* bidw = H.bw;
+  double* aw = H.aw;
+  int32_t* owner = H.pm;
+  volatile int* vn = ctl->n;
+  __shared__ double s_chunk[kGT];
+  __shared__ double s_w[kGT];
+  for (int j = gtid; j < m; j += gthreads) price[j] = 0.0;
+  for (int j = gtid; j < mc; j += gthreads) {
+    owner[j] = -1;
+    colbid[j] = 0ull;
+    colkey[j] = ~0ull;
+  }
+  if (!grid_barrier(ctl, nb, status)) return false;
+  for (int r = gtid; r < k; r += gthreads) {
+    bidcol[r] = -1;
+    if (R.count(r) > 0) {
+      rowcol[r] = -1;
+      lists[0][atomicAdd(&ctl->n[0], 1)] = r;
+    } else {
+      rowcol[r] = mc + r;
+      aw[r] = diag_t[r];
+    }
+  }
+  // D = sum of diag(p) in point order, the largest diag(t), eps: block 0
+  double dsum = 0.0, cmax = 0.0;
+  if (blockIdx.x == 0) {
+    for (int c0 = 0; c0 < npg; c0 += kGT) {
+      int i = c0 + threadIdx.x;
+      if (i < npg) s_chunk[threadIdx.x] = cost_diag(pts[gpts[i]].b, pts[gpts[i]].d);
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int q = 0, n = min(kGT, npg - c0); q < n; ++q) dsum = __dadd_rn(dsum, s_chunk[q]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      for (int r = 0; r < k; ++r) cmax = fmax(cmax, diag_t[r]);
+      double emin = ldexp(cmax, -40);
+      if (!(emin > 0.0)) emin = 2.2250738585072014e-308;  // smallest normal double
+      double e = __dmul_rn(cmax, 0.25);
+      ctl->eps = e < emin ? emin : e;
+    }
+  }
+  if (!grid_barrier(ctl, nb, status)) return false;
+  double eps = __ldcg(&ctl->eps);
+  const double onep = __dadd_rn(1.0, prec);
+  int cur = 0;
+  unsigned round = 0;
+  int phase = 0, checks = 0;
+  for (;; ++phase) {
+    if (phase > 0) {
+      for (;; ++checks) {  // release the rows that break eps-complementary slackness
+        for (int j = gtid; j < mc; j += gthreads)
+          if (__ldcg(owner + j) < 0) price[j] = 0.0;
+        for (int r = gtid; r < k; r += gthreads)
+          if (__ldcg(rowcol + r) != mc + r) price[mc + r] = 0.0;
+        if (lead) ctl->nv = 0;
+        if (!grid_barrier(ctl, nb, status)) return false;
+        for (int r = gwarp; r < k; r += gwarps) {
+          const int jr = __ldcg(rowcol + r);
+          if (jr < 0) continue;
+          const double n1 = auction_min_cg(R, r, mc, diag_t, price);
+          if (lane == 0 && __dadd_rn(__ldcg(aw + r), __ldcg(price + jr)) > __dadd_rn(n1, eps)) {
+            bidcol[r] = -2;
+            atomicAdd(&ctl->nv, 1);
+          }
+        }
+        if (!grid_barrier(ctl, nb, status)) return false;
+        if (*(volatile int*)&ctl->nv == 0) break;
+        for (int r = gtid; r < k; r += gthreads) {
+          if (__ldcg(bidcol + r) != -2) continue;
+          bidcol[r] = -1;
+          const int jr = __ldcg(rowcol + r);
+          if (jr < mc) owner[jr] = -1;
+          rowcol[r] = -1;
+          lists[cur][atomicAdd(&ctl->n[cur], 1)] = r;
+        }
+        if (!grid_barrier(ctl, nb, status)) return false;
+      }
+    }
+    for (;; ++round) {
+      if (round >= (unsigned)kAuctionRounds) {
+        if (lead) atomicOr(status, kErrRounds);
+        return false;
+      }
+      const int ncur = vn[cur];
+      const int nxt = cur ^ 1;
+      if (ncur == 0) break;
+      const int32_t* L = lists[cur];
+      int32_t* LN = lists[nxt];
+      for (int idx = gwarp; idx < ncur; idx += gwarps) {
+        const int r = __ldcg(L + idx);
+        const AucBest b = auction_best_cg(R, r, mc, diag_t, price);
+        if (lane == 0) {
+          double g = __dsub_rn(b.n2, b.n1);
+          g = __dadd_rn(g, eps);
+          const double bid = __dadd_rn(__ldcg(price + b.j1), g);
+          if (b.j1 >= mc) {
+            price[b.j1] = bid;
+            rowcol[r] = b.j1;
+            aw[r] = b.w1;
+          } else {
+            bidcol[r] = b.j1;
+            bidval[r] = bid;
+            bidw[r] = b.w1;
+            atomicMax(&colbid[b.j1], (unsigned long long)__double_as_longlong(bid));
+          }
+        }
+      }
+      if (!grid_barrier(ctl, nb, status)) return false;
+      const unsigned long long tag = (unsigned long long)(0xFFFFFFFFu - round) << 32;
+      for (int idx = gtid; idx < ncur; idx += gthreads) {
+        const int r = __ldcg(L + idx);
+        const int j = __ldcg(bidcol + r);
+        if (j >= 0 && __ldcg(colbid + j) == (unsigned long long)__double_as_longlong(__ldcg(bidval + r)))
+          atomicMin(&colkey[j], tag | (unsigned)r);
+      }
+      if (!grid_barrier(ctl, nb, status)) return false;
+      for (int idx = gtid; idx < ncur; idx += gthreads) {
+        const int r = __ldcg(L + idx);
+        const int j = __ldcg(bidcol + r);
+        if (j < 0) continue;
+        bidcol[r] = -1;
+        if (__ldcg(colkey + j) == (tag | (unsigned)r)) {
+          const int old = __ldcg(owner + j);
+          if (old >= 0) {
+            rowcol[old] = -1;
+            LN[atomicAdd(&ctl->n[nxt], 1)] = old;
+          }
+          owner[j] = r;
+          rowcol[r] = j;
+          aw[r] = __ldcg(bidw + r);
+          price[j] = __ldcg(bidval + r);
+          colbid[j] = 0ull;
+        } else {
+          LN[atomicAdd(&ctl->n[nxt], 1)] = r;
+        }
+      }
+      if (lead) ctl->n[cur] = 0;
+      if (!grid_barrier(ctl, nb, status)) return false;
+      cur = nxt;
+    }
+    // phase end: W, LB and the stop test
+    for (int r = gwarp; r < k; r += gwarps) {
+      const double n1 = auction_min_cg(R, r, mc, diag_t, price);
+      if (lane == 0) bidval[r] = n1;
+    }
+    if (!grid_barrier(ctl, nb, status)) return false;
+    if (blockIdx.x == 0) {
+      double W = 0.0, U = 0.0, P = 0.0;
+      for (int c0 = 0; c0 < k; c0 += kGT) {
+        const int r = c0 + threadIdx.x;
+        if (r < k) {
+          s_w[threadIdx.x] = __ldcg(aw + r);
+          s_chunk[threadIdx.x] = __ldcg(bidval + r);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int i = 0, n = min(kGT, k - c0); i < n; ++i) {
+            W = __dadd_rn(W, s_w[i]);
+            U = __dadd_rn(U, s_chunk[i]);
+          }
+        __syncthreads();
+      }
+      for (int c0 = 0; c0 < m; c0 += kGT) {
+        const int j = c0 + threadIdx.x;
+        if (j < m) s_chunk[threadIdx.x] = __ldcg(price + j);
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int i = 0, n = min(kGT, m - c0); i < n; ++i) P = __dadd_rn(P, s_chunk[i]);
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        double lb = __dsub_rn(U, P);
+        double lhs = __dadd_rn(W, dsum);
+        double rhs = __dadd_rn(lb, dsum);
+        rhs = __dmul_rn(rhs, onep);
+        double emin = ldexp(cmax, -40);
+        if (!(emin > 0.0)) emin = 2.2250738585072014e-308;
+        int stop = (lhs <= rhs || !(eps > emin)) ? 1 : 0;
+        if (!stop) {
+          double e = __ddiv_rn(eps, 5.0);
+          ctl->eps = e < emin ? emin : e;
+        }
+        ctl->stop = stop;
+      }
+    }
+    if (!grid_barrier(ctl, nb, status)) return false;
+    if (*(volatile int*)&ctl->stop) break;
+    eps = __ldcg(&ctl->eps);
+  }
+  if (lead && rounds_out) {
+    atomicAdd(rounds_out, (int)round);
+    atomicAdd(rounds_out + 1, phase + 1);
+    atomicAdd(rounds_out + 2, checks);
+  }
+  return grid_barrier(ctl, nb, status);
+}
+
+// Group g of the fused path, when it has at least kGridMin free targets (the
+// single-block k_asg_solve prepared its columns and left it to this launch).
+__global__ void __launch_bounds__(kGT) k_auction_grid_group(AsgDev A, Pt* __restrict__ pts, int g, double prec,
+                                                            AucCtl* ctl, uint32_t* status) {
+  if (A.counts[8]) return;
+  const int npg = A.counts[g], k = A.counts[4 + g];
+  if (k < kGridMin || npg == 0) return;
+  int pbase = 0, tbase = 0, wbase = 0;
+  for (int gg = 0; gg < g; ++gg) {
+    pbase += A.counts[gg];
+    tbase += A.counts[4 + gg];
+    wbase += A.counts[gg] + A.counts[4 + gg] + 2;
+  }
+  const int mc = A.counts[13 + g];
+  HungWork H;
+  H.u = A.H.u + wbase;
+  H.v = A.H.v + wbase;
+  H.minv = A.H.minv + wbase;
+  H.list = A.H.list + wbase;
+  H.pm = A.H.pm + wbase;
+  H.way = A.H.way + wbase;
+  H.used = A.H.used + wbase;
+  H.key = A.H.key + wbase;
+  H.aw = A.H.aw + wbase;
+  H.bw = A.H.bw + wbase;
+  const int wg = npg + k + 2;
+  if (!auction_grid(k, mc, KeptRows{A.kept, A.kept_off + tbase, A.nkept + tbase, A.colpos + pbase},
+                    A.diag_t + tbase, prec, pts, A.plist + pbase, npg, H, A.aux + 4 * wbase, wg, ctl + g,
+                    A.counts + 10, status))
+    return;
+  for (int j = blockIdx.x * kGT + threadIdx.x; j < mc; j += gridDim.x * kGT) {
+    const int r = __ldcg(H.pm + j);
+    if (r >= 0) pts[A.plist[pbase + A.col_point[wbase + j]]].tgt = A.tlist[tbase + r];
+  }
+}
+
+// The group-by-group path's problem, over the whole GPU.
+__global__ void __launch_bounds__(kGT) k_auction_grid(int k, int mc, const Cand* __restrict__ kept,
+                                                      const uint32_t* __restrict__ koff,
+                                                      const uint32_t* __restrict__ nkept,
+                                                      const uint32_t* __restrict__ colpos,
+                                                      const double* __restrict__ diag_t, double prec,
+                                                      const Pt* __restrict__ pts, const int32_t* __restrict__ plist,
+                                                      int npg, HungWork H, int32_t* aux, int stride, AucCtl* ctl,
+                                                      int32_t* __restrict__ col_to_row, int32_t* rounds_out,
+                                                      uint32_t* status) {
+  if (!auction_grid(k, mc, KeptRows{kept, koff, nkept, colpos}, diag_t, prec, pts, plist, npg, H, aux, stride, ctl,
+                    rounds_out, status))
+    return;
+  for (int j = blockIdx.x * kGT + threadIdx.x; j < mc; j += gridDim.x * kGT) col_to_row[j] = __ldcg(H.pm + j);
+}
+
+// Blocks of the grid auction: co-resident on at most 128 SMs (one block each).
+static int grid_auction_blocks() {
+  static std::atomic<int> nb{0};
+  int v = nb.load(std::memory_order_acquire);
+  if (v == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_auction_grid, kGT, 0);
+    v = std::max(1, std::min(sms, 128) * std::min(per, 1));
+    nb.store(v, std::memory_order_release);
+  }
+  return v;
 }
 
 __global__ void k_colpos(int npg, const uint32_t* __restrict__ is_col, const uint32_t* __restrict__ pos,
@@ -1050,6 +1475,9 @@ __global__ void __launch_bounds__(1024) k_asg_partition(int np, const Pt* __rest
     }
     A.counts[8] = 0;
     A.counts[9] = 0;
+    A.counts[10] = 0;  // auction rounds, phases, release passes
+    A.counts[11] = 0;
+    A.counts[12] = 0;
     for (int g = 0; g < 8; ++g) run[g] = base[g];
   }
   __syncthreads();
@@ -1235,13 +1663,18 @@ __global__ void __launch_bounds__(kHT) k_asg_solve(AsgDev A, Pt* __restrict__ pt
   H.used = A.H.used + wbase;
   H.key = A.H.key + wbase;
   H.aw = A.H.aw + wbase;
+  H.bw = A.H.bw + wbase;
   double* diag_t = A.diag_t + tbase;
   for (int t = threadIdx.x; t < k; t += kHT) diag_t[t] = cost_diag(T[A.tlist[tbase + t]].b, T[A.tlist[tbase + t]].d);
   __syncthreads();
   if (prec > 0.0) {
+    if (k >= kGridMin) {  // k_auction_grid_group solves it over the whole GPU
+      if (threadIdx.x == 0) A.counts[13 + g] = mc;
+      return;
+    }
     const int wg = npg + k + 2;
     if (!auction_solve(k, mc, KeptRows{A.kept, A.kept_off + tbase, A.nkept + tbase, A.colpos + pbase}, diag_t, prec,
-                       pts, A.plist + pbase, npg, H, A.aux + 4 * wbase, wg, status))
+                       pts, A.plist + pbase, npg, H, A.aux + 4 * wbase, wg, A.counts + 10, status))
       return;
     for (int j = threadIdx.x; j < mc; j += kHT) {
       int r = H.pm[j];
@@ -1277,11 +1710,30 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double p
   k_asg_partition<<<1, 1024, 0, st>>>(np, pts, nt, T, B.taken, B.A, pts); note_launch();
   k_asg_candidates<<<max(nt, 1), 512, 0, st>>>(pts, T, B.A); note_launch();
   k_asg_solve<<<3, kHT, 0, st>>>(B.A, pts, T, prec, status); note_launch();
-  int32_t hc[10];
+  if (prec > 0.0) {  // groups with many free targets: the auction over the whole GPU
+    const int nb = grid_auction_blocks();
+    cudaMemsetAsync(B.actl, 0, 3 * sizeof(AucCtl), st);
+    for (int g = 0; g < 3; ++g) {
+      AsgDev A = B.A;
+      Pt* p = pts;
+      int gg = g;
+      double pr = prec;
+      AucCtl* c = static_cast<AucCtl*>(B.actl);
+      void* args[] = {&A, &p, &gg, &pr, &c, &status};
+      if (cudaLaunchCooperativeKernel((const void*)k_auction_grid_group, dim3(nb), dim3(kGT), args, 0, st) !=
+          cudaSuccess)
+        return -4;
+      note_launch();
+    }
+  }
+  int32_t hc[13];
   cudaMemcpyAsync(hc, B.A.counts, sizeof(hc), cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&as->status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   as->status_valid = !hc[8];
+  as->rounds = hc[10];
+  as->phases = hc[11];
+  as->checks = hc[12];
   for (int g = 0; g < 4; ++g) as->k[g] = hc[4 + g];
   if (!hc[8]) return 0;
   return assign_groups(np, pts, nt, T, prec, B, status, as, st);
@@ -1326,13 +1778,42 @@ int assign_groups(int np, Pt* pts, int nt, const Tg* T, double prec, SolverBufs&
     if (mc + k + 1 > B.cap_cols) return -3;
     k_colpos<<<(npg + 255) / 256, 256, 0, st>>>(npg, B.is_col, B.colpos, B.colpos, B.col_point); note_launch();
     k_diag_t<<<(k + 255) / 256, 256, 0, st>>>(k, B.tlist, T, B.diag_t); note_launch();
-    if (prec > 0.0) {
+    if (prec > 0.0 && k >= kGridMin) {
+      const int nb = grid_auction_blocks();
+      cudaMemsetAsync(B.actl, 0, sizeof(AucCtl), st);
+      const Cand* kept = B.kept;
+      const uint32_t *koff = B.u32b, *nk = B.nkept, *cp = B.colpos;
+      const double* dt = B.diag_t;
+      const Pt* cpts = pts;
+      const int32_t* pl = B.plist;
+      HungWork H = B.H;
+      int32_t* aux = B.aux;
+      int stride = B.cap_cols + 1;
+      AucCtl* c = static_cast<AucCtl*>(B.actl);
+      int32_t* ctr = B.col_to_row;
+      int32_t* ro = B.A.counts + 10;
+      int kk = k, mm = mc, nn = npg;
+      double pr = prec;
+      void* args[] = {&kk, &mm, &kept, &koff, &nk, &cp, &dt, &pr, &cpts, &pl, &nn, &H, &aux, &stride, &c, &ctr, &ro,
+                      &status};
+      if (cudaLaunchCooperativeKernel((const void*)k_auction_grid, dim3(nb), dim3(kGT), args, 0, st) != cudaSuccess)
+        return -4;
+      note_launch();
+    } else if (prec > 0.0) {
       k_auction<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, prec, pts, B.plist, npg, B.H,
-                                   B.aux, B.cap_cols + 1, B.col_to_row, status); note_launch();
+                                   B.aux, B.cap_cols + 1, B.col_to_row, B.A.counts + 10, status); note_launch();
     } else {
       k_hungarian<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, B.H, B.col_to_row, status); note_launch();
     }
     k_apply_assignment<<<(mc + 255) / 256, 256, 0, st>>>(mc, B.col_to_row, B.col_point, B.plist, B.tlist, pts); note_launch();
+  }
+  if (prec > 0.0) {  // rounds of the fused attempt plus these
+    int32_t r[3] = {0, 0, 0};
+    cudaMemcpyAsync(r, B.A.counts + 10, sizeof(r), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    as->rounds = r[0];
+    as->phases = r[1];
+    as->checks = r[2];
   }
   return 0;
 }

@@ -104,6 +104,7 @@ struct tsf_field {
   int d1_cols = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
+  int64_t assign_rounds = 0, assign_phases = 0, assign_checks = 0;
   // profiling: event pairs recorded around stages, resolved after each call
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -309,6 +310,7 @@ void grow_solver(tsf_field* F, int np, int nt) {
     dev_free(A.H.used);
     dev_free(A.H.key);
     dev_free(A.H.aw);
+    dev_free(A.H.bw);
     dev_free(A.aux);
     size_t w = (size_t)cp + ctt + 8;
     A.cap_kept = (int)std::min<int64_t>((int64_t)ctt * 2048, std::max<int64_t>((int64_t)16 * cp, 1 << 18));
@@ -325,6 +327,7 @@ void grow_solver(tsf_field* F, int np, int nt) {
     ck(dev_alloc(&A.H.used, w));
     ck(dev_alloc(&A.H.key, w));
     ck(dev_alloc(&A.H.aw, w));
+    ck(dev_alloc(&A.H.bw, w));
     ck(dev_alloc(&A.aux, 4 * w));
     A.plist = B.plist;
     A.tlist = B.tlist;
@@ -337,6 +340,7 @@ void grow_solver(tsf_field* F, int np, int nt) {
   if (!B.count) ck(dev_alloc(&B.count, 4));
   if (!B.dsum) ck(dev_alloc(&B.dsum, 1));
   if (!B.counters) ck(dev_alloc(&B.counters, 4));
+  if (!B.actl) ck(cudaMalloc(&B.actl, 256));
   B.cap_k = ctt;
   F->cap_pts = cp;
   F->cap_t = ctt;
@@ -373,6 +377,7 @@ void grow_assign(tsf_field* F, int cand, int cols) {
     dev_free(H.used);
     dev_free(H.key);
     dev_free(H.aw);
+    dev_free(H.bw);
     dev_free(B.aux);
     dev_free(B.col_to_row);
     ck(dev_alloc(&H.u, c + 1));
@@ -384,6 +389,7 @@ void grow_assign(tsf_field* F, int cand, int cols) {
     ck(dev_alloc(&H.used, c + 1));
     ck(dev_alloc(&H.key, c + 1));
     ck(dev_alloc(&H.aw, c + 1));
+    ck(dev_alloc(&H.bw, c + 1));
     ck(dev_alloc(&B.aux, 4 * ((size_t)c + 1)));
     ck(dev_alloc(&B.col_to_row, c + 1));
     B.cap_cols = c;
@@ -534,12 +540,16 @@ int run_assign(tsf_field* F, const Pt* ref, int nr, double prec = 0.0) {
     if (r == 0) break;
     if (r == -2) grow_assign(F, std::max(2 * F->B.cap_cand, 4096), 0);
     else if (r == -3) grow_assign(F, 0, std::max(2 * F->B.cap_cols, 4096));
+    else if (r == -4) return TSF_ECUDA;  // a cooperative launch was refused
     else return TSF_EINTERNAL;
     // the failed pass may have written partial assignments: restart from the still step
   }
   uint32_t s = as.status_valid ? as.status : read_status(F);
   if (status_code(s) != TSF_OK) return status_code(s);
   F->ms_assign = now_ms() - t0;
+  F->assign_rounds = as.rounds;
+  F->assign_phases = as.phases;
+  F->assign_checks = as.checks;
   return TSF_OK;
 }
 
@@ -571,6 +581,9 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
   out->d1_star_updates = (int64_t)F->d1_stats[4];
   out->ms_diagram = F->ms_diag;
   out->ms_assign = F->ms_assign;
+  out->assign_rounds = F->assign_rounds;
+  out->assign_phases = F->assign_phases;
+  out->assign_checks = F->assign_checks;
   out->ms_step = F->ms_step;
   (void)p;
 }
@@ -764,7 +777,9 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(B.H.way);
   dev_free(B.H.used);
   dev_free(B.H.key);
+  if (B.actl) cudaFree(B.actl);
   dev_free(B.H.aw);
+  dev_free(B.H.bw);
   dev_free(B.aux);
   dev_free(B.terms);
   dev_free(B.dsum);
@@ -783,6 +798,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(B.A.H.used);
   dev_free(B.A.H.key);
   dev_free(B.A.H.aw);
+  dev_free(B.A.H.bw);
   dev_free(B.A.aux);
   if (F->h_flags) cudaFreeHost(F->h_flags);
   for (auto e : F->ev_pool) cudaEventDestroy(e);

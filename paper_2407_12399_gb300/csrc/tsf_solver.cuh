@@ -42,6 +42,7 @@ struct HungWork {
   int32_t* list;  // columns reached by the current row's search
   unsigned long long* key;  // auction: round-tagged winner of a column
   double* aw;               // auction: cost of each row's assigned option
+  double* bw;               // auction: cost of each row's bid option
   int32_t* pm;
   int32_t* way;
   uint8_t* used;
@@ -79,6 +80,7 @@ struct SolverBufs {
   uint32_t* colpos;
   int32_t* col_point;
   int32_t* aux;  // auction scratch of the group-by-group path: 4 x (cap_cols + 1)
+  void* actl;    // control blocks (barrier, counters) of the grid auction, one per group
   int32_t* col_to_row;
   double* diag_t;
   HungWork H;
@@ -95,6 +97,9 @@ struct AssignStats {
   int k[4];
   uint32_t status;    // the status word, read with the group counts (fast path)
   bool status_valid;
+  int32_t rounds;     // auction rounds (all groups)
+  int32_t phases;     // auction eps phases (all groups)
+  int32_t checks;     // auction release passes (all groups)
 };
 
 int build_diagram(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, int n3, const PairOut& P,
