@@ -512,16 +512,149 @@ __device__ __forceinline__ int block_exscan_int1024(int v, int& total) {
 // tree and their diagonal columns; every other column keeps minv = +inf
 // (inf - delta = inf) and never takes part in a decision.  So each step works
 // on the list of reached columns instead of all m columns: the same
-// arithmetic on the same columns, O(reached) per step.  Rows: count(r) and
+// arithmetic on the same columns, O(reached) per step.  Once a row's search
+// has reached more than m/8 columns it sweeps all m columns instead (cheaper
+// than gathering through the list; identical results).  Rows: count(r) and
 // get(r, c, j, w) give row r's c-th candidate as 1-based column j, weight w.
+// The textbook dense form of the same search, for problems small enough
+// that sweeping all m columns per step is cheaper than gathering the
+// reached ones: row i0's costs are scattered into a dense row (H.aw, +inf
+// elsewhere), then one pass relaxes and takes the argmin, one pass moves
+// the potentials.  Identical arithmetic and ties.
+constexpr int kSapDenseMax = 16384;
+
+template <class Rows>
+__device__ bool sap_dense(int k, int mc, const Rows& R, const double* __restrict__ diag_t, HungWork H,
+                          uint32_t* status) {
+  const int m = mc + k;
+  const double INF = __longlong_as_double(0x7FF0000000000000ll);
+  double* row = H.aw;
+  __shared__ int s_j0;
+  __shared__ double s_val[kHT / 32];
+  __shared__ int s_idx[kHT / 32];
+  __shared__ double s_delta;
+  __shared__ int s_j1;
+  for (int j = threadIdx.x; j <= m; j += kHT) {
+    H.v[j] = 0.0;
+    H.pm[j] = 0;
+    H.way[j] = 0;
+  }
+  for (int i = threadIdx.x; i <= k; i += kHT) H.u[i] = 0.0;
+  __syncthreads();
+  for (int i = 1; i <= k; ++i) {
+    for (int j = threadIdx.x; j <= m; j += kHT) {
+      H.minv[j] = INF;
+      H.used[j] = 0;
+    }
+    if (threadIdx.x == 0) {
+      H.pm[0] = i;
+      s_j0 = 0;
+    }
+    __syncthreads();
+    for (int guard = 0;; ++guard) {
+      if (guard > m + 2) {
+        if (threadIdx.x == 0) atomicOr(status, kErrRounds);
+        return false;
+      }
+      const int j0 = s_j0;
+      if (threadIdx.x == 0) H.used[j0] = 1;
+      const int i0 = H.pm[j0];
+      for (int j = 1 + threadIdx.x; j <= m; j += kHT) row[j] = INF;
+      __syncthreads();
+      const int n = R.count(i0 - 1);
+      for (int c = threadIdx.x; c < n; c += kHT) {
+        int j;
+        double w;
+        R.get(i0 - 1, c, j, w);
+        row[j] = w;
+      }
+      if (threadIdx.x == 0) row[1 + mc + (i0 - 1)] = diag_t[i0 - 1];
+      __syncthreads();
+      const double ui0 = H.u[i0];
+      double bv = INF;
+      int bj = 0x7FFFFFFF;
+      for (int j = 1 + threadIdx.x; j <= m; j += kHT) {
+        if (H.used[j]) continue;
+        double cur = __dsub_rn(__dsub_rn(row[j], ui0), H.v[j]);
+        double mv = H.minv[j];
+        if (cur < mv) {
+          mv = cur;
+          H.minv[j] = cur;
+          H.way[j] = j0;
+        }
+        if (mv < bv || (mv == bv && j < bj)) {
+          bv = mv;
+          bj = j;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        double ov = __shfl_down_sync(0xFFFFFFFFu, bv, o);
+        int oj = __shfl_down_sync(0xFFFFFFFFu, bj, o);
+        if (ov < bv || (ov == bv && oj < bj)) {
+          bv = ov;
+          bj = oj;
+        }
+      }
+      if ((threadIdx.x & 31) == 0) {
+        s_val[threadIdx.x >> 5] = bv;
+        s_idx[threadIdx.x >> 5] = bj;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double v0 = s_val[0];
+        int j1 = s_idx[0];
+        for (int w = 1; w < kHT / 32; ++w)
+          if (s_val[w] < v0 || (s_val[w] == v0 && s_idx[w] < j1)) {
+            v0 = s_val[w];
+            j1 = s_idx[w];
+          }
+        s_delta = v0;
+        s_j1 = j1;
+      }
+      __syncthreads();
+      const double delta = s_delta;
+      const int j1 = s_j1;
+      if (j1 == 0x7FFFFFFF) {
+        if (threadIdx.x == 0) atomicOr(status, kErrInconsistent);
+        return false;
+      }
+      for (int j = threadIdx.x; j <= m; j += kHT) {
+        if (H.used[j]) {
+          int r = H.pm[j];
+          H.u[r] = __dadd_rn(H.u[r], delta);
+          H.v[j] = __dsub_rn(H.v[j], delta);
+        } else {
+          H.minv[j] = __dsub_rn(H.minv[j], delta);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_j0 = j1;
+      __syncthreads();
+      if (H.pm[j1] == 0) break;
+    }
+    if (threadIdx.x == 0) {
+      int j0 = s_j0;
+      do {
+        int j1 = H.way[j0];
+        H.pm[j0] = H.pm[j1];
+        j0 = j1;
+      } while (j0);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 template <class Rows>
 __device__ bool sap_solve(int k, int mc, const Rows& R, const double* __restrict__ diag_t, HungWork H,
                           uint32_t* status) {
+  if (mc + k <= kSapDenseMax) return sap_dense(k, mc, R, diag_t, H, status);
   const int m = mc + k;
   const double INF = __longlong_as_double(0x7FF0000000000000ll);
   __shared__ int s_nl;
   __shared__ double s_val[kHT / 32];
   __shared__ int s_idx[kHT / 32];
+  const int dense_at = m / 8;
   for (int j = threadIdx.x; j <= m; j += kHT) {
     H.v[j] = 0.0;
     H.pm[j] = 0;
@@ -536,6 +669,7 @@ __device__ bool sap_solve(int k, int mc, const Rows& R, const double* __restrict
     if (threadIdx.x == 0) H.pm[0] = i;
     __syncthreads();
     int j0 = 0;
+    bool dense = false;
     for (int guard = 0;; ++guard) {
       if (guard > m + 2) {
         if (threadIdx.x == 0) atomicOr(status, kErrRounds);
@@ -545,37 +679,62 @@ __device__ bool sap_solve(int k, int mc, const Rows& R, const double* __restrict
       const int i0 = H.pm[j0];
       const double ui0 = H.u[i0];
       const int n = R.count(i0 - 1);
-      for (int c = threadIdx.x; c <= n; c += kHT) {
-        int j;
-        double w;
-        if (c < n) {
-          R.get(i0 - 1, c, j, w);
-        } else {
-          j = 1 + mc + (i0 - 1);
-          w = diag_t[i0 - 1];
+      for (int c0 = 0; c0 <= n; c0 += kHT) {  // whole warps iterate: the appends are warp-aggregated
+        const int c = c0 + threadIdx.x;
+        int j = 0;
+        bool app = false;
+        if (c <= n) {
+          double w;
+          if (c < n) {
+            R.get(i0 - 1, c, j, w);
+          } else {
+            j = 1 + mc + (i0 - 1);
+            w = diag_t[i0 - 1];
+          }
+          if (j != j0 && !H.used[j]) {
+            double cur = __dsub_rn(__dsub_rn(w, ui0), H.v[j]);
+            double mv = H.minv[j];
+            app = mv == INF && !dense;
+            if (cur < mv) {
+              H.minv[j] = cur;
+              H.way[j] = j0;
+            }
+          }
         }
-        if (j == j0 || H.used[j]) continue;
-        double cur = __dsub_rn(__dsub_rn(w, ui0), H.v[j]);
-        double mv = H.minv[j];
-        if (mv == INF) H.list[atomicAdd(&s_nl, 1)] = j;
-        if (cur < mv) {
-          H.minv[j] = cur;
-          H.way[j] = j0;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, app);
+        if (bal) {
+          const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(&s_nl, __popc(bal));
+          base = __shfl_sync(0xFFFFFFFFu, base, leader);
+          if (app) H.list[base + __popc(bal & ((1u << lane) - 1u))] = j;
         }
       }
       if (threadIdx.x == 0) H.used[j0] = 1;
       __syncthreads();
       // argmin of minv over the reached unused columns, lowest index on ties
       const int nl = s_nl;
+      if (!dense && nl > dense_at) dense = true;  // uniform: every thread reads the same s_nl
       double bv = INF;
       int bj = 0x7FFFFFFF;
-      for (int q = threadIdx.x; q < nl; q += kHT) {
-        int j = H.list[q];
-        if (H.used[j]) continue;
-        double mv = H.minv[j];
-        if (mv < bv || (mv == bv && j < bj)) {
-          bv = mv;
-          bj = j;
+      if (dense) {
+        for (int j = 1 + threadIdx.x; j <= m; j += kHT) {
+          if (H.used[j]) continue;
+          double mv = H.minv[j];
+          if (mv < bv) {  // unreached columns (minv = inf) never win
+            bv = mv;
+            bj = j;
+          }
+        }
+      } else {
+        for (int q = threadIdx.x; q < nl; q += kHT) {
+          int j = H.list[q];
+          if (H.used[j]) continue;
+          double mv = H.minv[j];
+          if (mv < bv || (mv == bv && j < bj)) {
+            bv = mv;
+            bj = j;
+          }
         }
       }
       for (int o = 16; o; o >>= 1) {
@@ -609,14 +768,26 @@ __device__ bool sap_solve(int k, int mc, const Rows& R, const double* __restrict
         H.u[r] = __dadd_rn(H.u[r], delta);
         H.v[0] = __dsub_rn(H.v[0], delta);
       }
-      for (int q = threadIdx.x; q < nl; q += kHT) {
-        int j = H.list[q];
-        if (H.used[j]) {
-          int r = H.pm[j];
-          H.u[r] = __dadd_rn(H.u[r], delta);
-          H.v[j] = __dsub_rn(H.v[j], delta);
-        } else {
-          H.minv[j] = __dsub_rn(H.minv[j], delta);
+      if (dense) {
+        for (int j = 1 + threadIdx.x; j <= m; j += kHT) {
+          if (H.used[j]) {
+            int r = H.pm[j];
+            H.u[r] = __dadd_rn(H.u[r], delta);
+            H.v[j] = __dsub_rn(H.v[j], delta);
+          } else if (H.minv[j] != INF) {
+            H.minv[j] = __dsub_rn(H.minv[j], delta);
+          }
+        }
+      } else {
+        for (int q = threadIdx.x; q < nl; q += kHT) {
+          int j = H.list[q];
+          if (H.used[j]) {
+            int r = H.pm[j];
+            H.u[r] = __dadd_rn(H.u[r], delta);
+            H.v[j] = __dsub_rn(H.v[j], delta);
+          } else {
+            H.minv[j] = __dsub_rn(H.minv[j], delta);
+          }
         }
       }
       __syncthreads();
@@ -632,11 +803,18 @@ __device__ bool sap_solve(int k, int mc, const Rows& R, const double* __restrict
       } while (j);
     }
     // back to the untouched state for the next row
-    const int nl = s_nl;
-    for (int q = threadIdx.x; q < nl; q += kHT) {
-      int j = H.list[q];
-      H.minv[j] = INF;
-      H.used[j] = 0;
+    if (dense) {
+      for (int j = 1 + threadIdx.x; j <= m; j += kHT) {
+        H.minv[j] = INF;
+        H.used[j] = 0;
+      }
+    } else {
+      const int nl = s_nl;
+      for (int q = threadIdx.x; q < nl; q += kHT) {
+        int j = H.list[q];
+        H.minv[j] = INF;
+        H.used[j] = 0;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1624,8 +1802,11 @@ __global__ void __launch_bounds__(512) k_asg_candidates(const Pt* __restrict__ p
 // one block per finite group: column map (candidate points in point order,
 // then one private diagonal column per target) and the shortest augmenting
 // path solve, exactly as k_hungarian
-__global__ void __launch_bounds__(kHT) k_asg_solve(AsgDev A, Pt* __restrict__ pts, const Tg* __restrict__ T,
-                                                   double prec, uint32_t* status) {
+// AUCTION: the auction (prec > 0) instead of the exact search; two kernels so
+// that neither carries the other's registers.
+template <bool AUCTION>
+__global__ void __launch_bounds__(kHT, 1) k_asg_solve(AsgDev A, Pt* __restrict__ pts, const Tg* __restrict__ T,
+                                                      double prec, uint32_t* status) {
   const int g = blockIdx.x;
   if (A.counts[8]) return;
   int npg = A.counts[g], k = A.counts[4 + g];
@@ -1667,7 +1848,7 @@ __global__ void __launch_bounds__(kHT) k_asg_solve(AsgDev A, Pt* __restrict__ pt
   double* diag_t = A.diag_t + tbase;
   for (int t = threadIdx.x; t < k; t += kHT) diag_t[t] = cost_diag(T[A.tlist[tbase + t]].b, T[A.tlist[tbase + t]].d);
   __syncthreads();
-  if (prec > 0.0) {
+  if constexpr (AUCTION) {
     if (k >= kGridMin) {  // k_auction_grid_group solves it over the whole GPU
       if (threadIdx.x == 0) A.counts[13 + g] = mc;
       return;
@@ -1681,12 +1862,13 @@ __global__ void __launch_bounds__(kHT) k_asg_solve(AsgDev A, Pt* __restrict__ pt
       if (r >= 0) pts[A.plist[pbase + A.col_point[wbase + j]]].tgt = A.tlist[tbase + r];
     }
     return;
-  }
+  } else {
   if (!sap_solve(k, mc, KeptRows{A.kept, A.kept_off + tbase, A.nkept + tbase, A.colpos + pbase}, diag_t, H, status))
     return;
   for (int j = 1 + threadIdx.x; j <= mc; j += kHT) {
     int r = H.pm[j] - 1;
     if (r >= 0) pts[A.plist[pbase + A.col_point[wbase + j - 1]]].tgt = A.tlist[tbase + r];
+  }
   }
 }
 
@@ -1709,7 +1891,12 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double p
   cudaMemsetAsync(B.A.is_col, 0, sizeof(uint32_t) * (size_t)np, st);
   k_asg_partition<<<1, 1024, 0, st>>>(np, pts, nt, T, B.taken, B.A, pts); note_launch();
   k_asg_candidates<<<max(nt, 1), 512, 0, st>>>(pts, T, B.A); note_launch();
-  k_asg_solve<<<3, kHT, 0, st>>>(B.A, pts, T, prec, status); note_launch();
+  if (prec > 0.0) {
+    k_asg_solve<true><<<3, kHT, 0, st>>>(B.A, pts, T, prec, status);
+  } else {
+    k_asg_solve<false><<<3, kHT, 0, st>>>(B.A, pts, T, prec, status);
+  }
+  note_launch();
   if (prec > 0.0) {  // groups with many free targets: the auction over the whole GPU
     const int nb = grid_auction_blocks();
     cudaMemsetAsync(B.actl, 0, 3 * sizeof(AucCtl), st);
