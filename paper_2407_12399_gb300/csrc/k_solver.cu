@@ -4,6 +4,7 @@
 // (Eq. 2).
 #include <atomic>
 #include "tsf_kernels.cuh"
+#include "tsf_grid.cuh"
 #include "tsf_solver.cuh"
 
 namespace tsf {
@@ -1208,8 +1209,8 @@ __global__ void __launch_bounds__(kHT, 1) k_auction(int k, int mc, const Cand* _
 // warp of the grid.  Identical arithmetic in identical order (the sums still
 // run on one thread); a large reduced problem then bids with thousands of
 // warps instead of 32.  State shared between blocks is read through L2
-// (__ldcg); the barrier gives up after ~2^24 polls, sets kErrSpin and the
-// auction returns false on every block.
+// (__ldcg); the barrier (tsf_grid.cuh) gives up after ~2^24 polls, sets
+// kErrSpin and the auction returns false on every block.
 // ---------------------------------------------------------------------------
 constexpr int kGT = 512;        // threads per block of the grid auction
 constexpr int kGridMin = 192;   // fewer rows: the single-block auction
@@ -1222,36 +1223,6 @@ struct AucCtl {
   int pad[2];
   double eps;
 };
-
-__device__ __forceinline__ bool grid_barrier(AucCtl* c, unsigned nblocks, uint32_t* status) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned* vgen = &c->bar[1];
-    const unsigned gen = *vgen;
-    __threadfence();
-    if (atomicAdd(&c->bar[0], 1u) == nblocks - 1) {
-      atomicExch(&c->bar[0], 0u);
-      __threadfence();
-      atomicAdd(&c->bar[1], 1u);
-    } else {
-      unsigned it = 0;
-      while (*vgen == gen) {
-        if (++it > (1u << 24)) {
-          atomicOr(status, kErrSpin);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 template <class Rows>
 __device__ __forceinline__ AucBest auction_best_cg(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
@@ -1327,7 +1298,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
     colbid[j] = 0ull;
     colkey[j] = ~0ull;
   }
-  if (!grid_barrier(ctl, nb, status)) return false;
+  if (!grid_barrier(ctl->bar, nb, status)) return false;
   for (int r = gtid; r < k; r += gthreads) {
     bidcol[r] = -1;
     if (R.count(r) > 0) {
@@ -1357,7 +1328,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
       ctl->eps = e < emin ? emin : e;
     }
   }
-  if (!grid_barrier(ctl, nb, status)) return false;
+  if (!grid_barrier(ctl->bar, nb, status)) return false;
   double eps = __ldcg(&ctl->eps);
   const double onep = __dadd_rn(1.0, prec);
   int cur = 0;
@@ -1371,7 +1342,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
         for (int r = gtid; r < k; r += gthreads)
           if (__ldcg(rowcol + r) != mc + r) price[mc + r] = 0.0;
         if (lead) ctl->nv = 0;
-        if (!grid_barrier(ctl, nb, status)) return false;
+        if (!grid_barrier(ctl->bar, nb, status)) return false;
         for (int r = gwarp; r < k; r += gwarps) {
           const int jr = __ldcg(rowcol + r);
           if (jr < 0) continue;
@@ -1381,7 +1352,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
             atomicAdd(&ctl->nv, 1);
           }
         }
-        if (!grid_barrier(ctl, nb, status)) return false;
+        if (!grid_barrier(ctl->bar, nb, status)) return false;
         if (*(volatile int*)&ctl->nv == 0) break;
         for (int r = gtid; r < k; r += gthreads) {
           if (__ldcg(bidcol + r) != -2) continue;
@@ -1391,7 +1362,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
           rowcol[r] = -1;
           lists[cur][atomicAdd(&ctl->n[cur], 1)] = r;
         }
-        if (!grid_barrier(ctl, nb, status)) return false;
+        if (!grid_barrier(ctl->bar, nb, status)) return false;
       }
     }
     for (;; ++round) {
@@ -1423,7 +1394,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
           }
         }
       }
-      if (!grid_barrier(ctl, nb, status)) return false;
+      if (!grid_barrier(ctl->bar, nb, status)) return false;
       const unsigned long long tag = (unsigned long long)(0xFFFFFFFFu - round) << 32;
       for (int idx = gtid; idx < ncur; idx += gthreads) {
         const int r = __ldcg(L + idx);
@@ -1431,7 +1402,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
         if (j >= 0 && __ldcg(colbid + j) == (unsigned long long)__double_as_longlong(__ldcg(bidval + r)))
           atomicMin(&colkey[j], tag | (unsigned)r);
       }
-      if (!grid_barrier(ctl, nb, status)) return false;
+      if (!grid_barrier(ctl->bar, nb, status)) return false;
       for (int idx = gtid; idx < ncur; idx += gthreads) {
         const int r = __ldcg(L + idx);
         const int j = __ldcg(bidcol + r);
@@ -1453,7 +1424,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
         }
       }
       if (lead) ctl->n[cur] = 0;
-      if (!grid_barrier(ctl, nb, status)) return false;
+      if (!grid_barrier(ctl->bar, nb, status)) return false;
       cur = nxt;
     }
     // phase end: W, LB and the stop test
@@ -1461,7 +1432,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
       const double n1 = auction_min_cg(R, r, mc, diag_t, price);
       if (lane == 0) bidval[r] = n1;
     }
-    if (!grid_barrier(ctl, nb, status)) return false;
+    if (!grid_barrier(ctl->bar, nb, status)) return false;
     if (blockIdx.x == 0) {
       double W = 0.0, U = 0.0, P = 0.0;
       for (int c0 = 0; c0 < k; c0 += kGT) {
@@ -1501,7 +1472,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
         ctl->stop = stop;
       }
     }
-    if (!grid_barrier(ctl, nb, status)) return false;
+    if (!grid_barrier(ctl->bar, nb, status)) return false;
     if (*(volatile int*)&ctl->stop) break;
     eps = __ldcg(&ctl->eps);
   }
@@ -1510,7 +1481,7 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
     atomicAdd(rounds_out + 1, phase + 1);
     atomicAdd(rounds_out + 2, checks);
   }
-  return grid_barrier(ctl, nb, status);
+  return grid_barrier(ctl->bar, nb, status);
 }
 
 // Group g of the fused path, when it has at least kGridMin free targets (the
@@ -1563,21 +1534,6 @@ __global__ void __launch_bounds__(kGT) k_auction_grid(int k, int mc, const Cand*
                     rounds_out, status))
     return;
   for (int j = blockIdx.x * kGT + threadIdx.x; j < mc; j += gridDim.x * kGT) col_to_row[j] = __ldcg(H.pm + j);
-}
-
-// Blocks of the grid auction: co-resident on at most 128 SMs (one block each).
-static int grid_auction_blocks() {
-  static std::atomic<int> nb{0};
-  int v = nb.load(std::memory_order_acquire);
-  if (v == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_auction_grid, kGT, 0);
-    v = std::max(1, std::min(sms, 128) * std::min(per, 1));
-    nb.store(v, std::memory_order_release);
-  }
-  return v;
 }
 
 __global__ void k_colpos(int npg, const uint32_t* __restrict__ is_col, const uint32_t* __restrict__ pos,
@@ -1898,7 +1854,8 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double p
   }
   note_launch();
   if (prec > 0.0) {  // groups with many free targets: the auction over the whole GPU
-    const int nb = grid_auction_blocks();
+    const int nb = cooperative_blocks((const void*)k_auction_grid_group, kGT);
+    if (nb == 0) return -4;
     cudaMemsetAsync(B.actl, 0, 3 * sizeof(AucCtl), st);
     for (int g = 0; g < 3; ++g) {
       AsgDev A = B.A;
@@ -1907,10 +1864,8 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double p
       double pr = prec;
       AucCtl* c = static_cast<AucCtl*>(B.actl);
       void* args[] = {&A, &p, &gg, &pr, &c, &status};
-      if (cudaLaunchCooperativeKernel((const void*)k_auction_grid_group, dim3(nb), dim3(kGT), args, 0, st) !=
-          cudaSuccess)
+      if (cooperative_launch((const void*)k_auction_grid_group, dim3(nb), dim3(kGT), args, st) != cudaSuccess)
         return -4;
-      note_launch();
     }
   }
   int32_t hc[13];
@@ -1966,7 +1921,8 @@ int assign_groups(int np, Pt* pts, int nt, const Tg* T, double prec, SolverBufs&
     k_colpos<<<(npg + 255) / 256, 256, 0, st>>>(npg, B.is_col, B.colpos, B.colpos, B.col_point); note_launch();
     k_diag_t<<<(k + 255) / 256, 256, 0, st>>>(k, B.tlist, T, B.diag_t); note_launch();
     if (prec > 0.0 && k >= kGridMin) {
-      const int nb = grid_auction_blocks();
+      const int nb = cooperative_blocks((const void*)k_auction_grid, kGT);
+      if (nb == 0) return -4;
       cudaMemsetAsync(B.actl, 0, sizeof(AucCtl), st);
       const Cand* kept = B.kept;
       const uint32_t *koff = B.u32b, *nk = B.nkept, *cp = B.colpos;
@@ -1983,9 +1939,7 @@ int assign_groups(int np, Pt* pts, int nt, const Tg* T, double prec, SolverBufs&
       double pr = prec;
       void* args[] = {&kk, &mm, &kept, &koff, &nk, &cp, &dt, &pr, &cpts, &pl, &nn, &H, &aux, &stride, &c, &ctr, &ro,
                       &status};
-      if (cudaLaunchCooperativeKernel((const void*)k_auction_grid, dim3(nb), dim3(kGT), args, 0, st) != cudaSuccess)
-        return -4;
-      note_launch();
+      if (cooperative_launch((const void*)k_auction_grid, dim3(nb), dim3(kGT), args, st) != cudaSuccess) return -4;
     } else if (prec > 0.0) {
       k_auction<<<1, kHT, 0, st>>>(k, mc, B.kept, B.u32b, B.nkept, B.colpos, B.diag_t, prec, pts, B.plist, npg, B.H,
                                    B.aux, B.cap_cols + 1, B.col_to_row, B.A.counts + 10, status); note_launch();
