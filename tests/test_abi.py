@@ -100,3 +100,31 @@ def test_binding_constants_match_the_header():
     for name in ("TSF_OK", "TSF_EINVAL", "TSF_ENAN", "TSF_ENOMEM", "TSF_ECUDA", "TSF_ETIMEOUT", "TSF_ENOTARGET",
                  "TSF_ECAPACITY", "TSF_EINTERNAL"):
         assert getattr(tsf, name) == defs[name], name
+
+
+def test_batch_argument_checks_need_no_gpu(libpath):
+    import numpy as np
+    L = tsf.lib()
+    out = ctypes.c_void_p()
+    dims = (ctypes.c_int * 1)(4)
+    vals = (ctypes.c_void_p * 1)(1)
+    assert L.tsf_batch_create(0, dims, dims, dims, vals, 0, ctypes.byref(out)) == tsf.TSF_EINVAL
+    assert L.tsf_batch_create(1, None, dims, dims, vals, 0, ctypes.byref(out)) == tsf.TSF_EINVAL
+    assert L.tsf_batch_create(1, dims, dims, dims, None, 0, ctypes.byref(out)) == tsf.TSF_EINVAL
+    assert L.tsf_batch_create(1, dims, dims, dims, vals, 0, None) == tsf.TSF_EINVAL
+    assert L.tsf_batch_destroy(None) == tsf.TSF_OK
+    assert L.tsf_batch_size(None) == 0
+    assert L.tsf_batch_field(None, 0, ctypes.byref(out)) == tsf.TSF_EINVAL
+    assert L.tsf_batch_set_signal_thresholds(None, None) == tsf.TSF_EINVAL
+    p = tsf.params()
+    assert L.tsf_batch_step(None, ctypes.byref(p), None) == tsf.TSF_EINVAL
+    assert L.tsf_batch_simplify(None, ctypes.byref(p), None) == tsf.TSF_EINVAL
+    with pytest.raises(ValueError):
+        tsf.Batch([np.zeros((4, 4), np.float32)])
+
+
+def test_params_carry_the_assignment_precision():
+    p = tsf.params(assignment_precision=0.01)
+    assert abs(p.assignment_precision - 0.01) < 1e-9
+    assert tsf.params().assignment_precision == 0.0
+    assert "assign_rounds" in dict(tsf.tsf_stats._fields_)
