@@ -363,20 +363,31 @@ def run_gpu(args):
     ablation = None
     if rank == 0 and not args.no_e2e and not args.no_ablation:
         host = np.ascontiguousarray(f0)
+
+        def solve(tau, **kw):
+            h = tsf.tsf_create_field(SHAPE[2], SHAPE[1], SHAPE[0], host.ctypes.data, 0, stream.cuda_stream)
+            tsf.tsf_set_signal_threshold(h, tau)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st = tsf.tsf_simplify(h, tsf.params(stop_s=0.01, **kw), None, 0)
+            dt = time.perf_counter() - t
+            tsf.tsf_destroy_field(h)
+            return {"iterations": int(st.iters), "solve_s": dt, "iters_per_s": int(st.iters) / dt,
+                    "final_loss": float(st.loss), "non_signal_remaining": int(st.n_uncancelled)}
+
+        # Section 4.2 / 4.3 accelerations on and off (Table 2), at the
+        # benchmark threshold and at the aggressive 45 % of Appendix A; then
+        # the cut and fill modes of Section 5.3 (alpha_d = 0, alpha_b = 0)
         ablation = {}
-        for fg in (1, 0):
-            for fa in (1, 0):
-                h = tsf.tsf_create_field(SHAPE[2], SHAPE[1], SHAPE[0], host.ctypes.data, 0, stream.cuda_stream)
-                tsf.tsf_set_signal_threshold(h, TAU)
-                torch.cuda.synchronize()
-                t = time.perf_counter()
-                st = tsf.tsf_simplify(h, tsf.params(stop_s=0.01, fast_gradient_update=fg, fast_assignment_update=fa),
-                                      None, 0)
-                dt = time.perf_counter() - t
-                tsf.tsf_destroy_field(h)
-                ablation[f"gradient_update_{'fast' if fg else 'full'}/assignment_{'reuse' if fa else 'full'}"] = {
-                    "iterations": int(st.iters), "solve_s": dt, "iters_per_s": int(st.iters) / dt,
-                    "final_loss": float(st.loss)}
+        for tau in (TAU, 0.45):
+            runs = {}
+            for fg in (1, 0):
+                for fa in (1, 0):
+                    runs[f"gradient_update_{'fast' if fg else 'full'}/assignment_{'reuse' if fa else 'full'}"] = \
+                        solve(tau, fast_gradient_update=fg, fast_assignment_update=fa)
+            ablation[f"threshold_{tau:g}"] = runs
+        ablation["modes"] = {"cut (alpha_d = 0)": solve(TAU, alpha_d=0.0),
+                             "fill (alpha_b = 0)": solve(TAU, alpha_b=0.0)}
 
     if rank != 0:
         if world > 1:

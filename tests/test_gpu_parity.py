@@ -277,3 +277,24 @@ def test_auction_step_is_within_its_precision_of_the_exact_step():
     with pytest.raises(tsf.TsfError) as e:
         b.step(assignment_precision=-0.5)
     assert e.value.code == tsf.TSF_EINVAL
+
+
+@pytest.mark.parametrize("tau,alpha_b,alpha_d", [(0.1, 0.5, 0.0), (0.1, 0.0, 0.5), (0.45, 0.5, 0.5)],
+                         ids=["cut", "fill", "aggressive_45"])
+def test_cut_fill_and_aggressive_trajectories_are_bit_exact(tau, alpha_b, alpha_d):
+    """Section 5.3's cut (alpha_d = 0) and fill (alpha_b = 0) modes and
+    Appendix A's aggressive threshold (45 % of the range): field,
+    assignment and loss equal the oracle's at every step."""
+    f0 = S.plain_32()
+    fld = gpu_field(f0)
+    fld.set_threshold(tau)
+    ref = oracle.Solver(f0, tau=tau)
+    for j in range(5):
+        st = fld.step(alpha_b=alpha_b, alpha_d=alpha_d, stop_s=0.0)
+        ref.iterate(alpha_b=alpha_b, alpha_d=alpha_d, stop_s=0.0)
+        assert np.array_equal(bits(fld.values()), bits(ref.field())), f"field differs after step {j + 1}"
+        tgt, still = fld.assignment()
+        P = ref.points()
+        assert tgt.tolist() == P["tgt"].tolist()
+        assert still.tolist() == P["still"].tolist()
+        assert st["loss"] == pytest.approx(ref.stats()["loss"], rel=1e-12, abs=1e-300)
