@@ -281,3 +281,36 @@ def uneven_batch(n=48, seed=2, dims=(48, 64, 96, 128, 160)):
     shapes, thresholds, seeds = uneven_batch_shapes(n, seed, dims)
     fields = [gaussian_mixture(s, n_bumps=16, seed=k, noise_frac=0.05) for s, k in zip(shapes, seeds)]
     return fields, thresholds
+
+
+# Learned warm start (not in the paper): training inputs and the large
+# evaluation field.
+def warm_start_inputs(n, seed=4, shape=(64, 64, 64)):
+    """n training inputs (field, threshold fraction), alternating the two
+    benchmark generators at `shape`: a Gaussian mixture (8 bumps + 5 %
+    uniform noise, threshold 0.1) and a filament field (shape[0] // 8
+    loops, threshold 0.05), each with its own seed drawn from `seed`.
+    The matching targets g are the solver's simplified fields."""
+    rng = np.random.default_rng(seed)
+    seeds = rng.integers(0, 2 ** 31 - 1, size=n)
+    out = []
+    for i, k in enumerate(seeds):
+        if i % 2 == 0:
+            out.append((gaussian_mixture(shape, n_bumps=8, seed=int(k), noise_frac=0.05), 0.1))
+        else:
+            out.append((filament_field(shape, seed=int(k), n_loops=max(shape[0] // 8, 1)), 0.05))
+    return out
+
+
+def warm_start_field(shape=(256, 256, 256), seed=5):
+    """Evaluation field of the warm start: the mean of a 64-bump Gaussian
+    mixture and a 64-loop filament field (each normalised, the mixture
+    without noise, the filament field with its gradient noise), plus
+    U[0, 0.05) uniform noise, normalised; threshold 0.05."""
+    rng = np.random.default_rng(seed)
+    s1, s2, s3 = (int(x) for x in rng.integers(0, 2 ** 31 - 1, size=3))
+    g = gaussian_mixture(shape, n_bumps=64, seed=s1, noise_frac=0.0).astype(np.float64)
+    fl = filament_field(shape, seed=s2, n_loops=64).astype(np.float64)
+    f = 0.5 * (g + fl)
+    f = f + np.random.default_rng(s3).uniform(0.0, 0.05, size=shape)
+    return _normalise(f)
