@@ -107,3 +107,17 @@ def test_batch_with_the_auction_equals_lone_solves():
         assert np.array_equal(bits(b.fields[i].values()), bits(g))
         assert stats[i]["iters"] == st["iters"] and stats[i]["loss"] == st["loss"]
     b.close()
+
+
+def test_batch_of_one_field_is_a_lone_solve():
+    import paper_2407_12399_gb300 as tsf
+    f0 = S.plain_32()
+    b = tsf.Batch([f0])
+    b.set_thresholds(np.array([0.1], np.float32))
+    st = b.simplify(stop_s=0.01)
+    lone = tsf.Field(f0)
+    lone.set_threshold(0.1)
+    g, sl = lone.simplify(stop_s=0.01)
+    assert st[0]["iters"] == sl["iters"]
+    assert np.array_equal(bits(b.values()[0]), bits(g))
+    b.close()

@@ -298,3 +298,28 @@ def test_cut_fill_and_aggressive_trajectories_are_bit_exact(tau, alpha_b, alpha_
         assert tgt.tolist() == P["tgt"].tolist()
         assert still.tolist() == P["still"].tolist()
         assert st["loss"] == pytest.approx(ref.stats()["loss"], rel=1e-12, abs=1e-300)
+
+
+def test_auction_with_explicit_targets_matches_oracle():
+    """Explicit target diagram (tsf_set_signal_pairs) with targets moved off
+    their points, matched by the auction: trajectory equal to the oracle's."""
+    f0 = S.gaussian_mixture((16, 15, 14), n_bumps=6, seed=21)
+    d = oracle.diagram(f0)["pairs"]
+    flat = f0.ravel()
+    pers = flat[d["vd"]] - flat[d["vb"]]
+    keep = np.argsort(-pers)[:12]
+    import paper_2407_12399_gb300 as tsf
+    tg = np.zeros(len(keep), tsf.PAIR_DTYPE)
+    tg["dim"], tg["essential"] = d["dim"][keep], d["essential"][keep]
+    tg["v_birth"], tg["v_death"] = d["vb"][keep], d["vd"][keep]
+    tg["birth"], tg["death"] = flat[d["vb"][keep]], flat[d["vd"][keep]] - np.float32(0.02)
+    fld = gpu_field(f0)
+    fld.set_targets(tg)
+    ref = oracle.Solver(f0, targets={"dim": tg["dim"], "essential": tg["essential"], "vb": tg["v_birth"],
+                                     "vd": tg["v_death"], "birth": tg["birth"], "death": tg["death"]},
+                        assignment_precision=0.01)
+    for j in range(4):
+        fld.step(stop_s=0.0, assignment_precision=0.01)
+        ref.iterate(stop_s=0.0)
+        assert fld.assignment()[0].tolist() == ref.points()["tgt"].tolist()
+        assert np.array_equal(bits(fld.values()), bits(ref.field())), f"field differs after step {j + 1}"
