@@ -83,9 +83,10 @@ typedef struct {
  *   either way.
  * assignment_precision: 0 solves each reduced assignment exactly (shortest
  *   augmenting paths); p > 0 uses the Auction algorithm, as the paper's
- *   implementation does (Section 5, p = 0.01), whose reduced W2^2 is within
- *   a factor (1 + p) of the minimum: much faster when many targets compete
- *   for the same points.  Deterministic either way.  Must be finite, >= 0. */
+ *   implementation does (Section 5, p = 0.01), whose reduced Wasserstein
+ *   distance sqrt(W2^2) is within a factor (1 + p) of the minimum: much
+ *   faster when many targets compete for the same points.  Deterministic
+ *   either way.  Must be finite, >= 0. */
 typedef struct {
   float alpha_b, alpha_d;
   float stop_s;

@@ -70,8 +70,9 @@ int or_solver_done(or_solver* s, float stop_s, float cancel_eps, int max_iters);
 void or_solver_set_fast_assignment(or_solver* s, int on);
 /* Assignment of the following iterations: prec = 0 (default) the exact
  * reduced assignment; prec > 0 the Auction algorithm at that relative
- * precision (Section 5), its reduced W2^2 within a factor (1 + prec) of the
- * optimum.  An iteration returns -4 if an auction did not finish. */
+ * precision (Section 5), its reduced Wasserstein distance sqrt(W2^2) within
+ * a factor (1 + prec) of the optimum.  An iteration returns -4 if an
+ * auction did not finish. */
 void or_solver_set_assignment_precision(or_solver* s, double prec);
 /* Topological loss of `values` (nv floats) against the target diagram:
  * diagram, full exact matching, *loss = Eq. 2 with q = 2, grad[nv] = dL/df

@@ -967,6 +967,52 @@ __device__ __forceinline__ double auction_min(const Rows& R, int r, int mc, cons
   return m;
 }
 
+// Cheapest net cost of row r with the tightened prices pt (double bits,
+// every one >= 0), all lanes, with the same early stop.
+template <class Rows>
+__device__ __forceinline__ double auction_min_bits(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
+                                                   const unsigned long long* pt, bool l2) {
+  const int lane = threadIdx.x & 31;
+  const int n = R.count(r);
+  auto P = [&](int j) { return __longlong_as_double((long long)(l2 ? __ldcg(pt + j) : pt[j])); };
+  double m = __dadd_rn(diag_t[r], P(mc + r));
+  for (int base = 0; base < n; base += 32) {
+    const int c = base + lane;
+    double w = 0.0, v = m;
+    if (c < n) {
+      int j;
+      R.get(r, c, j, w);
+      v = __dadd_rn(w, P(j - 1));
+    }
+    for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    m = fmin(m, v);
+    const double wlast = __shfl_sync(0xFFFFFFFFu, w, min(31, n - 1 - base));
+    if (wlast > m) break;
+  }
+  return m;
+}
+
+// One warp: raise pt(j) to u - w(r,j) over row r's options (scatter-max).
+template <class Rows>
+__device__ __forceinline__ void auction_need(const Rows& R, int r, int mc, const double* __restrict__ diag_t,
+                                             double u, unsigned long long* pt) {
+  const int lane = threadIdx.x & 31;
+  const int n = R.count(r);
+  for (int c = lane; c <= n; c += 32) {
+    int j;
+    double w;
+    if (c < n) {
+      R.get(r, c, j, w);
+      j -= 1;
+    } else {
+      j = mc + r;
+      w = diag_t[r];
+    }
+    const double need = __dsub_rn(u, w);
+    if (need > 0.0) atomicMax(pt + j, (unsigned long long)__double_as_longlong(need));
+  }
+}
+
 template <class Rows>
 __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __restrict__ diag_t, double prec,
                               const Pt* __restrict__ pts, const int32_t* __restrict__ gpts, int npg, HungWork H,
@@ -1030,7 +1076,8 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
   }
   __syncthreads();
   double eps = s_eps;
-  const double onep = __dadd_rn(1.0, prec);
+  double onep = __dadd_rn(1.0, prec);  // the precision is on sqrt(W2^2)
+  onep = __dmul_rn(onep, onep);
   int cur = 0;
   unsigned round = 0;
   int phase = 0, checks = 0;
@@ -1161,8 +1208,38 @@ __device__ bool auction_solve(int k, int mc, const Rows& R, const double* __rest
         for (int i = 0, n = min(kHT, m - c0); i < n; ++i) P = __dadd_rn(P, s_chunk[i]);
       __syncthreads();
     }
+    // a second dual bound: prices down to what the row values u_r (in bidval)
+    // need, then the row values up to their new minima (colbid is zero here)
+    unsigned long long* pt = colbid;
+    for (int r = warp; r < k; r += kHT / 32) auction_need(R, r, mc, diag_t, bidval[r], pt);
+    __syncthreads();
+    for (int r = warp; r < k; r += kHT / 32) {
+      const double u2 = auction_min_bits(R, r, mc, diag_t, pt, false);
+      if (lane == 0) bidw[r] = u2;
+    }
+    __syncthreads();
+    double U2 = 0.0, P2 = 0.0;
+    for (int c0 = 0; c0 < k; c0 += kHT) {
+      const int r = c0 + threadIdx.x;
+      if (r < k) s_chunk[threadIdx.x] = bidw[r];
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int i = 0, n = min(kHT, k - c0); i < n; ++i) U2 = __dadd_rn(U2, s_chunk[i]);
+      __syncthreads();
+    }
+    for (int c0 = 0; c0 < m; c0 += kHT) {
+      const int j = c0 + threadIdx.x;
+      if (j < m) s_chunk[threadIdx.x] = __longlong_as_double((long long)pt[j]);
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int i = 0, n = min(kHT, m - c0); i < n; ++i) P2 = __dadd_rn(P2, s_chunk[i]);
+      __syncthreads();
+    }
+    for (int j = threadIdx.x; j < m; j += kHT) pt[j] = 0ull;
     if (threadIdx.x == 0) {
       double lb = __dsub_rn(U, P);
+      const double lb2 = __dsub_rn(U2, P2);
+      if (lb2 > lb) lb = lb2;
       double lhs = __dadd_rn(W, dsum);
       double rhs = __dadd_rn(lb, dsum);
       rhs = __dmul_rn(rhs, onep);
@@ -1330,7 +1407,8 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
   }
   if (!grid_barrier(ctl->bar, nb, status)) return false;
   double eps = __ldcg(&ctl->eps);
-  const double onep = __dadd_rn(1.0, prec);
+  double onep = __dadd_rn(1.0, prec);  // the precision is on sqrt(W2^2)
+  onep = __dmul_rn(onep, onep);
   int cur = 0;
   unsigned round = 0;
   int phase = 0, checks = 0;
@@ -1433,8 +1511,17 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
       if (lane == 0) bidval[r] = n1;
     }
     if (!grid_barrier(ctl->bar, nb, status)) return false;
+    // a second dual bound (see auction_solve): colbid is zero here
+    unsigned long long* pt = colbid;
+    for (int r = gwarp; r < k; r += gwarps) auction_need(R, r, mc, diag_t, __ldcg(bidval + r), pt);
+    if (!grid_barrier(ctl->bar, nb, status)) return false;
+    for (int r = gwarp; r < k; r += gwarps) {
+      const double u2 = auction_min_bits(R, r, mc, diag_t, pt, true);
+      if (lane == 0) bidw[r] = u2;
+    }
+    if (!grid_barrier(ctl->bar, nb, status)) return false;
     if (blockIdx.x == 0) {
-      double W = 0.0, U = 0.0, P = 0.0;
+      double W = 0.0, U = 0.0, P = 0.0, U2 = 0.0, P2 = 0.0;
       for (int c0 = 0; c0 < k; c0 += kGT) {
         const int r = c0 + threadIdx.x;
         if (r < k) {
@@ -1457,8 +1544,26 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
           for (int i = 0, n = min(kGT, m - c0); i < n; ++i) P = __dadd_rn(P, s_chunk[i]);
         __syncthreads();
       }
+      for (int c0 = 0; c0 < k; c0 += kGT) {
+        const int r = c0 + threadIdx.x;
+        if (r < k) s_chunk[threadIdx.x] = __ldcg(bidw + r);
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int i = 0, n = min(kGT, k - c0); i < n; ++i) U2 = __dadd_rn(U2, s_chunk[i]);
+        __syncthreads();
+      }
+      for (int c0 = 0; c0 < m; c0 += kGT) {
+        const int j = c0 + threadIdx.x;
+        if (j < m) s_chunk[threadIdx.x] = __longlong_as_double((long long)__ldcg(pt + j));
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int i = 0, n = min(kGT, m - c0); i < n; ++i) P2 = __dadd_rn(P2, s_chunk[i]);
+        __syncthreads();
+      }
       if (threadIdx.x == 0) {
         double lb = __dsub_rn(U, P);
+        const double lb2 = __dsub_rn(U2, P2);
+        if (lb2 > lb) lb = lb2;
         double lhs = __dadd_rn(W, dsum);
         double rhs = __dadd_rn(lb, dsum);
         rhs = __dmul_rn(rhs, onep);
@@ -1475,6 +1580,8 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
     if (!grid_barrier(ctl->bar, nb, status)) return false;
     if (*(volatile int*)&ctl->stop) break;
     eps = __ldcg(&ctl->eps);
+    // zero again before the next phase's bids (a barrier comes first)
+    for (int j = gtid; j < m; j += gthreads) pt[j] = 0ull;
   }
   if (lead && rounds_out) {
     atomicAdd(rounds_out, (int)round);

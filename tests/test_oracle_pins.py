@@ -242,8 +242,8 @@ def test_assignment_is_optimal_by_brute_force(seed):
 @pytest.mark.parametrize("seed", range(12))
 def test_auction_is_within_its_precision_of_brute_force(seed, prec):
     """The auction (Section 5's assignment solver) at relative precision
-    prec: a valid matching whose W2^2 is between the brute-force minimum and
-    (1 + prec) times it."""
+    prec on the distance: a valid matching whose W2^2 is between the
+    brute-force minimum and (1 + prec)^2 times it."""
     rng = np.random.default_rng(100 + seed)
     n = int(rng.integers(1, 8))
     k = int(rng.integers(1, 5))
@@ -258,7 +258,7 @@ def test_auction_is_within_its_precision_of_brute_force(seed, prec):
         tb[:m], td[:m] = pb[:m] + np.float32(0.01), pd[:m]
     tgt, cost = oracle.assign(pb, pd, tb, td, precision=prec)
     ref = _brute_assign(pb, pd, tb, td)
-    assert ref * (1 - 1e-12) <= cost <= (1 + prec) * ref * (1 + 1e-12) + 1e-15
+    assert ref * (1 - 1e-12) <= cost <= (1 + prec) ** 2 * ref * (1 + 1e-12) + 1e-15
     used = tgt[tgt >= 0]
     assert len(used) == len(set(used.tolist()))
 
@@ -298,7 +298,7 @@ def test_exact_and_auction_against_a_library_solver_on_crowded_diagrams(seed):
     assert exact == pytest.approx(ref, rel=1e-12)
     for prec in (0.1, 0.01):
         tgt, cost = oracle.assign(pb, pd, tb, td, precision=prec)
-        assert ref * (1 - 1e-12) <= cost <= (1 + prec) * ref * (1 + 1e-12)
+        assert ref * (1 - 1e-12) <= cost <= (1 + prec) ** 2 * ref * (1 + 1e-12)
         used = tgt[tgt >= 0]
         assert len(used) == len(set(used.tolist()))
     _, fine = oracle.assign(pb, pd, tb, td, precision=1e-7)
@@ -318,7 +318,7 @@ def test_auction_resolves_a_two_target_contest():
 def test_auction_solver_step_is_within_its_precision_of_the_exact_one():
     """Both solvers start from the identity at j = 0 and take the same first
     step, so they see the same D(f_1) and the same still pairs; the
-    auction's loss lies between the exact one and (1 + prec) times it."""
+    auction's loss lies between the exact one and (1 + prec)^2 times it."""
     f0 = S.gaussian_mixture((12, 11, 10), n_bumps=6, seed=2)
     ex = oracle.Solver(f0, tau=0.02)
     au = oracle.Solver(f0, tau=0.02, assignment_precision=0.01)
@@ -327,7 +327,7 @@ def test_auction_solver_step_is_within_its_precision_of_the_exact_one():
     au.iterate(stop_s=0.0)
     assert np.array_equal(ex.field(), au.field())
     le, la = ex.stats()["loss"], au.stats()["loss"]
-    assert le * (1 - 1e-12) <= la <= 1.01 * le * (1 + 1e-12)
+    assert le * (1 - 1e-12) <= la <= 1.01 ** 2 * le * (1 + 1e-12)
     au.run(stop_s=0.01)
     assert au.stats()["loss"] <= 0.01 * au.stats()["loss0"]
 
