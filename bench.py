@@ -401,7 +401,8 @@ def run_gpu(args):
         avg = ms / max(calls, 1)
         return nbytes / (avg * 1e-3) / 1e9, avg
 
-    # algorithmic bytes per launch (per-unit figures in the design doc)
+    # algorithmic bytes per launch: units of work per launch times the bytes
+    # one unit must move (stated beside each figure below)
     n_grad = float(np.mean([s["n_gradient_vertices"] for s in stats]))
     visits = float(np.mean([s["d1_blocks_total"] for s in stats]))
     n_upd = float(np.mean([s["n_updated_vertices"] for s in stats]))

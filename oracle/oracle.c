@@ -27,8 +27,8 @@
  *     diagram) keep their previous assignment; the rest is solved on the
  *     reduced diagram against the reduced target.
  *   - Algorithm 1: the iteration order (step, diagram, assignment).
- * Readings where the paper is silent are listed in the design doc of the project
- * and restated at the function that implements them.
+ * Where the paper is silent, the reading taken is stated at the function
+ * that implements it.
  */
 #include "oracle.h"
 
