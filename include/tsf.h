@@ -120,6 +120,9 @@ typedef struct {
   int64_t assign_rounds;      /* auction rounds of the last assignment (0 when exact) */
   int64_t assign_phases;      /* ... its eps phases */
   int64_t assign_checks;      /* ... its passes releasing rows off eps-complementary slackness */
+  int64_t d1_reduce_rounds;   /* rounds of the saddle-saddle column reduction */
+  int64_t d1_reduce_merged;   /* entries written by its column additions */
+  int64_t d1_reduce_longest;  /* longest column an addition produced */
 } tsf_stats;
 
 /* Creates a field from lx*ly*lz values (host or device memory, copied).

@@ -56,7 +56,9 @@ class tsf_stats(ctypes.Structure):
                 ("d1_rounds_total", ctypes.c_int64), ("d1_rounds_max", ctypes.c_int64),
                 ("d1_star_updates", ctypes.c_int64), ("ms_diagram", ctypes.c_double),
                 ("ms_assign", ctypes.c_double), ("ms_step", ctypes.c_double), ("assign_rounds", ctypes.c_int64),
-                ("assign_phases", ctypes.c_int64), ("assign_checks", ctypes.c_int64)]
+                ("assign_phases", ctypes.c_int64), ("assign_checks", ctypes.c_int64),
+                ("d1_reduce_rounds", ctypes.c_int64), ("d1_reduce_merged", ctypes.c_int64),
+                ("d1_reduce_longest", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

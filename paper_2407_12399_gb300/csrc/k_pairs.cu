@@ -1145,11 +1145,16 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
       while (y < no) d[m++] = b[y++];
       W.hoff[j] = off;
       W.hsize[j] = m;
+      atomicAdd(&W.stats[6], (unsigned long long)m);  // entries written by merges
+      atomicMax(&W.stats[7], (unsigned long long)m);  // longest merged column
       if (m == 0) atomicOr(status, kErrEmptyColumn);
       else d1_list_push(nxt, &s_nb, mark, j, round);
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_na = s_nb;
+    if (threadIdx.x == 0) {
+      s_na = s_nb;
+      W.stats[5] = (unsigned long long)(round + 1);  // rounds so far
+    }
     int32_t* t = cur;
     cur = nxt;
     nxt = t;

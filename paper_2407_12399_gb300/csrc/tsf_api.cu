@@ -100,7 +100,7 @@ struct tsf_field {
   double loss = 0, loss0 = 0;
   unsigned long long counts[4] = {0, 0, 0, 0};
   int64_t n_updated = 0, n_gradient = 0;
-  unsigned long long d1_stats[5] = {0, 0, 0, 0, 0};
+  unsigned long long d1_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int d1_cols = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
@@ -579,6 +579,9 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
   out->d1_rounds_total = (int64_t)F->d1_stats[2];
   out->d1_rounds_max = (int64_t)F->d1_stats[3];
   out->d1_star_updates = (int64_t)F->d1_stats[4];
+  out->d1_reduce_rounds = (int64_t)F->d1_stats[5];
+  out->d1_reduce_merged = (int64_t)F->d1_stats[6];
+  out->d1_reduce_longest = (int64_t)F->d1_stats[7];
   out->ms_diagram = F->ms_diag;
   out->ms_assign = F->ms_assign;
   out->assign_rounds = F->assign_rounds;
