@@ -1081,6 +1081,59 @@ static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + sca
 // that phase) and is listed again.  A settled owner that a smaller column
 // displaces is listed for the next round; columns not listed own their lows
 // and stay as they are, so a round costs as much as its list.
+// Number of entries of a strictly decreasing column greater than v.
+__device__ __forceinline__ uint32_t d1_count_greater(unsigned long long v, const unsigned long long* arr,
+                                                    uint32_t len) {
+  uint32_t lo = 0, hi = len;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (arr[mid] > v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One warp writes the sum over Z/2 of two strictly decreasing columns a (n)
+// and b (nb) to d, decreasing, and returns its length.  An entry x of a that
+// b lacks lands at x + (entries of b above it) - 2 (entries of a above it
+// that b also has): everything above it, minus the cancelled pairs.  Same
+// for b.  Positions outside [0, n + nb) set kErrInconsistent.
+__device__ uint32_t d1_warp_add(const unsigned long long* a, uint32_t n, const unsigned long long* b, uint32_t nb,
+                                unsigned long long* d, uint32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t cap = n + nb;
+  uint32_t common = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const unsigned long long* p = pass == 0 ? a : b;
+    const unsigned long long* q = pass == 0 ? b : a;
+    const uint32_t np_ = pass == 0 ? n : nb, nq = pass == 0 ? nb : n;
+    uint32_t before = 0;
+    for (uint32_t x0 = 0; x0 < np_; x0 += 32) {
+      const uint32_t x = x0 + lane;
+      bool found = false;
+      uint32_t c = 0;
+      unsigned long long v = 0;
+      if (x < np_) {
+        v = p[x];
+        c = d1_count_greater(v, q, nq);
+        found = c < nq && q[c] == v;
+      }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, found);
+      if (x < np_ && !found) {
+        const uint32_t pos = x + c - 2u * (before + __popc(bal & ((1u << lane) - 1u)));
+        if (pos < cap) d[pos] = v;
+        else atomicOr(status, kErrInconsistent);
+      }
+      before += __popc(bal);
+    }
+    common = before;
+  }
+  return cap - 2u * common;
+}
+
+constexpr uint32_t kLongAdd = 64;  // column additions at least this long run on a warp
+constexpr int kLongCap = 1024;     // ... at most this many per round (the rest on one thread)
+
 __device__ __forceinline__ void d1_list_push(int32_t* next, int* n_next, int32_t* mark, int j, int round) {
   if (atomicExch(&mark[j], round) != round) next[atomicAdd(n_next, 1)] = j;
 }
@@ -1091,7 +1144,8 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
   int32_t* listA = W.lowc;
   int32_t* listB = reinterpret_cast<int32_t*>(W.hcap);
   int32_t* mark = W.redo;
-  __shared__ int s_na, s_nb;
+  __shared__ int s_na, s_nb, s_nlong;
+  __shared__ int32_t s_long[kLongCap];
   for (int k = threadIdx.x; k < n1; k += kUFT) W.owner[k] = 0x7FFFFFFF;
   if (threadIdx.x == 0) s_na = 0;
   __syncthreads();
@@ -1109,7 +1163,10 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
       if (threadIdx.x == 0) atomicOr(status, kErrRounds);
       break;
     }
-    if (threadIdx.x == 0) s_nb = 0;
+    if (threadIdx.x == 0) {
+      s_nb = 0;
+      s_nlong = 0;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < na; i += kUFT) {
       int j = cur[i];
@@ -1124,6 +1181,13 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
       int o = W.owner[(int)a[0]];
       if (o == j) continue;
       uint32_t no = W.hsize[o];
+      if (n + no >= kLongAdd) {  // long: one warp adds it below
+        const int q = atomicAdd(&s_nlong, 1);
+        if (q < kLongCap) {
+          s_long[q] = j;
+          continue;
+        }
+      }
       const unsigned long long* b = W.pool + W.hoff[o];
       uint32_t cap = n + no;
       uint32_t off = atomicAdd(W.pool_head, cap);
@@ -1149,6 +1213,35 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
       atomicMax(&W.stats[7], (unsigned long long)m);  // longest merged column
       if (m == 0) atomicOr(status, kErrEmptyColumn);
       else d1_list_push(nxt, &s_nb, mark, j, round);
+    }
+    __syncthreads();
+    {  // the long additions, one warp each
+      const int nlong = min(s_nlong, kLongCap), lane = threadIdx.x & 31;
+      for (int q = threadIdx.x >> 5; q < nlong; q += kUFT / 32) {
+        const int j = s_long[q];
+        const uint32_t n = W.hsize[j];
+        const unsigned long long* a = W.pool + W.hoff[j];
+        const int o = W.owner[(int)a[0]];
+        const uint32_t no = W.hsize[o];
+        const unsigned long long* b = W.pool + W.hoff[o];
+        const uint32_t cap = n + no;
+        uint32_t off = 0;
+        if (lane == 0) off = atomicAdd(W.pool_head, cap);
+        off = __shfl_sync(0xFFFFFFFFu, off, 0);
+        if ((unsigned long long)off + cap > W.pool_cap) {
+          if (lane == 0) atomicOr(status, kErrPool);
+          continue;
+        }
+        const uint32_t m = d1_warp_add(a, n, b, no, W.pool + off, status);
+        if (lane == 0) {
+          W.hoff[j] = off;
+          W.hsize[j] = m;
+          atomicAdd(&W.stats[6], (unsigned long long)m);
+          atomicMax(&W.stats[7], (unsigned long long)m);
+          if (m == 0) atomicOr(status, kErrEmptyColumn);
+          else d1_list_push(nxt, &s_nb, mark, j, round);
+        }
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
