@@ -305,6 +305,27 @@ def test_exact_and_auction_against_a_library_solver_on_crowded_diagrams(seed):
     assert fine == pytest.approx(ref, rel=1e-6)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_assignment_with_many_equal_costs(seed):
+    """Points and targets on a coarse lattice (many exactly equal costs, a
+    target with no candidate at all): the exact solve reaches the brute-force
+    minimum and the auction stays within its precision."""
+    rng = np.random.default_rng(200 + seed)
+    n, k = int(rng.integers(2, 8)), int(rng.integers(1, 5))
+    pb = (rng.integers(0, 4, n) * 0.25).astype(np.float32)
+    pd = (pb + rng.integers(0, 3, n) * 0.25).astype(np.float32)
+    tb = (rng.integers(0, 4, k) * 0.25).astype(np.float32)
+    td = (tb + rng.integers(1, 3, k) * 0.25).astype(np.float32)
+    tb[0], td[0] = np.float32(10.0), np.float32(10.25)  # far from every point
+    ref = _brute_assign(pb, pd, tb, td)
+    for prec in (0.0, 0.01, 0.3):
+        tgt, cost = oracle.assign(pb, pd, tb, td, precision=prec)
+        assert ref * (1 - 1e-12) <= cost <= (1 + prec) ** 2 * ref * (1 + 1e-12) + 1e-15
+        assert 0 not in tgt.tolist()  # the far target has no candidate
+        used = tgt[tgt >= 0]
+        assert len(used) == len(set(used.tolist()))
+
+
 def test_auction_resolves_a_two_target_contest():
     """One point (0, 1) and targets (0, 1), (0.1, 1): the first takes the
     point (W2^2 = 0 + 0.405) rather than the second (0.01 + 0.5); at 1 %
