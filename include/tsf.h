@@ -197,7 +197,8 @@ int tsf_loss_and_gradient(tsf_field* field, const float* values, int values_on_d
  * tsf_simplify on it, so a field's result does not depend on its batch.
  *
  * tsf_batch_create: n fields, field i of lx[i]*ly[i]*lz[i] values copied
- *   from values[i] (host or device); the batch owns fields and streams.
+ *   from values[i] (host or device); the batch owns fields and streams, all
+ *   on the device current at this call (its worker threads select it too).
  *   Errors: TSF_EINVAL, TSF_ENOMEM, TSF_ECUDA, TSF_ENAN.
  * tsf_batch_field: the i-th field (owned by the batch; use it with the
  *   single-field calls, but not while a batch call runs).

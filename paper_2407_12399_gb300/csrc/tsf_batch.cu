@@ -16,6 +16,7 @@
 #include "../../include/tsf.h"
 
 struct tsf_batch {
+  int device = 0;  // current when the batch was created; the workers use it too
   std::vector<tsf_field*> fields;
   std::vector<cudaStream_t> streams;
   // worker pool: run(job) calls job(i) for every field index, spread over
@@ -29,6 +30,7 @@ struct tsf_batch {
   bool stop = false;
 
   void worker(int w, int nw) {
+    cudaSetDevice(device);  // the current device is per host thread
     long long seen = 0;
     for (;;) {
       std::function<void(int)> j;
@@ -90,6 +92,10 @@ int tsf_batch_create(int n, const int* lx, const int* ly, const int* lz, const f
     b = new tsf_batch();
   } catch (...) {
     return TSF_ENOMEM;
+  }
+  if (cudaGetDevice(&b->device) != cudaSuccess) {
+    delete b;
+    return TSF_ECUDA;
   }
   for (int i = 0; i < n; ++i) {
     cudaStream_t s = nullptr;
