@@ -125,7 +125,9 @@ typedef struct {
   int64_t d1_reduce_longest;  /* longest column an addition produced */
 } tsf_stats;
 
-/* Creates a field from lx*ly*lz values (host or device memory, copied).
+/* Creates a field from lx*ly*lz values (host or device memory, copied),
+ * on the device current at this call; every later call on the field runs
+ * on that device and leaves the caller's current device as it was.
  * cuda_stream: a cudaStream_t, or NULL.  Errors: TSF_EINVAL, TSF_ENAN,
  * TSF_ENOMEM, TSF_ECUDA.  On success *out owns all device memory. */
 int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_device, void* cuda_stream,

@@ -53,6 +53,7 @@ double now_ms() {
 }  // namespace
 
 struct tsf_field {
+  int device = 0;  // the device current when the field was created
   Dims d{};
   NbrDelta nd{};
   cudaStream_t st = nullptr;
@@ -662,8 +663,29 @@ int guarded(Fn&& fn) {
   }
 }
 
+// Makes the field's device current for one call (the current device is per
+// host thread) and restores the caller's afterwards.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(const tsf_field* F) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev >= 0 && prev != F->device) cudaSetDevice(F->device);
+  }
+  ~DeviceScope() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+template <class Fn>
+int guarded_dev(tsf_field* F, Fn&& fn) {
+  DeviceScope ds(F);
+  return guarded(fn);
+}
+
 template <class Fn>
 int guarded_f(tsf_field* F, Fn&& fn) {
+  DeviceScope ds(F);
   int r = guarded(fn);
   profile_resolve(F);
   return r;
@@ -690,6 +712,7 @@ const char* tsf_status_string(int s) {
 
 int tsf_destroy_field(tsf_field* F) {
   if (!F) return TSF_OK;
+  DeviceScope ds(F);
   cudaStreamSynchronize(F->st);
   dev_free(F->f);
   dev_free(F->order);
@@ -817,6 +840,10 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
   *out = nullptr;
   tsf_field* F = new (std::nothrow) tsf_field();
   if (!F) return TSF_ENOMEM;
+  if (cudaGetDevice(&F->device) != cudaSuccess) {
+    delete F;
+    return TSF_ECUDA;
+  }
   int r = guarded([&]() {
     F->d.lx = lx;
     F->d.ly = ly;
@@ -1044,7 +1071,7 @@ int tsf_loss_and_gradient(tsf_field* F, const float* values, int values_on_devic
 
 int tsf_get_field(tsf_field* F, float* out, int out_on_device) {
   if (!F || !out) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_dev(F, [&]() {
     ck(cudaMemcpyAsync(out, F->f, sizeof(float) * F->d.nv,
                        out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, F->st));
     ck(cudaStreamSynchronize(F->st));
@@ -1054,7 +1081,7 @@ int tsf_get_field(tsf_field* F, float* out, int out_on_device) {
 
 int tsf_set_field(tsf_field* F, const float* values, int values_on_device) {
   if (!F || !values) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_dev(F, [&]() {
     ck(cudaMemcpyAsync(F->f, values, sizeof(float) * F->d.nv,
                        values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, F->st));
     ck(cudaStreamSynchronize(F->st));
@@ -1069,7 +1096,7 @@ int tsf_set_field(tsf_field* F, const float* values, int values_on_device) {
 
 int tsf_get_assignment(tsf_field* F, int32_t* target, int32_t* still, int64_t cap, int64_t* n_out) {
   if (!F || !n_out) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_dev(F, [&]() {
     *n_out = F->np;
     if (F->np > cap) return TSF_ECAPACITY;
     std::vector<Pt> h(F->np);
@@ -1085,7 +1112,7 @@ int tsf_get_assignment(tsf_field* F, int32_t* target, int32_t* still, int64_t ca
 
 int tsf_get_targets(tsf_field* F, tsf_pair* out, int64_t cap, int64_t* n_out) {
   if (!F || !n_out) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_dev(F, [&]() {
     *n_out = F->nt;
     if (F->nt > cap) return TSF_ECAPACITY;
     std::vector<Tg> h(F->nt);
@@ -1107,7 +1134,7 @@ int tsf_get_targets(tsf_field* F, tsf_pair* out, int64_t cap, int64_t* n_out) {
 
 int tsf_zero_pairs(tsf_field* F, uint64_t* out, int64_t cap_pairs, int64_t* n_out) {
   if (!F || !n_out || cap_pairs < 0) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_dev(F, [&]() {
     ck(cudaMemsetAsync(F->status, 0, 4, F->st));
     vertex_order(F->f, F->d.nv, F->order, F->rank, F->skey, F->sort_scratch, F->status, F->st);
     uint32_t s = read_status(F);
@@ -1136,7 +1163,7 @@ int tsf_zero_pairs(tsf_field* F, uint64_t* out, int64_t cap_pairs, int64_t* n_ou
 
 int tsf_profile_enable(tsf_field* F, int enable) {
   if (!F) return TSF_EINVAL;
-  return guarded([&]() {
+  return guarded_dev(F, [&]() {
     profile_resolve(F);
     F->prof = enable != 0;
     for (int i = 0; i < TSF_NSTAGES; ++i) {
