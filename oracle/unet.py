@@ -214,3 +214,37 @@ def adam_step(p, g, state, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         vhat = v / (1.0 - beta2 ** t)
         p[k] -= lr * mhat / (np.sqrt(vhat) + eps)
     return p
+
+
+def forward_bf16(p, f, tau):
+    """The forward pass with the roundings of bf16 storage: weights, biases,
+    the input channels and every layer's output (after bias and ReLU, and
+    the pooled / upsampled copies, which are exact or averages of bf16
+    values) rounded to bfloat16; each layer accumulates exactly (fp64) in
+    between.  The GPU accumulates in fp32, so a layer can differ from this
+    by the fp32 error of a K-term sum before its rounding (K = 27 x input
+    channels): at most one bf16 ulp per value where that error crosses a
+    rounding boundary.  Returns g0 (fp32 values) and the stored
+    activations."""
+    def r(a):
+        return bf16(np.asarray(a, np.float32)).astype(np.float64)
+
+    q = {k: r(v) for k, v in p.items()}
+    f = np.asarray(f, np.float64)
+    x = r(np.stack([f, np.full_like(f, float(tau))]))
+    acts = {"x": x}
+
+    def block(name, inp):
+        y = r(relu(conv3d(inp, q[name + ".w"], q[name + ".b"])))
+        acts[name] = y
+        return y
+
+    s1 = block("e1b", block("e1a", x))
+    s2 = block("e2b", block("e2a", r(avgpool2(s1))))
+    s3 = block("e3b", block("e3a", r(avgpool2(s2))))
+    u2 = block("d2b", block("d2a", np.concatenate([upsample2(s3), s2])))
+    u1 = block("d1b", block("d1a", np.concatenate([upsample2(u2), s1])))
+    head = r(conv1(u1, q["head.w"], q["head.b"])[0])
+    acts["head"] = head
+    g0 = (np.asarray(f, np.float32) + head.astype(np.float32)).astype(np.float32)
+    return g0, acts

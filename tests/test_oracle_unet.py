@@ -154,3 +154,32 @@ def test_a_few_adam_steps_lower_the_loss():
         U.adam_step(p, U.backward(p, cache, gg), st, lr=3e-3)
     assert losses[-1] < losses[0]
 
+
+
+def test_bf16_forward_stores_bf16_and_is_exact_on_dyadic_values():
+    """Every stored activation is a bfloat16 value; with weights, inputs
+    and biases small dyadic numbers (exact in bf16, sums exact) the bf16
+    forward equals the fp64 one."""
+    rng = np.random.default_rng(7)
+    ch = (2, 2, 2)
+    p = U.init_params(seed=7, channels=ch)
+    for k in p:
+        p[k] = rng.integers(-2, 3, size=p[k].shape) * 0.0625
+    f = (rng.integers(0, 4, size=(8, 8, 8)) * 0.25).astype(np.float32)
+    g_ref, _ = U.forward(p, f, 0.25)
+    g_b, acts = U.forward_bf16(p, f, 0.25)
+    for name, a in acts.items():
+        a32 = np.asarray(a, np.float32)
+        assert np.array_equal(U.bf16(a32), a32), name
+    assert np.array_equal(g_b, g_ref.astype(np.float32))
+
+
+def test_bf16_forward_stays_close_to_fp64():
+    rng = np.random.default_rng(8)
+    p = U.init_params(seed=8, channels=(4, 4, 4))
+    p["head.w"] = rng.normal(0, 0.1, p["head.w"].shape)
+    f = rng.uniform(size=(8, 8, 8)).astype(np.float32)
+    g_ref, _ = U.forward(p, f, 0.1)
+    g_b, _ = U.forward_bf16(p, f, 0.1)
+    # a handful of bf16 roundings (relative 2^-9 each) separate the two
+    assert np.max(np.abs(g_b - g_ref)) <= 0.05 * (np.max(np.abs(g_ref - f)) + 1e-3)
