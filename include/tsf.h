@@ -280,7 +280,11 @@ int64_t tsf_kernel_launches(void);
  * finds the previous call's contents in it; calls that overlap on the GPU
  * (other streams, other threads) race and must be serialised by the caller.
  * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture. */
+ * that device current.  Every call ends by copying the pair count and the
+ * status word to the host and synchronising cuda_stream, so a call cannot
+ * be recorded into a CUDA graph.  Errors as tsf_zero_pairs: TSF_EINVAL,
+ * TSF_ENAN (a NaN or infinite value), TSF_ETIMEOUT (a bounded device wait
+ * of the sort gave up), TSF_ECAPACITY, TSF_ECUDA, TSF_EINTERNAL. */
 #define TSF_STATIC_MAX_VERTICES 262144
 int tsf_zero_pairs_static(int lx, int ly, int lz, const float* values, uint64_t* out, int64_t cap_pairs,
                           int64_t* n_out, void* cuda_stream);

@@ -1596,6 +1596,9 @@ __device__ bool auction_grid(int k, int mc, const Rows& R, const double* __restr
 __global__ void __launch_bounds__(kGT) k_auction_grid_group(AsgDev A, Pt* __restrict__ pts, int g, double prec,
                                                             AucCtl* ctl, uint32_t* status) {
   if (A.counts[8]) return;
+  // an earlier group's launch gave up at a barrier: the call already fails
+  // with a timeout, so later groups do not spend their own barrier limits
+  if (*static_cast<volatile uint32_t*>(status) & kErrSpin) return;
   const int npg = A.counts[g], k = A.counts[4 + g];
   if (k < kGridMin || npg == 0) return;
   int pbase = 0, tbase = 0, wbase = 0;

@@ -404,12 +404,7 @@ uint32_t read_status(tsf_field* F) {
   return s;
 }
 
-int status_code(uint32_t s) {
-  if (s & kErrNaN) return TSF_ENAN;
-  if (s & (kErrTrace | kErrRounds | kErrSpin)) return TSF_ETIMEOUT;
-  if (s & (kErrInconsistent | kErrEmptyColumn | kErrCapacity | kErrPool)) return TSF_EINTERNAL;
-  return TSF_OK;
-}
+static_assert(TSF_ENAN == -2 && TSF_ETIMEOUT == -5 && TSF_EINTERNAL == -8, "status_code() values");
 
 // Stages 1-4 of the diagram: vertex order, lower-star gradient, critical
 // cells, pairs, points (in F->pts, diagram order).

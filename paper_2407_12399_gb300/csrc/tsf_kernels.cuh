@@ -11,6 +11,16 @@ namespace tsf {
 
 enum : uint32_t { kErrNaN = 1u << 7 };
 
+// C-ABI status of a device status word: NaN/Inf input, then any bound that
+// was hit (trace steps, rounds, spin-waits), then internal inconsistencies.
+// The values are those of TSF_ENAN, TSF_ETIMEOUT and TSF_EINTERNAL.
+inline int status_code(uint32_t s) {
+  if (s & kErrNaN) return -2;
+  if (s & (kErrTrace | kErrRounds | kErrSpin)) return -5;
+  if (s & (kErrInconsistent | kErrEmptyColumn | kErrCapacity | kErrPool)) return -8;
+  return 0;
+}
+
 // Number of kernels this library has launched (process-wide).
 void note_launch();
 long long launches();

@@ -69,14 +69,18 @@ extern "C" int tsf_zero_pairs_static(int lx, int ly, int lz, const float* values
   d.lz = lz;
   d.nv = nv;
   tsf::launch_zero_pairs(d, rank, reinterpret_cast<unsigned long long*>(out), cap_pairs, counter, status, st);
+  // launch errors are checked right after the launches, with a peek that
+  // leaves the thread's error state as the caller had it
+  if (cudaPeekAtLastError() != cudaSuccess) return TSF_ECUDA;
   unsigned long long n = 0;
   uint32_t s = 0;
   if (cudaMemcpyAsync(&n, counter, sizeof(n), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TSF_ECUDA;
   if (cudaMemcpyAsync(&s, status, sizeof(s), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TSF_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return TSF_ECUDA;
-  if (cudaGetLastError() != cudaSuccess) return TSF_ECUDA;
   *n_out = (int64_t)n;
-  if (s & tsf::kErrNaN) return TSF_ENAN;
-  if (s & tsf::kErrInconsistent) return TSF_EINTERNAL;
+  // the same mapping as every other entry point: NaN/Inf, then a device wait
+  // that gave up (a sort look-back spin), then an internal inconsistency
+  const int code = tsf::status_code(s);
+  if (code != TSF_OK) return code;
   return (int64_t)n > cap_pairs ? TSF_ECAPACITY : TSF_OK;
 }

@@ -490,3 +490,146 @@ def test_loss_gradient_matches_central_differences(seed):
     assert checked >= 20
     # back at f0 the loss is unchanged
     assert s.loss_grad(f0)[0] == L0
+
+
+def _step_by_hand(f, P, T, alpha_b, alpha_d):
+    """Section 4.1's step written out from the diagram and its assignment:
+    a point (b, d) matched to target t moves its birth vertex by
+    alpha_b * 2 (b - t_b) and its death vertex by alpha_d * 2 (d - t_d); a
+    point matched to the diagonal uses t = Delta(p) = (m, m), m = (b + d) / 2;
+    the essential class moves its birth vertex only.  Contributions to one
+    vertex are added in fp32 from +0 in increasing value order (the
+    summation-order reading), then subtracted from the vertex value."""
+    f32 = np.float32
+    contrib = {}
+    for i in range(len(P["vb"])):
+        b, d = f32(P["birth"][i]), f32(P["death"][i])
+        t = int(P["tgt"][i])
+        if t >= 0:
+            tb, td = f32(T["birth"][t]), f32(T["death"][t])
+        else:
+            tb = td = f32(f32(b + d) * f32(0.5))
+        contrib.setdefault(int(P["vb"][i]), []).append(f32(f32(alpha_b) * f32(f32(2.0) * f32(b - tb))))
+        if not P["essential"][i]:
+            contrib.setdefault(int(P["vd"][i]), []).append(f32(f32(alpha_d) * f32(f32(2.0) * f32(d - td))))
+    g = f.ravel().copy()
+    for v, cs in contrib.items():
+        acc = f32(0.0)
+        for c in sorted(cs, key=float):
+            acc = f32(acc + c)
+        g[v] = f32(g[v] - acc)
+    return g.reshape(f.shape), contrib
+
+
+@pytest.mark.parametrize("alphas", [(0.5, 0.5), (0.3, 0.7), (0.0, 0.5), (0.5, 0.0)])
+def test_step_adds_every_contribution_of_a_shared_vertex(alphas):
+    """Section 4.1 on vertices that carry several pairs: a vertex that is the
+    death of one non-signal pair and the birth of another (or the death of
+    two) receives both contributions, each with its own step size; fill
+    (alpha_b = 0) and cut (alpha_d = 0) keep only the death or birth part."""
+    ab, ad = alphas
+    seen_mixed = 0
+    cases = [((7, 6, 5), 4, 0.3), ((7, 6, 5), 9, 0.3), ((7, 6, 5), 11, 0.3), ((8, 7, 6), 31, 0.6)]
+    for shape, seed, tau in cases:
+        f = S.random_field(shape, seed=seed, kind="uniform")
+        s = oracle.Solver(f, tau=tau)
+        P, T = s.points(), s.targets()
+        want, contrib = _step_by_hand(f, P, T, ab, ad)
+        births = set(P["vb"][P["tgt"] < 0].tolist())
+        deaths = set(P["vd"][(P["tgt"] < 0) & (P["essential"] == 0)].tolist())
+        seen_mixed += len(births & deaths)
+        assert sum(len(c) >= 2 for c in contrib.values()) > 0
+        s.iterate(ab, ad, stop_s=0.0)
+        got = s.field()
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert seen_mixed > 0  # some vertex is both a death and a birth
+
+
+def test_step_sums_three_contributions_in_increasing_value_order():
+    """The paper does not fix the order in which several contributions to one
+    vertex are added; the reading is increasing value order from +0 (fp32).
+    On this field a vertex carries three contributions whose fp32 sum depends
+    on that order, so another order would show in the stepped value."""
+    f32 = np.float32
+    f = S.random_field((8, 7, 6), seed=31, kind="uniform")
+    s = oracle.Solver(f, tau=0.6)
+    want, contrib = _step_by_hand(f, s.points(), s.targets(), 0.5, 0.5)
+    sensitive = []
+    for v, cs in contrib.items():
+        down = f32(0.0)
+        for c in sorted(cs, key=float, reverse=True):
+            down = f32(down + c)
+        up = f32(0.0)
+        for c in sorted(cs, key=float):
+            up = f32(up + c)
+        if len(cs) >= 3 and up != down:
+            sensitive.append(v)
+    assert sensitive
+    s.iterate(0.5, 0.5, stop_s=0.0)
+    got = s.field().ravel()
+    for v in sensitive:
+        assert got[v].view(np.uint32) == want.ravel()[v].view(np.uint32)
+
+
+def _keys(P):
+    return list(zip(P["dim"].tolist(), P["essential"].tolist(), P["vb"].tolist(), P["vd"].tolist()))
+
+
+def _check_inheritance(P0, P1):
+    """Section 4.3: a point of D(f_{j+1}) with the same (dim, v_b, v_d) as a
+    point of D(f_j) is still and keeps that point's target; points sharing a
+    key are matched across the two diagrams in birth-cell order; a key absent
+    from D(f_j) is never still."""
+    k0, k1 = _keys(P0), _keys(P1)
+    by0, by1 = {}, {}
+    for i, k in enumerate(k0):
+        by0.setdefault(k, []).append(i)
+    for i, k in enumerate(k1):
+        by1.setdefault(k, []).append(i)
+    n_dup = 0
+    for k, idx1 in by1.items():
+        idx0 = sorted(by0.get(k, []), key=lambda i: int(P0["cb"][i]))
+        idx1 = sorted(idx1, key=lambda i: int(P1["cb"][i]))
+        n_dup += len(idx1) > 1 and len(idx0) > 1
+        for a, b in zip(idx0, idx1):
+            assert P1["still"][b] == 1
+            assert P1["tgt"][b] == P0["tgt"][a]
+        for b in idx1[len(idx0):]:
+            assert P1["still"][b] == 0
+    return n_dup
+
+
+def test_still_pairs_inherit_their_previous_target():
+    f = S.random_field((7, 6, 5), seed=2, kind="uniform")
+    s = oracle.Solver(f, tau=0.3)
+    moved = 0
+    for _ in range(4):
+        P0 = s.points()
+        s.iterate(0.5, 0.5, stop_s=0.0)
+        P1 = s.points()
+        _check_inheritance(P0, P1)
+        moved += int((P1["still"] == 0).sum())
+    assert moved > 0  # the diagram changed, so not every point was still
+
+
+def test_duplicate_keys_inherit_in_birth_cell_order():
+    """Several saddle-saddle pairs can share (dim, v_b, v_d) when one lower
+    star holds several critical edges or triangles; on these fields two such
+    points carry different targets, so a swapped order would show."""
+    n_dup = 0
+    n_uneven = 0
+    for shape, seed, tau in (((8, 7, 6), 2, 0.3), ((8, 7, 6), 11, 0.3), ((10, 9, 8), 3, 0.6), ((10, 9, 8), 38, 0.6)):
+        f = S.random_field(shape, seed=seed, kind="ties")
+        s = oracle.Solver(f, tau=tau)
+        P0 = s.points()
+        k0 = _keys(P0)
+        dups = [k for k in set(k0) if k0.count(k) > 1]
+        assert dups and any(len({int(P0["tgt"][i]) for i in range(len(k0)) if k0[i] == k}) > 1 for k in dups)
+        s.iterate(0.5, 0.5, stop_s=0.0)
+        P1 = s.points()
+        n_dup += _check_inheritance(P0, P1)
+        # a key held twice before and once after: which target survives is
+        # decided by the birth-cell order alone
+        k1 = _keys(P1)
+        n_uneven += sum(1 for k in dups if 0 < k1.count(k) < k0.count(k))
+    assert n_dup >= 2 and n_uneven >= 2

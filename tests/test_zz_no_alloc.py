@@ -43,3 +43,34 @@ def test_no_alloc_rejects_sizes_beyond_its_array():
     out = torch.zeros(2, dtype=torch.int64, device="cuda")
     r, n = tsf.tsf_zero_pairs_static(70, 70, 70, big.data_ptr(), out.data_ptr(), 1)
     assert r == tsf.TSF_EINVAL
+
+
+def test_no_alloc_capacity_and_nan_contracts():
+    """cap 0 with no output buffer and a cap below the count both report the
+    true count with TSF_ECAPACITY; a NaN value is TSF_ENAN."""
+    import torch
+
+    import paper_2407_12399_gb300 as tsf
+    from paper_2407_12399_gb300 import synthetic as S
+
+    shape = (16, 12, 10)
+    f = S.random_field(shape, seed=5, kind="uniform")
+    fld = tsf.Field(torch.from_numpy(f).cuda())
+    n_true = len(fld.zero_pairs())
+    fld.close()
+    lz, ly, lx = shape
+    dev = torch.from_numpy(f).cuda()
+    r, n = tsf.tsf_zero_pairs_static(lx, ly, lz, dev.data_ptr(), None, 0)
+    assert r == tsf.TSF_ECAPACITY and n == n_true
+    small = torch.zeros(2 * 7, dtype=torch.int64, device="cuda")
+    r, n = tsf.tsf_zero_pairs_static(lx, ly, lz, dev.data_ptr(), small.data_ptr(), 7)
+    assert r == tsf.TSF_ECAPACITY and n == n_true
+    bad = f.copy()
+    bad.flat[123] = np.nan
+    devb = torch.from_numpy(bad).cuda()
+    out = torch.zeros(2 * n_true, dtype=torch.int64, device="cuda")
+    r, _ = tsf.tsf_zero_pairs_static(lx, ly, lz, devb.data_ptr(), out.data_ptr(), n_true)
+    assert r == tsf.TSF_ENAN
+    # and the array still serves a good call afterwards
+    r, n = tsf.tsf_zero_pairs_static(lx, ly, lz, dev.data_ptr(), out.data_ptr(), n_true)
+    assert r == tsf.TSF_OK and n == n_true
