@@ -62,14 +62,17 @@ def gaussian_mixture(shape=(32, 32, 32), n_bumps=8, seed=0, noise_frac=0.05,
     return _normalise(f)
 
 
-def _perlin_octave(shape, freq, rng):
-    """Lattice-gradient noise, `freq` cells across the unit cube."""
+def _perlin_octave(shape, freq, rng, slab=8):
+    """Lattice-gradient noise, `freq` cells across the unit cube.
+
+    Per grid point: the 8 surrounding lattice gradients dotted with the
+    offsets to their lattice points, blended with the quintic fade weights.
+    Evaluated slab by slab in z from per-axis arrays (each value is the same
+    sequence of float64 operations as a whole-grid evaluation)."""
     g = rng.normal(size=(freq + 1, freq + 1, freq + 1, 3))
     g /= np.linalg.norm(g, axis=-1, keepdims=True)
     z, y, x = _coords(shape)
-    px = np.broadcast_to(x * freq, shape)
-    py = np.broadcast_to(y * freq, shape)
-    pz = np.broadcast_to(z * freq, shape)
+    px, py, pz = x * freq, y * freq, z * freq
     ix = np.minimum(np.floor(px).astype(np.int64), freq - 1)
     iy = np.minimum(np.floor(py).astype(np.int64), freq - 1)
     iz = np.minimum(np.floor(pz).astype(np.int64), freq - 1)
@@ -79,14 +82,19 @@ def _perlin_octave(shape, freq, rng):
         return t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
 
     wx, wy, wz = fade(tx), fade(ty), fade(tz)
+    side = freq + 1
+    gc = [np.ascontiguousarray(g[..., k]).ravel() for k in range(3)]  # g[ix, iy, iz, k] at (ix*side+iy)*side+iz
     out = np.zeros(shape, dtype=np.float64)
-    for cz in (0, 1):
-        for cy in (0, 1):
-            for cx in (0, 1):
-                gg = g[ix + cx, iy + cy, iz + cz]
-                dot = gg[..., 0] * (tx - cx) + gg[..., 1] * (ty - cy) + gg[..., 2] * (tz - cz)
-                w = (wx if cx else 1 - wx) * (wy if cy else 1 - wy) * (wz if cz else 1 - wz)
-                out += w * dot
+    for z0 in range(0, shape[0], slab):
+        sl = slice(z0, min(shape[0], z0 + slab))
+        o = out[sl]
+        for cz in (0, 1):
+            for cy in (0, 1):
+                for cx in (0, 1):
+                    idx = ((ix + cx) * side + (iy + cy)) * side + (iz[sl] + cz)
+                    dot = gc[0][idx] * (tx - cx) + gc[1][idx] * (ty - cy) + gc[2][idx] * (tz[sl] - cz)
+                    w = (wx if cx else 1 - wx) * (wy if cy else 1 - wy) * (wz[sl] if cz else 1 - wz[sl])
+                    o += w * dot
     return out
 
 
@@ -291,15 +299,16 @@ def warm_start_inputs(n, seed=4, shape=(64, 64, 64)):
     uniform noise, threshold 0.1) and a filament field (shape[0] // 8
     loops, threshold 0.05), each with its own seed drawn from `seed`.
     The matching targets g are the solver's simplified fields."""
+    return [warm_start_input(i, n, seed, shape) for i in range(n)]
+
+
+def warm_start_input(i, n, seed=4, shape=(64, 64, 64)):
+    """The i-th of warm_start_inputs(n, seed, shape), generated alone."""
     rng = np.random.default_rng(seed)
-    seeds = rng.integers(0, 2 ** 31 - 1, size=n)
-    out = []
-    for i, k in enumerate(seeds):
-        if i % 2 == 0:
-            out.append((gaussian_mixture(shape, n_bumps=8, seed=int(k), noise_frac=0.05), 0.1))
-        else:
-            out.append((filament_field(shape, seed=int(k), n_loops=max(shape[0] // 8, 1)), 0.05))
-    return out
+    k = int(rng.integers(0, 2 ** 31 - 1, size=n)[i])
+    if i % 2 == 0:
+        return gaussian_mixture(shape, n_bumps=8, seed=k, noise_frac=0.05), 0.1
+    return filament_field(shape, seed=k, n_loops=max(shape[0] // 8, 1)), 0.05
 
 
 def warm_start_field(shape=(256, 256, 256), seed=5):

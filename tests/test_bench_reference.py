@@ -20,4 +20,5 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "iters/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"] == "filament_128"
+    assert d["config"]["workload"] == "warm_start_256" and d["config"]["grid"] == [256, 256, 256]
+    assert "host" in d["cpu_baseline"] and d["cpu_baseline"]["host"]["nproc"] >= 1

@@ -201,3 +201,60 @@ def test_sampled_d0_pairs_are_elder_rule_deaths(full):
         assert int(r["cell_death"]) == (1 << 60) | (base << 6) | m_
         assert int(r["v_death"]) == hi
     assert checked >= 20
+
+
+def _rows(f, P):
+    """Oracle points as (dim, essential, v_b, v_d, birth cell, death cell,
+    birth bits, death bits), in diagram order."""
+    flat = np.asarray(f, np.float32).ravel()
+    bits = lambda x: int(np.float32(x).view(np.uint32))
+    rows = [(int(P["dim"][i]), int(P["essential"][i]), int(P["vb"][i]), int(P["vd"][i]), int(P["cb"][i]),
+             int(P["cd"][i]), bits(flat[P["vb"][i]]), bits(flat[P["vd"][i]])) for i in range(len(P["vb"]))]
+    return sorted(rows, key=lambda r: (float(np.uint32(r[6]).view(np.float32)), float(np.uint32(r[7]).view(np.float32)),
+                                       r[2], r[3], r[4]))
+
+
+def _gpu_rows(d):
+    bits = lambda x: int(np.float32(x).view(np.uint32))
+    return [(int(r["dim"]), int(r["essential"]), int(r["v_birth"]), int(r["v_death"]), int(r["cell_birth"]),
+             int(r["cell_death"]), bits(r["birth"]), bits(r["death"])) for r in d]
+
+
+def test_full_diagram_and_three_solver_steps_are_bit_exact(full):
+    """The whole 128^3 diagram (all of D0, D1 and D2: cells and value bits, in
+    diagram order) against the oracle's plain reduction of the lexicographic
+    filtration (Section 2.2); then three iterations of Algorithm 1 at threshold
+    0.05: assignment and still flags before each step, field bits after it,
+    and the next diagram's points.  (The oracle needs one to two minutes per
+    diagram of this filament field.)"""
+    import torch
+
+    import paper_2407_12399_gb300 as tsf
+    f0, d = full
+    ref = oracle.Solver(f0, tau=0.05)
+    P = ref.points()
+    got = _gpu_rows(d)
+    want = _rows(f0, {k: P[k] for k in ("dim", "essential", "vb", "vd", "cb", "cd")})
+    assert len(got) == len(want) and got == want
+    fld = tsf.Field(torch.from_numpy(f0).cuda())
+    fld.set_threshold(0.05)
+    T, RT = fld.targets(), ref.targets()
+    assert list(zip(T["v_birth"].tolist(), T["v_death"].tolist(), T["dim"].tolist())) == \
+        list(zip(RT["vb"].tolist(), RT["vd"].tolist(), RT["dim"].tolist()))
+    for j in range(3):
+        tgt, still = fld.assignment()
+        P = ref.points()
+        assert tgt.tolist() == P["tgt"].tolist(), f"assignment differs at j={j}"
+        assert still.tolist() == P["still"].tolist(), f"still flags differ at j={j}"
+        st = fld.step(stop_s=0.0)
+        ref.iterate(stop_s=0.0)
+        g, r = fld.values(), ref.field()
+        assert np.array_equal(g.view(np.uint32), r.view(np.uint32)), f"field differs after step {j + 1}"
+        got = [x[:6] for x in _gpu_rows(fld.diagram())]
+        P = ref.points()
+        assert got == list(zip(P["dim"].tolist(), P["essential"].tolist(), P["vb"].tolist(), P["vd"].tolist(),
+                               P["cb"].tolist(), P["cd"].tolist()))
+        rs = ref.stats()
+        assert st["n_still"] == rs["still"] and st["n_updated_vertices"] == rs["updated"]
+        assert st["loss"] == pytest.approx(rs["loss"], rel=1e-12)
+    fld.close()
