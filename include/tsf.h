@@ -224,6 +224,16 @@ int tsf_batch_simplify(tsf_batch* batch, const tsf_params* params, tsf_stats* st
  * history is reset, so the next assignment starts cold). */
 int tsf_set_field(tsf_field* field, const float* values, int values_on_device);
 
+/* Warm start (not in the paper): replaces the current values by a start
+ * field g0 (lx*ly*lz floats, host or device) and keeps the target diagram
+ * and loss_0 of the field the targets were set from.  The diagram of g0 is
+ * computed (Sections 2.2, 4.2), every point is matched by the exact solver
+ * (no still pairs: Section 4.3 has no previous diagram to reuse), and the
+ * solver restarts at iteration 0 from g0, so tsf_simplify's stop rule
+ * L <= stop_s * loss_0 refers to the original field's loss.  Errors:
+ * TSF_EINVAL, TSF_ENOTARGET before a target was set, TSF_ENAN. */
+int tsf_set_start_field(tsf_field* field, const float* values, int values_on_device);
+
 /* The current assignment, in the order of the last diagram: target[i] is the
  * index of point i's target in the target list (tsf_get_targets), or -1 for
  * the diagonal; still[i] is 1 for still points.  Host memory, cap entries
@@ -255,6 +265,19 @@ const char* tsf_stage_name(int stage);
 
 /* Number of kernels this library has launched in this process. */
 int64_t tsf_kernel_launches(void);
+
+/* Test and tuning knobs of the D0/D2 union-find (process-wide, not in the
+ * paper; results never depend on them, only the schedule and the bounds):
+ *   1: items from which the union-find rounds run over the whole GPU
+ *      (default 65536; below, one block runs them);
+ *   2: active items below which one block finishes the rounds (default 8192);
+ *   3: cap on the union-find rounds (default 0 = none; a cap that is hit
+ *      makes the call fail with TSF_ETIMEOUT);
+ *   4: polls a block waits at a grid barrier of those rounds before it gives
+ *      up (default 2^24; giving up makes the call fail with TSF_ETIMEOUT).
+ * Returns the previous value, or -1 for an unknown knob.  Set them only
+ * while no call of this library is running. */
+int64_t tsf_debug_set(int what, int64_t value);
 
 /* After a step that changed at most this many vertex values, the next
  * diagram merges the changed vertices into the previous vertex order instead
@@ -288,6 +311,63 @@ int64_t tsf_kernel_launches(void);
 #define TSF_STATIC_MAX_VERTICES 262144
 int tsf_zero_pairs_static(int lx, int ly, int lz, const float* values, uint64_t* out, int64_t cap_pairs,
                           int64_t* n_out, void* cuda_stream);
+
+/* Learned warm start.  The paper has no learned component: this network
+ * proposes a starting field g0 for a field f, and the solver (Algorithm 1)
+ * then refines g0 against f's own target diagram, judging the result.
+ *
+ * Network: a 3-level 3D U-Net on an (lz, ly, lx) grid (each side a multiple
+ * of 4, at least 8), channels 16/32/64; per level two 3x3x3 convolutions
+ * with zero padding, bias and ReLU; 2x2x2 average pooling down, nearest x2
+ * upsampling up, the skip features concatenated after the upsampled ones; a
+ * 1x1 head to one channel.  Inputs: f and a constant channel holding the
+ * threshold fraction tau; output g0 = f + head.  Weights and activations
+ * are stored in bfloat16 and every sum is accumulated in fp32; the
+ * convolutions run on the tensor cores.  Training minimises mean((g0 -
+ * g)^2) over the voxels by Adam (beta1 0.9, beta2 0.999, eps 1e-8) on an
+ * fp32 master copy of the parameters.
+ *
+ * Parameters: TSF_UNET_NPARAMS floats, layer by layer in the order e1a e1b
+ * e2a e2b e3a e3b d2a d2b d1a d1b head; per convolution the weights
+ * (cout, cin, 3, 3, 3) indexed (dz, dy, dx) as a cross-correlation, then the
+ * cout biases; the head's 16 weights, then its bias.  Channels: e1a 2->16,
+ * e1b 16->16, e2a 16->32, e2b 32->32, e3a 32->64, e3b 64->64, d2a 96->32
+ * (upsampled e3b, then e2b), d2b 32->32, d1a 48->16 (upsampled d2b, then
+ * e1b), d1b 16->16.
+ *
+ * tsf_unet_create: a network from host parameters, on the device current at
+ *   this call; work is enqueued on cuda_stream (NULL = legacy default) and
+ *   every call has finished when it returns.  Errors: TSF_EINVAL (n !=
+ *   TSF_UNET_NPARAMS), TSF_ENOMEM.
+ * tsf_unet_get_params: the current fp32 parameters (host, n floats).
+ * tsf_unet_forward: g0 for the field f (lx*ly*lz floats, layout as
+ *   tsf_create_field); f and g0 both host or both device (on_device).
+ * tsf_unet_gradients: loss mean((g0 - g)^2) (*loss, fp64, may be NULL) and
+ *   its gradient with respect to every parameter (grad: host, n floats, may
+ *   be NULL) for the pair (f, g), without an update.
+ * tsf_unet_train_step: the same, then one Adam step with learning rate lr.
+ * tsf_unet_debug: every layer's stored activation as fp32 (host acts, in the
+ *   order x e1a e1b e2a e2b e3a e3b d2a d2b d1a d1b g0, each (C, z, y, x) at
+ *   its level: full grid for x e1a e1b d1a d1b g0, half for e2a e2b d2a d2b,
+ *   quarter for e3a e3b) and, when g is not NULL, every convolution's
+ *   gradient with respect to its pre-activation output (host gz, order d1b
+ *   d1a d2b d2a e3b e3a e2b e2a e1b e1a); TSF_ECAPACITY if a buffer is too
+ *   small.  For verification; f and g are host memory.
+ * Grid errors: TSF_EINVAL.  A bounded device wait that gave up:
+ *   TSF_ETIMEOUT. */
+typedef struct tsf_unet tsf_unet;
+#define TSF_UNET_NPARAMS 353713
+int64_t tsf_unet_num_params(void);
+int tsf_unet_create(const float* params, int64_t n, void* cuda_stream, tsf_unet** out);
+int tsf_unet_destroy(tsf_unet* net);
+int tsf_unet_get_params(tsf_unet* net, float* out, int64_t n);
+int tsf_unet_forward(tsf_unet* net, int lx, int ly, int lz, const float* f, float tau, float* g0, int on_device);
+int tsf_unet_gradients(tsf_unet* net, int lx, int ly, int lz, const float* f, const float* g, int on_device, float tau,
+                       float* grad, double* loss);
+int tsf_unet_train_step(tsf_unet* net, int lx, int ly, int lz, const float* f, const float* g, int on_device,
+                        float tau, float lr, double* loss);
+int tsf_unet_debug(tsf_unet* net, int lx, int ly, int lz, const float* f, const float* g, float tau, float* acts,
+                   int64_t acts_cap, float* gz, int64_t gz_cap);
 
 /* Human-readable name of a status code. */
 const char* tsf_status_string(int status);

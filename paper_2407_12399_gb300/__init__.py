@@ -73,7 +73,10 @@ EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_
            "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
            "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static",
            "tsf_loss_and_gradient", "tsf_batch_create", "tsf_batch_destroy", "tsf_batch_size", "tsf_batch_field",
-           "tsf_batch_set_signal_thresholds", "tsf_batch_step", "tsf_batch_simplify")
+           "tsf_batch_set_signal_thresholds", "tsf_batch_step", "tsf_batch_simplify", "tsf_unet_num_params", "tsf_set_start_field", "tsf_debug_set",
+           "tsf_unet_create", "tsf_unet_destroy", "tsf_unet_get_params", "tsf_unet_forward", "tsf_unet_gradients",
+           "tsf_unet_train_step", "tsf_unet_debug")
+TSF_UNET_NPARAMS = 353713
 TSF_NSTAGES = 12
 INCREMENTAL_ORDER_MAX = 8192  # TSF_INCREMENTAL_ORDER_MAX
 
@@ -112,6 +115,15 @@ def lib():
             "tsf_batch_set_signal_thresholds": [P, P],
             "tsf_batch_step": [P, ctypes.POINTER(tsf_params), P],
             "tsf_batch_simplify": [P, ctypes.POINTER(tsf_params), P],
+            "tsf_set_start_field": [P, P, I],
+            "tsf_unet_create": [P, I64, P, ctypes.POINTER(P)],
+            "tsf_unet_destroy": [P],
+            "tsf_unet_get_params": [P, P, I64],
+            "tsf_unet_forward": [P, I, I, I, P, ctypes.c_float, P, I],
+            "tsf_unet_gradients": [P, I, I, I, P, P, I, ctypes.c_float, P, ctypes.POINTER(ctypes.c_double)],
+            "tsf_unet_train_step": [P, I, I, I, P, P, I, ctypes.c_float, ctypes.c_float,
+                                    ctypes.POINTER(ctypes.c_double)],
+            "tsf_unet_debug": [P, I, I, I, P, P, ctypes.c_float, P, I64, P, I64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -127,6 +139,10 @@ def lib():
         L.tsf_stage_name.restype = ctypes.c_char_p
         L.tsf_kernel_launches.argtypes = []
         L.tsf_kernel_launches.restype = ctypes.c_int64
+        L.tsf_debug_set.argtypes = [I, ctypes.c_int64]
+        L.tsf_debug_set.restype = ctypes.c_int64
+        L.tsf_unet_num_params.argtypes = []
+        L.tsf_unet_num_params.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -186,6 +202,10 @@ def tsf_simplify(h, params, out_ptr=None, out_on_device=0, stats=None):
 
 def tsf_get_field(h, out_ptr, out_on_device=0):
     _check(lib().tsf_get_field(h, out_ptr, out_on_device), "tsf_get_field")
+
+
+def tsf_set_start_field(h, values_ptr, values_on_device=0):
+    _check(lib().tsf_set_start_field(h, values_ptr, values_on_device), "tsf_set_start_field")
 
 
 def tsf_set_field(h, values_ptr, values_on_device=0):
@@ -282,6 +302,11 @@ def tsf_profile_read(h):
 
 def tsf_stage_name(i):
     return lib().tsf_stage_name(i).decode()
+
+
+def tsf_debug_set(what, value):
+    """Test and tuning knob (include/tsf.h); returns the previous value."""
+    return int(lib().tsf_debug_set(what, value))
 
 
 def tsf_kernel_launches():
@@ -467,3 +492,172 @@ class Batch:
 
     def values(self):
         return [f.values() for f in self.fields]
+
+
+# --- learned warm start (tsf_unet_*) --------------------------------------
+def tsf_unet_num_params():
+    return int(lib().tsf_unet_num_params())
+
+
+def tsf_unet_create(params_ptr, n, cuda_stream=0):
+    h = ctypes.c_void_p()
+    _check(lib().tsf_unet_create(params_ptr, n, cuda_stream or None, ctypes.byref(h)), "tsf_unet_create")
+    return h
+
+
+def tsf_unet_destroy(h):
+    return lib().tsf_unet_destroy(h)
+
+
+def tsf_unet_get_params(h, out_ptr, n):
+    _check(lib().tsf_unet_get_params(h, out_ptr, n), "tsf_unet_get_params")
+
+
+def tsf_unet_forward(h, lx, ly, lz, f_ptr, tau, g0_ptr, on_device):
+    _check(lib().tsf_unet_forward(h, lx, ly, lz, f_ptr, tau, g0_ptr, on_device), "tsf_unet_forward")
+
+
+def tsf_unet_gradients(h, lx, ly, lz, f_ptr, g_ptr, on_device, tau, grad_ptr):
+    loss = ctypes.c_double(0.0)
+    _check(lib().tsf_unet_gradients(h, lx, ly, lz, f_ptr, g_ptr, on_device, tau, grad_ptr, ctypes.byref(loss)),
+           "tsf_unet_gradients")
+    return loss.value
+
+
+def tsf_unet_train_step(h, lx, ly, lz, f_ptr, g_ptr, on_device, tau, lr):
+    loss = ctypes.c_double(0.0)
+    _check(lib().tsf_unet_train_step(h, lx, ly, lz, f_ptr, g_ptr, on_device, tau, lr, ctypes.byref(loss)),
+           "tsf_unet_train_step")
+    return loss.value
+
+
+def tsf_unet_debug(h, lx, ly, lz, f_ptr, g_ptr, tau, acts_ptr, acts_cap, gz_ptr, gz_cap):
+    _check(lib().tsf_unet_debug(h, lx, ly, lz, f_ptr, g_ptr, tau, acts_ptr, acts_cap, gz_ptr, gz_cap),
+           "tsf_unet_debug")
+
+
+UNET_CHANNELS = (16, 32, 64)
+
+
+def unet_layer_shapes():
+    """(name, weight shape, bias length) of every layer, in parameter order
+    (the order tsf.h states)."""
+    c1, c2, c3 = UNET_CHANNELS
+    convs = [("e1a", c1, 2), ("e1b", c1, c1), ("e2a", c2, c1), ("e2b", c2, c2), ("e3a", c3, c2), ("e3b", c3, c3),
+             ("d2a", c2, c3 + c2), ("d2b", c2, c2), ("d1a", c1, c2 + c1), ("d1b", c1, c1)]
+    return [(n, (co, ci, 3, 3, 3), co) for n, co, ci in convs] + [("head", (1, c1), 1)]
+
+
+def unet_flatten(p):
+    """Parameter dict {name.w, name.b} -> the flat float32 vector."""
+    return np.concatenate([np.asarray(p[n + k], np.float64).ravel() for n, _, _ in unet_layer_shapes()
+                           for k in (".w", ".b")]).astype(np.float32)
+
+
+def unet_unflatten(flat):
+    out, o = {}, 0
+    for n, ws, nb in unet_layer_shapes():
+        k = int(np.prod(ws))
+        out[n + ".w"] = np.asarray(flat[o:o + k]).reshape(ws)
+        out[n + ".b"] = np.asarray(flat[o + k:o + k + nb])
+        o += k + nb
+    return out
+
+
+def unet_init(seed=0):
+    """He-normal weights (std sqrt(2 / fan_in)), zero biases, a zero head (the
+    untrained network returns f), as a flat float32 vector."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for n, ws, nb in unet_layer_shapes():
+        fan_in = int(np.prod(ws[1:]))
+        p[n + ".w"] = np.zeros(ws) if n == "head" else rng.normal(0.0, np.sqrt(2.0 / fan_in), ws)
+        p[n + ".b"] = np.zeros(nb)
+    return unet_flatten(p)
+
+
+class UNet:
+    """The warm-start network on the current CUDA device."""
+
+    def __init__(self, params=None, seed=0, stream=None):
+        flat = unet_init(seed) if params is None else np.ascontiguousarray(params, np.float32)
+        assert flat.size == TSF_UNET_NPARAMS
+        self._h = tsf_unet_create(flat.ctypes.data, flat.size, stream.cuda_stream if stream is not None else 0)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            tsf_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(TSF_UNET_NPARAMS, np.float32)
+        tsf_unet_get_params(self._h, out.ctypes.data, out.size)
+        return out
+
+    def forward(self, f, tau):
+        """g0 for f: a torch CUDA tensor (returns one) or a numpy array."""
+        if hasattr(f, "data_ptr"):
+            import torch
+            g0 = torch.empty_like(f)
+            lz, ly, lx = f.shape
+            tsf_unet_forward(self._h, lx, ly, lz, f.data_ptr(), tau, g0.data_ptr(), 1)
+            return g0
+        f = np.ascontiguousarray(f, np.float32)
+        g0 = np.empty_like(f)
+        lz, ly, lx = f.shape
+        tsf_unet_forward(self._h, lx, ly, lz, f.ctypes.data, tau, g0.ctypes.data, 0)
+        return g0
+
+    def gradients(self, f, g, tau):
+        f = np.ascontiguousarray(f, np.float32)
+        g = np.ascontiguousarray(g, np.float32)
+        grad = np.empty(TSF_UNET_NPARAMS, np.float32)
+        lz, ly, lx = f.shape
+        loss = tsf_unet_gradients(self._h, lx, ly, lz, f.ctypes.data, g.ctypes.data, 0, tau, grad.ctypes.data)
+        return loss, grad
+
+    def train_step(self, f, g, tau, lr):
+        """One Adam step on the pair (f, g): torch CUDA tensors or numpy arrays."""
+        lz, ly, lx = f.shape
+        if hasattr(f, "data_ptr"):
+            return tsf_unet_train_step(self._h, lx, ly, lz, f.data_ptr(), g.data_ptr(), 1, tau, lr)
+        f = np.ascontiguousarray(f, np.float32)
+        g = np.ascontiguousarray(g, np.float32)
+        return tsf_unet_train_step(self._h, lx, ly, lz, f.ctypes.data, g.ctypes.data, 0, tau, lr)
+
+    ACT_KEYS = (("x", 2, 1), ("e1a", 16, 1), ("e1b", 16, 1), ("e2a", 32, 2), ("e2b", 32, 2), ("e3a", 64, 4),
+                ("e3b", 64, 4), ("d2a", 32, 2), ("d2b", 32, 2), ("d1a", 16, 1), ("d1b", 16, 1), ("g0", 1, 1))
+    GZ_KEYS = (("d1b", 16, 1), ("d1a", 16, 1), ("d2b", 32, 2), ("d2a", 32, 2), ("e3b", 64, 4), ("e3a", 64, 4),
+               ("e2b", 32, 2), ("e2a", 32, 2), ("e1b", 16, 1), ("e1a", 16, 1))
+
+    def debug(self, f, tau, g=None):
+        """Every stored activation (and, with g, every pre-activation
+        gradient) as float32 arrays (C, z, y, x) keyed by layer."""
+        f = np.ascontiguousarray(f, np.float32)
+        lz, ly, lx = f.shape
+
+        def layout(keys):
+            out, o = [], 0
+            for k, c, s in keys:
+                shape = (c, lz // s, ly // s, lx // s)
+                out.append((k, o, shape))
+                o += int(np.prod(shape))
+            return out, o
+
+        al, an = layout(self.ACT_KEYS)
+        gl, gn = layout(self.GZ_KEYS)
+        acts = np.empty(an, np.float32)
+        gz = np.empty(gn, np.float32) if g is not None else None
+        gp = np.ascontiguousarray(g, np.float32) if g is not None else None
+        tsf_unet_debug(self._h, lx, ly, lz, f.ctypes.data, gp.ctypes.data if gp is not None else None, tau,
+                       acts.ctypes.data, an, gz.ctypes.data if gz is not None else None, gn if gz is not None else 0)
+        A = {k: acts[o:o + int(np.prod(sh))].reshape(sh) for k, o, sh in al}
+        A["g0"] = A["g0"][0]
+        G = {k: gz[o:o + int(np.prod(sh))].reshape(sh) for k, o, sh in gl} if gz is not None else None
+        return A, G

@@ -745,6 +745,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->PS.listB);
   dev_free(F->PS.parent);
   dev_free(F->PS.reserve);
+  dev_free(F->PS.counter);
   dev_free(F->PO.d0_min);
   dev_free(F->PO.d0_killed);
   dev_free(F->PO.d0mask);
@@ -872,6 +873,7 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
     ck(dev_alloc(&F->totals, 1));
     ck(dev_alloc(&F->status, 1));
     ck(dev_alloc(&F->counter, 1));
+    ck(dev_alloc(&F->PS.counter, 16));
     ck(cudaMallocHost((void**)&F->h_flags, 16));
     ck(cudaMemcpyAsync(F->f, values, sizeof(float) * nv,
                        values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, F->st));
@@ -1064,6 +1066,37 @@ int tsf_loss_and_gradient(tsf_field* F, const float* values, int values_on_devic
   });
 }
 
+int tsf_set_start_field(tsf_field* F, const float* values, int values_on_device) {
+  if (!F || !values) return TSF_EINVAL;
+  if (!F->have_targets) return TSF_ENOTARGET;
+  return guarded_f(F, [&]() {
+    // the start field replaces the values; the targets and loss_0 stay those
+    // of f_0, and the solver restarts at iteration 0 from the new diagram
+    const float* in = values;
+    if (!values_on_device) {
+      if (!F->lstage) ck(dev_alloc(&F->lstage, (size_t)F->d.nv));
+      ck(cudaMemcpyAsync(F->lstage, values, sizeof(float) * F->d.nv, cudaMemcpyHostToDevice, F->st));
+      in = F->lstage;
+    }
+    replace_values(F->d.nv, in, F->f, F->upd, F->counter, F->st);
+    unsigned long long nchanged = 0;
+    ck(cudaMemcpyAsync(&nchanged, F->counter, sizeof(nchanged), cudaMemcpyDeviceToHost, F->st));
+    ck(cudaStreamSynchronize(F->st));
+    F->n_updated = (int64_t)nchanged;
+    F->upd_valid = true;
+    std::swap(F->pts, F->prev);  // the previous diagram is not consulted
+    F->nprev = F->np;
+    int r = compute_diagram(F, true);
+    if (r) return r;
+    r = run_assign(F, F->prev, 0);
+    if (r) return r;
+    F->iter = 0;
+    eval(F, 0.0f);
+    ck(cudaStreamSynchronize(F->st));
+    return TSF_OK;
+  });
+}
+
 int tsf_get_field(tsf_field* F, float* out, int out_on_device) {
   if (!F || !out) return TSF_EINVAL;
   return guarded_dev(F, [&]() {
@@ -1186,5 +1219,7 @@ const char* tsf_stage_name(int s) {
 }
 
 int64_t tsf_kernel_launches(void) { return (int64_t)tsf::launches(); }
+
+int64_t tsf_debug_set(int what, int64_t value) { return tsf::set_knob(what, value); }
 
 }  // extern "C"
