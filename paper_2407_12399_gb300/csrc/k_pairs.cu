@@ -18,6 +18,7 @@
 #include <atomic>
 #include <utility>
 
+#include "tsf_grid.cuh"
 #include "tsf_group.cuh"
 #include "tsf_kernels.cuh"
 #include "tsf_star.cuh"
@@ -25,6 +26,31 @@
 namespace tsf {
 
 constexpr int kUFT = 1024;
+// Schedule of the union-find rounds (process-wide; tsf_debug_set changes
+// them for tests): items from which the rounds start over the whole GPU,
+// active items below which one block finishes them, a cap on the rounds
+// (0: the bound n + 2 that can never be reached) and the grid barrier's poll
+// limit.
+std::atomic<int64_t> g_uf_grid_min{1 << 16};
+std::atomic<int64_t> g_uf_handoff{1 << 13};
+std::atomic<int64_t> g_uf_round_cap{0};
+std::atomic<int64_t> g_barrier_limit{1 << 24};
+
+int64_t set_knob(int what, int64_t value) {
+  std::atomic<int64_t>* k = what == 1 ? &g_uf_grid_min : what == 2 ? &g_uf_handoff : what == 3 ? &g_uf_round_cap
+                            : what == 4 ? &g_barrier_limit : nullptr;
+  if (!k) return -1;
+  return k->exchange(value);
+}
+
+// Control block of the whole-GPU union-find rounds (PairScratch::counter).
+struct UfCtl {
+  unsigned bar[2];  // grid barrier: arrivals, generation
+  int n[2];         // lengths of listA, listB
+  int which;        // list holding the active items
+  int rounds;       // rounds done
+  int pad[10];
+};
 
 // ---------------------------------------------------------------------------
 // integral lines
@@ -139,6 +165,19 @@ __global__ void k_d2_trace(Dims d, int n2, int n3, CritLists L, const uint32_t* 
 // ---------------------------------------------------------------------------
 constexpr int kFindLimit = 1 << 26;
 
+// For kernels spread over several SMs: every read of the union-find state
+// goes to L2 (another SM may have linked a root since this SM cached it).
+__device__ __forceinline__ int uf_root_cg(int32_t* parent, int x) {
+  for (int s = 0; s < kFindLimit; ++s) {
+    const int p = __ldcg(&parent[x]);
+    if (p == x) return x;
+    const int gp = __ldcg(&parent[p]);
+    if (gp != p) parent[x] = gp;
+    x = gp;
+  }
+  return x;
+}
+
 __device__ __forceinline__ int uf_root(int32_t* parent, int x) {
   for (int s = 0; s < kFindLimit; ++s) {
     int p = parent[x];
@@ -182,27 +221,43 @@ __device__ __forceinline__ int block_exscan_int(int v, int& total) {
 // n items (priority i, or n-1-i when `reverse`), nn nodes.  Younger node =
 // larger index (reverse = false) or smaller index (reverse = true).
 // kill[i] = node killed by item i, or -1 (item closes a cycle).
+// `ctl` (may be null): resume after k_uf_rounds_grid, from its active list
+// (ctl->which selects listA or listB, ctl->n[which] its length) and its
+// union-find state.
 __global__ void __launch_bounds__(kUFT) k_uf_rounds(int n, int nn, bool reverse, const int32_t* __restrict__ ends,
                                                     int32_t* parent, int32_t* reserve, int32_t* listA,
                                                     int32_t* listB, int32_t* roots, int32_t* kill,
-                                                    uint32_t* status) {
+                                                    const UfCtl* ctl, int cap, uint32_t* status) {
   __shared__ int s_n;
-  for (int x = threadIdx.x; x < nn; x += kUFT) {
-    parent[x] = x;
-    reserve[x] = 0x7FFFFFFF;
-  }
-  for (int i = threadIdx.x; i < n; i += kUFT) {
-    kill[i] = -1;
-    listA[i] = i;
-  }
-  if (threadIdx.x == 0) s_n = n;
-  __syncthreads();
   int32_t* cur = listA;
   int32_t* nxt = listB;
-  for (int round = 0;; ++round) {
+  int round0 = 0;
+  if (ctl) {
+    // the whole-GPU rounds gave up (a barrier or the round cap): their lists
+    // may be partly written, so nothing resumes from them
+    if (*reinterpret_cast<const volatile uint32_t*>(status) & (kErrSpin | kErrRounds)) return;
+    if (ctl->which) {
+      cur = listB;
+      nxt = listA;
+    }
+    if (threadIdx.x == 0) s_n = ctl->n[ctl->which];
+    round0 = ctl->rounds;
+  } else {
+    for (int x = threadIdx.x; x < nn; x += kUFT) {
+      parent[x] = x;
+      reserve[x] = 0x7FFFFFFF;
+    }
+    for (int i = threadIdx.x; i < n; i += kUFT) {
+      kill[i] = -1;
+      listA[i] = i;
+    }
+    if (threadIdx.x == 0) s_n = n;
+  }
+  __syncthreads();
+  for (int round = round0;; ++round) {
     int m = s_n;
     if (m == 0) break;
-    if (round > n + 2) {
+    if (round > n + 2 || (cap > 0 && round >= cap)) {
       if (threadIdx.x == 0) atomicOr(status, kErrRounds);
       break;
     }
@@ -274,13 +329,131 @@ __global__ void k_d0mask_set(int n1, CritLists L, const int32_t* __restrict__ ki
   if (i < n1 && kill[i] >= 0) atomicOr(&d0mask[L.c1_vn[i] >> 4], 1u << (L.c1_vn[i] & 15u));
 }
 
+// The same rounds over the whole GPU (cooperative launch, grid barriers
+// between the phases of a round), while the active list holds at least
+// `handoff` items; then it stops and k_uf_rounds resumes from ctl.  The
+// list order within a round does not matter (reservations compare item
+// priorities), so blocks append survivors with atomics.
+__global__ void __launch_bounds__(kUFT) k_uf_rounds_grid(int n, int nn, bool reverse,
+                                                         const int32_t* __restrict__ ends, int32_t* parent,
+                                                         int32_t* reserve, int32_t* listA, int32_t* listB,
+                                                         int32_t* roots, int32_t* kill, UfCtl* ctl, int handoff,
+                                                         int cap, unsigned limit, uint32_t* status) {
+  __shared__ int s_cnt, s_base;
+  const unsigned nb = gridDim.x;
+  const int gt = blockIdx.x * kUFT + threadIdx.x, gn = nb * kUFT;
+  for (int x = gt; x < nn; x += gn) {
+    parent[x] = x;
+    reserve[x] = 0x7FFFFFFF;
+  }
+  for (int i = gt; i < n; i += gn) {
+    kill[i] = -1;
+    listA[i] = i;
+  }
+  if (gt == 0) {
+    ctl->n[0] = n;
+    ctl->n[1] = 0;
+    ctl->which = 0;
+    ctl->rounds = 0;
+  }
+  if (!grid_barrier(ctl->bar, nb, status, limit)) return;
+  int which = 0;
+  for (int round = 0;; ++round) {
+    const int m = *reinterpret_cast<volatile int*>(&ctl->n[which]);
+    if (m == 0 || m < handoff) break;
+    if (round > n + 2 || (cap > 0 && round >= cap)) {
+      if (gt == 0) atomicOr(status, kErrRounds);
+      break;
+    }
+    const int32_t* cur = which ? listB : listA;
+    int32_t* nxt = which ? listA : listB;
+    for (int k = gt; k < m; k += gn) {
+      const int i = __ldcg(&cur[k]);
+      const int a = uf_root_cg(parent, ends[2 * i]), b = uf_root_cg(parent, ends[2 * i + 1]);
+      roots[2 * i] = a;
+      roots[2 * i + 1] = b;
+      if (a != b) {
+        const int pr = reverse ? n - 1 - i : i;
+        atomicMin(&reserve[a], pr);
+        atomicMin(&reserve[b], pr);
+      }
+    }
+    if (gt == 0) ctl->n[which ^ 1] = 0;
+    if (!grid_barrier(ctl->bar, nb, status, limit)) return;
+    for (int k = gt; k < m; k += gn) {
+      const int i = __ldcg(&cur[k]);
+      const int a = __ldcg(&roots[2 * i]), b = __ldcg(&roots[2 * i + 1]);
+      if (a == b) continue;
+      const int young = reverse ? min(a, b) : max(a, b);
+      const int old = a + b - young;
+      const int pr = reverse ? n - 1 - i : i;
+      if (__ldcg(&reserve[young]) == pr) {
+        parent[young] = old;
+        kill[i] = young;
+      }
+    }
+    if (!grid_barrier(ctl->bar, nb, status, limit)) return;
+    // clear the reservations and keep the items still joining two components
+    for (int base = blockIdx.x * kUFT; base < m; base += gn) {
+      const int k = base + threadIdx.x;
+      int keep = 0, i = 0;
+      if (k < m) {
+        i = __ldcg(&cur[k]);
+        const int a = __ldcg(&roots[2 * i]), b = __ldcg(&roots[2 * i + 1]);
+        if (a != b) {
+          reserve[a] = 0x7FFFFFFF;
+          reserve[b] = 0x7FFFFFFF;
+        }
+        keep = (a != b) && __ldcg(&kill[i]) < 0;
+      }
+      int tot;
+      const int ex = block_exscan_int(keep, tot);
+      if (threadIdx.x == 0) {
+        s_cnt = tot;
+        s_base = tot ? atomicAdd(&ctl->n[which ^ 1], tot) : 0;
+      }
+      __syncthreads();
+      if (keep) nxt[s_base + ex] = i;
+      __syncthreads();
+    }
+    which ^= 1;
+    if (gt == 0) {
+      ctl->which = which;
+      ctl->rounds = round + 1;
+    }
+    if (!grid_barrier(ctl->bar, nb, status, limit)) return;
+  }
+}
+
+// Union-find rounds of n items: over the whole GPU while the active list
+// is long, then on one block.
+void uf_rounds(int n, int nn, bool reverse, PairScratch& S, int32_t* kill, uint32_t* status, cudaStream_t st) {
+  int cap = (int)std::min<int64_t>(g_uf_round_cap.load(), 1 << 30);
+  const int nb = n >= g_uf_grid_min.load() ? cooperative_blocks((const void*)k_uf_rounds_grid, kUFT) : 0;
+  if (nb > 0) {
+    UfCtl* ctl = reinterpret_cast<UfCtl*>(S.counter);
+    cudaMemsetAsync(ctl, 0, sizeof(UfCtl), st);
+    int handoff = (int)std::min<int64_t>(g_uf_handoff.load(), 1 << 30);
+    unsigned limit = (unsigned)std::min<int64_t>(std::max<int64_t>(g_barrier_limit.load(), 1), 1u << 30);
+    void* args[] = {&n,        &nn,   &reverse, &S.ends, &S.parent, &S.reserve, &S.listA, &S.listB, &S.roots,
+                    &kill,     &ctl,  &handoff, &cap,    &limit,    &status};
+    if (cooperative_launch((const void*)k_uf_rounds_grid, dim3(nb), dim3(kUFT), args, st) == cudaSuccess) {
+      k_uf_rounds<<<1, kUFT, 0, st>>>(n, nn, reverse, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots, kill,
+                                      ctl, cap, status); note_launch();
+      return;
+    }
+    cudaGetLastError();  // not launched: the single block does every round
+  }
+  k_uf_rounds<<<1, kUFT, 0, st>>>(n, nn, reverse, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots, kill,
+                                  nullptr, cap, status); note_launch();
+}
+
 void launch_d0(const Dims& d, const NbrDelta& nd, const CritLists& L, int n0, int n1, const uint8_t* vnext8,
                const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status, cudaStream_t st) {
   if (n1 > 0) {
     k_d0_trace<<<(unsigned)((2 * (int64_t)n1 + 255) / 256), 256, 0, st>>>(n1, d.nv, L, vnext8, cidx, nd, S.ends,
                                                                          status); note_launch();
-    k_uf_rounds<<<1, kUFT, 0, st>>>(n1, n0, false, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
-                                    P.d0_min, status); note_launch();
+    uf_rounds(n1, n0, false, S, P.d0_min, status, st);
     k_mark_d0<<<(n1 + 255) / 256, 256, 0, st>>>(n1, P.d0_min, P.d0_killed); note_launch();
     k_d0mask_clear<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, P.d0mask); note_launch();
     k_d0mask_set<<<(n1 + 255) / 256, 256, 0, st>>>(n1, L, P.d0_min, P.d0mask); note_launch();
@@ -293,8 +466,7 @@ void launch_d2(const Dims& d, const NbrDelta& nd, const CritLists& L, int n2, in
   if (n2 > 0) {
     k_d2_trace<<<(unsigned)((2 * (int64_t)n2 + 127) / 128), 128, 0, st>>>(d, n2, n3, L, rank, rec, cidx, nd, S.ends,
                                                                          status); note_launch();
-    k_uf_rounds<<<1, kUFT, 0, st>>>(n2, n3 + 1, true, S.ends, S.parent, S.reserve, S.listA, S.listB, S.roots,
-                                    P.d2_max, status); note_launch();
+    uf_rounds(n2, n3 + 1, true, S, P.d2_max, status, st);
   }
 }
 

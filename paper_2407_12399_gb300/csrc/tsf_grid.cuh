@@ -11,10 +11,12 @@ namespace tsf {
 
 // Grid barrier over the co-resident blocks of a cooperative launch.
 // bar[0] counts arrivals, bar[1] is the generation (both start at 0).  A
-// block that waits more than ~2^24 polls sets kErrSpin and gets false; the
+// block that waits more than `limit` polls (~2^24 by default) sets kErrSpin
+// and gets false; the
 // caller then returns, so every block leaves at its next barrier and the
 // kernel ends with the error bit set instead of hanging.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, uint32_t* status) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, uint32_t* status,
+                                             unsigned limit = 1u << 24) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -29,7 +31,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, ui
     } else {
       unsigned it = 0;
       while (*vgen == gen) {
-        if (++it > (1u << 24)) {
+        if (++it > limit) {
           atomicOr(status, kErrSpin);
           ok = 0;
           break;

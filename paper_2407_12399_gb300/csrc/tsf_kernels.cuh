@@ -21,6 +21,10 @@ inline int status_code(uint32_t s) {
   return 0;
 }
 
+// Test and tuning knobs of the pairing kernels (tsf_debug_set); returns the
+// previous value, -1 for an unknown knob.
+int64_t set_knob(int what, int64_t value);
+
 // Number of kernels this library has launched (process-wide).
 void note_launch();
 long long launches();

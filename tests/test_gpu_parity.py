@@ -324,3 +324,54 @@ def test_auction_with_explicit_targets_matches_oracle():
         ref.iterate(stop_s=0.0)
         assert fld.assignment()[0].tolist() == ref.points()["tgt"].tolist()
         assert np.array_equal(bits(fld.values()), bits(ref.field())), f"field differs after step {j + 1}"
+
+
+def _knobs(**kw):
+    """Sets union-find knobs (tsf_debug_set) and returns a restorer."""
+    import paper_2407_12399_gb300 as tsf
+    ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4}
+    old = {k: tsf.tsf_debug_set(ids[k], v) for k, v in kw.items()}
+    return lambda: [tsf.tsf_debug_set(ids[k], v) for k, v in old.items()]
+
+
+@pytest.mark.parametrize("handoff", [64, 0])
+@pytest.mark.parametrize("name", ["plain_32", "filament_40", "filament_64"])
+def test_union_find_over_the_whole_gpu_matches_the_oracle(name, handoff):
+    """D0/D2 union-find rounds run as one cooperative launch over the GPU
+    (forced here even for small diagrams), then one block finishes the
+    rounds below `handoff` active items: the same diagram as the oracle."""
+    restore = _knobs(grid_min=0, handoff=handoff)
+    try:
+        f = NAMED[name]()
+        got = gpu_rows(gpu_field(f).diagram())
+    finally:
+        restore()
+    assert got == oracle_rows(f, oracle.diagram(f)["pairs"])
+
+
+def test_bounded_waits_run_out_and_the_field_recovers():
+    """A cap on the union-find rounds and a grid barrier that gives up after
+    a poll or two both end the call with TSF_ETIMEOUT (no hang, the GPU stays
+    usable); with the defaults restored the same field, reset to f_0, steps
+    exactly like a fresh field."""
+    import torch
+
+    import paper_2407_12399_gb300 as tsf
+    f0 = NAMED["filament_64"]()
+    fld = gpu_field(f0)
+    for kw in ({"round_cap": 1}, {"grid_min": 0, "handoff": 0, "barrier_limit": 1}):
+        restore = _knobs(**kw)
+        try:
+            r, _ = tsf.tsf_compute_diagram(fld._h, None, 0)
+        finally:
+            restore()
+        assert r == tsf.TSF_ETIMEOUT, (kw, tsf.tsf_status_string(r))
+    dev = torch.from_numpy(f0).cuda()
+    tsf.tsf_set_field(fld._h, dev.data_ptr(), 1)
+    fld.set_threshold(0.05)
+    fld.step(stop_s=0.0)
+    fresh = gpu_field(f0)
+    fresh.set_threshold(0.05)
+    fresh.step(stop_s=0.0)
+    assert np.array_equal(bits(fld.values()), bits(fresh.values()))
+    assert gpu_rows(fld.diagram()) == gpu_rows(fresh.diagram())
