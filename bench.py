@@ -568,6 +568,9 @@ def run_gpu(args):
                    "d1_columns": float(np.mean([s["d1_columns"] for s in stats])),
                    "d1_rounds_max_column": float(np.mean([s["d1_rounds_max"] for s in stats])),
                    "d1_reduce_rounds": float(np.mean([s["d1_reduce_rounds"] for s in stats])),
+                   "d1_reduce_big_rounds": float(np.mean([s["d1_reduce_big_rounds"] for s in stats])),
+                   "d1_reduce_big_cycle_share": float(np.sum([s["d1_reduce_big_cycles"] for s in stats]) /
+                                                      max(np.sum([s["d1_reduce_cycles"] for s in stats]), 1)),
                    "step_ms": [round(x, 3) for x in step_ms]},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

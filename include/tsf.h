@@ -123,6 +123,9 @@ typedef struct {
   int64_t d1_reduce_rounds;   /* rounds of the saddle-saddle column reduction */
   int64_t d1_reduce_merged;   /* entries written by its column additions */
   int64_t d1_reduce_longest;  /* longest column an addition produced */
+  int64_t d1_reduce_big_rounds; /* its rounds with at least 4096 active columns */
+  int64_t d1_reduce_big_cycles; /* SM clock cycles spent in those rounds */
+  int64_t d1_reduce_cycles;     /* SM clock cycles of the whole reduction */
 } tsf_stats;
 
 /* Creates a field from lx*ly*lz values (host or device memory, copied),

@@ -58,7 +58,8 @@ class tsf_stats(ctypes.Structure):
                 ("ms_assign", ctypes.c_double), ("ms_step", ctypes.c_double), ("assign_rounds", ctypes.c_int64),
                 ("assign_phases", ctypes.c_int64), ("assign_checks", ctypes.c_int64),
                 ("d1_reduce_rounds", ctypes.c_int64), ("d1_reduce_merged", ctypes.c_int64),
-                ("d1_reduce_longest", ctypes.c_int64)]
+                ("d1_reduce_longest", ctypes.c_int64), ("d1_reduce_big_rounds", ctypes.c_int64),
+                ("d1_reduce_big_cycles", ctypes.c_int64), ("d1_reduce_cycles", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

@@ -1328,6 +1328,8 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
   __syncthreads();
   int32_t* cur = listA;
   int32_t* nxt = listB;
+  const long long c_start = clock64();
+  long long c_round = c_start;
   for (int round = 0;; ++round) {
     int na = s_na;
     if (na == 0) break;
@@ -1338,6 +1340,7 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
     if (threadIdx.x == 0) {
       s_nb = 0;
       s_nlong = 0;
+      c_round = clock64();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < na; i += kUFT) {
@@ -1419,12 +1422,17 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
     if (threadIdx.x == 0) {
       s_na = s_nb;
       W.stats[5] = (unsigned long long)(round + 1);  // rounds so far
+      if (na >= 4096) {  // rounds with many active columns and their cycles
+        W.stats[8] += 1;
+        W.stats[9] += (unsigned long long)(clock64() - c_round);
+      }
     }
     int32_t* t = cur;
     cur = nxt;
     nxt = t;
     __syncthreads();
   }
+  if (threadIdx.x == 0) W.stats[10] = (unsigned long long)(clock64() - c_start);
   for (int j = threadIdx.x; j < ncols; j += kUFT)
     d1_edge[W.cols[j]] = W.hsize[j] > 0 ? (int)W.pool[W.hoff[j]] : -1;
 }
@@ -1461,7 +1469,7 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   c.d0mask = P.d0mask;
   c.f = f;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
-  cudaMemsetAsync(W.stats, 0, 72, st);
+  cudaMemsetAsync(W.stats, 0, 12 * sizeof(unsigned long long), st);
   cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
   size_t sa = d1_group_smem(kFrontA, kStageA), sb = d1_group_smem(kFrontB, kStageB);
   int dev = 0;

@@ -1693,80 +1693,123 @@ constexpr int kCandTile = 2048;
 
 
 
-// one block: stable partition of the non-still points and the free targets by
-// group (finite dimension 0/1/2, essential = 3); the essential group is
-// matched in order here
-__global__ void __launch_bounds__(1024) k_asg_partition(int np, const Pt* __restrict__ pts, int nt,
-                                                        const Tg* __restrict__ T, const uint8_t* __restrict__ taken,
-                                                        AsgDev A, Pt* __restrict__ pw) {
-  __shared__ int cnt[8], base[8], run[8];
-  if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+// Stable partition of the non-still points and the free targets by group
+// (finite dimension 0/1/2, essential = 3) over many blocks.  Items are the np
+// points, then the nt targets; group 0..3 for a non-still point, 4..7 for a
+// free target.  k_part_count counts per block and group,
+// k_part_scan turns the counts into output offsets (and the group sizes),
+// k_part_scatter writes every item in its block's order, k_part_essential
+// matches the essential class in order.
+constexpr int kPartT = 1024;
+
+__device__ __forceinline__ int part_group(int i, int np, const Pt* __restrict__ pts, int nt, const Tg* __restrict__ T,
+                                          const uint8_t* __restrict__ taken) {
+  if (i < np) return pts[i].still ? -1 : (pts[i].ess ? 3 : pts[i].dim);
+  const int t = i - np;
+  if (t < nt) return taken[t] ? -1 : 4 + (T[t].ess ? 3 : T[t].dim);
+  return -1;
+}
+
+__global__ void __launch_bounds__(kPartT) k_part_count(int np, const Pt* __restrict__ pts, int nt,
+                                                       const Tg* __restrict__ T, const uint8_t* __restrict__ taken,
+                                                       int32_t* __restrict__ bc) {
+  __shared__ int c[8];
+  if (threadIdx.x < 8) c[threadIdx.x] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < np; i += blockDim.x)
-    if (!pts[i].still) atomicAdd(&cnt[pts[i].ess ? 3 : pts[i].dim], 1);
-  for (int t = threadIdx.x; t < nt; t += blockDim.x)
-    if (!taken[t]) atomicAdd(&cnt[4 + (T[t].ess ? 3 : T[t].dim)], 1);
+  const int g = part_group(blockIdx.x * kPartT + threadIdx.x, np, pts, nt, T, taken);
+  const int lane = threadIdx.x & 31;
+  for (int gg = 0; gg < 8; ++gg) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, g == gg);
+    if (lane == 0 && m) atomicAdd(&c[gg], __popc(m));
+  }
   __syncthreads();
+  if (threadIdx.x < 8) bc[blockIdx.x * 8 + threadIdx.x] = c[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kPartT) k_part_scan(int nblk, int32_t* __restrict__ bc, AsgDev A) {
+  __shared__ int sw[kPartT / 32 + 1];
+  __shared__ int tot[8];
+  const int per = (nblk + kPartT - 1) / kPartT;
+  const int b0 = threadIdx.x * per, b1 = min(nblk, b0 + per);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int g = 0; g < 8; ++g) {
+    int v = 0;
+    for (int b = b0; b < b1; ++b) v += bc[b * 8 + g];
+    int inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) sw[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      const int x = sw[lane];
+      int xi = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+        if (lane >= o) xi += t;
+      }
+      sw[lane] = xi - x;
+      if (lane == 31) tot[g] = xi;
+    }
+    __syncthreads();
+    int run = sw[wid] + inc - v;
+    for (int b = b0; b < b1; ++b) {
+      const int c = bc[b * 8 + g];
+      bc[b * 8 + g] = run;  // offset inside the group, added to the group base below
+      run += c;
+    }
+    __syncthreads();
+  }
+  // group bases: points 0..3 in plist, targets 4..7 in tlist
+  __shared__ int base[8];
   if (threadIdx.x == 0) {
     int b = 0, c = 0;
     for (int g = 0; g < 4; ++g) {
       base[g] = b;
-      b += cnt[g];
+      b += tot[g];
       base[4 + g] = c;
-      c += cnt[4 + g];
-      A.counts[g] = cnt[g];
-      A.counts[4 + g] = cnt[4 + g];
+      c += tot[4 + g];
+      A.counts[g] = tot[g];
+      A.counts[4 + g] = tot[4 + g];
     }
     A.counts[8] = 0;
     A.counts[9] = 0;
     A.counts[10] = 0;  // auction rounds, phases, release passes
     A.counts[11] = 0;
     A.counts[12] = 0;
-    for (int g = 0; g < 8; ++g) run[g] = base[g];
   }
   __syncthreads();
-  // order-preserving compaction: chunks of blockDim, warp ballots per group
-  __shared__ int wc[32][8];
-  for (int pass = 0; pass < 2; ++pass) {
-    int n = pass == 0 ? np : nt;
-    for (int b0 = 0; b0 < n; b0 += blockDim.x) {
-      int i = b0 + threadIdx.x;
-      int g = -1;
-      if (i < n) {
-        if (pass == 0) {
-          if (!pts[i].still) g = pts[i].ess ? 3 : pts[i].dim;
-        } else if (!taken[i]) {
-          g = T[i].ess ? 3 : T[i].dim;
-        }
-      }
-      int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-      int myoff = 0;
-      for (int gg = 0; gg < 4; ++gg) {
-        unsigned m = __ballot_sync(0xFFFFFFFFu, g == gg);
-        if (lane == 0) wc[w][gg] = __popc(m);
-        if (g == gg) myoff = __popc(m & ((1u << lane) - 1u));
-      }
-      __syncthreads();
-      if (g >= 0) {
-        int o = run[pass * 4 + g] + myoff;
-        for (int ww = 0; ww < w; ++ww) o += wc[ww][g];
-        if (pass == 0) A.plist[o] = i;
-        else A.tlist[o] = i;
-      }
-      __syncthreads();
-      if (threadIdx.x < 4) {
-        int add = 0;
-        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) add += wc[ww][threadIdx.x];
-        run[pass * 4 + threadIdx.x] += add;
-      }
-      __syncthreads();
-    }
+  for (int i = threadIdx.x; i < nblk * 8; i += kPartT) bc[i] += base[i & 7];
+}
+
+__global__ void __launch_bounds__(kPartT) k_part_scatter(int np, const Pt* __restrict__ pts, int nt,
+                                                         const Tg* __restrict__ T, const uint8_t* __restrict__ taken,
+                                                         const int32_t* __restrict__ bc, AsgDev A) {
+  __shared__ int wc[kPartT / 32][8];
+  const int i = blockIdx.x * kPartT + threadIdx.x;
+  const int g = part_group(i, np, pts, nt, T, taken);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int myoff = 0;
+  for (int gg = 0; gg < 8; ++gg) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, g == gg);
+    if (lane == 0) wc[w][gg] = __popc(m);
+    if (g == gg) myoff = __popc(m & ((1u << lane) - 1u));
   }
-  // essential class: infinite points only match infinite targets, in order
-  if (threadIdx.x == 0) {
-    int n3 = min(cnt[3], cnt[7]);
-    for (int i = 0; i < n3; ++i) pw[A.plist[base[3] + i]].tgt = A.tlist[base[7] + i];
+  __syncthreads();
+  if (g >= 0) {
+    int o = bc[blockIdx.x * 8 + g] + myoff;
+    for (int ww = 0; ww < w; ++ww) o += wc[ww][g];
+    if (g < 4) A.plist[o] = i;
+    else A.tlist[o] = i - np;
   }
+}
+
+__global__ void k_part_essential(AsgDev A, Pt* __restrict__ pw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int b3 = A.counts[0] + A.counts[1] + A.counts[2], b7 = A.counts[4] + A.counts[5] + A.counts[6];
+  const int n3 = min(A.counts[3], A.counts[7]);
+  for (int i = 0; i < n3; ++i) pw[A.plist[b3 + i]].tgt = A.tlist[b7 + i];
 }
 
 __device__ __forceinline__ void group_of_target(const int32_t* counts, int t, int& g, int& local, int& pbase,
@@ -1787,38 +1830,9 @@ __device__ __forceinline__ void group_of_target(const int32_t* counts, int t, in
   }
 }
 
-// one block per free finite target: candidates p with w(p,t) < diag(t),
-// bitonic-sorted by (w, point index) in shared memory, the k cheapest kept
-__global__ void __launch_bounds__(512) k_asg_candidates(const Pt* __restrict__ pts, const Tg* __restrict__ T,
-                                                        AsgDev A) {
-  __shared__ double sw[kCandTile];
-  __shared__ int sp[kCandTile];
-  __shared__ int fill;
-  int g, local, pbase, tbase;
-  group_of_target(A.counts, blockIdx.x, g, local, pbase, tbase);
-  if (g < 0) return;
-  int npg = A.counts[g], k = A.counts[4 + g];
-  const Tg tg = T[A.tlist[tbase + local]];
-  double dt = cost_diag(tg.b, tg.d);
-  if (threadIdx.x == 0) fill = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < npg; i += blockDim.x) {
-    const Pt& p = pts[A.plist[pbase + i]];
-    double w = __dsub_rn(cost_pt(p.b, p.d, tg.b, tg.d), cost_diag(p.b, p.d));
-    if (w < dt) {
-      int s = atomicAdd(&fill, 1);
-      if (s < kCandTile) {
-        sw[s] = w;
-        sp[s] = i;
-      }
-    }
-  }
-  __syncthreads();
-  int n = fill;
-  if (n > kCandTile) {
-    if (threadIdx.x == 0) A.counts[8] = 1;  // too many: the general path takes over
-    return;
-  }
+// Bitonic sort of n (w, point) pairs in shared memory by (w, point),
+// ascending; entries from n up to the next power of two are padding.
+__device__ void cand_sort(double* sw, int* sp, int n) {
   int n2 = 1;
   while (n2 < n) n2 <<= 1;
   for (int i = n + threadIdx.x; i < n2; i += blockDim.x) {
@@ -1845,6 +1859,62 @@ __global__ void __launch_bounds__(512) k_asg_candidates(const Pt* __restrict__ p
       }
       __syncthreads();
     }
+}
+
+// one block per free finite target: its k cheapest candidates p (w(p,t) <
+// diag(t), ordered by (w, point index)).  Points are scanned in chunks of
+// the block size in increasing index; whenever the shared buffer could
+// overflow, it is sorted and cut to the k cheapest, whose largest (w, p)
+// becomes the bar a later point must beat (later points have larger
+// indices, so w below the bar's w).  Groups with more than kCandTile - 512
+// free targets leave the problem to the general path.
+__global__ void __launch_bounds__(512) k_asg_candidates(const Pt* __restrict__ pts, const Tg* __restrict__ T,
+                                                        AsgDev A) {
+  __shared__ double sw[kCandTile];
+  __shared__ int sp[kCandTile];
+  __shared__ int fill;
+  __shared__ double bar;
+  int g, local, pbase, tbase;
+  group_of_target(A.counts, blockIdx.x, g, local, pbase, tbase);
+  if (g < 0) return;
+  int npg = A.counts[g], k = A.counts[4 + g];
+  if (k > kCandTile - 512) {
+    if (threadIdx.x == 0) A.counts[8] = 1;  // the general path takes over
+    return;
+  }
+  const Tg tg = T[A.tlist[tbase + local]];
+  const double dt = cost_diag(tg.b, tg.d);
+  if (threadIdx.x == 0) {
+    fill = 0;
+    bar = dt;
+  }
+  __syncthreads();
+  for (int base = 0; base < npg; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const double b = bar;
+    if (i < npg) {
+      const Pt& p = pts[A.plist[pbase + i]];
+      const double w = __dsub_rn(cost_pt(p.b, p.d, tg.b, tg.d), cost_diag(p.b, p.d));
+      if (w < b) {
+        const int s = atomicAdd(&fill, 1);
+        sw[s] = w;
+        sp[s] = i;
+      }
+    }
+    __syncthreads();
+    const int n = fill;
+    __syncthreads();  // every thread has read fill before the next chunk appends
+    if (n > kCandTile - (int)blockDim.x && base + (int)blockDim.x < npg) {
+      cand_sort(sw, sp, n);
+      if (threadIdx.x == 0) {
+        fill = min(n, k);
+        if (n >= k) bar = sw[k - 1];
+      }
+      __syncthreads();
+    }
+  }
+  const int n = fill;
+  cand_sort(sw, sp, n);
   int keep = min(n, k);
   __shared__ uint32_t off;
   if (threadIdx.x == 0) {
@@ -1949,13 +2019,29 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double p
   // 1) still pairs
   cudaMemsetAsync(B.taken, 0, (size_t)max(nt, 1), st);
   int32_t* ck = merge_sort(np, B.idxA, B.idxB, KeyLess{pts}, st);
-  int32_t* rk = nr > 0 ? merge_sort(nr, B.idxC, B.idxD, KeyLess{ref}, st) : B.idxC;
+  int32_t* rk = B.idxC;
+  if (nr > 0) {
+    // the reference is the previous assignment's points: their key order
+    // was kept (the keys of an array do not change once it is built)
+    if (ref == B.keyord_for && nr == B.keyord_n) rk = B.keyord;
+    else rk = merge_sort(nr, B.idxC, B.idxD, KeyLess{ref}, st);
+  }
   k_still<<<(np + 255) / 256, 256, 0, st>>>(np, pts, ck, nr, ref, rk, B.tmp_pts, B.taken); note_launch();
   cudaMemcpyAsync(pts, B.tmp_pts, sizeof(Pt) * (size_t)np, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(B.keyord, ck, sizeof(int32_t) * (size_t)np, cudaMemcpyDeviceToDevice, st);
+  B.keyord_for = pts;
+  B.keyord_n = np;
   // 2) reduced problems: three launches, no host round-trip; the general
   // group-by-group path runs only when a candidate list overflows its tile
   cudaMemsetAsync(B.A.is_col, 0, sizeof(uint32_t) * (size_t)np, st);
-  k_asg_partition<<<1, 1024, 0, st>>>(np, pts, nt, T, B.taken, B.A, pts); note_launch();
+  {
+    const int nblk = max(1, (np + nt + kPartT - 1) / kPartT);
+    int32_t* bc = reinterpret_cast<int32_t*>(B.u32a);  // 8 counters per block
+    k_part_count<<<nblk, kPartT, 0, st>>>(np, pts, nt, T, B.taken, bc); note_launch();
+    k_part_scan<<<1, kPartT, 0, st>>>(nblk, bc, B.A); note_launch();
+    k_part_scatter<<<nblk, kPartT, 0, st>>>(np, pts, nt, T, B.taken, bc, B.A); note_launch();
+    k_part_essential<<<1, 32, 0, st>>>(B.A, pts); note_launch();
+  }
   k_asg_candidates<<<max(nt, 1), 512, 0, st>>>(pts, T, B.A); note_launch();
   if (prec > 0.0) {
     k_asg_solve<true><<<3, kHT, 0, st>>>(B.A, pts, T, prec, status);

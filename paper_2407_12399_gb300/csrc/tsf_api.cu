@@ -101,7 +101,7 @@ struct tsf_field {
   double loss = 0, loss0 = 0;
   unsigned long long counts[4] = {0, 0, 0, 0};
   int64_t n_updated = 0, n_gradient = 0;
-  unsigned long long d1_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long d1_stats[11] = {};
   int d1_cols = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
@@ -259,6 +259,8 @@ void grow_solver(tsf_field* F, int np, int nt) {
   dev_free(F->T);
   F->T = nt_;
   dev_free(B.tmp_pts);
+  dev_free(B.keyord);
+  B.keyord_for = nullptr;
   dev_free(B.idxA);
   dev_free(B.idxB);
   dev_free(B.idxC);
@@ -277,6 +279,7 @@ void grow_solver(tsf_field* F, int np, int nt) {
   dev_free(B.terms);
   dev_free(B.contrib);
   ck(dev_alloc(&B.tmp_pts, cp));
+  ck(dev_alloc(&B.keyord, cp));
   ck(dev_alloc(&B.idxA, ci));
   ck(dev_alloc(&B.idxB, ci));
   int cicd = std::max(ci, B.cap_cand + 64);
@@ -485,7 +488,7 @@ int compute_diagram(tsf_field* F, bool incremental) {
     F->W.pool_cap = F->pool_cap;
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
-    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 9));
+    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 12));
     if (attempt > 0) ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
     launch_d1_prepare(F->n2, F->W, F->PO, st);
@@ -578,6 +581,9 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
   out->d1_reduce_rounds = (int64_t)F->d1_stats[5];
   out->d1_reduce_merged = (int64_t)F->d1_stats[6];
   out->d1_reduce_longest = (int64_t)F->d1_stats[7];
+  out->d1_reduce_big_rounds = (int64_t)F->d1_stats[8];
+  out->d1_reduce_big_cycles = (int64_t)F->d1_stats[9];
+  out->d1_reduce_cycles = (int64_t)F->d1_stats[10];
   out->ms_diagram = F->ms_diag;
   out->ms_assign = F->ms_assign;
   out->assign_rounds = F->assign_rounds;
@@ -604,6 +610,7 @@ int start_solver(tsf_field* F) {
   // j = 0: the targets play the previous diagram, each assigned to itself
   grow_solver(F, F->np, F->nt);
   targets_as_points(F->nt, F->T, F->prev, F->st);
+  F->B.keyord_for = nullptr;  // prev now holds the targets
   F->nprev = F->nt;
   int r = run_assign(F, F->prev, F->nt);
   if (r) return r;
@@ -772,6 +779,8 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->prev);
   dev_free(F->T);
   dev_free(B.tmp_pts);
+  dev_free(B.keyord);
+  B.keyord_for = nullptr;
   dev_free(B.idxA);
   dev_free(B.idxB);
   dev_free(B.idxC);

@@ -91,6 +91,11 @@ struct SolverBufs {
   int cap_k, cap_cand, cap_cols;
   int64_t cap_kept;
   AsgDev A;
+  // key order (KeyLess) of the points of the last assignment: the next
+  // iteration's reference diagram is that array, unchanged
+  int32_t* keyord;
+  const Pt* keyord_for;
+  int keyord_n;
 };
 
 struct AssignStats {

@@ -56,8 +56,8 @@ def solve_pairs(inputs, stop_s=0.01, max_iters=1000):
         fd = torch.from_numpy(np.ascontiguousarray(f)).cuda()
         fld = Field(fd)
         fld.set_threshold(float(tau))
-        st = fld.simplify(stop_s=stop_s, max_iters=max_iters)
-        g = torch.from_numpy(fld.values()).cuda()
+        g_host, st = fld.simplify(stop_s=stop_s, max_iters=max_iters)
+        g = torch.from_numpy(g_host).cuda()
         fld.close()
         out.append((fd, float(tau), g, int(st["iters"])))
     return out
@@ -122,3 +122,44 @@ def load(path, stream=None):
 
 
 __all__ = ["generate_inputs", "solve_pairs", "train", "solve", "warm_solve", "save", "load", "TRAIN_SHAPE"]
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "unet_warm_start.npy")
+
+
+def train_default(n_pairs=2000, epochs=4, lr=1e-3, seed=4, out=WEIGHTS, log=print):
+    """The warm-start network of this package: n_pairs 64^3 solver pairs from
+    the mixture and filament generators, trained from unet_init(0); writes
+    the fp32 parameters to `out`.  Returns (net, training report)."""
+    import torch
+    t0 = time.perf_counter()
+    inputs = generate_inputs(n_pairs, seed=seed)
+    t1 = time.perf_counter()
+    pairs = solve_pairs(inputs)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    net = UNet(seed=0)
+    hist = train(net, pairs, epochs=epochs, lr=lr, seed=seed, log=log)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    if out:
+        save(net, out)
+    base = float(np.mean([float(((p[0] - p[2]) ** 2).mean()) for p in pairs]))
+    rep = {"pairs": n_pairs, "shape": list(TRAIN_SHAPE), "epochs": epochs, "lr": lr, "seed": seed,
+           "generate_s": t1 - t0, "solve_s": t2 - t1, "train_s": t3 - t2,
+           "solver_iterations_mean": float(np.mean([p[3] for p in pairs])),
+           "epoch_loss": hist, "identity_loss": base}
+    return net, rep
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="train the warm-start network on solver pairs (GPU)")
+    ap.add_argument("--pairs", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", default=WEIGHTS)
+    a = ap.parse_args()
+    _, rep = train_default(a.pairs, a.epochs, a.lr, out=a.out)
+    print(json.dumps(rep))
