@@ -451,6 +451,47 @@ def ablation_128(tsf, stream):
     return out
 
 
+def warm_start_block(tsf, torch, f0, stream):
+    """Learned warm start (not in the paper) on the headline field: the
+    network's g0 = net(f), then the solver from g0 against f's own targets,
+    against the plain solve from f, both timed from host memory to the host
+    result.  Reported: wall times, iterations, final losses, ||g - f||_2 and
+    the non-signal pairs of D(f) each solve cancelled (the same set?)."""
+    from paper_2407_12399_gb300 import warm_start as W
+    if not os.path.exists(W.WEIGHTS):
+        return {"unavailable": f"no trained weights at {os.path.relpath(W.WEIGHTS, ROOT)}"}
+    net = W.load(W.WEIGHTS, stream=stream)
+    fd = torch.from_numpy(np.ascontiguousarray(f0)).cuda()
+    net.forward(fd, TAU)  # buffers for this grid
+    torch.cuda.synchronize()
+    g_plain, st_p, t_plain = W.solve(f0, TAU, stream=stream)
+    g_warm, st_w, t_warm, t_inf = W.warm_solve(net, f0, TAU, stream=stream)
+    theta = np.float32(np.float32(TAU) * np.float32(f0.max() - f0.min()))
+
+    def keys(values, nonsignal_only):
+        fld = tsf.Field(torch.from_numpy(np.ascontiguousarray(values)).cuda(), stream=stream)
+        d = fld.diagram()
+        fld.close()
+        pers = d["death"] - d["birth"]
+        sel = (d["essential"] == 0) & ((pers < theta) if nonsignal_only else (pers > 0))
+        return set(zip(d["dim"][sel].tolist(), d["v_birth"][sel].tolist(), d["v_death"][sel].tolist()))
+
+    nonsig = keys(f0, True)
+    left_p, left_w = keys(g_plain, False) & nonsig, keys(g_warm, False) & nonsig
+    canc_p, canc_w = nonsig - left_p, nonsig - left_w
+    l2 = lambda g: float(np.sqrt(((g.astype(np.float64) - f0.astype(np.float64)) ** 2).sum()))
+    return {"plain": {"wall_s": t_plain, "iterations": int(st_p.iters), "final_loss": float(st_p.loss),
+                      "l2_to_f": l2(g_plain), "non_signal_cancelled": len(canc_p)},
+            "warm": {"wall_s": t_warm, "inference_s": t_inf, "iterations": int(st_w.iters),
+                     "final_loss": float(st_w.loss), "l2_to_f": l2(g_warm), "non_signal_cancelled": len(canc_w)},
+            "non_signal_pairs_of_f": len(nonsig),
+            "cancelled_sets_equal": canc_p == canc_w,
+            "cancelled_symmetric_difference": len(canc_p ^ canc_w),
+            "l2_ratio_warm_over_plain": l2(g_warm) / max(l2(g_plain), 1e-300),
+            "speedup_plain_over_warm": t_plain / t_warm,
+            "loss0": float(st_p.loss0)}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -576,6 +617,8 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "e2e": e2e,
     }
+    if not args.no_warm_start:
+        line["warm_start"] = warm_start_block(tsf, torch, f0, stream)
     if not args.no_secondary:
         line["filament_128"] = secondary_filament_128(tsf, torch, stream, flush, 20)
     if not args.no_ablation:
@@ -604,6 +647,7 @@ def main():
     ap.add_argument("--no-ablation", action="store_true", help="skip the Section 4.2/4.3 on/off solves")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched solve of 48 uneven fields")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 128^3 filament figures")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -269,15 +269,19 @@ const char* tsf_stage_name(int stage);
 /* Number of kernels this library has launched in this process. */
 int64_t tsf_kernel_launches(void);
 
-/* Test and tuning knobs of the D0/D2 union-find (process-wide, not in the
- * paper; results never depend on them, only the schedule and the bounds):
+/* Test and tuning knobs of the pairing (process-wide, not in the paper;
+ * results never depend on them, only the schedule and the bounds):
  *   1: items from which the union-find rounds run over the whole GPU
  *      (default 65536; below, one block runs them);
  *   2: active items below which one block finishes the rounds (default 8192);
  *   3: cap on the union-find rounds (default 0 = none; a cap that is hit
  *      makes the call fail with TSF_ETIMEOUT);
- *   4: polls a block waits at a grid barrier of those rounds before it gives
- *      up (default 2^24; giving up makes the call fail with TSF_ETIMEOUT).
+ *   4: polls a block waits at a grid barrier of the whole-GPU rounds (union-
+ *      find and D1 reduction) before it gives up (default 2^24; giving up
+ *      makes the call fail with TSF_ETIMEOUT);
+ *   5: D1 columns from which the reduction rounds run over the whole GPU
+ *      (default 65536);
+ *   6: active D1 columns below which one block finishes them (default 4096).
  * Returns the previous value, or -1 for an unknown knob.  Set them only
  * while no call of this library is running. */
 int64_t tsf_debug_set(int what, int64_t value);

@@ -35,10 +35,19 @@ std::atomic<int64_t> g_uf_grid_min{1 << 16};
 std::atomic<int64_t> g_uf_handoff{1 << 13};
 std::atomic<int64_t> g_uf_round_cap{0};
 std::atomic<int64_t> g_barrier_limit{1 << 24};
+// ... and of the D1 reduction: columns from which its rounds start over the
+// whole GPU, active columns below which one block finishes them
+std::atomic<int64_t> g_d1_grid_min{1 << 16};
+std::atomic<int64_t> g_d1_handoff{1 << 12};
 
 int64_t set_knob(int what, int64_t value) {
-  std::atomic<int64_t>* k = what == 1 ? &g_uf_grid_min : what == 2 ? &g_uf_handoff : what == 3 ? &g_uf_round_cap
-                            : what == 4 ? &g_barrier_limit : nullptr;
+  std::atomic<int64_t>* k = what == 1   ? &g_uf_grid_min
+                            : what == 2 ? &g_uf_handoff
+                            : what == 3 ? &g_uf_round_cap
+                            : what == 4 ? &g_barrier_limit
+                            : what == 5 ? &g_d1_grid_min
+                            : what == 6 ? &g_d1_handoff
+                                        : nullptr;
   if (!k) return -1;
   return k->exchange(value);
 }
@@ -1254,12 +1263,21 @@ static size_t d1_group_smem(int fcap, int scap) { return (2 * (size_t)fcap + sca
 // displaces is listed for the next round; columns not listed own their lows
 // and stay as they are, so a round costs as much as its list.
 // Number of entries of a strictly decreasing column greater than v.
+// Loads of column entries: from L2 when other SMs may have written them in
+// this kernel (CG), plain otherwise.
+template <bool CG>
+__device__ __forceinline__ unsigned long long d1_ld(const unsigned long long* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <bool CG = false>
 __device__ __forceinline__ uint32_t d1_count_greater(unsigned long long v, const unsigned long long* arr,
                                                     uint32_t len) {
   uint32_t lo = 0, hi = len;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (arr[mid] > v) lo = mid + 1;
+    if (d1_ld<CG>(arr + mid) > v) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -1270,6 +1288,7 @@ __device__ __forceinline__ uint32_t d1_count_greater(unsigned long long v, const
 // b lacks lands at x + (entries of b above it) - 2 (entries of a above it
 // that b also has): everything above it, minus the cancelled pairs.  Same
 // for b.  Positions outside [0, n + nb) set kErrInconsistent.
+template <bool CG = false>
 __device__ uint32_t d1_warp_add(const unsigned long long* a, uint32_t n, const unsigned long long* b, uint32_t nb,
                                 unsigned long long* d, uint32_t* status) {
   const int lane = threadIdx.x & 31;
@@ -1286,9 +1305,9 @@ __device__ uint32_t d1_warp_add(const unsigned long long* a, uint32_t n, const u
       uint32_t c = 0;
       unsigned long long v = 0;
       if (x < np_) {
-        v = p[x];
-        c = d1_count_greater(v, q, nq);
-        found = c < nq && q[c] == v;
+        v = d1_ld<CG>(p + x);
+        c = d1_count_greater<CG>(v, q, nq);
+        found = c < nq && d1_ld<CG>(q + c) == v;
       }
       const unsigned bal = __ballot_sync(0xFFFFFFFFu, found);
       if (x < np_ && !found) {
@@ -1310,7 +1329,10 @@ __device__ __forceinline__ void d1_list_push(int32_t* next, int* n_next, int32_t
   if (atomicExch(&mark[j], round) != round) next[atomicAdd(n_next, 1)] = j;
 }
 
-__global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d1_edge, uint32_t* status) {
+// `ctl` (may be null): resume after k_d1_reduce_grid from its lists, owners
+// and marks.
+__global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d1_edge, const D1Ctl* ctl,
+                                                    uint32_t* status) {
   const int ncols = W.flags[1];
   // free per-column scratch by now: two lists and a "listed in round" mark
   int32_t* listA = W.lowc;
@@ -1318,19 +1340,32 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
   int32_t* mark = W.redo;
   __shared__ int s_na, s_nb, s_nlong;
   __shared__ int32_t s_long[kLongCap];
-  for (int k = threadIdx.x; k < n1; k += kUFT) W.owner[k] = 0x7FFFFFFF;
-  if (threadIdx.x == 0) s_na = 0;
-  __syncthreads();
-  for (int j = threadIdx.x; j < ncols; j += kUFT) {
-    mark[j] = -1;
-    if (W.hsize[j] > 0) listA[atomicAdd(&s_na, 1)] = j;
-  }
-  __syncthreads();
   int32_t* cur = listA;
   int32_t* nxt = listB;
+  int round0 = 0;
+  if (ctl) {
+    // the whole-GPU rounds gave up (a barrier, the round bound or the pool):
+    // their lists may be partly written, so nothing resumes from them
+    if (*reinterpret_cast<const volatile uint32_t*>(status) & (kErrSpin | kErrRounds | kErrPool)) return;
+    if (ctl->which) {
+      cur = listB;
+      nxt = listA;
+    }
+    if (threadIdx.x == 0) s_na = ctl->n[ctl->which];
+    round0 = ctl->rounds;
+  } else {
+    for (int k = threadIdx.x; k < n1; k += kUFT) W.owner[k] = 0x7FFFFFFF;
+    if (threadIdx.x == 0) s_na = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < ncols; j += kUFT) {
+      mark[j] = -1;
+      if (W.hsize[j] > 0) listA[atomicAdd(&s_na, 1)] = j;
+    }
+  }
+  __syncthreads();
   const long long c_start = clock64();
   long long c_round = c_start;
-  for (int round = 0;; ++round) {
+  for (int round = round0;; ++round) {
     int na = s_na;
     if (na == 0) break;
     if (round > ncols + 2) {
@@ -1432,7 +1467,7 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
     nxt = t;
     __syncthreads();
   }
-  if (threadIdx.x == 0) W.stats[10] = (unsigned long long)(clock64() - c_start);
+  if (threadIdx.x == 0) W.stats[10] += (unsigned long long)(clock64() - c_start);
   for (int j = threadIdx.x; j < ncols; j += kUFT)
     d1_edge[W.cols[j]] = W.hsize[j] > 0 ? (int)W.pool[W.hoff[j]] : -1;
 }
@@ -1486,9 +1521,153 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   k_d1_morse<<<(n2 + 63) / 64, 64, 0, st>>>(c, W, status); note_launch();
 }
 
-void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st) {
+// The same rounds over the whole GPU (cooperative launch, grid barriers
+// between the phases) while at least `handoff` columns are active; then
+// k_d1_reduce resumes from ctl on one block.  Any schedule of these rounds
+// gives a left-to-right reduction with the same pivots; list order, pool
+// offsets and which SM adds what do not change the pairs.  Every read of
+// state that another SM may have written in this kernel goes to L2.
+__global__ void __launch_bounds__(kUFT) k_d1_reduce_grid(D1Work W, int n1, D1Ctl* ctl, int handoff, unsigned limit,
+                                                         uint32_t* status) {
+  const int ncols = W.flags[1];
+  int32_t* listA = W.lowc;
+  int32_t* listB = reinterpret_cast<int32_t*>(W.hcap);
+  int32_t* mark = W.redo;
+  __shared__ int s_nlong;
+  __shared__ int32_t s_long[kLongCap];
+  const unsigned nb = gridDim.x;
+  const int gt = blockIdx.x * kUFT + threadIdx.x, gn = nb * kUFT;
+  const long long c_start = clock64();
+  for (int k = gt; k < n1; k += gn) W.owner[k] = 0x7FFFFFFF;
+  for (int j = gt; j < ncols; j += gn) {
+    mark[j] = -1;
+    if (W.hsize[j] > 0) listA[atomicAdd(&ctl->n[0], 1)] = j;
+  }
+  if (!grid_barrier(ctl->bar, nb, status, limit)) return;
+  int which = 0;
+  for (int round = 0;; ++round) {
+    const int na = *reinterpret_cast<volatile int*>(&ctl->n[which]);
+    if (na == 0 || na < handoff) break;
+    if (round > ncols + 2) {
+      if (gt == 0) atomicOr(status, kErrRounds);
+      break;
+    }
+    const long long c_round = clock64();
+    const int32_t* cur = which ? listB : listA;
+    int32_t* nxt = which ? listA : listB;
+    int* n_next = &ctl->n[which ^ 1];
+    if (threadIdx.x == 0) s_nlong = 0;
+    for (int i = gt; i < na; i += gn) {
+      const int j = __ldcg(&cur[i]);
+      const int old = atomicMin(&W.owner[(int)__ldcg(&W.pool[__ldcg(&W.hoff[j])])], j);
+      if (old > j && old != 0x7FFFFFFF) d1_list_push(nxt, n_next, mark, old, round);  // displaced owner
+    }
+    if (!grid_barrier(ctl->bar, nb, status, limit)) return;
+    for (int i = gt; i < na; i += gn) {
+      const int j = __ldcg(&cur[i]);
+      const uint32_t n = __ldcg(&W.hsize[j]);
+      const unsigned long long* a = W.pool + __ldcg(&W.hoff[j]);
+      const int o = __ldcg(&W.owner[(int)__ldcg(a)]);
+      if (o == j) continue;
+      const uint32_t no = __ldcg(&W.hsize[o]);
+      if (n + no >= kLongAdd) {  // long: one warp of this block adds it below
+        const int q = atomicAdd(&s_nlong, 1);
+        if (q < kLongCap) {
+          s_long[q] = j;
+          continue;
+        }
+      }
+      const unsigned long long* b = W.pool + __ldcg(&W.hoff[o]);
+      const uint32_t cap = n + no;
+      const uint32_t off = atomicAdd(W.pool_head, cap);
+      if ((unsigned long long)off + cap > W.pool_cap) {
+        atomicOr(status, kErrPool);
+        continue;
+      }
+      unsigned long long* d = W.pool + off;
+      uint32_t x = 0, y = 0, m = 0;
+      unsigned long long ax = x < n ? __ldcg(a) : 0, by = y < no ? __ldcg(b) : 0;
+      while (x < n && y < no) {  // both decreasing: symmetric difference
+        if (ax > by) {
+          d[m++] = ax;
+          ax = ++x < n ? __ldcg(a + x) : 0;
+        } else if (by > ax) {
+          d[m++] = by;
+          by = ++y < no ? __ldcg(b + y) : 0;
+        } else {
+          ax = ++x < n ? __ldcg(a + x) : 0;
+          by = ++y < no ? __ldcg(b + y) : 0;
+        }
+      }
+      for (; x < n; ++x) d[m++] = __ldcg(a + x);
+      for (; y < no; ++y) d[m++] = __ldcg(b + y);
+      W.hoff[j] = off;
+      W.hsize[j] = m;
+      atomicAdd(&W.stats[6], (unsigned long long)m);
+      atomicMax(&W.stats[7], (unsigned long long)m);
+      if (m == 0) atomicOr(status, kErrEmptyColumn);
+      else d1_list_push(nxt, n_next, mark, j, round);
+    }
+    __syncthreads();
+    {  // this block's long additions, one warp each
+      const int nlong = min(s_nlong, kLongCap), lane = threadIdx.x & 31;
+      for (int q = threadIdx.x >> 5; q < nlong; q += kUFT / 32) {
+        const int j = s_long[q];
+        const uint32_t n = __ldcg(&W.hsize[j]);
+        const unsigned long long* a = W.pool + __ldcg(&W.hoff[j]);
+        const int o = __ldcg(&W.owner[(int)__ldcg(a)]);
+        const uint32_t no = __ldcg(&W.hsize[o]);
+        const unsigned long long* b = W.pool + __ldcg(&W.hoff[o]);
+        const uint32_t cap = n + no;
+        uint32_t off = 0;
+        if (lane == 0) off = atomicAdd(W.pool_head, cap);
+        off = __shfl_sync(0xFFFFFFFFu, off, 0);
+        if ((unsigned long long)off + cap > W.pool_cap) {
+          if (lane == 0) atomicOr(status, kErrPool);
+          continue;
+        }
+        const uint32_t m = d1_warp_add<true>(a, n, b, no, W.pool + off, status);
+        if (lane == 0) {
+          W.hoff[j] = off;
+          W.hsize[j] = m;
+          atomicAdd(&W.stats[6], (unsigned long long)m);
+          atomicMax(&W.stats[7], (unsigned long long)m);
+          if (m == 0) atomicOr(status, kErrEmptyColumn);
+          else d1_list_push(nxt, n_next, mark, j, round);
+        }
+      }
+    }
+    which ^= 1;
+    if (gt == 0) {
+      ctl->n[which ^ 1] = 0;  // the list the next round fills
+      ctl->which = which;
+      ctl->rounds = round + 1;
+      W.stats[5] = (unsigned long long)(round + 1);
+      W.stats[8] += 1;
+      W.stats[9] += (unsigned long long)(clock64() - c_round);
+    }
+    if (!grid_barrier(ctl->bar, nb, status, limit)) return;
+  }
+  if (gt == 0) W.stats[10] += (unsigned long long)(clock64() - c_start);
+}
+
+static_assert(sizeof(UfCtl) <= 64 && sizeof(D1Ctl) <= 64, "control blocks share PairScratch::counter (64 bytes)");
+
+void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, D1Ctl* ctl, cudaStream_t st) {
   if (n2 == 0) return;
-  k_d1_reduce<<<1, kUFT, 0, st>>>(W, n1, P.d1_edge, status); note_launch();
+  const int nb = n2 >= g_d1_grid_min.load() ? cooperative_blocks((const void*)k_d1_reduce_grid, kUFT) : 0;
+  if (nb > 0) {
+    cudaMemsetAsync(ctl, 0, sizeof(D1Ctl), st);
+    int handoff = (int)std::min<int64_t>(g_d1_handoff.load(), 1 << 30);
+    unsigned limit = (unsigned)std::min<int64_t>(std::max<int64_t>(g_barrier_limit.load(), 1), 1u << 30);
+    void* args[] = {&W, &n1, &ctl, &handoff, &limit, &status};
+    if (cooperative_launch((const void*)k_d1_reduce_grid, dim3(nb), dim3(kUFT), args, st) == cudaSuccess) {
+      k_d1_reduce<<<1, kUFT, 0, st>>>(W, n1, P.d1_edge, ctl, status); note_launch();
+      return;
+    }
+    cudaGetLastError();  // not launched: the single block does every round
+  }
+  k_d1_reduce<<<1, kUFT, 0, st>>>(W, n1, P.d1_edge, nullptr, status); note_launch();
 }
 
 }  // namespace tsf

@@ -498,7 +498,7 @@ int compute_diagram(tsf_field* F, bool incremental) {
                     F->PO, F->status, st);
     stage_end(F, kD1Morse);
     stage_begin(F, kD1Reduce);
-    launch_d1_reduce(F->n1, F->n2, F->W, F->PO, F->status, st);
+    launch_d1_reduce(F->n1, F->n2, F->W, F->PO, F->status, reinterpret_cast<D1Ctl*>(F->PS.counter), st);
     stage_end(F, kD1Reduce);
     int32_t ncols = 0;
     for (auto& x : F->d1_stats) x = 0;

@@ -106,6 +106,15 @@ void launch_d2(const Dims& d, const NbrDelta& nd, const CritLists& L, int n2, in
                const Rec* rec, const uint32_t* cidx, PairScratch& S, PairOut& P, uint32_t* status,
                cudaStream_t st);
 
+// Control block of the whole-GPU D1 reduction rounds.
+struct D1Ctl {
+  unsigned bar[2];  // grid barrier: arrivals, generation
+  int n[2];         // lengths of the two column lists
+  int which;        // list holding the active columns
+  int rounds;       // rounds done
+  int pad[10];
+};
+
 struct D1Work {
   int32_t* cols;          // candidate triangle index per column
   unsigned long long* low;  // current low per column (0 = to be recomputed)
@@ -131,6 +140,6 @@ void launch_d1_prepare(int n2, D1Work& W, PairOut& P, cudaStream_t st);
 void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, const uint32_t* rank,
                      const uint32_t* order, const float* f, const Rec* rec, const D1Tab* tab, const uint32_t* c1base,
                      D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st);
-void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, cudaStream_t st);
+void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, D1Ctl* ctl, cudaStream_t st);
 
 }  // namespace tsf

@@ -329,18 +329,19 @@ def test_auction_with_explicit_targets_matches_oracle():
 def _knobs(**kw):
     """Sets union-find knobs (tsf_debug_set) and returns a restorer."""
     import paper_2407_12399_gb300 as tsf
-    ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4}
+    ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4, "d1_grid_min": 5, "d1_handoff": 6}
     old = {k: tsf.tsf_debug_set(ids[k], v) for k, v in kw.items()}
     return lambda: [tsf.tsf_debug_set(ids[k], v) for k, v in old.items()]
 
 
 @pytest.mark.parametrize("handoff", [64, 0])
-@pytest.mark.parametrize("name", ["plain_32", "filament_40", "filament_64"])
-def test_union_find_over_the_whole_gpu_matches_the_oracle(name, handoff):
-    """D0/D2 union-find rounds run as one cooperative launch over the GPU
-    (forced here even for small diagrams), then one block finishes the
-    rounds below `handoff` active items: the same diagram as the oracle."""
-    restore = _knobs(grid_min=0, handoff=handoff)
+@pytest.mark.parametrize("name", ["plain_32", "filament_40", "filament_64", "ring_21"])
+def test_pairing_rounds_over_the_whole_gpu_match_the_oracle(name, handoff):
+    """The D0/D2 union-find rounds and the D1 reduction rounds run as
+    cooperative launches over the GPU (forced here even for small diagrams),
+    then one block finishes the rounds below `handoff` active items: the
+    same diagram as the oracle."""
+    restore = _knobs(grid_min=0, handoff=handoff, d1_grid_min=0, d1_handoff=handoff)
     try:
         f = NAMED[name]()
         got = gpu_rows(gpu_field(f).diagram())
@@ -359,7 +360,8 @@ def test_bounded_waits_run_out_and_the_field_recovers():
     import paper_2407_12399_gb300 as tsf
     f0 = NAMED["filament_64"]()
     fld = gpu_field(f0)
-    for kw in ({"round_cap": 1}, {"grid_min": 0, "handoff": 0, "barrier_limit": 1}):
+    for kw in ({"round_cap": 1}, {"grid_min": 0, "handoff": 0, "barrier_limit": 1},
+               {"d1_grid_min": 0, "d1_handoff": 0, "barrier_limit": 1}):
         restore = _knobs(**kw)
         try:
             r, _ = tsf.tsf_compute_diagram(fld._h, None, 0)
