@@ -119,7 +119,7 @@ def make_field():
     temporary directory so a second run on the same machine reuses it."""
     from paper_2407_12399_gb300 import synthetic
     import tempfile
-    path = os.path.join(tempfile.gettempdir(), f"tsf_bench_{WORKLOAD}_seed{SEED}.npy")
+    path = os.path.join(tempfile.gettempdir(), f"tsf_bench_{WORKLOAD}_{SHAPE[0]}_seed{SEED}.npy")
     if os.path.exists(path):
         try:
             f = np.load(path)
@@ -648,7 +648,14 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched solve of 48 uneven fields")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 128^3 filament figures")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--grid", type=int, default=256,
+                    help="side of the evaluation field (256 = the headline; smaller grids for profiling)")
     args = ap.parse_args()
+    if args.grid != 256:
+        global SHAPE, WORKLOAD, METRIC
+        SHAPE = (args.grid,) * 3
+        WORKLOAD = f"warm_start_{args.grid}"
+        METRIC = METRIC.replace("256^3", f"{args.grid}^3")
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

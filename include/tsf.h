@@ -230,9 +230,10 @@ int tsf_set_field(tsf_field* field, const float* values, int values_on_device);
 /* Warm start (not in the paper): replaces the current values by a start
  * field g0 (lx*ly*lz floats, host or device) and keeps the target diagram
  * and loss_0 of the field the targets were set from.  The diagram of g0 is
- * computed (Sections 2.2, 4.2), every point is matched by the exact solver
- * (no still pairs: Section 4.3 has no previous diagram to reuse), and the
- * solver restarts at iteration 0 from g0, so tsf_simplify's stop rule
+ * computed (Sections 2.2, 4.2) and matched as after a solver step: points
+ * with the (dim, v_b, v_d) of a point of the current diagram keep its
+ * assignment, the rest go to the exact reduced assignment (Section 4.3);
+ * the solver restarts at iteration 0 from g0, so tsf_simplify's stop rule
  * L <= stop_s * loss_0 refers to the original field's loss.  Errors:
  * TSF_EINVAL, TSF_ENOTARGET before a target was set, TSF_ENAN. */
 int tsf_set_start_field(tsf_field* field, const float* values, int values_on_device);

@@ -72,6 +72,8 @@ def lib():
         L.or_solver_loss_grad.restype = ctypes.c_int
         L.or_solver_loss_grad.argtypes = [P, P, P, P]
         L.or_solver_field.argtypes = [P, P]
+        L.or_solver_set_start.restype = ctypes.c_int
+        L.or_solver_set_start.argtypes = [P, P]
         L.or_solver_num_points.restype = I64
         L.or_solver_num_points.argtypes = [P]
         L.or_solver_num_targets.restype = I64
@@ -250,6 +252,15 @@ class Solver:
         if r < 0:
             raise ValueError(f"oracle loss failed ({r})")
         return float(loss[0]), grad
+
+    def set_start(self, values):
+        """Continue from the start field `values` (warm start): same targets
+        and loss_0, its diagram matched as after a step, j back to 0."""
+        v = np.ascontiguousarray(values, np.float32)
+        assert v.shape == self.shape
+        r = lib().or_solver_set_start(self._h, _ptr(v))
+        if r < 0:
+            raise ValueError(f"oracle set_start failed ({r})")
 
     def run(self, alpha_b=0.5, alpha_d=0.5, stop_s=0.01, cancel_eps=0.0, max_iters=1000):
         while not self.done(stop_s, cancel_eps, max_iters):

@@ -1336,6 +1336,36 @@ int or_solver_iterate(or_solver* s, float alpha_b, float alpha_d, float stop_s, 
   return or_solver_done(s, stop_s, cancel_eps, max_iters);
 }
 
+/*
+ * Warm start (not in the paper): the values are replaced by a start field
+ * g0 and the solver continues from it with the same target diagram and
+ * loss_0.  Reading: g0 takes the place of the next iterate, so its diagram
+ * is matched as after a step (Section 4.3): points with the (dim,
+ * essential, v_b, v_d) of a point of the current diagram keep that point's
+ * assignment, the others go to the exact reduced assignment; the iteration
+ * count restarts at 0.
+ */
+int or_solver_set_start(or_solver* s, const float* values) {
+  for (int64_t v = 0; v < s->g.nv; ++v) {
+    if (!isfinite(values[v])) return -2;
+  }
+  memcpy(s->f, values, sizeof(float) * (size_t)s->g.nv);
+  opoint_t* prev = s->P;
+  int64_t nprev = s->np;
+  int st = compute_points(&s->g, s->f, &s->P, &s->np);
+  if (st) {
+    s->P = prev;
+    s->np = nprev;
+    return st;
+  }
+  int ast = assign_points(s, prev, nprev, 0, 0.0);
+  free(prev);
+  if (ast) return -4;
+  s->j = 0;
+  eval_loss(s);
+  return 0;
+}
+
 void or_solver_set_fast_assignment(or_solver* s, int on) { s->fast_assign = on ? 1 : 0; }
 
 void or_solver_set_assignment_precision(or_solver* s, double prec) { s->assign_prec = prec > 0.0 ? prec : 0.0; }

@@ -80,6 +80,10 @@ void or_solver_set_assignment_precision(or_solver* s, double prec);
  * essential class contributes at both its vertices).  The solver's state
  * becomes this field.  Returns 0, or a negative status. */
 int or_solver_loss_grad(or_solver* s, const float* values, double* loss, double* grad);
+/* Warm start: continue from the start field `values` with the same targets
+ * and loss_0; its diagram is matched as after a step (Section 4.3), the
+ * iteration count restarts at 0.  Returns 0, or negative on error. */
+int or_solver_set_start(or_solver* s, const float* values);
 void or_solver_field(const or_solver* s, float* out);
 int64_t or_solver_num_points(const or_solver* s);
 int64_t or_solver_num_targets(const or_solver* s);

@@ -1093,11 +1093,13 @@ int tsf_set_start_field(tsf_field* F, const float* values, int values_on_device)
     ck(cudaStreamSynchronize(F->st));
     F->n_updated = (int64_t)nchanged;
     F->upd_valid = true;
-    std::swap(F->pts, F->prev);  // the previous diagram is not consulted
+    // the current diagram (with its assignment) is the still-pair reference
+    // of the start field's diagram, as after a solver step (Section 4.3)
+    std::swap(F->pts, F->prev);
     F->nprev = F->np;
     int r = compute_diagram(F, true);
     if (r) return r;
-    r = run_assign(F, F->prev, 0);
+    r = run_assign(F, F->prev, F->nprev);
     if (r) return r;
     F->iter = 0;
     eval(F, 0.0f);

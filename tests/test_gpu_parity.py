@@ -377,3 +377,33 @@ def test_bounded_waits_run_out_and_the_field_recovers():
     fresh.step(stop_s=0.0)
     assert np.array_equal(bits(fld.values()), bits(fresh.values()))
     assert gpu_rows(fld.diagram()) == gpu_rows(fresh.diagram())
+
+
+@pytest.mark.parametrize("name,tau", [("plain_32", 0.1), ("filament_40", 0.05)])
+def test_warm_start_restart_matches_the_oracle(name, tau):
+    """tsf_set_start_field: continue from a start field with f_0's targets and
+    loss_0, the start field's diagram matched as after a step; then three
+    solver steps, all bit-exact against the oracle."""
+    import torch
+
+    import paper_2407_12399_gb300 as tsf
+    f0 = NAMED[name]()
+    rng = np.random.default_rng(3)
+    g0 = (f0 + rng.uniform(-0.01, 0.01, f0.shape)).astype(np.float32)
+    fld = gpu_field(f0)
+    fld.set_threshold(tau)
+    tsf.tsf_set_start_field(fld._h, torch.from_numpy(g0).cuda().data_ptr(), 1)
+    ref = oracle.Solver(f0, tau=tau)
+    ref.set_start(g0)
+    for j in range(4):
+        tgt, still = fld.assignment()
+        P = ref.points()
+        assert tgt.tolist() == P["tgt"].tolist(), f"assignment differs at j={j}"
+        assert still.tolist() == P["still"].tolist()
+        if j == 3:
+            break
+        st = fld.step(stop_s=0.0)
+        ref.iterate(stop_s=0.0)
+        assert np.array_equal(bits(fld.values()), bits(ref.field())), f"field differs after step {j + 1}"
+        assert st["loss"] == pytest.approx(ref.stats()["loss"], rel=1e-12)
+        assert st["loss0"] == pytest.approx(ref.stats()["loss0"], rel=1e-12)

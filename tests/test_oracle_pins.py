@@ -633,3 +633,32 @@ def test_duplicate_keys_inherit_in_birth_cell_order():
         k1 = _keys(P1)
         n_uneven += sum(1 for k in dups if 0 < k1.count(k) < k0.count(k))
     assert n_dup >= 2 and n_uneven >= 2
+
+
+def test_start_field_equal_to_the_field_changes_nothing():
+    """Warm start with g0 = f_0: every point of the new diagram is still, so
+    the assignment, the loss and the stop state are those of iteration 0."""
+    f = S.random_field((7, 6, 5), seed=13)
+    s = oracle.Solver(f, tau=0.3)
+    P0, st0 = s.points(), s.stats()
+    s.set_start(f)
+    P1, st1 = s.points(), s.stats()
+    assert np.all(P1["still"] == 1)
+    assert P1["tgt"].tolist() == P0["tgt"].tolist()
+    assert st1["loss"] == st0["loss0"] and st1["loss0"] == st0["loss0"] and st1["iter"] == 0
+
+
+def test_start_field_from_a_step_matches_the_step():
+    """Warm start with g0 = the field one step produces: the same diagram and
+    assignment as that step (both match the new diagram against the previous
+    one), with the iteration count back at 0."""
+    f = S.random_field((7, 6, 5), seed=14)
+    a = oracle.Solver(f, tau=0.3)
+    a.iterate(stop_s=0.0)
+    g1 = a.field()
+    b = oracle.Solver(f, tau=0.3)
+    b.set_start(g1)
+    Pa, Pb = a.points(), b.points()
+    for k in ("dim", "vb", "vd", "cb", "cd", "tgt", "still"):
+        assert Pa[k].tolist() == Pb[k].tolist(), k
+    assert b.stats()["loss"] == a.stats()["loss"] and b.stats()["iter"] == 0
