@@ -282,7 +282,10 @@ int64_t tsf_kernel_launches(void);
  *      makes the call fail with TSF_ETIMEOUT);
  *   5: D1 columns from which the reduction rounds run over the whole GPU
  *      (default 65536);
- *   6: active D1 columns below which one block finishes them (default 4096).
+ *   6: active D1 columns below which one block finishes them (default 4096);
+ *   7: shared-memory buffers per column of the D1 Morse boundaries' first
+ *      phase: 0 the default (64 + 128 entries), 1 twice, 2 four times that
+ *      (columns that outgrow them continue in the second phase).
  * Returns the previous value, or -1 for an unknown knob.  Set them only
  * while no call of this library is running. */
 int64_t tsf_debug_set(int what, int64_t value);

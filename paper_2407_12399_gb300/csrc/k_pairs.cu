@@ -39,6 +39,9 @@ std::atomic<int64_t> g_barrier_limit{1 << 24};
 // whole GPU, active columns below which one block finishes them
 std::atomic<int64_t> g_d1_grid_min{1 << 16};
 std::atomic<int64_t> g_d1_handoff{1 << 12};
+// shared-memory buffers of the D1 Morse boundaries' phase A: 0 the default
+// (64 frontier + 128 stage entries per column), 1 twice, 2 four times that
+std::atomic<int64_t> g_d1_phase_a{0};
 
 int64_t set_knob(int what, int64_t value) {
   std::atomic<int64_t>* k = what == 1   ? &g_uf_grid_min
@@ -47,6 +50,7 @@ int64_t set_knob(int what, int64_t value) {
                             : what == 4 ? &g_barrier_limit
                             : what == 5 ? &g_d1_grid_min
                             : what == 6 ? &g_d1_handoff
+                            : what == 7 ? &g_d1_phase_a
                                         : nullptr;
   if (!k) return -1;
   return k->exchange(value);
@@ -1246,10 +1250,12 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 12 : 4) k_d1_morse_group(D1Ctx 
   }
 }
 
-// Phase A keeps its shared memory small so that every column's warp is
-// resident at once; a visit appends 1.1 updates on average, 14 at most.
+// Phase A keeps its shared memory small (4 KB per column's warp) so that the
+// register file, not shared memory, limits the warps per SM (24 of 64): the
+// rounds are latency-bound.  A visit appends 1.1 updates on average, 14 at
+// most; a column that outgrows the buffers continues in phase B.
 constexpr int kThreadsB = 128;
-constexpr int kFrontA = 256, kStageA = 512;
+constexpr int kFrontA = 64, kStageA = 128;
 constexpr int kFrontB = 1024, kStageB = 1024;
 static_assert(kFrontA + kStageA <= kStageB, "a phase A handoff fits phase B's stage");
 
@@ -1322,6 +1328,8 @@ __device__ uint32_t d1_warp_add(const unsigned long long* a, uint32_t n, const u
   return cap - 2u * common;
 }
 
+constexpr int kChainMax = 64;      // active columns up to which a round chains additions (one warp each)
+constexpr int kChainSteps = 1 << 16;  // chained additions of one column in one round, at most
 constexpr uint32_t kLongAdd = 64;  // column additions at least this long run on a warp
 constexpr int kLongCap = 1024;     // ... at most this many per round (the rest on one thread)
 
@@ -1384,6 +1392,59 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
       if (old > j && old != 0x7FFFFFFF) d1_list_push(nxt, &s_nb, mark, old, round);  // displaced owner
     }
     __syncthreads();
+    if (na <= kChainMax) {
+      // short list: one warp per column, chained additions.  During this
+      // phase every owner owns its low and does not change (a column that
+      // does not own its low holds no owner entry), so after adding its
+      // owner a column may go on adding the owner of its new low while that
+      // owner is an earlier column: each step is still a left-to-right
+      // addition.  It stops when it owns its low, or the low's owner is
+      // later or absent (it claims the low next round).
+      const int lane = threadIdx.x & 31;
+      for (int q = threadIdx.x >> 5; q < na; q += kUFT / 32) {
+        const int j = cur[q];
+        for (int step = 0;; ++step) {
+          const uint32_t n = W.hsize[j];
+          const unsigned long long* a = W.pool + W.hoff[j];
+          const int o = W.owner[(int)a[0]];
+          if (o == j) break;
+          if (o == 0x7FFFFFFF || o > j || step >= kChainSteps) {
+            if (lane == 0) d1_list_push(nxt, &s_nb, mark, j, round);
+            break;
+          }
+          const uint32_t no = W.hsize[o];
+          const unsigned long long* b = W.pool + W.hoff[o];
+          const uint32_t cap = n + no;
+          uint32_t off = 0;
+          if (lane == 0) off = atomicAdd(W.pool_head, cap);
+          off = __shfl_sync(0xFFFFFFFFu, off, 0);
+          if ((unsigned long long)off + cap > W.pool_cap) {
+            if (lane == 0) atomicOr(status, kErrPool);
+            break;
+          }
+          const uint32_t m = d1_warp_add(a, n, b, no, W.pool + off, status);
+          if (lane == 0) {
+            W.hoff[j] = off;
+            W.hsize[j] = m;
+            atomicAdd(&W.stats[6], (unsigned long long)m);
+            atomicMax(&W.stats[7], (unsigned long long)m);
+            if (m == 0) atomicOr(status, kErrEmptyColumn);
+          }
+          __syncwarp();
+          if (m == 0) break;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_na = s_nb;
+        W.stats[5] = (unsigned long long)(round + 1);
+      }
+      int32_t* t = cur;
+      cur = nxt;
+      nxt = t;
+      __syncthreads();
+      continue;
+    }
     for (int i = threadIdx.x; i < na; i += kUFT) {
       int j = cur[i];
       uint32_t n = W.hsize[j];
@@ -1506,17 +1567,38 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, 12 * sizeof(unsigned long long), st);
   cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
-  size_t sa = d1_group_smem(kFrontA, kStageA), sb = d1_group_smem(kFrontB, kStageB);
+  size_t sb = d1_group_smem(kFrontB, kStageB);
   int dev = 0;
   cudaGetDevice(&dev);
   static std::atomic<bool> attr[64] = {};  // fields may be driven from several host threads
   if (dev >= 0 && dev < 64 && !attr[dev].load(std::memory_order_acquire)) {
-    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)d1_group_smem(kFrontA, kStageA));
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA * 2, kStageA * 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)d1_group_smem(kFrontA * 2, kStageA * 2));
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA * 4, kStageA * 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)d1_group_smem(kFrontA * 4, kStageA * 4));
     cudaFuncSetAttribute(k_d1_morse_group<kThreadsB, kFrontB, kStageB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
     attr[dev].store(true, std::memory_order_release);
   }
-  k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, sa, st>>>(c, W, kRoundsA, status); note_launch();
+  // phase A buffers: the default, or 2x / 4x larger (more shared memory per
+  // warp, fewer warps per SM; a column that outgrows them continues in
+  // phase B)
+  switch (g_d1_phase_a.load()) {
+    case 1:
+      k_d1_morse_group<32, kFrontA * 2, kStageA * 2><<<n2, 32, d1_group_smem(kFrontA * 2, kStageA * 2), st>>>(
+          c, W, kRoundsA, status);
+      break;
+    case 2:
+      k_d1_morse_group<32, kFrontA * 4, kStageA * 4><<<n2, 32, d1_group_smem(kFrontA * 4, kStageA * 4), st>>>(
+          c, W, kRoundsA, status);
+      break;
+    default:
+      k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, kRoundsA,
+                                                                                             status);
+  }
+  note_launch();
   k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<n2, kThreadsB, sb, st>>>(c, W, 0, status); note_launch();
   k_d1_morse<<<(n2 + 63) / 64, 64, 0, st>>>(c, W, status); note_launch();
 }
