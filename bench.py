@@ -243,6 +243,11 @@ def batched_solve(prec=0.01, converge_tau=0.025):
             x.close()
         return t
 
+    # the batch autotuner picks the D1 phase-A tile on these fields' own
+    # diagrams (process-wide choice; results never depend on it)
+    bt = tsf.Batch(dev)
+    choice, tune_ms = bt.autotune()
+    bt.close()
     tb, st, gb = first_iteration_batch()
     tl = first_iteration_lone()
     targets = [int(s["n_points"]) for s in st]
@@ -270,7 +275,9 @@ def batched_solve(prec=0.01, converge_tau=0.025):
         x.close()
     crowded = [{"field": i, "grid": list(fields[i].shape), "signal_threshold": float(taus[i])}
                for i in range(len(fields)) if i not in sub]
+    tsf.tsf_debug_set(7, 0)
     return {"workload": "uneven_batch_48", "fields": len(fields), "voxels": vox, "assignment_precision": prec,
+            "autotune": {"tiles": ["64+128", "128+256", "256+512"], "diagram_ms": tune_ms, "chosen": choice},
             "first_iteration": {"batch_s": tb, "one_at_a_time_s": tl, "speedup": tl / tb,
                                 "field_iterations_per_s": len(fields) / tb, "device_gb": gb},
             "to_simplified_field": {"fields": len(sub), "threshold_min": converge_tau, "batch_s": tcb,
@@ -593,7 +600,7 @@ def run_gpu(args):
                    "steps": "iterations 1..K from f_0 with the stop rule off",
                    "l2": "flushed (256 MiB write) before every timed step; working set several GB",
                    "parallelism": f"replicas x{world}", "input_generation_s": t_gen},
-        "roofline": {"kernel": f"{dom} (largest stage with a byte model)", "bound": "hbm", "achieved": r["achieved_gbs"],
+        "roofline": {"kernel": dom, "selection": "largest stage with a byte model", "bound": "hbm", "achieved": r["achieved_gbs"],
                      "peak": hbm, "unit": "GB/s", "frac": r["frac"], "traffic": None, "peak_kind": peak_kind,
                      "avg_launch_ms": r["avg_ms"], "algorithmic_bytes_per_launch": r["algorithmic_bytes"],
                      "units_per_launch": r["units"], "unit_of_work": r["unit_of_work"],

@@ -222,6 +222,17 @@ int tsf_batch_field(tsf_batch* batch, int i, tsf_field** out);
 int tsf_batch_set_signal_thresholds(tsf_batch* batch, const float* fractions);
 int tsf_batch_step(tsf_batch* batch, const tsf_params* params, tsf_stats* stats);
 int tsf_batch_simplify(tsf_batch* batch, const tsf_params* params, tsf_stats* stats);
+/* Autotuner of the batch (not in the paper): times the full persistence
+ * diagram of every field (all fields concurrently, each candidate twice,
+ * the second pass counted) for each candidate tile of the D1 Morse
+ * boundaries' first phase — 64 + 128, 128 + 256 or 256 + 512 frontier and
+ * stage entries per column (tsf_debug_set knob 7) — and keeps the fastest.
+ * The choice applies process-wide; results never depend on it.  *choice
+ * receives it (0, 1, 2), ms[c] (cap entries, may be NULL when cap is 0) the
+ * time of candidate c in milliseconds.  Call it before the signal
+ * thresholds are set (it replaces each field's current diagram): TSF_EINVAL
+ * if a field has a target diagram. */
+int tsf_batch_autotune(tsf_batch* batch, int* choice, double* ms, int cap);
 
 /* Overwrites the current values (restart from a saved field; the still-pair
  * history is reset, so the next assignment starts cold). */

@@ -74,7 +74,7 @@ EXPORTS = ("tsf_create_field", "tsf_destroy_field", "tsf_compute_diagram", "tsf_
            "tsf_get_assignment", "tsf_get_targets", "tsf_zero_pairs", "tsf_status_string", "tsf_profile_enable",
            "tsf_profile_read", "tsf_stage_name", "tsf_kernel_launches", "tsf_zero_pairs_static",
            "tsf_loss_and_gradient", "tsf_batch_create", "tsf_batch_destroy", "tsf_batch_size", "tsf_batch_field",
-           "tsf_batch_set_signal_thresholds", "tsf_batch_step", "tsf_batch_simplify", "tsf_unet_num_params", "tsf_set_start_field", "tsf_debug_set",
+           "tsf_batch_set_signal_thresholds", "tsf_batch_step", "tsf_batch_simplify", "tsf_unet_num_params", "tsf_set_start_field", "tsf_debug_set", "tsf_batch_autotune",
            "tsf_unet_create", "tsf_unet_destroy", "tsf_unet_get_params", "tsf_unet_forward", "tsf_unet_gradients",
            "tsf_unet_train_step", "tsf_unet_debug")
 TSF_UNET_NPARAMS = 353713
@@ -116,6 +116,7 @@ def lib():
             "tsf_batch_set_signal_thresholds": [P, P],
             "tsf_batch_step": [P, ctypes.POINTER(tsf_params), P],
             "tsf_batch_simplify": [P, ctypes.POINTER(tsf_params), P],
+            "tsf_batch_autotune": [P, ctypes.POINTER(I), P, I],
             "tsf_set_start_field": [P, P, I],
             "tsf_unet_create": [P, I64, P, ctypes.POINTER(P)],
             "tsf_unet_destroy": [P],
@@ -288,6 +289,14 @@ def tsf_batch_simplify(h, params, n):
     st = (tsf_stats * n)()
     _check(lib().tsf_batch_simplify(h, ctypes.byref(params), st), "tsf_batch_simplify")
     return [s.as_dict() for s in st]
+
+
+def tsf_batch_autotune(h, ncand=3):
+    """Chooses the D1 phase-A tile for the batch; returns (choice, ms per candidate)."""
+    c = ctypes.c_int(0)
+    ms = np.zeros(ncand, np.float64)
+    _check(lib().tsf_batch_autotune(h, ctypes.byref(c), ms.ctypes.data, ncand), "tsf_batch_autotune")
+    return c.value, ms.tolist()
 
 
 def tsf_profile_enable(h, enable=1):
@@ -481,6 +490,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def autotune(self):
+        """Before set_thresholds: time each candidate D1 tile on the batch and
+        keep the fastest; returns (choice, ms per candidate)."""
+        return tsf_batch_autotune(self._h)
 
     def set_thresholds(self, fractions):
         tsf_batch_set_signal_thresholds(self._h, fractions)

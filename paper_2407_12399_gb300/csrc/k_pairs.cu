@@ -43,15 +43,24 @@ std::atomic<int64_t> g_d1_handoff{1 << 12};
 // (64 frontier + 128 stage entries per column), 1 twice, 2 four times that
 std::atomic<int64_t> g_d1_phase_a{0};
 
+static std::atomic<int64_t>* knob(int what) {
+  return what == 1   ? &g_uf_grid_min
+         : what == 2 ? &g_uf_handoff
+         : what == 3 ? &g_uf_round_cap
+         : what == 4 ? &g_barrier_limit
+         : what == 5 ? &g_d1_grid_min
+         : what == 6 ? &g_d1_handoff
+         : what == 7 ? &g_d1_phase_a
+                     : nullptr;
+}
+
+int64_t get_knob(int what) {
+  std::atomic<int64_t>* k = knob(what);
+  return k ? k->load() : -1;
+}
+
 int64_t set_knob(int what, int64_t value) {
-  std::atomic<int64_t>* k = what == 1   ? &g_uf_grid_min
-                            : what == 2 ? &g_uf_handoff
-                            : what == 3 ? &g_uf_round_cap
-                            : what == 4 ? &g_barrier_limit
-                            : what == 5 ? &g_d1_grid_min
-                            : what == 6 ? &g_d1_handoff
-                            : what == 7 ? &g_d1_phase_a
-                                        : nullptr;
+  std::atomic<int64_t>* k = knob(what);
   if (!k) return -1;
   return k->exchange(value);
 }

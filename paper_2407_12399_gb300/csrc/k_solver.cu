@@ -101,6 +101,50 @@ static int32_t* merge_sort(int n, int32_t* a, int32_t* b, Less less, cudaStream_
 }
 
 // ---------------------------------------------------------------------------
+// Stable order of n items by a 64-bit key: two stable LSD radix sorts of the
+// 32-bit halves (low, then high), each four onesweep passes.  Items at or
+// beyond *n_dev (when given) get the largest key.  Equal keys keep their
+// index order, like the merge sort above.  Returns out (n indices).
+// ---------------------------------------------------------------------------
+template <class KeyFn>
+__global__ void k_key64(int n, const int* __restrict__ n_dev, KeyFn kf, uint32_t* __restrict__ lo,
+                        uint32_t* __restrict__ hi, uint32_t* __restrict__ iota) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int m = n_dev ? min(*n_dev, n) : n;
+  const unsigned long long k = i < m ? kf(i) : ~0ull;
+  lo[i] = (uint32_t)k;
+  hi[i] = (uint32_t)(k >> 32);
+  iota[i] = (uint32_t)i;
+}
+
+__global__ void k_gather_u32(int n, const uint32_t* __restrict__ src, const uint32_t* __restrict__ perm,
+                             uint32_t* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+
+template <class KeyFn>
+static int32_t* radix_sort64(int n, const int* n_dev, KeyFn kf, uint32_t* rs, int32_t* tmp, int32_t* out,
+                             uint32_t* status, cudaStream_t st) {
+  if (n <= 0) return out;
+  uint32_t* lo = rs;
+  uint32_t* hi = lo + n;
+  uint32_t* hi2 = hi + n;
+  uint32_t* iota = hi2 + n;
+  uint32_t* scratch = iota + n;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  k_key64<<<nb, 256, 0, st>>>(n, n_dev, kf, lo, hi, iota); note_launch();
+  uint32_t* p1 = reinterpret_cast<uint32_t*>(tmp);
+  sort_u32_pairs(lo, iota, n, nullptr, p1, scratch, status, st);
+  k_gather_u32<<<nb, 256, 0, st>>>(n, hi, p1, hi2); note_launch();
+  sort_u32_pairs(hi2, p1, n, nullptr, reinterpret_cast<uint32_t*>(out), scratch, status, st);
+  return out;
+}
+
+int64_t radix_sort64_words(int64_t n) { return 4 * n + sort_scratch_words(n); }
+
+// ---------------------------------------------------------------------------
 // diagram assembly
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void xyz_of(const Dims& d, uint32_t v, int* o) { vxyz(d, v, o[0], o[1], o[2]); }
@@ -238,6 +282,19 @@ struct KeyLess {  // (essential, dim, v_b, v_d, birth cell)
     if (x.vb != y.vb) return x.vb < y.vb;
     if (x.vd != y.vd) return x.vd < y.vd;
     return x.cb < y.cb;
+  }
+};
+
+// KeyLess as one 64-bit key when vertex ids fit 30 bits: (essential, dim,
+// v_b, v_d); equal keys keep index order, which is birth-cell order in a
+// diagram (points with the same vertices share their values, and diagram
+// order then goes by birth cell).
+struct KeyBits {
+  const Pt* p;
+  __device__ unsigned long long operator()(int i) const {
+    const Pt& x = p[i];
+    return ((unsigned long long)(x.ess != 0) << 62) | ((unsigned long long)(x.dim & 3) << 60) |
+           ((unsigned long long)x.vb << 30) | (unsigned long long)x.vd;
   }
 };
 
@@ -2018,12 +2075,15 @@ int assign(int np, Pt* pts, int nr, const Pt* ref, int nt, const Tg* T, double p
            uint32_t* status, AssignStats* as, cudaStream_t st) {
   // 1) still pairs
   cudaMemsetAsync(B.taken, 0, (size_t)max(nt, 1), st);
-  int32_t* ck = merge_sort(np, B.idxA, B.idxB, KeyLess{pts}, st);
+  const bool radix = B.ids30 && np <= B.cap_rsort && nr <= B.cap_rsort;
+  int32_t* ck = radix ? radix_sort64(np, nullptr, KeyBits{pts}, B.rsort, B.idxB, B.idxA, status, st)
+                      : merge_sort(np, B.idxA, B.idxB, KeyLess{pts}, st);
   int32_t* rk = B.idxC;
   if (nr > 0) {
     // the reference is the previous assignment's points: their key order
     // was kept (the keys of an array do not change once it is built)
     if (ref == B.keyord_for && nr == B.keyord_n) rk = B.keyord;
+    else if (radix) rk = radix_sort64(nr, nullptr, KeyBits{ref}, B.rsort, B.idxD, B.idxC, status, st);
     else rk = merge_sort(nr, B.idxC, B.idxD, KeyLess{ref}, st);
   }
   k_still<<<(np + 255) / 256, 256, 0, st>>>(np, pts, ck, nr, ref, rk, B.tmp_pts, B.taken); note_launch();
@@ -2252,6 +2312,11 @@ struct ContribLess {
   }
 };
 
+struct ContribBits {  // ContribLess as one 64-bit key
+  const Contrib* c;
+  __device__ unsigned long long operator()(int i) const { return ((unsigned long long)c[i].v << 32) | c[i].key; }
+};
+
 // one thread per vertex segment: acc = +0, acc += c in increasing value order
 __global__ void k_apply_step(int nc, const int* __restrict__ nc_dev, const int32_t* __restrict__ idx,
                              const Contrib* __restrict__ C, float* __restrict__ f, uint32_t* __restrict__ upd,
@@ -2273,13 +2338,15 @@ __global__ void k_apply_step(int nc, const int* __restrict__ nc_dev, const int32
 }
 
 int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float alpha_d, float* f, uint32_t* upd,
-                      SolverBufs& B, cudaStream_t st) {
+                      SolverBufs& B, uint32_t* status, cudaStream_t st) {
   cudaMemsetAsync(B.count, 0, sizeof(int), st);
   cudaMemsetAsync(B.counters, 0, sizeof(unsigned long long), st);
   if (np == 0) return 0;
   k_contrib<<<(np + 255) / 256, 256, 0, st>>>(np, pts, T, alpha_b, alpha_d, B.contrib, B.count); note_launch();
   // at most two contributions per point: sized by 2 np, counted on the device
-  int32_t* idx = merge_sort(2 * np, B.idxA, B.idxB, ContribLess{B.contrib}, st, B.count);
+  int32_t* idx = 2 * np <= B.cap_rsort
+                     ? radix_sort64(2 * np, B.count, ContribBits{B.contrib}, B.rsort, B.idxB, B.idxA, status, st)
+                     : merge_sort(2 * np, B.idxA, B.idxB, ContribLess{B.contrib}, st, B.count);
   k_apply_step<<<(2 * np + 255) / 256, 256, 0, st>>>(2 * np, B.count, idx, B.contrib, f, upd, B.counters);
   note_launch();
   unsigned long long nupd = 0;

@@ -260,6 +260,61 @@ __global__ void __launch_bounds__(kRT) k_os_pass(int64_t n, int shift, bool firs
   }
 }
 
+// Digit histograms of u32 keys (all four 8-bit digits at once).
+__global__ void k_os_hist_u32(int64_t n, const uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[4][256];
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool in = i < n;
+    const uint32_t k = in ? __ldg(keys + i) : 0u;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const uint32_t dg = in ? (k >> (8 * d)) & 255u : 256u;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+      if (dg < 256 && lane == __ffs(peers) - 1) atomicAdd(&h[d][dg], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(hist + i, c);
+  }
+}
+
+// Stable sort of (key, value) pairs by the u32 key: histogram, then four
+// onesweep passes.  keys_out may be null.  scratch: sort_scratch_words(n).
+void sort_u32_pairs(const uint32_t* keys, const uint32_t* vals, int64_t n, uint32_t* keys_out, uint32_t* vals_out,
+                    uint32_t* scratch, uint32_t* status, cudaStream_t st) {
+  if (n <= 0) return;
+  const int ntiles = (int)((n + kRTile - 1) / kRTile);
+  uint32_t* kA = scratch;
+  uint32_t* vA = kA + n;
+  uint32_t* kB = vA + n;
+  uint32_t* vB = kB + n;
+  uint32_t* hist = vB + n;
+  uint32_t* counters = hist + 1024;
+  uint32_t* lookback = counters + 64;
+  cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (1024 + 64 + 4 * 256 * (size_t)ntiles), st);
+  k_os_hist_u32<<<std::min(ntiles, 1216), 256, 0, st>>>(n, keys, hist); note_launch();
+  k_os_bases<<<1, 256, 0, st>>>(hist); note_launch();
+  const uint32_t* kin = keys;
+  const uint32_t* vin = vals;
+  for (int pass = 0; pass < 4; ++pass) {
+    const bool last = pass == 3;
+    uint32_t* kout = last ? keys_out : ((pass & 1) ? kB : kA);
+    uint32_t* vout = last ? vals_out : ((pass & 1) ? vB : vA);
+    if (!last && !kout) kout = (pass & 1) ? kB : kA;
+    k_os_pass<<<ntiles, kRT, 0, st>>>(n, 8 * pass, false, last, nullptr, kin, vin, kout, vout, hist + 256 * pass,
+                                      lookback + (size_t)pass * 256 * ntiles, counters + pass, status); note_launch();
+    kin = kout;
+    vin = vout;
+  }
+}
+
 int64_t sort_scratch_words(int64_t n) {
   int64_t ntiles = (n + kRTile - 1) / kRTile;
   // keys/ids ping-pong, 4 digit histograms, 4 tile counters, 4 look-back tables

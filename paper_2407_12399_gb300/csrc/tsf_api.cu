@@ -280,6 +280,9 @@ void grow_solver(tsf_field* F, int np, int nt) {
   dev_free(B.contrib);
   ck(dev_alloc(&B.tmp_pts, cp));
   ck(dev_alloc(&B.keyord, cp));
+  dev_free(B.rsort);
+  B.cap_rsort = 2 * (int64_t)cp;
+  ck(dev_alloc(&B.rsort, (size_t)radix_sort64_words(B.cap_rsort)));
   ck(dev_alloc(&B.idxA, ci));
   ck(dev_alloc(&B.idxB, ci));
   int cicd = std::max(ci, B.cap_cand + 64);
@@ -634,7 +637,8 @@ int step(tsf_field* F, const tsf_params* p, tsf_stats* stats) {
   double t0 = now_ms();
   bool fast = p->fast_gradient_update != 0;
   stage_begin(F, kStep);
-  F->n_updated = gradient_step(F->np, F->pts, F->T, p->alpha_b, p->alpha_d, F->f, fast ? F->upd : nullptr, F->B, st);
+  F->n_updated =
+      gradient_step(F->np, F->pts, F->T, p->alpha_b, p->alpha_d, F->f, fast ? F->upd : nullptr, F->B, F->status, st);
   stage_end(F, kStep);
   F->upd_valid = fast;
   F->ms_step = now_ms() - t0;
@@ -780,6 +784,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->T);
   dev_free(B.tmp_pts);
   dev_free(B.keyord);
+  dev_free(B.rsort);
   B.keyord_for = nullptr;
   dev_free(B.idxA);
   dev_free(B.idxB);
@@ -854,6 +859,7 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
     F->d.ly = ly;
     F->d.lz = lz;
     F->d.nv = nv;
+    F->B.ids30 = nv <= ((int64_t)1 << 30);
     F->st = (cudaStream_t)cuda_stream;
     for (int i = 0; i < 14; ++i)
       F->nd.d[i] = kGeo.off[i][0] + lx * (kGeo.off[i][1] + ly * kGeo.off[i][2]);
@@ -896,6 +902,21 @@ int tsf_create_field(int lx, int ly, int lz, const float* values, int values_on_
   *out = F;
   return TSF_OK;
 }
+
+}  // extern "C"
+
+namespace tsf {
+// Full diagram of a field's current values, for timing (the batch
+// autotuner); refused once a target diagram is set, since it replaces the
+// diagram the solver's assignment refers to.
+int full_diagram_for_tuning(tsf_field* F) {
+  if (!F) return TSF_EINVAL;
+  if (F->have_targets) return TSF_EINVAL;
+  return guarded_f(F, [&]() { return compute_diagram(F, false); });
+}
+}  // namespace tsf
+
+extern "C" {
 
 int tsf_compute_diagram(tsf_field* F, tsf_pair* out, int64_t cap, int64_t* n_out, int out_on_device) {
   if (!F || !n_out || cap < 0 || (cap > 0 && !out)) return TSF_EINVAL;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <mutex>
@@ -14,6 +15,11 @@
 #include <vector>
 
 #include "../../include/tsf.h"
+#include "tsf_kernels.cuh"
+
+namespace tsf {
+int full_diagram_for_tuning(tsf_field* F);
+}
 
 struct tsf_batch {
   int device = 0;  // current when the batch was created; the workers use it too
@@ -149,6 +155,39 @@ int tsf_batch_step(tsf_batch* b, const tsf_params* params, tsf_stats* stats) {
   std::vector<int> codes(b->fields.size(), TSF_OK);
   b->run([&](int i) { codes[i] = tsf_solver_step(b->fields[i], params, stats ? stats + i : nullptr); });
   return first_error(codes);
+}
+
+int tsf_batch_autotune(tsf_batch* b, int* choice, double* ms, int cap) {
+  if (!b || !choice || cap < 0 || (cap > 0 && !ms)) return TSF_EINVAL;
+  // candidates: the D1 Morse boundaries' phase-A tile (frontier + stage
+  // entries per column's warp): 64 + 128, twice, four times that
+  constexpr int kCand = 3;
+  const int64_t keep = tsf::get_knob(7);
+  double best = -1.0;
+  int arg = 0;
+  for (int c = 0; c < kCand; ++c) {
+    tsf::set_knob(7, c);
+    double t = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first pass sizes buffers; the second is timed
+      std::vector<int> codes(b->fields.size(), TSF_OK);
+      const auto t0 = std::chrono::steady_clock::now();
+      b->run([&](int i) { codes[i] = tsf::full_diagram_for_tuning(b->fields[i]); });
+      t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      const int r = first_error(codes);
+      if (r != TSF_OK) {
+        tsf::set_knob(7, keep);
+        return r;
+      }
+    }
+    if (c < cap) ms[c] = t;
+    if (best < 0.0 || t < best) {
+      best = t;
+      arg = c;
+    }
+  }
+  tsf::set_knob(7, arg);
+  *choice = arg;
+  return TSF_OK;
 }
 
 int tsf_batch_simplify(tsf_batch* b, const tsf_params* params, tsf_stats* stats) {

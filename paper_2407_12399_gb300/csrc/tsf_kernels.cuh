@@ -21,9 +21,15 @@ inline int status_code(uint32_t s) {
   return 0;
 }
 
+// Stable sort of n (key, value) pairs by the u32 key (four 8-bit onesweep
+// passes); keys_out may be null; scratch holds sort_scratch_words(n) words.
+void sort_u32_pairs(const uint32_t* keys, const uint32_t* vals, int64_t n, uint32_t* keys_out, uint32_t* vals_out,
+                    uint32_t* scratch, uint32_t* status, cudaStream_t st);
+
 // Test and tuning knobs of the pairing kernels (tsf_debug_set); returns the
 // previous value, -1 for an unknown knob.
 int64_t set_knob(int what, int64_t value);
+int64_t get_knob(int what);
 
 // Number of kernels this library has launched (process-wide).
 void note_launch();

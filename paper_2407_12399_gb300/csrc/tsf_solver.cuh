@@ -96,7 +96,14 @@ struct SolverBufs {
   int32_t* keyord;
   const Pt* keyord_for;
   int keyord_n;
+  // radix sorts of 64-bit keys: key halves, identity, sort scratch
+  uint32_t* rsort;
+  int64_t cap_rsort;  // items
+  bool ids30;         // vertex ids fit 30 bits (the still-pair key packs two)
 };
+
+// Words of scratch a 64-bit-key radix sort of n items needs.
+int64_t radix_sort64_words(int64_t n);
 
 struct AssignStats {
   int k[4];
@@ -125,6 +132,6 @@ void loss_and_counts(int np, const Pt* pts, int nt, const Tg* T, float cancel_ep
 // One gradient step (Eq. 3); returns the number of vertices whose value
 // changed and, with upd non-null, lists them there.
 int64_t gradient_step(int np, const Pt* pts, const Tg* T, float alpha_b, float alpha_d, float* f, uint32_t* upd,
-                      SolverBufs& B, cudaStream_t st);
+                      SolverBufs& B, uint32_t* status, cudaStream_t st);
 
 }  // namespace tsf

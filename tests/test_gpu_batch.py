@@ -121,3 +121,30 @@ def test_batch_of_one_field_is_a_lone_solve():
     assert st[0]["iters"] == sl["iters"]
     assert np.array_equal(bits(b.values()[0]), bits(g))
     b.close()
+
+
+def test_autotuned_batch_equals_lone_solves():
+    """The batch autotuner times each candidate D1 tile on the batch's own
+    diagrams and keeps the fastest; the solves that follow are bit-exact
+    with lone solves (the tile changes the schedule, never the result).
+    Once targets are set, tuning is refused."""
+    import paper_2407_12399_gb300 as tsf
+    fields, taus = S.uneven_batch(n=5, seed=9, dims=(24, 32, 40))
+    b = tsf.Batch(fields)
+    try:
+        choice, ms = b.autotune()
+        assert choice in (0, 1, 2) and len(ms) == 3 and all(t > 0 for t in ms)
+        assert ms[choice] == min(ms)
+        b.set_thresholds(taus)
+        with pytest.raises(tsf.TsfError):
+            b.autotune()
+        b.simplify(stop_s=0.01)
+        got = b.values()
+    finally:
+        tsf.tsf_debug_set(7, 0)
+    for f0, tau, g in zip(fields, taus, got):
+        lone = tsf.Field(f0)
+        lone.set_threshold(float(tau))
+        want, _ = lone.simplify(stop_s=0.01)
+        assert np.array_equal(bits(g), bits(want))
+    b.close()

@@ -227,3 +227,23 @@ def test_training_lowers_the_loss():
         last = net.train_step(f, g, 0.05, 1e-3)
     assert last < 0.5 * first
     net.close()
+
+
+def test_warm_started_solve_keeps_the_plain_targets_and_stops():
+    """warm_start.warm_solve on a small field: the network's g0 starts the
+    solver, the target diagram is f's own (the same as the plain solve's),
+    and the solve reaches the stop rule with L_0 from f."""
+    import paper_2407_12399_gb300 as tsf
+    from paper_2407_12399_gb300 import synthetic as S
+    from paper_2407_12399_gb300 import warm_start as W
+    f = S.gaussian_mixture((16, 16, 16), n_bumps=4, seed=21)
+    net = tsf.UNet(seed=2)
+    pairs = W.solve_pairs([(f, 0.1)])
+    for _ in range(5):
+        net.train_step(pairs[0][0], pairs[0][2], 0.1, 1e-3)
+    g_plain, st_p, _ = W.solve(f, 0.1)
+    g_warm, st_w, _, t_inf = W.warm_solve(net, f, 0.1)
+    assert st_w.loss0 == st_p.loss0
+    assert st_w.done == 1 and st_w.iters < 1000
+    assert t_inf > 0.0
+    net.close()
