@@ -128,6 +128,7 @@ __global__ void k_gradient_list(Dims d, const uint32_t* __restrict__ rank, const
   if (i < (int64_t)*count) gradient_star(d, rank, values, list[i], rec, vnext8, tab, status, sg);
 }
 
+
 // ---------------------------------------------------------------------------
 // Compaction of critical cells, in increasing rank of their highest vertex
 // (then the lexicographic order inside one lower star), which is the

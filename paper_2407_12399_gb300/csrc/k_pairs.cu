@@ -40,7 +40,8 @@ std::atomic<int64_t> g_barrier_limit{1 << 24};
 std::atomic<int64_t> g_d1_grid_min{1 << 16};
 std::atomic<int64_t> g_d1_handoff{1 << 12};
 // shared-memory buffers of the D1 Morse boundaries' phase A: 0 the default
-// (64 frontier + 128 stage entries per column), 1 twice, 2 four times that
+// (64 frontier + 128 stage entries per column, registers capped for 32
+// warps per SM), 1 twice, 2 four times that, 3 the default without the cap
 std::atomic<int64_t> g_d1_phase_a{0};
 
 static std::atomic<int64_t>* knob(int what) {
@@ -967,9 +968,8 @@ constexpr int kChain = 2, kOutCap = 28, kRoundsA = 16;
 // one warp; a column still open after max_rounds, or whose frontier outgrows
 // the warp's buffers, saves its entries and is listed for phase B (NT = 128,
 // one block per listed column).
-template <int NT, int FCAP, int SCAP>
-__global__ void __launch_bounds__(NT, NT == 32 ? 12 : 4) k_d1_morse_group(D1Ctx c, D1Work W, int max_rounds,
-                                                                    uint32_t* status) {
+template <int NT, int FCAP, int SCAP, int MINB = (NT == 32 ? 12 : 4)>
+__global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, int max_rounds, uint32_t* status) {
   const int ncols = W.flags[1];
   extern __shared__ __align__(16) unsigned char smem[];
   FEnt* front = reinterpret_cast<FEnt*>(smem);
@@ -1259,9 +1259,9 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 12 : 4) k_d1_morse_group(D1Ctx 
   }
 }
 
-// Phase A keeps its shared memory small (4 KB per column's warp) so that the
-// register file, not shared memory, limits the warps per SM (24 of 64): the
-// rounds are latency-bound.  A visit appends 1.1 updates on average, 14 at
+// Phase A keeps its shared memory small (4 KB per column's warp) and its
+// registers at 63 so that 32 warps (the block limit) share an SM: the rounds
+// are latency-bound.  A visit appends 1.1 updates on average, 14 at
 // most; a column that outgrows the buffers continues in phase B.
 constexpr int kThreadsB = 128;
 constexpr int kFrontA = 64, kStageA = 128;
@@ -1587,6 +1587,8 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
                          (int)d1_group_smem(kFrontA * 2, kStageA * 2));
     cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA * 4, kStageA * 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)d1_group_smem(kFrontA * 4, kStageA * 4));
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)d1_group_smem(kFrontA, kStageA));
     cudaFuncSetAttribute(k_d1_morse_group<kThreadsB, kFrontB, kStageB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
     attr[dev].store(true, std::memory_order_release);
@@ -1603,9 +1605,13 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
       k_d1_morse_group<32, kFrontA * 4, kStageA * 4><<<n2, 32, d1_group_smem(kFrontA * 4, kStageA * 4), st>>>(
           c, W, kRoundsA, status);
       break;
-    default:
+    case 3:  // the default tile without the register cap
       k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, kRoundsA,
                                                                                              status);
+      break;
+    default:  // registers capped (63) so that 32 warps fit an SM
+      k_d1_morse_group<32, kFrontA, kStageA, 32><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, kRoundsA,
+                                                                                                  status);
   }
   note_launch();
   k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<n2, kThreadsB, sb, st>>>(c, W, 0, status); note_launch();
