@@ -321,9 +321,20 @@ int build_diagram(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1,
 // ---------------------------------------------------------------------------
 // target diagram from a persistence threshold (Section 3)
 // ---------------------------------------------------------------------------
-__global__ void k_select_targets(int np, const Pt* __restrict__ pts, float theta, uint32_t* __restrict__ flag) {
+// Signal threshold of Section 3: theta = fl(fraction * fl(max f - min f)),
+// the extreme values read through the vertex order (first and last vertex).
+__device__ __forceinline__ float signal_theta(const uint32_t* __restrict__ order, const float* __restrict__ f,
+                                              int64_t nv, float fraction) {
+  const float lo = f[order[0]], hi = f[order[nv - 1]];
+  return __fmul_rn(fraction, __fsub_rn(hi, lo));
+}
+
+__global__ void k_select_targets(int np, const Pt* __restrict__ pts, const uint32_t* __restrict__ order,
+                                 const float* __restrict__ f, int64_t nv, float fraction,
+                                 uint32_t* __restrict__ flag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < np) {
+    const float theta = signal_theta(order, f, nv, fraction);
     float pers = __fsub_rn(pts[i].d, pts[i].b);
     flag[i] = (pts[i].ess || pers >= theta) ? 1u : 0u;
   }
@@ -344,10 +355,11 @@ __global__ void k_write_targets(int np, const Pt* __restrict__ pts, const uint32
   }
 }
 
-int make_targets(int np, const Pt* pts, float theta, SolverBufs& B, Tg* T, cudaStream_t st) {
+int make_targets(int np, const Pt* pts, const uint32_t* order, const float* f, int64_t nv, float fraction,
+                 SolverBufs& B, Tg* T, cudaStream_t st) {
   uint32_t* flag = B.u32a;
   uint32_t* pos = B.u32b;
-  k_select_targets<<<(np + 255) / 256, 256, 0, st>>>(np, pts, theta, flag); note_launch();
+  k_select_targets<<<(np + 255) / 256, 256, 0, st>>>(np, pts, order, f, nv, fraction, flag); note_launch();
   exclusive_scan_u32(flag, pos, np, B.u32c, st);
   k_write_targets<<<(np + 255) / 256, 256, 0, st>>>(np, pts, flag, pos, T); note_launch();
   uint32_t tail[2];

@@ -954,18 +954,8 @@ int tsf_set_signal_threshold(tsf_field* F, float fraction) {
   return guarded_f(F, [&]() {
     int r = compute_diagram(F, false);
     if (r) return r;
-    float lo = 0, hi = 0;
-    uint32_t ids[2];
-    ck(cudaMemcpyAsync(&ids[0], F->order, 4, cudaMemcpyDeviceToHost, F->st));
-    ck(cudaMemcpyAsync(&ids[1], F->order + F->d.nv - 1, 4, cudaMemcpyDeviceToHost, F->st));
-    ck(cudaStreamSynchronize(F->st));
-    ck(cudaMemcpyAsync(&lo, F->f + ids[0], 4, cudaMemcpyDeviceToHost, F->st));
-    ck(cudaMemcpyAsync(&hi, F->f + ids[1], 4, cudaMemcpyDeviceToHost, F->st));
-    ck(cudaStreamSynchronize(F->st));
-    volatile float range = hi - lo;
-    volatile float theta = fraction * range;
     grow_solver(F, F->np, F->np);
-    F->nt = make_targets(F->np, F->pts, theta, F->B, F->T, F->st);
+    F->nt = make_targets(F->np, F->pts, F->order, F->f, F->d.nv, fraction, F->B, F->T, F->st);
     return start_solver(F);
   });
 }

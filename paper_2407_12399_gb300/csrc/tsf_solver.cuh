@@ -116,7 +116,8 @@ struct AssignStats {
 
 int build_diagram(const Dims& d, const NbrDelta& nd, const CritLists& L, int n1, int n2, int n3, const PairOut& P,
                   const uint32_t* order, const float* f, SolverBufs& B, Pt* out, int cap, cudaStream_t st);
-int make_targets(int np, const Pt* pts, float theta, SolverBufs& B, Tg* T, cudaStream_t st);
+int make_targets(int np, const Pt* pts, const uint32_t* order, const float* f, int64_t nv, float fraction,
+                 SolverBufs& B, Tg* T, cudaStream_t st);
 void targets_as_points(int nt, const Tg* T, Pt* R, cudaStream_t st);
 // f[v] = in[v] where they differ, the changed vertices listed in upd, their
 // number in *count.

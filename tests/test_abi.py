@@ -128,3 +128,29 @@ def test_params_carry_the_assignment_precision():
     assert abs(p.assignment_precision - 0.01) < 1e-9
     assert tsf.params().assignment_precision == 0.0
     assert "assign_rounds" in dict(tsf.tsf_stats._fields_)
+
+
+def test_warm_start_and_knob_entry_points_check_arguments_without_a_gpu(libpath):
+    """The network's parameter count agrees between the header, the library
+    and the layer list; the new entry points reject bad arguments before any
+    CUDA call; the schedule knobs round-trip and refuse unknown ids."""
+    import numpy as np
+    L = tsf.lib()
+    text = open(os.path.join(ROOT, "include", "tsf.h")).read()
+    n = int(re.search(r"#define\s+TSF_UNET_NPARAMS\s+(\d+)", text).group(1))
+    assert tsf.TSF_UNET_NPARAMS == n == tsf.tsf_unet_num_params()
+    assert sum(int(np.prod(ws)) + nb for _, ws, nb in tsf.unet_layer_shapes()) == n
+    h = ctypes.c_void_p()
+    buf = np.zeros(4, np.float32)
+    assert L.tsf_unet_create(buf.ctypes.data, 4, None, ctypes.byref(h)) == tsf.TSF_EINVAL
+    assert L.tsf_unet_create(None, n, None, ctypes.byref(h)) == tsf.TSF_EINVAL
+    assert L.tsf_unet_destroy(None) == tsf.TSF_OK
+    assert L.tsf_unet_forward(None, 8, 8, 8, buf.ctypes.data, ctypes.c_float(0.1), buf.ctypes.data, 0) == tsf.TSF_EINVAL
+    assert L.tsf_unet_get_params(None, buf.ctypes.data, n) == tsf.TSF_EINVAL
+    assert L.tsf_set_start_field(None, buf.ctypes.data, 0) == tsf.TSF_EINVAL
+    c = ctypes.c_int(0)
+    assert L.tsf_batch_autotune(None, ctypes.byref(c), None, 0) == tsf.TSF_EINVAL
+    assert tsf.tsf_debug_set(99, 1) == -1
+    for knob in (1, 2, 3, 4, 5, 6, 7):
+        old = tsf.tsf_debug_set(knob, 5)
+        assert tsf.tsf_debug_set(knob, old) == 5
