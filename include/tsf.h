@@ -297,7 +297,9 @@ int64_t tsf_kernel_launches(void);
  *   7: shared-memory buffers per column of the D1 Morse boundaries' first
  *      phase: 0 the default (64 + 128 entries, registers capped for 32
  *      warps per SM), 1 twice, 2 four times that (columns that outgrow them
- *      continue in the second phase), 3 the default tile without the cap.
+ *      continue in the second phase), 3 the default tile without the cap;
+ *   8: register budget of the lower-star gradient kernels, as blocks of
+ *      128 threads per SM: 0 the default (6), 1 no cap, 2 five.
  * Returns the previous value, or -1 for an unknown knob.  Set them only
  * while no call of this library is running. */
 int64_t tsf_debug_set(int what, int64_t value);

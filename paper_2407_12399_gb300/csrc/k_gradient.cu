@@ -7,94 +7,416 @@
 
 namespace tsf {
 
-// The lower star of v (Section 4.2): its gradient record, the byte naming
-// the edge v is paired with, and (tab non-null) the saddle-saddle table row.
+// ---------------------------------------------------------------------------
+// The lower star of v (Section 4.2) in registers and a per-thread slice of
+// shared memory.  Lane-dependent array indices would otherwise put the star
+// in local memory, whose traffic outgrows L1 at full occupancy and spills
+// to DRAM.  Small tables are packed into 64-bit words:
+//   P  nibble i = rank position of neighbour i among the lower ones (15: not lower)
+//   B  nibble p = the neighbour at rank position p
+//   L  nibble p = the root (smallest rank position) of p's lower-link component
+//   D0, D1  5-bit fields: the root of each link triangle in the dual sweep
+//           (triangles 0..11 in D0, 12..23 in D1; 24 = outside the lower star)
+// Shared memory keeps, with the thread index innermost (a warp's accesses hit
+// 32 different banks), the link adjacency by neighbour, the dual record
+// codes, and per rank position the link edges of the forest path to its
+// root.
+// ---------------------------------------------------------------------------
+constexpr int kGT = 128;  // threads per block of the gradient kernels
+
+// The link tables the sweeps index with lane-dependent values, packed:
+//   edge_desc[e]  the two link triangles t_k on link edge e, each with the slot
+//                 j_k of its third vertex and that vertex c_k:
+//                 t0 | c0 << 5 | j0 << 9 | t1 << 11 | c1 << 16 | j1 << 20
+//   tri3[t]       the vertices of link triangle t: a | b << 4 | c << 8
+//   edge_idx      link edge of a neighbour pair (as in the full table)
+struct GradGeo {
+  uint32_t edge_desc[36];
+  uint32_t tri3[24];
+  int8_t edge_idx[14][14];
+  int8_t pad[4];
+};
+static_assert(sizeof(GradGeo) % 4 == 0, "copied as words");
+
+constexpr GradGeo make_grad_geo() {
+  GradGeo g{};
+  for (int e = 0; e < 36; ++e) {
+    uint32_t w = 0;
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t t = (uint32_t)kGeo.edge_tri[e][k], j = (uint32_t)kGeo.edge_third[e][k];
+      const uint32_t c = (uint32_t)kGeo.tri[t][j];
+      w |= (t | (c << 5) | (j << 9)) << (11 * k);
+    }
+    g.edge_desc[e] = w;
+  }
+  for (int t = 0; t < 24; ++t)
+    g.tri3[t] = (uint32_t)kGeo.tri[t][0] | ((uint32_t)kGeo.tri[t][1] << 4) | ((uint32_t)kGeo.tri[t][2] << 8);
+  for (int a = 0; a < 14; ++a)
+    for (int b = 0; b < 14; ++b) g.edge_idx[a][b] = kGeo.edge_idx[a][b];
+  return g;
+}
+constexpr bool grad_geo_matches() {
+  const GradGeo g = make_grad_geo();
+  for (int e = 0; e < 36; ++e)
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t dk = g.edge_desc[e] >> (11 * k);
+      const int t = (int)(dk & 31u), c = (int)((dk >> 5) & 15u), j = (int)((dk >> 9) & 3u);
+      if (t != kGeo.edge_tri[e][k] || j != kGeo.edge_third[e][k] || c != kGeo.tri[t][j]) return false;
+    }
+  for (int t = 0; t < 24; ++t)
+    for (int i = 0; i < 3; ++i)
+      if ((int)((g.tri3[t] >> (4 * i)) & 15u) != kGeo.tri[t][i]) return false;
+  return true;
+}
+static_assert(grad_geo_matches(), "packed link tables decode to the full ones");
+static __constant__ GradGeo c_grad_geo = make_grad_geo();
+
+// Every thread of the block must call this (it ends with a barrier).
+__device__ __forceinline__ void grad_geo_to_shared(GradGeo& sg) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&c_grad_geo);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sg);
+  for (int i = threadIdx.x; i < (int)(sizeof(GradGeo) / 4); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+struct GradSmem {
+  unsigned long long rp[14][kGT];  // forest path (link-edge mask) to the tree root, by rank position
+  uint32_t adj[7][kGT];            // rank-position adjacency of neighbour 2k (low half) and 2k+1 (high half)
+  uint32_t code[6][kGT];           // record code of link triangle t in byte t & 3 of word t >> 2
+};
+
+__device__ __forceinline__ int nib(uint64_t w, int i) { return (int)((w >> (4 * i)) & 15u); }
+
+// bit 4i set where nibble i of w equals v
+__device__ __forceinline__ uint64_t nib_eq(uint64_t w, int v) {
+  uint64_t x = w ^ (0x1111111111111111ull * (uint64_t)v);
+  x |= x >> 1;
+  x |= x >> 2;
+  return ~x & 0x1111111111111111ull;
+}
+
+constexpr uint64_t kF5 = 0x0084210842108421ull;  // bit 5i for i < 12
+__host__ __device__ constexpr uint64_t f5_iota(int base) {
+  uint64_t w = 0;
+  for (int i = 0; i < 12; ++i) w |= (uint64_t)(base + i) << (5 * i);
+  return w;
+}
+static_assert(kF5 == [] {
+  uint64_t m = 0;
+  for (int i = 0; i < 12; ++i) m |= 1ull << (5 * i);
+  return m;
+}(), "field mask");
+
+// bit 5i set where 5-bit field i of w equals v
+__device__ __forceinline__ uint64_t f5_eq(uint64_t w, int v) {
+  uint64_t x = w ^ (kF5 * (uint64_t)v);
+  x |= (x >> 1) | (x >> 2) | (x >> 3) | (x >> 4);
+  return ~x & kF5;
+}
+__device__ __forceinline__ int dual_root(uint64_t D0, uint64_t D1, int t) {
+  if (t >= 24) return 24;
+  return t < 12 ? (int)((D0 >> (5 * t)) & 31u) : (int)((D1 >> (5 * (t - 12))) & 31u);
+}
+
+template <int I>
+__device__ __forceinline__ uint32_t adj_positions(uint32_t lower, uint64_t P) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int j = 0; j < 14; ++j)
+    if ((geo_adj(I) >> j) & 1u)
+      if ((lower >> j) & 1u) r |= 1u << nib(P, j);
+  return r;
+}
+template <int... K>
+__device__ __forceinline__ void store_adj(GradSmem& sm, uint32_t lower, uint64_t P, std::integer_sequence<int, K...>) {
+  ((sm.adj[K][threadIdx.x] = adj_positions<2 * K>(lower, P) | (adj_positions<2 * K + 1>(lower, P) << 16)), ...);
+}
+__device__ __forceinline__ uint32_t adj_of(const GradSmem& sm, int a) {
+  return (sm.adj[a >> 1][threadIdx.x] >> (16 * (a & 1))) & 0xFFFFu;
+}
+
+// Initial record code of link triangle T: a maximum while v*T lies in the
+// lower star, else "not in the lower star".
+template <int T>
+__device__ __forceinline__ uint32_t initial_code(uint32_t lower) {
+  constexpr uint32_t m = (1u << kGeo.tri[T][0]) | (1u << kGeo.tri[T][1]) | (1u << kGeo.tri[T][2]);
+  return (lower & m) == m ? (uint32_t)kCodeMax : (uint32_t)kCodeNone;
+}
+template <int... K>
+__device__ __forceinline__ void store_codes(GradSmem& sm, uint32_t lower, std::integer_sequence<int, K...>) {
+  ((sm.code[K][threadIdx.x] = initial_code<4 * K>(lower) | (initial_code<4 * K + 1>(lower) << 8) |
+                              (initial_code<4 * K + 2>(lower) << 16) | (initial_code<4 * K + 3>(lower) << 24)),
+   ...);
+}
+
+// Neighbour pairs (i, j), i < j, numbered 0..90 for fully unrolled pair loops.
+__host__ __device__ constexpr int pair_i(int k) {
+  int i = 0;
+  while (k >= 13 - i) k -= 13 - i++;
+  return i;
+}
+__host__ __device__ constexpr int pair_j(int k) {
+  int i = 0;
+  while (k >= 13 - i) k -= 13 - i++;
+  return i + 1 + k;
+}
+// One comparison per pair: the neighbour ranked below the other adds one to
+// the other's count; for a link edge (i, j) the result is also kept.
+template <int K>
+__device__ __forceinline__ void rank_pair(const uint32_t* nr, int* cnt, unsigned long long& below36) {
+  constexpr int i = pair_i(K), j = pair_j(K), le = kGeo.edge_idx[i][j];
+  const bool jb = nr[j] < nr[i];
+  cnt[i] += jb ? 1 : 0;
+  cnt[j] += jb ? 0 : 1;
+  if constexpr (le >= 0) below36 |= (unsigned long long)jb << le;
+}
+template <int... K>
+__device__ __forceinline__ void rank_pairs(const uint32_t* nr, int* cnt, unsigned long long& below36,
+                                           std::integer_sequence<int, K...>) {
+  (rank_pair<K>(nr, cnt, below36), ...);
+}
+static_assert(pair_i(90) == 12 && pair_j(90) == 13 && pair_i(12) == 0 && pair_j(12) == 13 && pair_j(13) == 2,
+              "pair numbering");
+
+// Link edges (a, b), a < b, whose first vertex a is lower.
+__host__ __device__ constexpr unsigned long long edges_from(int a) {
+  unsigned long long m = 0;
+  for (int le = 0; le < 36; ++le)
+    if (kGeo.edge[le][0] == a) m |= 1ull << le;
+  return m;
+}
+template <int... A>
+__device__ __forceinline__ unsigned long long edges_from_lower(uint32_t lower, std::integer_sequence<int, A...>) {
+  return (((lower >> A) & 1u ? edges_from(A) : 0ull) | ...);
+}
+
+// Key of link triangle t in the backward sweep (larger = later in the filtration).
+__device__ __forceinline__ int tri_key(uint64_t P, int t, const GradGeo& G) {
+  const uint32_t w = G.tri3[t];
+  int p0 = nib(P, w & 15u), p1 = nib(P, (w >> 4) & 15u), p2 = nib(P, (w >> 8) & 15u);
+  int hi = max(p0, max(p1, p2)), lo = min(p0, min(p1, p2));
+  return hi * 196 + (p0 + p1 + p2 - hi - lo) * 14 + lo;
+}
+
+// The lower star of v: its gradient record, the byte naming the edge v is
+// paired with, and (tab non-null) the saddle-saddle table row.
+//
+// Forward sweep (0-dimensional persistence of the lower link, elder rule):
+// link vertices by rank position, each one's link edges to earlier ones by
+// increasing position; an edge joining two components kills the younger root.
+// Backward sweep: link edges in the reverse order over the dual graph (link
+// triangles of the lower link, plus one node for everything outside); an
+// edge joining two dual components kills the one whose root triangle comes
+// first in the filtration.  Same sweeps as the reference formulation of
+// tsf_star.cuh, with union-find replaced by always-compressed root labels.
+//
+// Closures: the chain of the table's closure of v*x (v*x -> v*y + path x..y
+// -> ...) runs through the older representatives x's component merged into,
+// and ends at the root of x's tree in the final link forest: the lowest edge
+// v*x0 (root position 0) or a critical edge.  Its link-edge sum telescopes
+// into the forest path from x to that root, which is kept per position while
+// the forest grows: when the component of root `young` joins `old` through
+// link edge e = (a, b), every member u of the young component extends its
+// path by path(a) + e + path(b).
 __device__ __forceinline__ void gradient_star(const Dims& d, const uint32_t* __restrict__ rank,
                                               const float* __restrict__ values, int64_t v, Rec* __restrict__ rec,
                                               uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
-                                              uint32_t* status, const Geo& sg) {
-  Star s;
-  star_load(s, d, (uint32_t)v, rank);
-  Fwd f;
-  int8_t y_of[14];
-  uint64_t path_of[14];
-  if (tab) star_forward_impl<true>(s, f, sg, y_of, path_of);
-  else star_forward(s, f, sg);
-  Dual du;
-  star_dual(s, f, du, sg);
-  if (du.inconsistent) atomicOr(status, kErrInconsistent);
-  Rec r = star_record(s, f, du);
+                                              uint32_t* status, const GradGeo& sg, GradSmem& sm) {
+  const int tid = threadIdx.x;
+  int vx, vy, vz;
+  vxyz(d, (uint32_t)v, vx, vy, vz);
+  const uint32_t rv = __ldg(rank + v);
+  uint32_t nr[14];
+  uint32_t valid = 0, lower = 0;
+#pragma unroll
+  for (int i = 0; i < 14; ++i) {
+    int nx, ny, nz;
+    nr[i] = 0xFFFFFFFFu;
+    if (nbr_xyz(d, vx, vy, vz, i, nx, ny, nz)) {
+      valid |= 1u << i;
+      nr[i] = __ldg(rank + vid(d, nx, ny, nz));
+      if (nr[i] < rv) lower |= 1u << i;
+    }
+  }
+  const int nl = __popc(lower);
+  // rank positions: a lower neighbour's position counts the neighbours ranked
+  // below it (all of them lower, as v is above them; outside ranks stay above)
+  int cnt[14];
+#pragma unroll
+  for (int i = 0; i < 14; ++i) cnt[i] = 0;
+  unsigned long long below36 = 0;  // link edge (a, b), a < b: b ranks below a
+  rank_pairs(nr, cnt, below36, std::make_integer_sequence<int, 91>{});
+  uint64_t P = 0, B = 0;
+#pragma unroll
+  for (int i = 0; i < 14; ++i) {
+    if ((lower >> i) & 1u) {
+      P |= (uint64_t)cnt[i] << (4 * i);
+      B |= (uint64_t)i << (4 * cnt[i]);
+    } else {
+      P |= 15ull << (4 * i);
+    }
+  }
+  store_adj(sm, lower, P, std::make_integer_sequence<int, 7>{});
+  if (tab) {
+#pragma unroll
+    for (int k = 0; k < 14; ++k) sm.rp[k][tid] = 0;
+  }
+
+  // forward sweep
+  constexpr uint64_t kIota4 = 0xFEDCBA9876543210ull;
+  uint64_t L = kIota4;
+  uint64_t link_pos = 0;
+  for (int p = 1; p < nl; ++p) {
+    const int a = nib(B, p);
+    for (uint32_t qm = adj_of(sm, a) & ((1u << p) - 1u); qm; qm &= qm - 1) {
+      const int q = __ffs(qm) - 1;
+      const int e = sg.edge_idx[a][nib(B, q)];
+      const int ra = nib(L, p), rb = nib(L, q);
+      if (ra == rb) {
+        link_pos |= 1ull << e;
+        continue;
+      }
+      const int young = max(ra, rb), old = min(ra, rb);
+      uint64_t fl = nib_eq(L, young);
+      L ^= fl * (uint64_t)(young ^ old);
+      if (tab) {
+        const unsigned long long c = sm.rp[p][tid] ^ sm.rp[q][tid] ^ (1ull << e);
+        for (; fl; fl &= fl - 1) sm.rp[(__ffsll((long long)fl) - 1) >> 2][tid] ^= c;
+      }
+    }
+  }
+  uint32_t crit_edges = 0;
+  {
+    const uint64_t span = nl > 1 ? (((1ull << (4 * nl)) - 1ull) & ~15ull) : 0ull;
+    for (uint64_t rm = nib_eq(L ^ kIota4, 0) & span; rm; rm &= rm - 1)
+      crit_edges |= 1u << nib(B, (__ffsll((long long)rm) - 1) >> 2);
+  }
+
+  // backward (dual) sweep
+  store_codes(sm, lower, std::make_integer_sequence<int, 6>{});
+  constexpr uint64_t kIota5a = f5_iota(0), kIota5b = f5_iota(12);
+  uint64_t D0 = kIota5a, D1 = kIota5b;
+  uint64_t crit_tris = 0;
+  bool inconsistent = false;
+  uint8_t* code8 = reinterpret_cast<uint8_t*>(&sm.code[0][0]);
+  for (int p = nl - 1; p >= 1; --p) {
+    const int a = nib(B, p);
+    for (uint32_t qm = adj_of(sm, a) & ((1u << p) - 1u); qm;) {
+      const int q = 31 - __clz(qm);
+      qm ^= 1u << q;
+      const int e = sg.edge_idx[a][nib(B, q)];
+      const uint32_t desc = sg.edge_desc[e];
+      int node[2], tcode[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t dk = desc >> (11 * k);
+        const int t = (int)(dk & 31u), c = (int)((dk >> 5) & 15u), j = (int)((dk >> 9) & 3u);
+        if (!((valid >> c) & 1u)) {
+          node[k] = 24;
+          tcode[k] = kCodeOut;
+        } else if ((lower >> c) & 1u) {
+          node[k] = t;
+          tcode[k] = t;
+        } else {
+          node[k] = 24;
+          tcode[k] = 24 + 3 * t + j;
+        }
+      }
+      const int r0 = dual_root(D0, D1, node[0]), r1 = dual_root(D0, D1, node[1]);
+      const bool lp = (link_pos >> e) & 1ull;
+      if (r0 == r1) {
+        if (lp) crit_tris |= 1ull << e;
+        continue;
+      }
+      const int k0 = r0 == 24 ? 0x7FFFFFFF : tri_key(P, r0, sg);
+      const int k1 = r1 == 24 ? 0x7FFFFFFF : tri_key(P, r1, sg);
+      const int dside = k0 < k1 ? 0 : 1;
+      const int rd = dside == 0 ? r0 : r1, ro = dside == 0 ? r1 : r0;
+      code8[((rd >> 2) * kGT + tid) * 4 + (rd & 3)] = (uint8_t)tcode[1 - dside];
+      const uint64_t x = (uint64_t)(rd ^ ro);
+      D0 ^= f5_eq(D0, rd) * x;
+      D1 ^= f5_eq(D1, rd) * x;
+      if (!lp) inconsistent = true;
+    }
+  }
+  if (inconsistent) atomicOr(status, kErrInconsistent);
+
+  // the record
+  Rec r;
+  r.w[0] = (nl > 0 ? (uint32_t)nib(B, 0) : (uint32_t)kVnextMin) | (crit_edges << 4) |
+           ((uint32_t)(crit_tris & 0x3FFFull) << 18);
+  r.w[1] = (uint32_t)((crit_tris >> 14) & 0x3FFFFFull);
+#pragma unroll
+  for (int i = 2; i < 8; ++i) r.w[i] = 0;
+  bool has_max = false;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const uint32_t w = sm.code[k][tid];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int t = 4 * k + b;
+      const uint32_t c = (w >> (8 * b)) & 0x7Fu;
+      has_max |= c == (uint32_t)kCodeMax;
+      const int off = 56 + 7 * t, wi = off >> 5, bi = off & 31;
+      r.w[wi] |= c << bi;
+      if (bi > 25) r.w[wi + 1] |= c >> (32 - bi);
+    }
+  }
+  r.w[1] |= (has_max ? 1u : 0u) << 22;
   uint4* dst = reinterpret_cast<uint4*>(rec + v);
   dst[0] = make_uint4(r.w[0], r.w[1], r.w[2], r.w[3]);
   dst[1] = make_uint4(r.w[4], r.w[5], r.w[6], r.w[7]);
   vnext8[v] = (uint8_t)(r.w[0] & 15u);
+
   if (tab) {
-    // closures by increasing rank position: v*y (pos(y) < pos(x)) is done
-    // before the v*x whose chain continues there
-    uint32_t crit = rec_crit_edges(r);
-    uint64_t cl[14];
-    int8_t end[14];
-    D1Tab t;
+    unsigned long long q[8];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) t.q[k] = 0;
+    for (int k = 0; k < 8; ++k) q[k] = 0;
     unsigned long long ends = ~0ull;
-    for (int p = 0; p < s.nl; ++p) {
-      int x = s.by_pos[p];
-      uint64_t c = 0;
-      int e = 15;
-      if (p > 0) {
-        if ((crit >> x) & 1u) {
-          e = x;
-        } else {
-          int y = y_of[x];
-          if (y < 0) {
-            atomicOr(status, kErrInconsistent);
-          } else {
-            c = path_of[x];
-            if (y != s.by_pos[0]) {
-              c ^= cl[y];
-              e = end[y];
-            }
-          }
-        }
-      }
-      cl[x] = c;
-      end[x] = (int8_t)e;
-      tab_set_closure(t, x, c);
-      ends = (ends & ~(15ull << (4 * x))) | ((unsigned long long)e << (4 * x));
-    }
-    unsigned long long orient = 0;
-    for (int le = 0; le < 36; ++le) {
-      int a = sg.edge[le][0], b = sg.edge[le][1];
-      if (((s.lower >> a) & (s.lower >> b) & 1u) && s.pos[a] > s.pos[b]) orient |= 1ull << le;
-    }
-    t.q[8] = ends;
-    t.q[9] = orient;
-    {
-      int x, y, z;
-      vxyz(d, (uint32_t)v, x, y, z);
 #pragma unroll
-      for (int i = 0; i < 14; ++i) {
-        int nx, ny, nz;
-        t.nkey[i] = nbr_xyz(d, x, y, z, i, nx, ny, nz) ? value_key(__ldg(values + vid(d, nx, ny, nz))) : 0u;
+    for (int x = 0; x < 14; ++x) {
+      if ((lower >> x) & 1u) {
+        const int p = nib(P, x);
+        const unsigned long long c = sm.rp[p][tid];
+        const int root = nib(L, p);
+        const int e = root == 0 ? 15 : nib(B, root);
+        const int off = 36 * x, wi = off >> 6, bi = off & 63;
+        q[wi] |= c << bi;
+        if (bi > 28) q[wi + 1] |= c >> (64 - bi);
+        ends = (ends & ~(15ull << (4 * x))) | ((unsigned long long)e << (4 * x));
       }
-      t.pad[0] = t.pad[1] = 0;
     }
+    // (a, b) is oriented when a is lower and b ranks below it (then b is lower too)
+    const unsigned long long orient = below36 & edges_from_lower(lower, std::make_integer_sequence<int, 14>{});
     uint4* dst4 = reinterpret_cast<uint4*>(tab + v);
-    const uint4* src4 = reinterpret_cast<const uint4*>(&t);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) dst4[k] = src4[k];
+    for (int k = 0; k < 4; ++k)
+      dst4[k] = make_uint4((uint32_t)q[2 * k], (uint32_t)(q[2 * k] >> 32), (uint32_t)q[2 * k + 1],
+                           (uint32_t)(q[2 * k + 1] >> 32));
+    dst4[4] = make_uint4((uint32_t)ends, (uint32_t)(ends >> 32), (uint32_t)orient, (uint32_t)(orient >> 32));
+    uint32_t nk[16];
+    const int64_t sy = d.lx, sz = (int64_t)d.lx * d.ly;
+#pragma unroll
+    for (int i = 0; i < 14; ++i)
+      nk[i] = ((valid >> i) & 1u)
+                  ? value_key(__ldg(values + v + c_geo.off[i][0] + sy * c_geo.off[i][1] + sz * c_geo.off[i][2]))
+                  : 0u;
+    nk[14] = nk[15] = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst4[5 + k] = make_uint4(nk[4 * k], nk[4 * k + 1], nk[4 * k + 2], nk[4 * k + 3]);
   }
 }
 
 // Every lower star (the first diagram of a field, or without the fast update).
-__global__ void k_gradient(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
+template <int MINB>
+__global__ void __launch_bounds__(kGT, MINB) k_gradient(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
                            Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
                            uint32_t* status) {
-  __shared__ Geo sg;
-  geo_to_shared(sg);
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < d.nv) gradient_star(d, rank, values, v, rec, vnext8, tab, status, sg);
+  __shared__ GradGeo sg;
+  __shared__ GradSmem sm;
+  grad_geo_to_shared(sg);
+  int64_t v = (int64_t)blockIdx.x * kGT + threadIdx.x;
+  if (v < d.nv) gradient_star(d, rank, values, v, rec, vnext8, tab, status, sg, sm);
 }
 
 // Section 4.2, fast persistence update: only the lower stars whose closed
@@ -118,14 +440,16 @@ __global__ void k_gradient_expand(Dims d, const uint32_t* __restrict__ upd, int6
   if (atomicExch(mark + w, gen) != gen) list[atomicAdd(count, 1ull)] = w;
 }
 
-__global__ void k_gradient_list(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
+template <int MINB>
+__global__ void __launch_bounds__(kGT, MINB) k_gradient_list(Dims d, const uint32_t* __restrict__ rank, const float* __restrict__ values,
                                 const uint32_t* __restrict__ list, const unsigned long long* __restrict__ count,
                                 Rec* __restrict__ rec, uint8_t* __restrict__ vnext8, D1Tab* __restrict__ tab,
                                 uint32_t* status) {
-  __shared__ Geo sg;
-  geo_to_shared(sg);
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < (int64_t)*count) gradient_star(d, rank, values, list[i], rec, vnext8, tab, status, sg);
+  __shared__ GradGeo sg;
+  __shared__ GradSmem sm;
+  grad_geo_to_shared(sg);
+  int64_t i = (int64_t)blockIdx.x * kGT + threadIdx.x;
+  if (i < (int64_t)*count) gradient_star(d, rank, values, list[i], rec, vnext8, tab, status, sg, sm);
 }
 
 
@@ -374,10 +698,18 @@ __global__ void k_zero_pairs(Dims d, const uint32_t* __restrict__ rank, unsigned
 
 namespace tsf {
 
+// Blocks per SM of the gradient kernels' register budget (tuning knob 8).
+static int gradient_blocks() { return (int)get_knob(8); }
+
 void launch_gradient(const Dims& d, const uint32_t* rank, const float* f, Rec* rec, uint8_t* vnext8, D1Tab* tab,
                      uint32_t* status, cudaStream_t st) {
-  unsigned nb = (unsigned)((d.nv + 127) / 128);
-  k_gradient<<<nb, 128, 0, st>>>(d, rank, f, rec, vnext8, tab, status); note_launch();
+  unsigned nb = (unsigned)((d.nv + kGT - 1) / kGT);
+  switch (gradient_blocks()) {
+    case 1: k_gradient<1><<<nb, kGT, 0, st>>>(d, rank, f, rec, vnext8, tab, status); break;
+    case 2: k_gradient<5><<<nb, kGT, 0, st>>>(d, rank, f, rec, vnext8, tab, status); break;
+    default: k_gradient<6><<<nb, kGT, 0, st>>>(d, rank, f, rec, vnext8, tab, status); break;
+  }
+  note_launch();
 }
 
 void launch_gradient_incremental(const Dims& d, const uint32_t* rank, const float* f, const uint32_t* upd, int64_t nu,
@@ -387,8 +719,13 @@ void launch_gradient_incremental(const Dims& d, const uint32_t* rank, const floa
   if (nu <= 0) return;
   unsigned nb = (unsigned)((nu * 15 + 255) / 256);
   k_gradient_expand<<<nb, 256, 0, st>>>(d, upd, nu, mark, gen, list, count); note_launch();
-  unsigned nl = (unsigned)((std::min<int64_t>(nu * 15, d.nv) + 127) / 128);
-  k_gradient_list<<<nl, 128, 0, st>>>(d, rank, f, list, count, rec, vnext8, tab, status); note_launch();
+  unsigned nl = (unsigned)((std::min<int64_t>(nu * 15, d.nv) + kGT - 1) / kGT);
+  switch (gradient_blocks()) {
+    case 1: k_gradient_list<1><<<nl, kGT, 0, st>>>(d, rank, f, list, count, rec, vnext8, tab, status); break;
+    case 2: k_gradient_list<5><<<nl, kGT, 0, st>>>(d, rank, f, list, count, rec, vnext8, tab, status); break;
+    default: k_gradient_list<6><<<nl, kGT, 0, st>>>(d, rank, f, list, count, rec, vnext8, tab, status); break;
+  }
+  note_launch();
 }
 
 int crit_tiles(int64_t nv) { return (int)((nv + kCTile - 1) / kCTile); }

@@ -43,6 +43,9 @@ std::atomic<int64_t> g_d1_handoff{1 << 12};
 // (64 frontier + 128 stage entries per column, registers capped for 32
 // warps per SM), 1 twice, 2 four times that, 3 the default without the cap
 std::atomic<int64_t> g_d1_phase_a{0};
+// blocks per SM the lower-star gradient kernels are compiled for: 0 the
+// default (six), 1 no register cap, 2 five
+std::atomic<int64_t> g_gradient_blocks{0};
 
 static std::atomic<int64_t>* knob(int what) {
   return what == 1   ? &g_uf_grid_min
@@ -52,6 +55,7 @@ static std::atomic<int64_t>* knob(int what) {
          : what == 5 ? &g_d1_grid_min
          : what == 6 ? &g_d1_handoff
          : what == 7 ? &g_d1_phase_a
+         : what == 8 ? &g_gradient_blocks
                      : nullptr;
 }
 
