@@ -126,6 +126,10 @@ typedef struct {
   int64_t d1_reduce_big_rounds; /* its rounds with at least 4096 active columns */
   int64_t d1_reduce_big_cycles; /* SM clock cycles spent in those rounds */
   int64_t d1_reduce_cycles;     /* SM clock cycles of the whole reduction */
+  int64_t d1_chain_adds;        /* additions chained in its short rounds (at most 64 active columns) */
+  int64_t d1_chain_longest;     /* ... by one column in one round, at most */
+  int64_t d1_chain_rounds;      /* its short rounds */
+  int64_t d1_chain_cycles;      /* SM clock cycles spent in those rounds */
 } tsf_stats;
 
 /* Creates a field from lx*ly*lz values (host or device memory, copied),
@@ -299,7 +303,11 @@ int64_t tsf_kernel_launches(void);
  *      warps per SM), 1 twice, 2 four times that (columns that outgrow them
  *      continue in the second phase), 3 the default tile without the cap;
  *   8: register budget of the lower-star gradient kernels, as blocks of
- *      128 threads per SM: 0 the default (6), 1 no cap, 2 five.
+ *      128 threads per SM: 0 the default (6), 1 no cap, 2 five;
+ *   9: entries of a column that the D1 reduction's short rounds (at most 64
+ *      active columns) keep in shared memory while they chain additions,
+ *      per group of 128 threads (default and maximum 1024; larger groups
+ *      scale it; longer sums, or all with 0, are added in the column pool).
  * Returns the previous value, or -1 for an unknown knob.  Set them only
  * while no call of this library is running. */
 int64_t tsf_debug_set(int what, int64_t value);

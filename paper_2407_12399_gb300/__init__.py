@@ -59,7 +59,9 @@ class tsf_stats(ctypes.Structure):
                 ("assign_phases", ctypes.c_int64), ("assign_checks", ctypes.c_int64),
                 ("d1_reduce_rounds", ctypes.c_int64), ("d1_reduce_merged", ctypes.c_int64),
                 ("d1_reduce_longest", ctypes.c_int64), ("d1_reduce_big_rounds", ctypes.c_int64),
-                ("d1_reduce_big_cycles", ctypes.c_int64), ("d1_reduce_cycles", ctypes.c_int64)]
+                ("d1_reduce_big_cycles", ctypes.c_int64), ("d1_reduce_cycles", ctypes.c_int64),
+                ("d1_chain_adds", ctypes.c_int64), ("d1_chain_longest", ctypes.c_int64),
+                ("d1_chain_rounds", ctypes.c_int64), ("d1_chain_cycles", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

@@ -46,6 +46,10 @@ std::atomic<int64_t> g_d1_phase_a{0};
 // blocks per SM the lower-star gradient kernels are compiled for: 0 the
 // default (six), 1 no register cap, 2 five
 std::atomic<int64_t> g_gradient_blocks{0};
+// entries of a column the D1 reduction's short rounds keep in shared memory
+// per warp while every warp is busy (at most 512, scaled up when fewer
+// warps share the buffers; 0: every chained addition runs in the pool)
+std::atomic<int64_t> g_chain_cap{512};
 
 static std::atomic<int64_t>* knob(int what) {
   return what == 1   ? &g_uf_grid_min
@@ -56,6 +60,7 @@ static std::atomic<int64_t>* knob(int what) {
          : what == 6 ? &g_d1_handoff
          : what == 7 ? &g_d1_phase_a
          : what == 8 ? &g_gradient_blocks
+         : what == 9 ? &g_chain_cap
                      : nullptr;
 }
 
@@ -1341,7 +1346,7 @@ __device__ uint32_t d1_warp_add(const unsigned long long* a, uint32_t n, const u
   return cap - 2u * common;
 }
 
-constexpr int kChainMax = 64;      // active columns up to which a round chains additions (one warp each)
+constexpr int kChainMax = 64;      // active columns up to which a round chains additions (one group each)
 constexpr int kChainSteps = 1 << 16;  // chained additions of one column in one round, at most
 constexpr uint32_t kLongAdd = 64;  // column additions at least this long run on a warp
 constexpr int kLongCap = 1024;     // ... at most this many per round (the rest on one thread)
@@ -1350,10 +1355,290 @@ __device__ __forceinline__ void d1_list_push(int32_t* next, int* n_next, int32_t
   if (atomicExch(&mark[j], round) != round) next[atomicAdd(n_next, 1)] = j;
 }
 
+// Chained additions of the short rounds in shared memory.  The block splits
+// into G groups of kUFT / G threads (G = 32 while more than 8 columns chain,
+// then 8, 4, 2, 1); a group keeps the column it reduces in shared memory
+// (32-bit entries: C1 indices are below 2^31) for up to kSubSteps
+// additions.  Each step loads only the owner's column (one coalesced read),
+// adds it to the group's copy there and writes the column back to the pool
+// when it stops.  Nobody else reads a column that does not own its low, so
+// the pool copy may lag behind until then.  The owner of the next low is
+// looked up while the group adds: the next low is the first entry of the
+// two columns that the other lacks, past the cancelled common top.  Columns
+// still chaining after kSubSteps additions go on in the next sub-round;
+// with fewer columns left, groups grow and their buffers with them.  A sum
+// longer than the group's buffers is added in the pool by its first warp
+// instead (d1_warp_add).
+constexpr int kCGroupsMax = kUFT / 32;                   // groups of one warp
+constexpr uint32_t kCBufWords = 49152;                   // 32-bit buffer entries of the block
+constexpr size_t kChainSmem = (size_t)kCBufWords * sizeof(uint32_t);
+constexpr int kSubSteps = 64;                            // chained additions of one column per sub-round
+constexpr uint32_t kCCap = kCBufWords / (3 * kCGroupsMax);  // entries per buffer with one warp per column (512)
+
+// Barrier of group g (gs threads): the warp itself, or named barrier g + 1
+// (groups of several warps: at most 8 of them).
+__device__ __forceinline__ void cg_bar(int g, int gs) {
+  if (gs == 32) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(gs) : "memory");
+}
+
+// d = a (n) + b (nb) over Z/2 by group g (gs threads), all in shared memory,
+// strictly decreasing.  Merge path: thread t walks positions [t*per,
+// (t+1)*per) of the merged order (ties: a first, so a common entry is a[i]
+// directly followed by b[j]); an entry is cancelled when the other column
+// holds it, which each thread sees from its neighbour in the walk (b[j] from
+// a[i-1], a[i] from b[j]).  A counting walk, a group scan (warp shuffles,
+// then one warp over the warp totals in wsum: gs / 32 + 1 ints), then the
+// writing walk.  Returns the length of d; the group sees d complete.
+__device__ uint32_t group_merge_add(const uint32_t* a, uint32_t n, const uint32_t* b, uint32_t nb, uint32_t* d,
+                                    int g, int gt, int gs, int* wsum) {
+  const int lane = gt & 31, w = gt >> 5, nw = gs >> 5;
+  const uint32_t N = n + nb, per = (N + (uint32_t)gs - 1) / (uint32_t)gs;
+  const uint32_t k0 = min(N, (uint32_t)gt * per), k1 = min(N, k0 + per);
+  // split: i = entries of a among the first k0 of the merged order
+  uint32_t lo = k0 > nb ? k0 - nb : 0u, hi = min(k0, n);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] >= b[k0 - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  const uint32_t i0 = lo, j0 = k0 - lo;
+  uint32_t cnt = 0, base = 0, total = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    uint32_t i = i0, j = j0, out = 0;
+    if (pass == 1) {
+      uint32_t inc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      if (nw == 1) {
+        total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+      } else {
+        if (lane == 31) wsum[w] = (int)inc;
+        cg_bar(g, gs);
+        if (w == 0) {
+          const uint32_t v = lane < nw ? (uint32_t)wsum[lane] : 0u;
+          uint32_t vi = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, vi, o);
+            if (lane >= o) vi += t;
+          }
+          if (lane < nw) wsum[lane] = (int)(vi - v);
+          if (lane == 31) wsum[nw] = (int)vi;
+        }
+        cg_bar(g, gs);
+        base = (uint32_t)wsum[w];
+        total = (uint32_t)wsum[nw];
+      }
+      out = base + inc - cnt;
+    }
+    uint32_t ai = i < n ? a[i] : 0u, bj = j < nb ? b[j] : 0u, ap = i > 0 ? a[i - 1] : 0xFFFFFFFFu;
+    for (uint32_t k = k0; k < k1; ++k) {
+      bool cancel;
+      uint32_t v;
+      if (i < n && (j >= nb || ai >= bj)) {
+        v = ai;
+        cancel = j < nb && ai == bj;
+        ap = ai;
+        ++i;
+        ai = i < n ? a[i] : 0u;
+      } else {
+        v = bj;
+        cancel = i > 0 && ap == bj;
+        ++j;
+        bj = j < nb ? b[j] : 0u;
+      }
+      if (!cancel) {
+        if (pass == 1) d[out] = v;
+        ++out;
+      }
+    }
+    if (pass == 0) cnt = out;
+  }
+  cg_bar(g, gs);  // d complete; wsum free again
+  return total;
+}
+
+// Writes the group's copy of column j (n entries) to fresh pool space;
+// false when the pool is full (the status word says so).
+__device__ bool cg_write_back(D1Work& W, int j, const uint32_t* col, uint32_t n, int g, int gt, int gs, int* ctl,
+                              uint32_t* status) {
+  if (gt == 0) {
+    const uint32_t off = atomicAdd(W.pool_head, n);
+    const bool ok = (unsigned long long)off + n <= W.pool_cap;
+    if (!ok) atomicOr(status, kErrPool);
+    ctl[3] = ok ? (int)off : -1;
+  }
+  cg_bar(g, gs);
+  const int off = ctl[3];
+  if (off >= 0) {
+    for (uint32_t i = gt; i < n; i += (uint32_t)gs) W.pool[(uint32_t)off + i] = col[i];
+    if (gt == 0) {
+      W.hoff[j] = (uint32_t)off;
+      W.hsize[j] = n;
+    }
+  }
+  cg_bar(g, gs);
+  return off >= 0;
+}
+
+// ctl[0..2] = the owner of a low (as the group leader loaded its index and
+// {index, pool offset, length} record), its column's offset and length.
+__device__ __forceinline__ void cg_publish(const D1Work& W, int j, int o, const uint4& r, int* ctl, uint32_t* status) {
+  // an owner writes its record before it is read, and its column lies in the pool
+  if (o != j && o != 0x7FFFFFFF && o < j &&
+      (r.x != (uint32_t)o || r.z == 0u || (unsigned long long)r.y + r.z > W.pool_cap)) {
+    atomicOr(status, kErrInconsistent);
+    o = j;
+  }
+  ctl[0] = o;
+  ctl[1] = (int)r.z;
+  ctl[2] = (int)r.y;
+}
+
+// Up to kSubSteps chained additions of column j by group g (gs threads);
+// buf holds its three buffers of cap entries.  Returns true when the column
+// is still chaining (it goes on in the next sub-round); adds = the additions
+// made.
+__device__ bool cg_chain(D1Work& W, int n1, int j, int round, uint32_t* buf, uint32_t cap, int g, int gt, int gs,
+                         int* wsum, int* ctl, int32_t* nxt, int* s_nb, int32_t* mark, int& adds, uint32_t* status) {
+  uint32_t* A = buf;
+  uint32_t* B = buf + cap;
+  uint32_t* D = buf + 2 * (size_t)cap;
+  uint32_t n = W.hsize[j];
+  bool in_smem = false, dirty = false, more = false;
+  adds = 0;
+  if (n == 0 || (unsigned long long)W.hoff[j] + n > W.pool_cap) {  // a listed column is never empty
+    if (gt == 0) atomicOr(status, kErrInconsistent);
+    return false;
+  }
+  if (n <= cap) {
+    const unsigned long long* a = W.pool + W.hoff[j];
+    for (uint32_t i = gt; i < n; i += (uint32_t)gs) A[i] = (uint32_t)a[i];
+    in_smem = true;
+  }
+  cg_bar(g, gs);
+  if (gt == 0) {
+    const uint32_t low = in_smem ? A[0] : (uint32_t)W.pool[W.hoff[j]];
+    if (low < (uint32_t)n1) {
+      cg_publish(W, j, W.owner[low], W.orec[low], ctl, status);
+    } else {
+      atomicOr(status, kErrInconsistent);
+      ctl[0] = j;
+    }
+  }
+  cg_bar(g, gs);
+  for (int step = 0;; ++step) {
+    const int o = ctl[0];
+    const uint32_t no = (uint32_t)ctl[1], ob = (uint32_t)ctl[2];
+    if (o == j) break;
+    if (o == 0x7FFFFFFF || o > j) {
+      if (gt == 0) d1_list_push(nxt, s_nb, mark, j, round);
+      break;
+    }
+    if (step >= kSubSteps) {
+      more = true;
+      break;
+    }
+    const uint32_t sum = n + no;
+    uint32_t m;
+    if (in_smem && sum <= cap) {
+      const unsigned long long* b = W.pool + ob;
+      for (uint32_t i = gt; i < no; i += (uint32_t)gs) B[i] = (uint32_t)b[i];
+      cg_bar(g, gs);  // B loaded; every thread has read ctl
+      // the leader finds the next low and loads its owner while the group adds
+      int o_next = j;
+      uint4 r_next = make_uint4(0u, 0u, 0u, 0u);
+      uint32_t nl = 0;
+      if (gt == 0) {
+        uint32_t x = 1, y = 1;
+        while (x < n && y < no && A[x] == B[y]) {
+          ++x;
+          ++y;
+        }
+        if (x < n || y < no) {  // else the sum is empty: stop (reported below)
+          nl = (y >= no || (x < n && A[x] > B[y])) ? A[x] : B[y];
+          if (nl < (uint32_t)n1) {
+            o_next = W.owner[(int)nl];
+            r_next = W.orec[(int)nl];
+          }
+        }
+      }
+      m = group_merge_add(A, n, B, no, D, g, gt, gs, wsum);
+      if (gt == 0) {
+        if (m > 0 && (D[0] != nl || A[0] != B[0] || nl >= (uint32_t)n1)) {  // the sum's low is the one looked up
+          atomicOr(status, kErrInconsistent);
+          o_next = j;
+        }
+        cg_publish(W, j, o_next, r_next, ctl, status);
+      }
+      cg_bar(g, gs);
+      uint32_t* t = A;
+      A = D;
+      D = t;
+      dirty = true;
+    } else {
+      if (in_smem && dirty && !cg_write_back(W, j, A, n, g, gt, gs, ctl, status)) return false;
+      in_smem = false;
+      dirty = false;
+      if (gt < 32) {
+        uint32_t off = 0;
+        if (gt == 0) off = atomicAdd(W.pool_head, sum);
+        off = __shfl_sync(0xFFFFFFFFu, off, 0);
+        if ((unsigned long long)off + sum > W.pool_cap) {
+          if (gt == 0) {
+            atomicOr(status, kErrPool);
+            ctl[3] = -1;
+          }
+        } else {
+          const uint32_t mm = d1_warp_add(W.pool + W.hoff[j], n, W.pool + ob, no, W.pool + off, status);
+          if (gt == 0) {
+            W.hoff[j] = off;
+            W.hsize[j] = mm;
+            ctl[3] = (int)mm;
+          }
+        }
+      }
+      cg_bar(g, gs);
+      if (ctl[3] < 0) return false;  // the pool is full: the status word says so
+      m = (uint32_t)ctl[3];
+      cg_bar(g, gs);  // every thread has read ctl[3]
+      if (m > 0 && m <= cap) {  // back into shared memory
+        const unsigned long long* a = W.pool + W.hoff[j];
+        for (uint32_t i = gt; i < m; i += (uint32_t)gs) A[i] = (uint32_t)a[i];
+        in_smem = true;
+      }
+      if (gt == 0 && m > 0) {
+        const uint32_t low = (uint32_t)W.pool[W.hoff[j]];
+        if (low < (uint32_t)n1) {
+          cg_publish(W, j, W.owner[low], W.orec[low], ctl, status);
+        } else {
+          atomicOr(status, kErrInconsistent);
+          ctl[0] = j;
+        }
+      }
+      cg_bar(g, gs);
+    }
+    n = m;
+    ++adds;
+    if (gt == 0) {
+      atomicAdd(&W.stats[6], (unsigned long long)m);
+      atomicMax(&W.stats[7], (unsigned long long)m);
+      if (m == 0) atomicOr(status, kErrEmptyColumn);
+    }
+    if (m == 0) break;
+  }
+  if (in_smem && dirty) cg_write_back(W, j, A, n, g, gt, gs, ctl, status);
+  return more;
+}
+
 // `ctl` (may be null): resume after k_d1_reduce_grid from its lists, owners
 // and marks.
 __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d1_edge, const D1Ctl* ctl,
-                                                    uint32_t* status) {
+                                                    uint32_t ccap, uint32_t* status) {
   const int ncols = W.flags[1];
   // free per-column scratch by now: two lists and a "listed in round" mark
   int32_t* listA = W.lowc;
@@ -1361,6 +1646,10 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
   int32_t* mark = W.redo;
   __shared__ int s_na, s_nb, s_nlong;
   __shared__ int32_t s_long[kLongCap];
+  __shared__ int32_t s_sub[2][kChainMax], s_subn[2][kChainMax];
+  __shared__ int s_cg[kCGroupsMax][4];
+  __shared__ int s_wsum[2 * kCGroupsMax];
+  __shared__ int s_nsub;
   int32_t* cur = listA;
   int32_t* nxt = listB;
   int round0 = 0;
@@ -1375,6 +1664,8 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
     if (threadIdx.x == 0) s_na = ctl->n[ctl->which];
     round0 = ctl->rounds;
   } else {
+    // an earlier stage failed (its results are discarded): nothing to reduce
+    if (*reinterpret_cast<const volatile uint32_t*>(status) & (kErrSpin | kErrRounds | kErrPool | kErrTrace)) return;
     for (int k = threadIdx.x; k < n1; k += kUFT) W.owner[k] = 0x7FFFFFFF;
     if (threadIdx.x == 0) s_na = 0;
     __syncthreads();
@@ -1406,51 +1697,68 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
     }
     __syncthreads();
     if (na <= kChainMax) {
-      // short list: one warp per column, chained additions.  During this
+      // short list: chained additions by groups of threads, in sub-rounds
+      // (in shared memory while a sum fits the group's buffers).  During this
       // phase every owner owns its low and does not change (a column that
       // does not own its low holds no owner entry), so after adding its
       // owner a column may go on adding the owner of its new low while that
       // owner is an earlier column: each step is still a left-to-right
       // addition.  It stops when it owns its low, or the low's owner is
       // later or absent (it claims the low next round).
-      const int lane = threadIdx.x & 31;
-      for (int q = threadIdx.x >> 5; q < na; q += kUFT / 32) {
-        const int j = cur[q];
-        for (int step = 0;; ++step) {
-          const uint32_t n = W.hsize[j];
-          const unsigned long long* a = W.pool + W.hoff[j];
-          const int o = W.owner[(int)a[0]];
-          if (o == j) break;
-          if (o == 0x7FFFFFFF || o > j || step >= kChainSteps) {
-            if (lane == 0) d1_list_push(nxt, &s_nb, mark, j, round);
-            break;
-          }
-          const uint32_t no = W.hsize[o];
-          const unsigned long long* b = W.pool + W.hoff[o];
-          const uint32_t cap = n + no;
-          uint32_t off = 0;
-          if (lane == 0) off = atomicAdd(W.pool_head, cap);
-          off = __shfl_sync(0xFFFFFFFFu, off, 0);
-          if ((unsigned long long)off + cap > W.pool_cap) {
-            if (lane == 0) atomicOr(status, kErrPool);
-            break;
-          }
-          const uint32_t m = d1_warp_add(a, n, b, no, W.pool + off, status);
-          if (lane == 0) {
-            W.hoff[j] = off;
-            W.hsize[j] = m;
-            atomicAdd(&W.stats[6], (unsigned long long)m);
-            atomicMax(&W.stats[7], (unsigned long long)m);
-            if (m == 0) atomicOr(status, kErrEmptyColumn);
-          }
-          __syncwarp();
-          if (m == 0) break;
+      extern __shared__ __align__(16) uint32_t chain_buf[];
+      // owner records of this round's new owners, before any column reads one
+      for (int i = threadIdx.x; i < na; i += kUFT) {
+        const int j = cur[i];
+        const int low = (int)W.pool[W.hoff[j]];
+        if (W.owner[low] == j) W.orec[low] = make_uint4((uint32_t)j, W.hoff[j], W.hsize[j], 0u);
+      }
+      for (int i = threadIdx.x; i < na; i += kUFT) {
+        s_sub[0][i] = cur[i];
+        s_subn[0][i] = 0;
+      }
+      if (threadIdx.x == 0) s_nsub = na;
+      __syncthreads();
+      for (int sub = 0, which = 0;; ++sub, which ^= 1) {
+        const int ns = s_nsub;
+        if (ns == 0) break;
+        __syncthreads();  // every thread has read s_nsub
+        if (sub >= kChainSteps / kSubSteps) {  // bounded: the rest claim their lows next round
+          for (int i = threadIdx.x; i < ns; i += kUFT) d1_list_push(nxt, &s_nb, mark, s_sub[which][i], round);
+          break;
         }
+        if (threadIdx.x == 0) s_nsub = 0;
+        __syncthreads();
+        // groups: one warp per column while more than 8 columns are left,
+        // then the next power of two of the columns left
+        const int G = ns > 8 ? kCGroupsMax : ns > 4 ? 8 : ns > 2 ? 4 : ns;
+        const int gs = kUFT / G, g = threadIdx.x / gs, gt = threadIdx.x % gs;
+        const uint32_t gbuf = kCBufWords / (3u * (uint32_t)G);
+        const uint32_t cap = min(gbuf, ccap * (uint32_t)(kCGroupsMax / G));
+        for (int q = g; q < ns; q += G) {
+          int adds = 0;
+          const int j = s_sub[which][q];
+          const bool more = cg_chain(W, n1, j, round, chain_buf + (size_t)g * 3 * gbuf, cap, g, gt, gs,
+                                     s_wsum + g * ((gs >> 5) + 1), s_cg[g], nxt, &s_nb, mark, adds, status);
+          if (gt == 0) {
+            const int total = s_subn[which][q] + adds;
+            atomicAdd(&W.stats[11], (unsigned long long)adds);
+            if (more) {
+              const int k = atomicAdd(&s_nsub, 1);
+              s_sub[which ^ 1][k] = j;
+              s_subn[which ^ 1][k] = total;
+            } else {
+              atomicMax(&W.stats[12], (unsigned long long)total);
+            }
+          }
+        }
+        __syncthreads();
       }
       __syncthreads();
       if (threadIdx.x == 0) {
         s_na = s_nb;
         W.stats[5] = (unsigned long long)(round + 1);
+        W.stats[13] += 1;  // short rounds and their cycles
+        W.stats[14] += (unsigned long long)(clock64() - c_round);
       }
       int32_t* t = cur;
       cur = nxt;
@@ -1463,7 +1771,10 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
       uint32_t n = W.hsize[j];
       const unsigned long long* a = W.pool + W.hoff[j];
       int o = W.owner[(int)a[0]];
-      if (o == j) continue;
+      if (o == j) {  // owns its low: its record for the short rounds
+        W.orec[(int)a[0]] = make_uint4((uint32_t)j, W.hoff[j], n, 0u);
+        continue;
+      }
       uint32_t no = W.hsize[o];
       if (n + no >= kLongAdd) {  // long: one warp adds it below
         const int q = atomicAdd(&s_nlong, 1);
@@ -1578,7 +1889,7 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   c.d0mask = P.d0mask;
   c.f = f;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
-  cudaMemsetAsync(W.stats, 0, 12 * sizeof(unsigned long long), st);
+  cudaMemsetAsync(W.stats, 0, kD1Stats * sizeof(unsigned long long), st);
   cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
   size_t sb = d1_group_smem(kFrontB, kStageB);
   int dev = 0;
@@ -1639,6 +1950,9 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce_grid(D1Work W, int n1, D1Ctl
   const unsigned nb = gridDim.x;
   const int gt = blockIdx.x * kUFT + threadIdx.x, gn = nb * kUFT;
   const long long c_start = clock64();
+  // an earlier stage failed (its results are discarded): every block returns
+  // before the first barrier, and the resuming block sees the same bits
+  if (*reinterpret_cast<const volatile uint32_t*>(status) & (kErrSpin | kErrRounds | kErrPool | kErrTrace)) return;
   for (int k = gt; k < n1; k += gn) W.owner[k] = 0x7FFFFFFF;
   for (int j = gt; j < ncols; j += gn) {
     mark[j] = -1;
@@ -1669,7 +1983,10 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce_grid(D1Work W, int n1, D1Ctl
       const uint32_t n = __ldcg(&W.hsize[j]);
       const unsigned long long* a = W.pool + __ldcg(&W.hoff[j]);
       const int o = __ldcg(&W.owner[(int)__ldcg(a)]);
-      if (o == j) continue;
+      if (o == j) {  // owns its low: its record for the short rounds
+        W.orec[(int)__ldcg(a)] = make_uint4((uint32_t)j, __ldcg(&W.hoff[j]), n, 0u);
+        continue;
+      }
       const uint32_t no = __ldcg(&W.hsize[o]);
       if (n + no >= kLongAdd) {  // long: one warp of this block adds it below
         const int q = atomicAdd(&s_nlong, 1);
@@ -1756,6 +2073,14 @@ static_assert(sizeof(UfCtl) <= 64 && sizeof(D1Ctl) <= 64, "control blocks share 
 
 void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, D1Ctl* ctl, cudaStream_t st) {
   if (n2 == 0) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::atomic<bool> attr[64] = {};
+  if (dev >= 0 && dev < 64 && !attr[dev].load(std::memory_order_acquire)) {
+    cudaFuncSetAttribute(k_d1_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmem);
+    attr[dev].store(true, std::memory_order_release);
+  }
+  const uint32_t ccap = (uint32_t)std::min<int64_t>(std::max<int64_t>(g_chain_cap.load(), 0), kCCap);
   const int nb = n2 >= g_d1_grid_min.load() ? cooperative_blocks((const void*)k_d1_reduce_grid, kUFT) : 0;
   if (nb > 0) {
     cudaMemsetAsync(ctl, 0, sizeof(D1Ctl), st);
@@ -1763,12 +2088,12 @@ void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, D
     unsigned limit = (unsigned)std::min<int64_t>(std::max<int64_t>(g_barrier_limit.load(), 1), 1u << 30);
     void* args[] = {&W, &n1, &ctl, &handoff, &limit, &status};
     if (cooperative_launch((const void*)k_d1_reduce_grid, dim3(nb), dim3(kUFT), args, st) == cudaSuccess) {
-      k_d1_reduce<<<1, kUFT, 0, st>>>(W, n1, P.d1_edge, ctl, status); note_launch();
+      k_d1_reduce<<<1, kUFT, kChainSmem, st>>>(W, n1, P.d1_edge, ctl, ccap, status); note_launch();
       return;
     }
     cudaGetLastError();  // not launched: the single block does every round
   }
-  k_d1_reduce<<<1, kUFT, 0, st>>>(W, n1, P.d1_edge, nullptr, status); note_launch();
+  k_d1_reduce<<<1, kUFT, kChainSmem, st>>>(W, n1, P.d1_edge, nullptr, ccap, status); note_launch();
 }
 
 }  // namespace tsf

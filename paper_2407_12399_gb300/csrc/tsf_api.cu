@@ -101,7 +101,7 @@ struct tsf_field {
   double loss = 0, loss0 = 0;
   unsigned long long counts[4] = {0, 0, 0, 0};
   int64_t n_updated = 0, n_gradient = 0;
-  unsigned long long d1_stats[11] = {};
+  unsigned long long d1_stats[15] = {};
   int d1_cols = 0;
   int32_t* h_flags = nullptr;  // pinned
   double ms_diag = 0, ms_assign = 0, ms_step = 0;
@@ -163,11 +163,13 @@ void grow_crit(tsf_field* F, int n0, int n1, int n2, int n3) {
     dev_free(F->PO.d0_min);
     dev_free(F->PO.d0_killed);
     dev_free(F->W.owner);
+    dev_free(F->W.orec);
     ck(dev_alloc(&F->L.c1_key, c1));
     ck(dev_alloc(&F->L.c1_vn, c1));
     ck(dev_alloc(&F->PO.d0_min, c1));
     ck(dev_alloc(&F->PO.d0_killed, c1));
     ck(dev_alloc(&F->W.owner, c1));
+    ck(dev_alloc(&F->W.orec, c1));
     F->cap_c1 = c1;
   }
   if (c2 != F->cap_c2) {
@@ -491,7 +493,7 @@ int compute_diagram(tsf_field* F, bool incremental) {
     F->W.pool_cap = F->pool_cap;
     if (!F->W.pool_head) ck(dev_alloc(&F->W.pool_head, 1));
     if (!F->W.flags) ck(dev_alloc(&F->W.flags, 4));
-    if (!F->W.stats) ck(dev_alloc(&F->W.stats, 12));
+    if (!F->W.stats) ck(dev_alloc(&F->W.stats, kD1Stats));
     if (attempt > 0) ck(cudaMemsetAsync(F->status, 0, 4, st));
     stage_begin(F, kD1);
     launch_d1_prepare(F->n2, F->W, F->PO, st);
@@ -587,6 +589,10 @@ void fill_stats(tsf_field* F, const tsf_params* p, tsf_stats* out, int done) {
   out->d1_reduce_big_rounds = (int64_t)F->d1_stats[8];
   out->d1_reduce_big_cycles = (int64_t)F->d1_stats[9];
   out->d1_reduce_cycles = (int64_t)F->d1_stats[10];
+  out->d1_chain_adds = (int64_t)F->d1_stats[11];
+  out->d1_chain_longest = (int64_t)F->d1_stats[12];
+  out->d1_chain_rounds = (int64_t)F->d1_stats[13];
+  out->d1_chain_cycles = (int64_t)F->d1_stats[14];
   out->ms_diagram = F->ms_diag;
   out->ms_assign = F->ms_assign;
   out->assign_rounds = F->assign_rounds;
@@ -769,6 +775,7 @@ int tsf_destroy_field(tsf_field* F) {
   dev_free(F->W.hsize);
   dev_free(F->W.lowc);
   dev_free(F->W.owner);
+  dev_free(F->W.orec);
   dev_free(F->W.pool);
   dev_free(F->W.pool_head);
   dev_free(F->W.flags);

@@ -121,6 +121,15 @@ struct D1Ctl {
   int pad[10];
 };
 
+// Counters of the D1 stages (D1Work::stats): [0] lower stars visited, [1]
+// by the largest column, [2] rounds over all columns, [3] of the longest,
+// [4] target-star updates, [5] reduction rounds, [6] entries merged, [7]
+// longest sum, [8] whole-GPU rounds, [9] their cycles, [10] all cycles of
+// the reduction, [11] chained additions of the short rounds, [12] the
+// longest chain of one column in one round, [13] short rounds, [14] their
+// cycles.
+constexpr int kD1Stats = 16;
+
 struct D1Work {
   int32_t* cols;          // candidate triangle index per column
   unsigned long long* low;  // current low per column (0 = to be recomputed)
@@ -129,6 +138,7 @@ struct D1Work {
   uint32_t* hsize;        // heap size
   int32_t* lowc;          // critical edge index of the low
   int32_t* owner;         // per critical edge: smallest column holding it as low
+  uint4* orec;            // ... and that column's {index, pool offset, length} while it owns it
   unsigned long long* pool;
   uint32_t pool_cap;
   uint32_t* pool_head;

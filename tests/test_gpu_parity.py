@@ -329,7 +329,8 @@ def test_auction_with_explicit_targets_matches_oracle():
 def _knobs(**kw):
     """Sets union-find knobs (tsf_debug_set) and returns a restorer."""
     import paper_2407_12399_gb300 as tsf
-    ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4, "d1_grid_min": 5, "d1_handoff": 6}
+    ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4, "d1_grid_min": 5, "d1_handoff": 6,
+           "chain_cap": 9}
     old = {k: tsf.tsf_debug_set(ids[k], v) for k, v in kw.items()}
     return lambda: [tsf.tsf_debug_set(ids[k], v) for k, v in old.items()]
 
@@ -342,6 +343,22 @@ def test_pairing_rounds_over_the_whole_gpu_match_the_oracle(name, handoff):
     then one block finishes the rounds below `handoff` active items: the
     same diagram as the oracle."""
     restore = _knobs(grid_min=0, handoff=handoff, d1_grid_min=0, d1_handoff=handoff)
+    try:
+        f = NAMED[name]()
+        got = gpu_rows(gpu_field(f).diagram())
+    finally:
+        restore()
+    assert got == oracle_rows(f, oracle.diagram(f)["pairs"])
+
+
+@pytest.mark.parametrize("chain_cap", [0, 4, 24])
+@pytest.mark.parametrize("name", ["filament_40", "filament_64", "ring_21"])
+def test_chained_d1_additions_in_shared_memory_or_the_pool_match_the_oracle(name, chain_cap):
+    """The D1 reduction's short rounds chain column additions in shared
+    memory while a sum fits the buffer and in the column pool otherwise;
+    tiny buffers (and none) force every mix of the two paths on one column:
+    the same diagram as the oracle."""
+    restore = _knobs(chain_cap=chain_cap)
     try:
         f = NAMED[name]()
         got = gpu_rows(gpu_field(f).diagram())
