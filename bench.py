@@ -243,7 +243,7 @@ def batched_solve(prec=0.01, converge_tau=0.025):
             x.close()
         return t
 
-    # the batch autotuner picks the D1 phase-A tile on these fields' own
+    # the batch autotuner picks the D1 phase-A schedule on these fields' own
     # diagrams (process-wide choice; results never depend on it)
     bt = tsf.Batch(dev)
     choice, tune_ms = bt.autotune()
@@ -277,7 +277,8 @@ def batched_solve(prec=0.01, converge_tau=0.025):
                for i in range(len(fields)) if i not in sub]
     tsf.tsf_debug_set(7, 0)
     return {"workload": "uneven_batch_48", "fields": len(fields), "voxels": vox, "assignment_precision": prec,
-            "autotune": {"tiles": ["64+128", "128+256", "256+512"], "diagram_ms": tune_ms, "chosen": choice},
+            "autotune": {"candidates": ["half warp 32+64", "half warp 64+128", "quarter warp 16+32", "warp 64+128"],
+                         "diagram_ms": tune_ms, "chosen": choice},
             "first_iteration": {"batch_s": tb, "one_at_a_time_s": tl, "speedup": tl / tb,
                                 "field_iterations_per_s": len(fields) / tb, "device_gb": gb},
             "to_simplified_field": {"fields": len(sub), "threshold_min": converge_tau, "batch_s": tcb,

@@ -228,14 +228,16 @@ int tsf_batch_step(tsf_batch* batch, const tsf_params* params, tsf_stats* stats)
 int tsf_batch_simplify(tsf_batch* batch, const tsf_params* params, tsf_stats* stats);
 /* Autotuner of the batch (not in the paper): times the full persistence
  * diagram of every field (all fields concurrently, each candidate twice,
- * the second pass counted) for each candidate tile of the D1 Morse
- * boundaries' first phase — 64 + 128, 128 + 256 or 256 + 512 frontier and
- * stage entries per column (tsf_debug_set knob 7) — and keeps the fastest.
- * The choice applies process-wide; results never depend on it.  *choice
- * receives it (0, 1, 2), ms[c] (cap entries, may be NULL when cap is 0) the
- * time of candidate c in milliseconds.  Call it before the signal
- * thresholds are set (it replaces each field's current diagram): TSF_EINVAL
- * if a field has a target diagram. */
+ * the second pass counted) for each candidate schedule of the D1 Morse
+ * boundaries' first phase — 0: half a warp per column with 32 + 64
+ * frontier and stage entries, 1: half a warp with 64 + 128, 2: a quarter of
+ * a warp with 16 + 32, 3: one warp with 64 + 128 (tsf_debug_set knob 7
+ * values 0, 5, 6, 4) — and keeps the fastest.  The choice applies
+ * process-wide; results never depend on it.  *choice receives it (0..3),
+ * ms[c] (cap entries, may be NULL when cap is 0) the time of candidate c in
+ * milliseconds.  Call it before the signal thresholds are set (it replaces
+ * each field's current diagram): TSF_EINVAL if a field has a target
+ * diagram. */
 int tsf_batch_autotune(tsf_batch* batch, int* choice, double* ms, int cap);
 
 /* Overwrites the current values (restart from a saved field; the still-pair
@@ -298,10 +300,13 @@ int64_t tsf_kernel_launches(void);
  *   5: D1 columns from which the reduction rounds run over the whole GPU
  *      (default 65536);
  *   6: active D1 columns below which one block finishes them (default 4096);
- *   7: shared-memory buffers per column of the D1 Morse boundaries' first
- *      phase: 0 the default (64 + 128 entries, registers capped for 32
- *      warps per SM), 1 twice, 2 four times that (columns that outgrow them
- *      continue in the second phase), 3 the default tile without the cap;
+ *   7: schedule of the D1 Morse boundaries' first phase: 0 the default
+ *      (half a warp per column, 32 + 64 frontier and stage entries, registers
+ *      capped for 32 warps per SM), 1 and 2 one warp per column with 128 +
+ *      256 and 256 + 512 entries, 3 one warp with 64 + 128 without the
+ *      register cap, 4 the same with it, 5 half a warp with 64 + 128, 6 a
+ *      quarter of a warp with 16 + 32 (columns that outgrow their buffers
+ *      continue in the second phase);
  *   8: register budget of the lower-star gradient kernels, as blocks of
  *      128 threads per SM: 0 the default (6), 1 no cap, 2 five;
  *   9: entries of a column that the D1 reduction's short rounds (at most 64

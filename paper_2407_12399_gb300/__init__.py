@@ -293,8 +293,8 @@ def tsf_batch_simplify(h, params, n):
     return [s.as_dict() for s in st]
 
 
-def tsf_batch_autotune(h, ncand=3):
-    """Chooses the D1 phase-A tile for the batch; returns (choice, ms per candidate)."""
+def tsf_batch_autotune(h, ncand=4):
+    """Chooses the D1 phase-A schedule for the batch; returns (choice, ms per candidate)."""
     c = ctypes.c_int(0)
     ms = np.zeros(ncand, np.float64)
     _check(lib().tsf_batch_autotune(h, ctypes.byref(c), ms.ctypes.data, ncand), "tsf_batch_autotune")

@@ -39,9 +39,10 @@ std::atomic<int64_t> g_barrier_limit{1 << 24};
 // whole GPU, active columns below which one block finishes them
 std::atomic<int64_t> g_d1_grid_min{1 << 16};
 std::atomic<int64_t> g_d1_handoff{1 << 12};
-// shared-memory buffers of the D1 Morse boundaries' phase A: 0 the default
-// (64 frontier + 128 stage entries per column, registers capped for 32
-// warps per SM), 1 twice, 2 four times that, 3 the default without the cap
+// schedule of the D1 Morse boundaries' phase A: 0 the default (half a warp
+// per column, 32 frontier + 64 stage entries), 1 and 2 one warp with 128 +
+// 256 and 256 + 512, 3 one warp with 64 + 128 uncapped, 4 capped, 5 half a
+// warp with 64 + 128, 6 a quarter of a warp with 16 + 32
 std::atomic<int64_t> g_d1_phase_a{0};
 // blocks per SM the lower-star gradient kernels are compiled for: 0 the
 // default (six), 1 no register cap, 2 five
@@ -914,24 +915,24 @@ __device__ __forceinline__ bool d1_visit(const D1Ctx& c, FEnt fe, const int32_t*
 // two): in registers for up to two entries per thread (the usual case),
 // else in shared memory (compact code: the unrolled networks for more
 // entries per thread only crowd the instruction cache).
-template <int NT, int SCAP>
+template <int GS, int SCAP>
 __device__ void group_sort_stage(FEnt* a, int n) {
-  static_assert(SCAP % NT == 0 && (SCAP & (SCAP - 1)) == 0, "a stage is a power of two");
-  if (n <= NT) group_sort_reg<NT, 1>(a, n);
-  else if (n <= 2 * NT && SCAP >= 2 * NT) group_sort_reg<NT, (SCAP >= 2 * NT ? 2 : 1)>(a, n);
-  else group_sort_smem<NT>(a, n);
+  static_assert(SCAP % GS == 0 && (SCAP & (SCAP - 1)) == 0, "a stage is a power of two");
+  if (n <= GS) group_sort_reg<GS, 1>(a, n);
+  else if (n <= 2 * GS && SCAP >= 2 * GS) group_sort_reg<GS, (SCAP >= 2 * GS ? 2 : 1)>(a, n);
+  else group_sort_smem<GS>(a, n);
 }
 
 // New frontier from the untaken rest (front[nb..nf), descending) and the
 // stage (ntot updates, any order): sort the stage, merge, combine equal keys.
 // Returns the new frontier size.  All threads of the group call it.
-template <int NT, int SCAP>
+template <int GS, int SCAP>
 __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* stage, int ntot, int* scan_sm) {
-  const int tid = threadIdx.x;
+  const int tid = gtid<GS>();
   int rest = nf - nb;
-  group_sort_stage<NT, SCAP>(stage, ntot);
+  group_sort_stage<GS, SCAP>(stage, ntot);
   int total = rest + ntot;
-  for (int k = tid; k < total; k += NT) {  // merge path
+  for (int k = tid; k < total; k += GS) {  // merge path
     int lo = max(0, k - ntot), hi = min(k, rest);
     while (lo < hi) {
       int mid = (lo + hi) >> 1;
@@ -941,9 +942,9 @@ __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* sta
     int i = lo, jb = k - lo;
     other[k] = (i < rest && (jb >= ntot || front[nb + i].key >= stage[jb].key)) ? front[nb + i] : stage[jb];
   }
-  gsync<NT>();
+  gsync<GS>();
   int kept = 0;
-  for (int base = 0; base < total; base += NT) {
+  for (int base = 0; base < total; base += GS) {
     int k = base + tid;
     int keep = 0;
     FEnt e;
@@ -958,11 +959,11 @@ __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* sta
       }
     }
     int t;
-    int off = gscan<NT>(keep, t, scan_sm);
+    int off = gscan<GS>(keep, t, scan_sm);
     if (keep) front[kept + off] = e;
     kept += t;
   }
-  gsync<NT>();
+  gsync<GS>();
   return kept;
 }
 
@@ -973,32 +974,45 @@ __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* sta
 // every round more than they shorten the longest column.)
 constexpr int kChain = 2, kOutCap = 28, kRoundsA = 16;
 
-// Round loop of one column.  Phase A (NT = 32, max_rounds > 0): every column,
-// one warp; a column still open after max_rounds, or whose frontier outgrows
-// the warp's buffers, saves its entries and is listed for phase B (NT = 128,
-// one block per listed column).
-template <int NT, int FCAP, int SCAP, int MINB = (NT == 32 ? 12 : 4)>
+// Round loop of one column.  Phase A (max_rounds > 0): every column, one
+// group of GS threads (a half or a whole warp; NT / GS columns per block);
+// a column still open after max_rounds, or whose frontier outgrows the
+// group's buffers, saves its entries and is listed for phase B (NT = GS =
+// 128, one block per listed column).  Groups of one block share nothing
+// but the neighbour offsets and synchronise only among themselves.
+template <int NT, int FCAP, int SCAP, int MINB = (NT == 32 ? 12 : 4), int GS = NT>
 __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, int max_rounds, uint32_t* status) {
+  static_assert(GS == NT || (NT == 32 && GS < 32), "several groups only within one warp");
+  constexpr int G = NT / GS;
   const int ncols = W.flags[1];
+  const int gi = (int)threadIdx.x / GS;
   extern __shared__ __align__(16) unsigned char smem[];
-  FEnt* front = reinterpret_cast<FEnt*>(smem);
+  FEnt* front = reinterpret_cast<FEnt*>(smem) + (size_t)gi * (2 * FCAP + SCAP);
   FEnt* other = front + FCAP;
   FEnt* stage = other + FCAP;
   __shared__ int32_t snd[16];
-  __shared__ int scan_sm[16];  // NT/32 + 1 <= 16
-  __shared__ int s_nf, s_flag, s_ntot, s_otot;
-  __shared__ Vec s_out, s_grow;
+  __shared__ int scan_sm[16];  // GS/32 + 1 <= 16 (blocks only)
+  __shared__ int sg_nf[G], sg_flag[G], sg_ntot[G], sg_otot[G];
+  __shared__ Vec sg_out[G], sg_grow[G], sg_fr[G], sg_fr2[G];
+  int& s_nf = sg_nf[gi];
+  int& s_flag = sg_flag[gi];
+  int& s_ntot = sg_ntot[gi];
+  int& s_otot = sg_otot[gi];
+  Vec& s_out = sg_out[gi];
+  Vec& s_grow = sg_grow[gi];
   if (threadIdx.x < 14) snd[threadIdx.x] = c.nd.d[threadIdx.x];
+  if (NT > 32) __syncthreads();
+  else __syncwarp();  // snd is read by every group
   const bool phase_b = max_rounds <= 0;
   int j;
   if (phase_b) {
     if ((int)blockIdx.x >= *W.nbig) return;
     j = W.big[blockIdx.x];
   } else {
-    j = blockIdx.x;
+    j = (int)blockIdx.x * G + gi;
     if (j >= ncols) return;
   }
-  const int tid = threadIdx.x;
+  const int tid = gtid<GS>();
   if (tid == 0) {
     s_flag = 0;
     s_nf = 0;
@@ -1033,19 +1047,19 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
       }
     }
   }
-  gsync<NT>();
+  gsync<GS>();
   if (phase_b) {
     uint4 cs = W.cont[j];
-    for (int i = tid; i < (int)cs.y; i += NT) stage[i] = fent_restore(W.pool + cs.x + 2 * (size_t)i);
+    for (int i = tid; i < (int)cs.y; i += GS) stage[i] = fent_restore(W.pool + cs.x + 2 * (size_t)i);
   }
-  gsync<NT>();
+  gsync<GS>();
   {
-    int n0 = group_combine<NT, SCAP>(front, 0, 0, other, stage, s_ntot, scan_sm);
+    int n0 = group_combine<GS, SCAP>(front, 0, 0, other, stage, s_ntot, scan_sm);
     if (tid == 0) {
       s_nf = n0;
       s_ntot = 0;
     }
-    gsync<NT>();
+    gsync<GS>();
   }
   int visits = 0, updates = 0, rounds = 0;
   bool failed = s_flag != 0;
@@ -1062,7 +1076,7 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
       break;
     }
     ++rounds;
-    int nb = min(NT, nf);
+    int nb = min(GS, nf);
     int myout = 0;
     unsigned long long myouts[kOutCap];
     if (tid < nb) {
@@ -1077,7 +1091,7 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
       }
     }
     int ooff = myout ? atomicAdd(&s_otot, myout) : 0;
-    gsync<NT>();
+    gsync<GS>();
     if (s_flag) {  // stage overflow: updates were dropped, recompute the column
       failed = true;
       break;
@@ -1096,22 +1110,22 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
           }
         }
       }
-      gsync<NT>();
+      gsync<GS>();
       if (s_flag) {
         failed = true;
         break;
       }
       if (s_grow.h) {
-        for (uint32_t i = tid; i < s_out.size; i += NT) s_grow.h[i] = s_out.h[i];
-        gsync<NT>();
+        for (uint32_t i = tid; i < s_out.size; i += GS) s_grow.h[i] = s_out.h[i];
+        gsync<GS>();
         if (tid == 0) {
           s_grow.size = s_out.size;
           s_out = s_grow;
         }
-        gsync<NT>();
+        gsync<GS>();
       }
       for (int k = 0; k < myout; ++k) s_out.h[s_out.size + ooff + k] = myouts[k];
-      gsync<NT>();
+      gsync<GS>();
       if (tid == 0) {
         s_out.size += otot;
         s_otot = 0;
@@ -1122,14 +1136,14 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
       handoff = !phase_b;
       failed = true;
       if (handoff) {  // phase A: the rest and the stage go to phase B as they are
-        __shared__ Vec s_fr;
+        Vec& s_fr = sg_fr[gi];
         int rest = nf - nb;
         if (tid == 0 && !vec_alloc(W, s_fr, 2u * (uint32_t)(rest + ntot), status)) s_flag = 1;
-        gsync<NT>();
+        gsync<GS>();
         if (!s_flag) {
-          for (int i = tid; i < rest; i += NT) fent_save(s_fr.h + 2 * i, front[nb + i]);
-          for (int i = tid; i < ntot; i += NT) fent_save(s_fr.h + 2 * (rest + i), stage[i]);
-          gsync<NT>();
+          for (int i = tid; i < rest; i += GS) fent_save(s_fr.h + 2 * i, front[nb + i]);
+          for (int i = tid; i < ntot; i += GS) fent_save(s_fr.h + 2 * (rest + i), stage[i]);
+          gsync<GS>();
           if (tid == 0) {
             W.cont[j] = make_uint4(s_fr.off, (uint32_t)(rest + ntot), s_out.off, s_out.size);
             W.cont_cap[j] = s_out.cap;
@@ -1141,36 +1155,36 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
       }
       break;
     }
-    if (nf == nb && ntot <= NT) {
+    if (nf == nb && ntot <= GS) {
       // every entry is taken next round, so neither their order nor
       // combining equal keys matters (a star listed twice is visited twice
       // with parts of its mask: the projection is linear)
-      for (int i = tid; i < ntot; i += NT) front[i] = stage[i];
-      gsync<NT>();  // every thread has read s_ntot before it is reset
+      for (int i = tid; i < ntot; i += GS) front[i] = stage[i];
+      gsync<GS>();  // every thread has read s_ntot before it is reset
       if (tid == 0) {
         s_nf = ntot;
         s_ntot = 0;
       }
-      gsync<NT>();
+      gsync<GS>();
       continue;
     }
-    gsync<NT>();
-    int nn = group_combine<NT, SCAP>(front, nb, nf, other, stage, ntot, scan_sm);
+    gsync<GS>();
+    int nn = group_combine<GS, SCAP>(front, nb, nf, other, stage, ntot, scan_sm);
     if (tid == 0) {
       s_nf = nn;
       s_ntot = 0;
     }
-    gsync<NT>();
+    gsync<GS>();
   }
   // visits and target updates of the whole group
   int vtot, utot;
-  gscan<NT>(visits, vtot, scan_sm);
-  gscan<NT>(updates, utot, scan_sm);
+  gscan<GS>(visits, vtot, scan_sm);
+  gscan<GS>(updates, utot, scan_sm);
   if (handoff || (!failed && !phase_b && s_nf > 0)) {
     if (!handoff) {  // still open after max_rounds: save the frontier for phase B
-      __shared__ Vec s_fr2;
+      Vec& s_fr2 = sg_fr2[gi];
       if (tid == 0 && !vec_alloc(W, s_fr2, 2u * (uint32_t)s_nf, status)) s_flag = 1;
-      gsync<NT>();
+      gsync<GS>();
       if (s_flag) {
         if (tid == 0) {
           W.redo[j] = 1;
@@ -1178,8 +1192,8 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
         }
         return;
       }
-      for (int i = tid; i < s_nf; i += NT) fent_save(s_fr2.h + 2 * i, front[i]);
-      gsync<NT>();
+      for (int i = tid; i < s_nf; i += GS) fent_save(s_fr2.h + 2 * i, front[i]);
+      gsync<GS>();
       if (tid == 0) {
         W.cont[j] = make_uint4(s_fr2.off, (uint32_t)s_nf, s_out.off, s_out.size);
         W.cont_cap[j] = s_out.cap;
@@ -1210,7 +1224,7 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
   unsigned long long* a = reinterpret_cast<unsigned long long*>(stage);
   if (n2 > 2 * SCAP) {  // too long for shared memory: sort in the pool
     if (tid == 0 && !vec_alloc(W, s_grow, (uint32_t)n2, status)) s_flag = 1;
-    gsync<NT>();
+    gsync<GS>();
     if (s_flag) {
       if (tid == 0) {
         W.redo[j] = 1;
@@ -1220,7 +1234,7 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
     }
     a = s_grow.h;
   }
-  for (int i = tid; i < n2; i += NT) {
+  for (int i = tid; i < n2; i += GS) {
     unsigned long long ci = 0;
     if (i < (int)nout) {
       uint32_t v = (uint32_t)(s_out.h[i] >> 4);
@@ -1235,10 +1249,10 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
     }
     a[i] = ci;
   }
-  gsync<NT>();
-  group_sort_desc<NT>(a, n2);
+  gsync<GS>();
+  group_sort_desc<GS>(a, n2);
   int kept = 0;
-  for (int base = 0; base < (int)nout; base += NT) {
+  for (int base = 0; base < (int)nout; base += GS) {
     int k = base + tid;
     int keep = 0;
     unsigned long long x = 0;
@@ -1251,11 +1265,11 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
       }
     }
     int t;
-    int off = gscan<NT>(keep, t, scan_sm);
+    int off = gscan<GS>(keep, t, scan_sm);
     if (keep) s_out.h[kept + off] = x;
     kept += t;
   }
-  gsync<NT>();
+  gsync<GS>();
   if (tid == 0) {
     W.hoff[j] = s_out.off;
     W.hsize[j] = (uint32_t)kept;
@@ -1268,12 +1282,16 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
   }
 }
 
-// Phase A keeps its shared memory small (4 KB per column's warp) and its
-// registers at 63 so that 32 warps (the block limit) share an SM: the rounds
-// are latency-bound.  A visit appends 1.1 updates on average, 14 at
-// most; a column that outgrows the buffers continues in phase B.
+// Phase A runs two columns per warp (half a warp each: a round visits ~9
+// lower stars on average, so a whole warp left most lanes idle), keeps its
+// shared memory small (2 KB per column) and its registers at 63 so that 32
+// one-warp blocks (the block limit), 64 columns, share an SM: the rounds are
+// latency-bound.  A visit appends 1.1 updates on average, 14 at most; a
+// column that outgrows the buffers continues in phase B.
 constexpr int kThreadsB = 128;
 constexpr int kFrontA = 64, kStageA = 128;
+constexpr int kFrontH = 32, kStageH = 64;  // per column with two columns per warp
+constexpr int kFrontQ = 16, kStageQ = 32;
 constexpr int kFrontB = 1024, kStageB = 1024;
 static_assert(kFrontA + kStageA <= kStageB, "a phase A handoff fits phase B's stage");
 
@@ -1904,6 +1922,12 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
                          (int)d1_group_smem(kFrontA * 4, kStageA * 4));
     cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)d1_group_smem(kFrontA, kStageA));
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontA, kStageA, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * d1_group_smem(kFrontA, kStageA)));
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontH, kStageH, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(2 * d1_group_smem(kFrontH, kStageH)));
+    cudaFuncSetAttribute(k_d1_morse_group<32, kFrontQ, kStageQ, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(4 * d1_group_smem(kFrontQ, kStageQ)));
     cudaFuncSetAttribute(k_d1_morse_group<kThreadsB, kFrontB, kStageB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sb);
     attr[dev].store(true, std::memory_order_release);
@@ -1920,13 +1944,25 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
       k_d1_morse_group<32, kFrontA * 4, kStageA * 4><<<n2, 32, d1_group_smem(kFrontA * 4, kStageA * 4), st>>>(
           c, W, kRoundsA, status);
       break;
-    case 3:  // the default tile without the register cap
+    case 3:  // one warp per column without the register cap
       k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, kRoundsA,
                                                                                              status);
       break;
-    default:  // registers capped (63) so that 32 warps fit an SM
+    case 4:  // one warp per column, registers capped (63) so that 32 warps fit an SM
       k_d1_morse_group<32, kFrontA, kStageA, 32><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, kRoundsA,
                                                                                                   status);
+      break;
+    case 5:  // half a warp per column with the larger tile
+      k_d1_morse_group<32, kFrontA, kStageA, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontA, kStageA), st>>>(
+          c, W, kRoundsA, status);
+      break;
+    case 6:  // a quarter of a warp per column with the smallest tile
+      k_d1_morse_group<32, kFrontQ, kStageQ, 32, 8><<<(n2 + 3) / 4, 32, 4 * d1_group_smem(kFrontQ, kStageQ), st>>>(
+          c, W, kRoundsA, status);
+      break;
+    default:  // half a warp per column (two columns per warp), registers capped for 32 warps per SM
+      k_d1_morse_group<32, kFrontH, kStageH, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontH, kStageH), st>>>(
+          c, W, kRoundsA, status);
   }
   note_launch();
   k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<n2, kThreadsB, sb, st>>>(c, W, 0, status); note_launch();

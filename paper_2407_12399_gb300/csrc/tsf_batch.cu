@@ -159,14 +159,16 @@ int tsf_batch_step(tsf_batch* b, const tsf_params* params, tsf_stats* stats) {
 
 int tsf_batch_autotune(tsf_batch* b, int* choice, double* ms, int cap) {
   if (!b || !choice || cap < 0 || (cap > 0 && !ms)) return TSF_EINVAL;
-  // candidates: the D1 Morse boundaries' phase-A tile (frontier + stage
-  // entries per column's warp): 64 + 128, twice, four times that
-  constexpr int kCand = 3;
+  // candidates: the D1 Morse boundaries' first phase (knob 7): half a warp
+  // per column with 32 + 64 frontier and stage entries, half a warp with
+  // 64 + 128, a quarter of a warp with 16 + 32, one warp with 64 + 128
+  constexpr int kCand = 4;
+  constexpr int64_t kKnob[kCand] = {0, 5, 6, 4};
   const int64_t keep = tsf::get_knob(7);
   double best = -1.0;
   int arg = 0;
   for (int c = 0; c < kCand; ++c) {
-    tsf::set_knob(7, c);
+    tsf::set_knob(7, kKnob[c]);
     double t = 0.0;
     for (int rep = 0; rep < 2; ++rep) {  // the first pass sizes buffers; the second is timed
       std::vector<int> codes(b->fields.size(), TSF_OK);
@@ -185,7 +187,7 @@ int tsf_batch_autotune(tsf_batch* b, int* choice, double* ms, int cap) {
       arg = c;
     }
   }
-  tsf::set_knob(7, arg);
+  tsf::set_knob(7, kKnob[arg]);
   *choice = arg;
   return TSF_OK;
 }

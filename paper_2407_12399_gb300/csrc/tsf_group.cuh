@@ -1,5 +1,5 @@
-// tsf_group.cuh -- cooperative helpers of a thread group (one warp or one
-// block): barrier, exclusive scan, and a descending bitonic sort of keyed
+// tsf_group.cuh -- cooperative helpers of a thread group (part of a warp,
+// a warp or a block): barrier, exclusive scan, and a descending bitonic sort of keyed
 // entries held in registers.
 #pragma once
 #include <cuda_runtime.h>
@@ -16,15 +16,39 @@ struct __align__(16) FEnt {
   uint32_t pad;
 };
 
-// Group-wide (NT threads: one warp or one block) helpers.
-template <int NT>
+// A group is GS threads: an aligned part of a warp (GS = 8 or 16, lanes
+// [GS*k, GS*(k+1))), one warp (GS = 32) or the whole block (GS = blockDim.x
+// > 32).  Helpers for the group of the calling thread.
+template <int GS>
+__device__ __forceinline__ int gtid() {
+  return GS > 32 ? (int)threadIdx.x : (int)(threadIdx.x & (GS - 1));
+}
+template <int GS>
+__device__ __forceinline__ unsigned gmask() {
+  static_assert(GS > 32 || (GS >= 1 && (GS & (GS - 1)) == 0), "a part of a warp is a power of two");
+  if (GS >= 32) return 0xFFFFFFFFu;
+  return ((GS == 32 ? 0xFFFFFFFFu : ((1u << GS) - 1u))) << ((threadIdx.x & 31u) & ~(unsigned)(GS - 1));
+}
+template <int GS>
 __device__ __forceinline__ void gsync() {
-  if (NT == 32) __syncwarp();
-  else __syncthreads();
+  if (GS > 32) __syncthreads();
+  else __syncwarp(gmask<GS>());
 }
 
-template <int NT>
-__device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive; sm: >= NT/32 + 1 ints
+template <int GS>
+__device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive; sm: >= GS/32 + 1 ints (GS > 32)
+  if (GS <= 32) {
+    const unsigned m = gmask<GS>();
+    const int lane = gtid<GS>();
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < GS; o <<= 1) {
+      int t = __shfl_up_sync(m, inc, o, GS);
+      if (lane >= o) inc += t;
+    }
+    total = __shfl_sync(m, inc, GS - 1, GS);
+    return inc - v;
+  }
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int inc = v;
 #pragma unroll
@@ -32,35 +56,31 @@ __device__ __forceinline__ int gscan(int v, int& total, int* sm) {  // exclusive
     int t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
     if (lane >= o) inc += t;
   }
-  if (NT == 32) {
-    total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    return inc - v;
-  }
   if (lane == 31) sm[w] = inc;
   __syncthreads();
   if (threadIdx.x == 0) {
     int run = 0;
-    for (int k = 0; k < NT / 32; ++k) {
+    for (int k = 0; k < GS / 32; ++k) {
       int t = sm[k];
       sm[k] = run;
       run += t;
     }
-    sm[NT / 32] = run;
+    sm[GS / 32] = run;
   }
   __syncthreads();
   int res = sm[w] + inc - v;
-  total = sm[NT / 32];
+  total = sm[GS / 32];
   __syncthreads();
   return res;
 }
 
 // Descending bitonic sort of a[0..n2) (n2 a power of two) by key, 64-bit
 // values (shared or global memory of the group; its barrier orders both).
-template <int NT>
+template <int GS>
 __device__ void group_sort_desc(unsigned long long* a, int n2) {
   for (int size = 2; size <= n2; size <<= 1)
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += NT) {
+      for (int i = gtid<GS>(); i < n2; i += GS) {
         int jx = i ^ stride;
         if (jx > i) {
           bool desc = (i & size) == 0;
@@ -71,23 +91,23 @@ __device__ void group_sort_desc(unsigned long long* a, int n2) {
           }
         }
       }
-      gsync<NT>();
+      gsync<GS>();
     }
 }
 // Descending bitonic sort of keyed entries a[0..n) in shared memory (a[]
 // holds the next power of two; compact code for the rare long stages).
-template <int NT>
+template <int GS>
 __device__ void group_sort_smem(FEnt* a, int n) {
   int n2 = 1;
   while (n2 < n) n2 <<= 1;
-  for (int i = n + threadIdx.x; i < n2; i += NT) {
+  for (int i = n + gtid<GS>(); i < n2; i += GS) {
     a[i].key = 0ull;
     a[i].mask = 0u;
   }
-  gsync<NT>();
+  gsync<GS>();
   for (int size = 2; size <= n2; size <<= 1)
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += NT) {
+      for (int i = gtid<GS>(); i < n2; i += GS) {
         int jx = i ^ stride;
         if (jx > i) {
           bool desc = (i & size) == 0;
@@ -98,19 +118,22 @@ __device__ void group_sort_smem(FEnt* a, int n) {
           }
         }
       }
-      gsync<NT>();
+      gsync<GS>();
     }
 }
 
-// Descending bitonic sort of a[0..n) (n <= NT * E) by key, E entries per
+// Descending bitonic sort of a[0..n) (n <= GS * E) by key, E entries per
 // thread in registers (entry i = thread * E + e): strides below E swap
-// registers, strides below 32 E exchange with a lane by shuffles, longer
-// strides (blocks of several warps only) go through a[] in shared memory.
+// registers, strides below min(GS, 32) E exchange with a lane by shuffles,
+// longer strides (blocks of several warps only) go through a[] in shared
+// memory.
 // Equal keys may stay in either order.  All threads of the group call it.
-template <int NT, int E>
+template <int GS, int E>
 __device__ void group_sort_reg(FEnt* a, int n) {
-  constexpr int N = NT * E;
-  const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int N = GS * E;
+  constexpr int W = GS < 32 ? GS : 32;  // threads that exchange by shuffles
+  const int tid = gtid<GS>(), lane = tid & 31;
+  const unsigned gm = gmask<GS>();
   unsigned long long k[E];
   uint32_t m[E];
 #pragma unroll
@@ -143,13 +166,13 @@ __device__ void group_sort_reg(FEnt* a, int n) {
             }
           }
         }
-      } else if (stride < 32 * E) {
+      } else if (stride < W * E) {
         const int lx = stride / E;
         const bool lower = (lane & lx) == 0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          unsigned long long ok = __shfl_xor_sync(0xFFFFFFFFu, k[e], lx);
-          uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, m[e], lx);
+          unsigned long long ok = __shfl_xor_sync(gm, k[e], lx);
+          uint32_t om = __shfl_xor_sync(gm, m[e], lx);
           bool desc = ((tid * E + e) & size) == 0;
           bool take = lower == desc ? ok > k[e] : ok < k[e];
           if (take) {
@@ -191,7 +214,7 @@ __device__ void group_sort_reg(FEnt* a, int n) {
     a[tid * E + e].key = k[e];
     a[tid * E + e].mask = m[e];
   }
-  gsync<NT>();
+  gsync<GS>();
 }
 
 }  // namespace tsf

@@ -330,7 +330,7 @@ def _knobs(**kw):
     """Sets union-find knobs (tsf_debug_set) and returns a restorer."""
     import paper_2407_12399_gb300 as tsf
     ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4, "d1_grid_min": 5, "d1_handoff": 6,
-           "chain_cap": 9}
+           "chain_cap": 9, "phase_a": 7}
     old = {k: tsf.tsf_debug_set(ids[k], v) for k, v in kw.items()}
     return lambda: [tsf.tsf_debug_set(ids[k], v) for k, v in old.items()]
 
@@ -359,6 +359,22 @@ def test_chained_d1_additions_in_shared_memory_or_the_pool_match_the_oracle(name
     tiny buffers (and none) force every mix of the two paths on one column:
     the same diagram as the oracle."""
     restore = _knobs(chain_cap=chain_cap)
+    try:
+        f = NAMED[name]()
+        got = gpu_rows(gpu_field(f).diagram())
+    finally:
+        restore()
+    assert got == oracle_rows(f, oracle.diagram(f)["pairs"])
+
+
+@pytest.mark.parametrize("phase_a", [1, 3, 4, 5, 6])
+@pytest.mark.parametrize("name", ["filament_40", "filament_64", "ring_21"])
+def test_d1_morse_phase_a_variants_match_the_oracle(name, phase_a):
+    """The D1 Morse boundaries' first phase with one warp per column (larger
+    tile 1; uncapped 3; capped 4) and with half a warp per column and the
+    larger tile (5), next to the default (half a warp, smaller tile): the
+    same diagram as the oracle."""
+    restore = _knobs(phase_a=phase_a)
     try:
         f = NAMED[name]()
         got = gpu_rows(gpu_field(f).diagram())
