@@ -311,8 +311,14 @@ int64_t tsf_kernel_launches(void);
  *      128 threads per SM: 0 the default (6), 1 no cap, 2 five;
  *   9: entries of a column that the D1 reduction's short rounds (at most 64
  *      active columns) keep in shared memory while they chain additions,
- *      per group of 128 threads (default and maximum 1024; larger groups
- *      scale it; longer sums, or all with 0, are added in the column pool).
+ *      with one warp per column (default and maximum 512; the larger groups
+ *      of the last columns scale it with their size; longer sums, or all
+ *      with 0, are added in the column pool);
+ *  10: lower-star visits a thread of the D1 Morse boundaries chains in one
+ *      round along updates with a single target star (0: the default, 1;
+ *      at most 8);
+ *  11: rounds of the D1 Morse boundaries' first phase before a column
+ *      moves to a block of the second (0: the default, 128).
  * Returns the previous value, or -1 for an unknown knob.  Set them only
  * while no call of this library is running. */
 int64_t tsf_debug_set(int what, int64_t value);

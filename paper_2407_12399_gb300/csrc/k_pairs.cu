@@ -51,6 +51,11 @@ std::atomic<int64_t> g_gradient_blocks{0};
 // per warp while every warp is busy (at most 512, scaled up when fewer
 // warps share the buffers; 0: every chained addition runs in the pool)
 std::atomic<int64_t> g_chain_cap{512};
+// D1 Morse boundaries: visits a thread chains per round along single-target
+// updates (0: the default), rounds of the first phase before a column moves
+// to a block (0: the default)
+std::atomic<int64_t> g_morse_chain{0};
+std::atomic<int64_t> g_morse_rounds{0};
 
 static std::atomic<int64_t>* knob(int what) {
   return what == 1   ? &g_uf_grid_min
@@ -62,6 +67,8 @@ static std::atomic<int64_t>* knob(int what) {
          : what == 7 ? &g_d1_phase_a
          : what == 8 ? &g_gradient_blocks
          : what == 9 ? &g_chain_cap
+         : what == 10 ? &g_morse_chain
+         : what == 11 ? &g_morse_rounds
                      : nullptr;
 }
 
@@ -518,6 +525,7 @@ struct D1Ctx {
   const uint8_t* d0_killed;
   const uint32_t* d0mask;
   const float* f;
+  int chain;  // visits one thread makes per round along single-target updates
 };
 
 __device__ __forceinline__ int nbr_of_pair(const Dims& d, uint32_t hi, uint32_t lo) {
@@ -969,10 +977,11 @@ __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* sta
 
 // Visits one thread makes per round along a chain of single-target updates;
 // room for the critical edges those visits keep.  Rounds of phase A before a
-// column moves to a block.  (Measured on the 128^3 filament field: chains of
-// 2 and 16 warp rounds gave the shortest D1 time; longer chains lengthen
-// every round more than they shorten the longest column.)
-constexpr int kChain = 2, kOutCap = 28, kRoundsA = 16;
+// column moves to a block.  (Measured on the 256^3 headline field with two
+// columns per warp: no chaining and 128 rounds gave the shortest D1 time,
+// 17.1 ms against 19.9 ms with chains of 2 and 16 rounds; beyond 64 rounds
+// nothing changes, as few columns need more.)
+constexpr int kChain = 1, kOutCap = 28, kRoundsA = 128;  // defaults of knobs 10 and 11
 
 // Round loop of one column.  Phase A (max_rounds > 0): every column, one
 // group of GS threads (a half or a whole warp; NT / GS columns per block);
@@ -1084,7 +1093,7 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
       for (int k = 0;; ++k) {
         ++visits;
         FEnt nxt;
-        bool more = k + 1 < kChain && myout + 14 <= kOutCap;
+        bool more = k + 1 < c.chain && myout + 14 <= kOutCap;
         if (!d1_visit<SCAP>(c, cur, snd, stage, &s_ntot, &s_flag, myouts, myout, updates, more, &nxt, status))
           break;
         cur = nxt;
@@ -1906,6 +1915,12 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   c.d0_killed = P.d0_killed;
   c.d0mask = P.d0mask;
   c.f = f;
+  {
+    const int64_t ch = g_morse_chain.load();
+    c.chain = ch > 0 ? (int)std::min<int64_t>(ch, 8) : kChain;
+  }
+  const int64_t mr = g_morse_rounds.load();
+  const int roundsA = mr > 0 ? (int)std::min<int64_t>(mr, 1 << 20) : kRoundsA;
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, kD1Stats * sizeof(unsigned long long), st);
   cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
@@ -1938,31 +1953,31 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   switch (g_d1_phase_a.load()) {
     case 1:
       k_d1_morse_group<32, kFrontA * 2, kStageA * 2><<<n2, 32, d1_group_smem(kFrontA * 2, kStageA * 2), st>>>(
-          c, W, kRoundsA, status);
+          c, W, roundsA, status);
       break;
     case 2:
       k_d1_morse_group<32, kFrontA * 4, kStageA * 4><<<n2, 32, d1_group_smem(kFrontA * 4, kStageA * 4), st>>>(
-          c, W, kRoundsA, status);
+          c, W, roundsA, status);
       break;
     case 3:  // one warp per column without the register cap
-      k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, kRoundsA,
+      k_d1_morse_group<32, kFrontA, kStageA><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, roundsA,
                                                                                              status);
       break;
     case 4:  // one warp per column, registers capped (63) so that 32 warps fit an SM
-      k_d1_morse_group<32, kFrontA, kStageA, 32><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, kRoundsA,
+      k_d1_morse_group<32, kFrontA, kStageA, 32><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, roundsA,
                                                                                                   status);
       break;
     case 5:  // half a warp per column with the larger tile
       k_d1_morse_group<32, kFrontA, kStageA, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontA, kStageA), st>>>(
-          c, W, kRoundsA, status);
+          c, W, roundsA, status);
       break;
     case 6:  // a quarter of a warp per column with the smallest tile
       k_d1_morse_group<32, kFrontQ, kStageQ, 32, 8><<<(n2 + 3) / 4, 32, 4 * d1_group_smem(kFrontQ, kStageQ), st>>>(
-          c, W, kRoundsA, status);
+          c, W, roundsA, status);
       break;
     default:  // half a warp per column (two columns per warp), registers capped for 32 warps per SM
       k_d1_morse_group<32, kFrontH, kStageH, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontH, kStageH), st>>>(
-          c, W, kRoundsA, status);
+          c, W, roundsA, status);
   }
   note_launch();
   k_d1_morse_group<kThreadsB, kFrontB, kStageB><<<n2, kThreadsB, sb, st>>>(c, W, 0, status); note_launch();

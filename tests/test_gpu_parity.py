@@ -330,7 +330,7 @@ def _knobs(**kw):
     """Sets union-find knobs (tsf_debug_set) and returns a restorer."""
     import paper_2407_12399_gb300 as tsf
     ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4, "d1_grid_min": 5, "d1_handoff": 6,
-           "chain_cap": 9, "phase_a": 7}
+           "chain_cap": 9, "phase_a": 7, "morse_chain": 10, "morse_rounds": 11}
     old = {k: tsf.tsf_debug_set(ids[k], v) for k, v in kw.items()}
     return lambda: [tsf.tsf_debug_set(ids[k], v) for k, v in old.items()]
 
@@ -375,6 +375,21 @@ def test_d1_morse_phase_a_variants_match_the_oracle(name, phase_a):
     larger tile (5), next to the default (half a warp, smaller tile): the
     same diagram as the oracle."""
     restore = _knobs(phase_a=phase_a)
+    try:
+        f = NAMED[name]()
+        got = gpu_rows(gpu_field(f).diagram())
+    finally:
+        restore()
+    assert got == oracle_rows(f, oracle.diagram(f)["pairs"])
+
+
+@pytest.mark.parametrize("chain,rounds", [(2, 16), (3, 4), (1, 1)])
+@pytest.mark.parametrize("name", ["filament_40", "filament_64", "ring_21"])
+def test_d1_morse_chains_and_early_handoffs_match_the_oracle(name, chain, rounds):
+    """Chained visits along single-target updates and columns handed to the
+    second phase after few rounds (knobs 10 and 11): the same diagram as the
+    oracle."""
+    restore = _knobs(morse_chain=chain, morse_rounds=rounds)
     try:
         f = NAMED[name]()
         got = gpu_rows(gpu_field(f).diagram())
