@@ -277,7 +277,7 @@ def batched_solve(prec=0.01, converge_tau=0.025):
                for i in range(len(fields)) if i not in sub]
     tsf.tsf_debug_set(7, 0)
     return {"workload": "uneven_batch_48", "fields": len(fields), "voxels": vox, "assignment_precision": prec,
-            "autotune": {"candidates": ["half warp 32+64", "half warp 64+128", "quarter warp 16+32", "warp 64+128"],
+            "autotune": {"candidates": ["half warp 64+128", "half warp 32+64", "quarter warp 16+32", "warp 64+128"],
                          "diagram_ms": tune_ms, "chosen": choice},
             "first_iteration": {"batch_s": tb, "one_at_a_time_s": tl, "speedup": tl / tb,
                                 "field_iterations_per_s": len(fields) / tb, "device_gb": gb},

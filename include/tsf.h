@@ -229,8 +229,8 @@ int tsf_batch_simplify(tsf_batch* batch, const tsf_params* params, tsf_stats* st
 /* Autotuner of the batch (not in the paper): times the full persistence
  * diagram of every field (all fields concurrently, each candidate twice,
  * the second pass counted) for each candidate schedule of the D1 Morse
- * boundaries' first phase — 0: half a warp per column with 32 + 64
- * frontier and stage entries, 1: half a warp with 64 + 128, 2: a quarter of
+ * boundaries' first phase — 0: half a warp per column with 64 + 128
+ * frontier and stage entries, 1: half a warp with 32 + 64, 2: a quarter of
  * a warp with 16 + 32, 3: one warp with 64 + 128 (tsf_debug_set knob 7
  * values 0, 5, 6, 4) — and keeps the fastest.  The choice applies
  * process-wide; results never depend on it.  *choice receives it (0..3),
@@ -301,10 +301,10 @@ int64_t tsf_kernel_launches(void);
  *      (default 65536);
  *   6: active D1 columns below which one block finishes them (default 4096);
  *   7: schedule of the D1 Morse boundaries' first phase: 0 the default
- *      (half a warp per column, 32 + 64 frontier and stage entries, registers
+ *      (half a warp per column, 64 + 128 frontier and stage entries, registers
  *      capped for 32 warps per SM), 1 and 2 one warp per column with 128 +
  *      256 and 256 + 512 entries, 3 one warp with 64 + 128 without the
- *      register cap, 4 the same with it, 5 half a warp with 64 + 128, 6 a
+ *      register cap, 4 the same with it, 5 half a warp with 32 + 64, 6 a
  *      quarter of a warp with 16 + 32 (columns that outgrow their buffers
  *      continue in the second phase);
  *   8: register budget of the lower-star gradient kernels, as blocks of
@@ -318,7 +318,9 @@ int64_t tsf_kernel_launches(void);
  *      round along updates with a single target star (0: the default, 1;
  *      at most 8);
  *  11: rounds of the D1 Morse boundaries' first phase before a column
- *      moves to a block of the second (0: the default, 128).
+ *      moves to a block of the second (0: the default, 128);
+ *  12: active columns up to which a round of the D1 reduction chains
+ *      additions in shared memory (0: the default, 64; at most 1024).
  * Returns the previous value, or -1 for an unknown knob.  Set them only
  * while no call of this library is running. */
 int64_t tsf_debug_set(int what, int64_t value);

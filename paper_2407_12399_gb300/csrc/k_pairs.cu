@@ -40,9 +40,9 @@ std::atomic<int64_t> g_barrier_limit{1 << 24};
 std::atomic<int64_t> g_d1_grid_min{1 << 16};
 std::atomic<int64_t> g_d1_handoff{1 << 12};
 // schedule of the D1 Morse boundaries' phase A: 0 the default (half a warp
-// per column, 32 frontier + 64 stage entries), 1 and 2 one warp with 128 +
+// per column, 64 frontier + 128 stage entries), 1 and 2 one warp with 128 +
 // 256 and 256 + 512, 3 one warp with 64 + 128 uncapped, 4 capped, 5 half a
-// warp with 64 + 128, 6 a quarter of a warp with 16 + 32
+// warp with 32 + 64, 6 a quarter of a warp with 16 + 32
 std::atomic<int64_t> g_d1_phase_a{0};
 // blocks per SM the lower-star gradient kernels are compiled for: 0 the
 // default (six), 1 no register cap, 2 five
@@ -56,6 +56,8 @@ std::atomic<int64_t> g_chain_cap{512};
 // to a block (0: the default)
 std::atomic<int64_t> g_morse_chain{0};
 std::atomic<int64_t> g_morse_rounds{0};
+// D1 reduction: active columns up to which a round chains additions (0: the default)
+std::atomic<int64_t> g_chain_max{0};
 
 static std::atomic<int64_t>* knob(int what) {
   return what == 1   ? &g_uf_grid_min
@@ -69,6 +71,7 @@ static std::atomic<int64_t>* knob(int what) {
          : what == 9 ? &g_chain_cap
          : what == 10 ? &g_morse_chain
          : what == 11 ? &g_morse_rounds
+         : what == 12 ? &g_chain_max
                      : nullptr;
 }
 
@@ -1293,13 +1296,12 @@ __global__ void __launch_bounds__(NT, MINB) k_d1_morse_group(D1Ctx c, D1Work W, 
 
 // Phase A runs two columns per warp (half a warp each: a round visits ~9
 // lower stars on average, so a whole warp left most lanes idle), keeps its
-// shared memory small (2 KB per column) and its registers at 63 so that 32
-// one-warp blocks (the block limit), 64 columns, share an SM: the rounds are
-// latency-bound.  A visit appends 1.1 updates on average, 14 at most; a
+// shared memory small (4 KB per column) and its registers at 63 so that 28
+// one-warp blocks, 56 columns, share an SM: the rounds are latency-bound.  A visit appends 1.1 updates on average, 14 at most; a
 // column that outgrows the buffers continues in phase B.
 constexpr int kThreadsB = 128;
 constexpr int kFrontA = 64, kStageA = 128;
-constexpr int kFrontH = 32, kStageH = 64;  // per column with two columns per warp
+constexpr int kFrontH = 32, kStageH = 64;
 constexpr int kFrontQ = 16, kStageQ = 32;
 constexpr int kFrontB = 1024, kStageB = 1024;
 static_assert(kFrontA + kStageA <= kStageB, "a phase A handoff fits phase B's stage");
@@ -1373,7 +1375,8 @@ __device__ uint32_t d1_warp_add(const unsigned long long* a, uint32_t n, const u
   return cap - 2u * common;
 }
 
-constexpr int kChainMax = 64;      // active columns up to which a round chains additions (one group each)
+constexpr int kChainMax = 64;      // active columns up to which a round chains additions (default of knob 12)
+constexpr int kChainLimit = 1024;  // ... at most
 constexpr int kChainSteps = 1 << 16;  // chained additions of one column in one round, at most
 constexpr uint32_t kLongAdd = 64;  // column additions at least this long run on a warp
 constexpr int kLongCap = 1024;     // ... at most this many per round (the rest on one thread)
@@ -1665,7 +1668,7 @@ __device__ bool cg_chain(D1Work& W, int n1, int j, int round, uint32_t* buf, uin
 // `ctl` (may be null): resume after k_d1_reduce_grid from its lists, owners
 // and marks.
 __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d1_edge, const D1Ctl* ctl,
-                                                    uint32_t ccap, uint32_t* status) {
+                                                    uint32_t ccap, int chain_max, uint32_t* status) {
   const int ncols = W.flags[1];
   // free per-column scratch by now: two lists and a "listed in round" mark
   int32_t* listA = W.lowc;
@@ -1673,7 +1676,7 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
   int32_t* mark = W.redo;
   __shared__ int s_na, s_nb, s_nlong;
   __shared__ int32_t s_long[kLongCap];
-  __shared__ int32_t s_sub[2][kChainMax], s_subn[2][kChainMax];
+  __shared__ int32_t s_sub[2][kChainLimit], s_subn[2][kChainLimit];
   __shared__ int s_cg[kCGroupsMax][4];
   __shared__ int s_wsum[2 * kCGroupsMax];
   __shared__ int s_nsub;
@@ -1723,7 +1726,7 @@ __global__ void __launch_bounds__(kUFT) k_d1_reduce(D1Work W, int n1, int32_t* d
       if (old > j && old != 0x7FFFFFFF) d1_list_push(nxt, &s_nb, mark, old, round);  // displaced owner
     }
     __syncthreads();
-    if (na <= kChainMax) {
+    if (na <= chain_max) {
       // short list: chained additions by groups of threads, in sub-rounds
       // (in shared memory while a sum fits the group's buffers).  During this
       // phase every owner owns its low and does not change (a column that
@@ -1967,8 +1970,8 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
       k_d1_morse_group<32, kFrontA, kStageA, 32><<<n2, 32, d1_group_smem(kFrontA, kStageA), st>>>(c, W, roundsA,
                                                                                                   status);
       break;
-    case 5:  // half a warp per column with the larger tile
-      k_d1_morse_group<32, kFrontA, kStageA, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontA, kStageA), st>>>(
+    case 5:  // half a warp per column with the smaller tile
+      k_d1_morse_group<32, kFrontH, kStageH, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontH, kStageH), st>>>(
           c, W, roundsA, status);
       break;
     case 6:  // a quarter of a warp per column with the smallest tile
@@ -1976,7 +1979,7 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
           c, W, roundsA, status);
       break;
     default:  // half a warp per column (two columns per warp), registers capped for 32 warps per SM
-      k_d1_morse_group<32, kFrontH, kStageH, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontH, kStageH), st>>>(
+      k_d1_morse_group<32, kFrontA, kStageA, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontA, kStageA), st>>>(
           c, W, roundsA, status);
   }
   note_launch();
@@ -2132,6 +2135,8 @@ void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, D
     attr[dev].store(true, std::memory_order_release);
   }
   const uint32_t ccap = (uint32_t)std::min<int64_t>(std::max<int64_t>(g_chain_cap.load(), 0), kCCap);
+  const int64_t cm = g_chain_max.load();
+  const int chain_max = cm > 0 ? (int)std::min<int64_t>(cm, kChainLimit) : kChainMax;
   const int nb = n2 >= g_d1_grid_min.load() ? cooperative_blocks((const void*)k_d1_reduce_grid, kUFT) : 0;
   if (nb > 0) {
     cudaMemsetAsync(ctl, 0, sizeof(D1Ctl), st);
@@ -2139,12 +2144,12 @@ void launch_d1_reduce(int n1, int n2, D1Work& W, PairOut& P, uint32_t* status, D
     unsigned limit = (unsigned)std::min<int64_t>(std::max<int64_t>(g_barrier_limit.load(), 1), 1u << 30);
     void* args[] = {&W, &n1, &ctl, &handoff, &limit, &status};
     if (cooperative_launch((const void*)k_d1_reduce_grid, dim3(nb), dim3(kUFT), args, st) == cudaSuccess) {
-      k_d1_reduce<<<1, kUFT, kChainSmem, st>>>(W, n1, P.d1_edge, ctl, ccap, status); note_launch();
+      k_d1_reduce<<<1, kUFT, kChainSmem, st>>>(W, n1, P.d1_edge, ctl, ccap, chain_max, status); note_launch();
       return;
     }
     cudaGetLastError();  // not launched: the single block does every round
   }
-  k_d1_reduce<<<1, kUFT, kChainSmem, st>>>(W, n1, P.d1_edge, nullptr, ccap, status); note_launch();
+  k_d1_reduce<<<1, kUFT, kChainSmem, st>>>(W, n1, P.d1_edge, nullptr, ccap, chain_max, status); note_launch();
 }
 
 }  // namespace tsf

@@ -160,8 +160,8 @@ int tsf_batch_step(tsf_batch* b, const tsf_params* params, tsf_stats* stats) {
 int tsf_batch_autotune(tsf_batch* b, int* choice, double* ms, int cap) {
   if (!b || !choice || cap < 0 || (cap > 0 && !ms)) return TSF_EINVAL;
   // candidates: the D1 Morse boundaries' first phase (knob 7): half a warp
-  // per column with 32 + 64 frontier and stage entries, half a warp with
-  // 64 + 128, a quarter of a warp with 16 + 32, one warp with 64 + 128
+  // per column with 64 + 128 frontier and stage entries, half a warp with
+  // 32 + 64, a quarter of a warp with 16 + 32, one warp with 64 + 128
   constexpr int kCand = 4;
   constexpr int64_t kKnob[kCand] = {0, 5, 6, 4};
   const int64_t keep = tsf::get_knob(7);

@@ -151,6 +151,6 @@ def test_warm_start_and_knob_entry_points_check_arguments_without_a_gpu(libpath)
     c = ctypes.c_int(0)
     assert L.tsf_batch_autotune(None, ctypes.byref(c), None, 0) == tsf.TSF_EINVAL
     assert tsf.tsf_debug_set(99, 1) == -1
-    for knob in (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11):
+    for knob in (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12):
         old = tsf.tsf_debug_set(knob, 5)
         assert tsf.tsf_debug_set(knob, old) == 5

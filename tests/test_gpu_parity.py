@@ -330,7 +330,8 @@ def _knobs(**kw):
     """Sets union-find knobs (tsf_debug_set) and returns a restorer."""
     import paper_2407_12399_gb300 as tsf
     ids = {"grid_min": 1, "handoff": 2, "round_cap": 3, "barrier_limit": 4, "d1_grid_min": 5, "d1_handoff": 6,
-           "chain_cap": 9, "phase_a": 7, "morse_chain": 10, "morse_rounds": 11}
+           "chain_cap": 9, "phase_a": 7, "morse_chain": 10, "morse_rounds": 11,
+           "chain_max": 12}
     old = {k: tsf.tsf_debug_set(ids[k], v) for k, v in kw.items()}
     return lambda: [tsf.tsf_debug_set(ids[k], v) for k, v in old.items()]
 
@@ -351,14 +352,15 @@ def test_pairing_rounds_over_the_whole_gpu_match_the_oracle(name, handoff):
     assert got == oracle_rows(f, oracle.diagram(f)["pairs"])
 
 
-@pytest.mark.parametrize("chain_cap", [0, 4, 24])
+@pytest.mark.parametrize("chain_cap,chain_max", [(0, 0), (4, 0), (24, 0), (512, 1024), (4, 1024)])
 @pytest.mark.parametrize("name", ["filament_40", "filament_64", "ring_21"])
-def test_chained_d1_additions_in_shared_memory_or_the_pool_match_the_oracle(name, chain_cap):
+def test_chained_d1_additions_in_shared_memory_or_the_pool_match_the_oracle(name, chain_cap, chain_max):
     """The D1 reduction's short rounds chain column additions in shared
     memory while a sum fits the buffer and in the column pool otherwise;
-    tiny buffers (and none) force every mix of the two paths on one column:
-    the same diagram as the oracle."""
-    restore = _knobs(chain_cap=chain_cap)
+    tiny buffers (and none) force every mix of the two paths on one column,
+    and a threshold of 1024 active columns makes every round of these fields
+    a chaining one: the same diagram as the oracle."""
+    restore = _knobs(chain_cap=chain_cap, chain_max=chain_max)
     try:
         f = NAMED[name]()
         got = gpu_rows(gpu_field(f).diagram())
@@ -371,9 +373,9 @@ def test_chained_d1_additions_in_shared_memory_or_the_pool_match_the_oracle(name
 @pytest.mark.parametrize("name", ["filament_40", "filament_64", "ring_21"])
 def test_d1_morse_phase_a_variants_match_the_oracle(name, phase_a):
     """The D1 Morse boundaries' first phase with one warp per column (larger
-    tile 1; uncapped 3; capped 4) and with half a warp per column and the
-    larger tile (5), next to the default (half a warp, smaller tile): the
-    same diagram as the oracle."""
+    tile 1; uncapped 3; capped 4), with half a warp per column and the
+    smaller tile (5) and with a quarter of a warp (6), next to the default
+    (half a warp, 64 + 128 entries): the same diagram as the oracle."""
     restore = _knobs(phase_a=phase_a)
     try:
         f = NAMED[name]()
