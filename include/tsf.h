@@ -232,7 +232,7 @@ int tsf_batch_simplify(tsf_batch* batch, const tsf_params* params, tsf_stats* st
  * boundaries' first phase — 0: half a warp per column with 64 + 128
  * frontier and stage entries, 1: half a warp with 32 + 64, 2: a quarter of
  * a warp with 16 + 32, 3: one warp with 64 + 128 (tsf_debug_set knob 7
- * values 0, 5, 6, 4) — and keeps the fastest.  The choice applies
+ * values 7, 5, 6, 4) — and keeps the fastest.  The choice applies
  * process-wide; results never depend on it.  *choice receives it (0..3),
  * ms[c] (cap entries, may be NULL when cap is 0) the time of candidate c in
  * milliseconds.  Call it before the signal thresholds are set (it replaces
@@ -301,12 +301,14 @@ int64_t tsf_kernel_launches(void);
  *      (default 65536);
  *   6: active D1 columns below which one block finishes them (default 4096);
  *   7: schedule of the D1 Morse boundaries' first phase: 0 the default
- *      (half a warp per column, 64 + 128 frontier and stage entries, registers
- *      capped for 32 warps per SM), 1 and 2 one warp per column with 128 +
- *      256 and 256 + 512 entries, 3 one warp with 64 + 128 without the
- *      register cap, 4 the same with it, 5 half a warp with 32 + 64, 6 a
- *      quarter of a warp with 16 + 32 (columns that outgrow their buffers
- *      continue in the second phase);
+ *      (half a warp per column, registers capped for 32 warps per SM; 64 +
+ *      128 frontier and stage entries for diagrams of at least 2^19
+ *      critical triangles, else 32 + 64), 1 and 2 one warp per column with
+ *      128 + 256 and 256 + 512 entries, 3 one warp with 64 + 128 without
+ *      the register cap, 4 the same with it, 5 half a warp with 32 + 64, 6
+ *      a quarter of a warp with 16 + 32, 7 half a warp with 64 + 128 at any
+ *      size (columns that outgrow their buffers continue in the second
+ *      phase);
  *   8: register budget of the lower-star gradient kernels, as blocks of
  *      128 threads per SM: 0 the default (6), 1 no cap, 2 five;
  *   9: entries of a column that the D1 reduction's short rounds (at most 64
@@ -315,10 +317,11 @@ int64_t tsf_kernel_launches(void);
  *      of the last columns scale it with their size; longer sums, or all
  *      with 0, are added in the column pool);
  *  10: lower-star visits a thread of the D1 Morse boundaries chains in one
- *      round along updates with a single target star (0: the default, 1;
- *      at most 8);
+ *      round along updates with a single target star (0: the default, 1
+ *      for diagrams of at least 2^19 critical triangles, else 2; at most 8);
  *  11: rounds of the D1 Morse boundaries' first phase before a column
- *      moves to a block of the second (0: the default, 128);
+ *      moves to a block of the second (0: the default, 128 for diagrams of
+ *      at least 2^19 critical triangles, else 16);
  *  12: active columns up to which a round of the D1 reduction chains
  *      additions in shared memory (0: the default, 64; at most 1024).
  * Returns the previous value, or -1 for an unknown knob.  Set them only

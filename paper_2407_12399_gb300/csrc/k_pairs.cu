@@ -40,9 +40,11 @@ std::atomic<int64_t> g_barrier_limit{1 << 24};
 std::atomic<int64_t> g_d1_grid_min{1 << 16};
 std::atomic<int64_t> g_d1_handoff{1 << 12};
 // schedule of the D1 Morse boundaries' phase A: 0 the default (half a warp
-// per column, 64 frontier + 128 stage entries), 1 and 2 one warp with 128 +
+// per column, 64 frontier + 128 stage entries for diagrams of at least 2^19
+// critical triangles, else as 5), 1 and 2 one warp with 128 +
 // 256 and 256 + 512, 3 one warp with 64 + 128 uncapped, 4 capped, 5 half a
-// warp with 32 + 64, 6 a quarter of a warp with 16 + 32
+// warp with 32 + 64, 6 a quarter of a warp with 16 + 32, 7 half a warp
+// with 64 + 128 at any size
 std::atomic<int64_t> g_d1_phase_a{0};
 // blocks per SM the lower-star gradient kernels are compiled for: 0 the
 // default (six), 1 no register cap, 2 five
@@ -53,7 +55,7 @@ std::atomic<int64_t> g_gradient_blocks{0};
 std::atomic<int64_t> g_chain_cap{512};
 // D1 Morse boundaries: visits a thread chains per round along single-target
 // updates (0: the default), rounds of the first phase before a column moves
-// to a block (0: the default)
+// to a block (0: the default); both defaults depend on the diagram's size
 std::atomic<int64_t> g_morse_chain{0};
 std::atomic<int64_t> g_morse_rounds{0};
 // D1 reduction: active columns up to which a round chains additions (0: the default)
@@ -979,12 +981,20 @@ __device__ int group_combine(FEnt* front, int nb, int nf, FEnt* other, FEnt* sta
 }
 
 // Visits one thread makes per round along a chain of single-target updates;
-// room for the critical edges those visits keep.  Rounds of phase A before a
-// column moves to a block.  (Measured on the 256^3 headline field with two
-// columns per warp: no chaining and 128 rounds gave the shortest D1 time,
-// 17.1 ms against 19.9 ms with chains of 2 and 16 rounds; beyond 64 rounds
-// nothing changes, as few columns need more.)
-constexpr int kChain = 1, kOutCap = 28, kRoundsA = 128;  // defaults of knobs 10 and 11
+// room for the critical edges those visits keep; rounds of phase A before a
+// column moves to a block.  The defaults depend on the diagram's size.  A
+// large diagram (at least kLargeD1 critical triangles) keeps enough columns
+// in flight in phase A to fill the GPU, so its columns stay there (no
+// chaining, 128 rounds, 64 + 128 entries per column).  A small one gains
+// from moving its long columns to 128-thread blocks early (chains of 2, 16
+// rounds, 32 + 64 entries).  Measured, ms per iteration on the 256^3
+// headline field (1.8 M critical triangles) / the 128^3 filament field
+// (~0.25 M): large settings 64.7 / 2.89, small settings 67.8 / 1.89;
+// 32 rounds with either tile lay in between on both (65.1-65.5 / 2.07-2.15).
+constexpr int kOutCap = 28;
+constexpr int kLargeD1 = 1 << 19;
+constexpr int kChainLarge = 1, kRoundsLarge = 128;  // defaults of knobs 10 and 11, large diagrams
+constexpr int kChainSmall = 2, kRoundsSmall = 16;   // ... small diagrams
 
 // Round loop of one column.  Phase A (max_rounds > 0): every column, one
 // group of GS threads (a half or a whole warp; NT / GS columns per block);
@@ -1920,10 +1930,11 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   c.f = f;
   {
     const int64_t ch = g_morse_chain.load();
-    c.chain = ch > 0 ? (int)std::min<int64_t>(ch, 8) : kChain;
+    c.chain = ch > 0 ? (int)std::min<int64_t>(ch, 8) : (n2 >= kLargeD1 ? kChainLarge : kChainSmall);
   }
   const int64_t mr = g_morse_rounds.load();
-  const int roundsA = mr > 0 ? (int)std::min<int64_t>(mr, 1 << 20) : kRoundsA;
+  const int roundsA =
+      mr > 0 ? (int)std::min<int64_t>(mr, 1 << 20) : (n2 >= kLargeD1 ? kRoundsLarge : kRoundsSmall);
   cudaMemsetAsync(W.pool_head, 0, 4, st);
   cudaMemsetAsync(W.stats, 0, kD1Stats * sizeof(unsigned long long), st);
   cudaMemsetAsync(W.nbig, 0, sizeof(int32_t), st);
@@ -1953,7 +1964,10 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
   // phase A buffers: the default, or 2x / 4x larger (more shared memory per
   // warp, fewer warps per SM; a column that outgrows them continues in
   // phase B)
-  switch (g_d1_phase_a.load()) {
+  // knob 7 = 0: the larger tile for large diagrams, the smaller one otherwise
+  int64_t phase_a = g_d1_phase_a.load();
+  if (phase_a == 0 && n2 < kLargeD1) phase_a = 5;
+  switch (phase_a) {
     case 1:
       k_d1_morse_group<32, kFrontA * 2, kStageA * 2><<<n2, 32, d1_group_smem(kFrontA * 2, kStageA * 2), st>>>(
           c, W, roundsA, status);
@@ -1978,7 +1992,7 @@ void launch_d1_morse(const Dims& d, const NbrDelta& nd, const CritLists& L, int 
       k_d1_morse_group<32, kFrontQ, kStageQ, 32, 8><<<(n2 + 3) / 4, 32, 4 * d1_group_smem(kFrontQ, kStageQ), st>>>(
           c, W, roundsA, status);
       break;
-    default:  // half a warp per column (two columns per warp), registers capped for 32 warps per SM
+    default:  // (0, 7) half a warp per column (two columns per warp), registers capped for 32 warps per SM
       k_d1_morse_group<32, kFrontA, kStageA, 32, 16><<<(n2 + 1) / 2, 32, 2 * d1_group_smem(kFrontA, kStageA), st>>>(
           c, W, roundsA, status);
   }

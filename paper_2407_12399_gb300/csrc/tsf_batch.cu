@@ -163,7 +163,7 @@ int tsf_batch_autotune(tsf_batch* b, int* choice, double* ms, int cap) {
   // per column with 64 + 128 frontier and stage entries, half a warp with
   // 32 + 64, a quarter of a warp with 16 + 32, one warp with 64 + 128
   constexpr int kCand = 4;
-  constexpr int64_t kKnob[kCand] = {0, 5, 6, 4};
+  constexpr int64_t kKnob[kCand] = {7, 5, 6, 4};
   const int64_t keep = tsf::get_knob(7);
   double best = -1.0;
   int arg = 0;
