@@ -207,8 +207,9 @@ __device__ __forceinline__ int tri_key(uint64_t P, int t, const GradGeo& G) {
 // Backward sweep: link edges in the reverse order over the dual graph (link
 // triangles of the lower link, plus one node for everything outside); an
 // edge joining two dual components kills the one whose root triangle comes
-// first in the filtration.  Same sweeps as the reference formulation of
-// tsf_star.cuh, with union-find replaced by always-compressed root labels.
+// first in the filtration.  The same sweeps as the plain formulation in
+// tsf_star.cuh (which the zero-pair test kernel and the single-thread D1
+// heap kernel use), with union-find replaced by always-compressed root labels.
 //
 // Closures: the chain of the table's closure of v*x (v*x -> v*y + path x..y
 // -> ...) runs through the older representatives x's component merged into,

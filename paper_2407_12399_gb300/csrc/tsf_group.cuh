@@ -27,7 +27,9 @@ template <int GS>
 __device__ __forceinline__ unsigned gmask() {
   static_assert(GS > 32 || (GS >= 1 && (GS & (GS - 1)) == 0), "a part of a warp is a power of two");
   if (GS >= 32) return 0xFFFFFFFFu;
-  return ((GS == 32 ? 0xFFFFFFFFu : ((1u << GS) - 1u))) << ((threadIdx.x & 31u) & ~(unsigned)(GS - 1));
+  // GS < 32 here; the guard keeps the shift in range when GS = 32 instantiates this line
+  constexpr unsigned low = GS >= 32 ? 0xFFFFFFFFu : ((1u << (GS & 31)) - 1u);
+  return low << ((threadIdx.x & 31u) & ~(unsigned)(GS - 1));
 }
 template <int GS>
 __device__ __forceinline__ void gsync() {
